@@ -1,0 +1,259 @@
+/*
+ * odp.h -- C ABI of libodp, a B300 (sm_103a) implementation of the
+ * data-parallel hot path of "Dynamic Detection of Inefficient Data Mapping
+ * Patterns in Heterogeneous OpenMP Applications" (PPoPP '26):
+ *
+ *   1. content fingerprinting of mapped/transferred buffers (the paper, Sec. 5
+ *      and 5.1, keeps a hash of the data of every transfer and assumes it
+ *      collision-free; the hash here is the project-defined FP128 v1);
+ *   2. detection over the mapping-event log of the patterns of Sec. 4
+ *      (duplicate transfers, round trips, repeated allocations, unused
+ *      allocations, unused transfers) with Algorithms 1-5 of Sec. 5, plus the
+ *      wasted-time estimate of Sec. 7.6.
+ *
+ * Conventions for every call:
+ *   - All pointers named "device" must be device memory of the current CUDA
+ *     device (or managed memory); "host" pointers are ordinary host memory.
+ *   - Calls are asynchronous on `stream` unless stated otherwise.  The caller
+ *     keeps inputs and outputs alive and unmodified until the stream work
+ *     completes.
+ *   - The return value is a synchronous status (ODP_OK or a negative error);
+ *     errors detected on the device are written to a device status word.
+ *   - No C++ exception crosses this interface; kernels never trap.
+ *   - Scratch memory comes from the allocator installed with
+ *     odp_set_allocator (default: cudaMallocAsync on the call's stream) and is
+ *     cached per (device, stream) between calls.
+ */
+#ifndef ODP_H
+#define ODP_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+
+enum {
+    ODP_OK = 0,
+    ODP_WARN_TRUNCATED = 1,     /* findings or site rows exceeded capacity  */
+    ODP_ERR_INVALID_ARG = -1,   /* null pointer with n > 0, bad sizes       */
+    ODP_ERR_CUDA = -2,          /* a CUDA runtime call failed               */
+    ODP_ERR_OOM = -3,           /* the allocator returned null              */
+    ODP_ERR_TIMEOUT = -4,       /* a bounded device-side wait ran out       */
+    ODP_ERR_MALFORMED = -5,     /* an event record failed validation        */
+    ODP_ERR_UNSORTED = -6,      /* event start times decrease               */
+    ODP_ERR_UNSUPPORTED = -7    /* input outside the implemented limits     */
+};
+
+/* Human-readable name of a status code (static string, never null). */
+const char* odp_status_string(int status);
+
+/* ----------------------------------------------------------- fingerprint */
+
+/* 128-bit fingerprint: lo = bits 0..63, hi = bits 64..127. */
+typedef struct odp_fp128 {
+    uint64_t lo, hi;
+} odp_fp128;
+
+/*
+ * odp_fingerprint -- FP128 v1 of n buffers (paper Sec. 5.1: a hash of the
+ * transferred data stands in for the data; this library's hash is defined
+ * in FP128 v1 below).
+ *
+ *   ptrs[i]   device array of n device pointers; buffer i starts there.
+ *             Any byte alignment is accepted (16-byte aligned buffers take
+ *             the fast path).  May be null when sizes[i] == 0.
+ *   sizes[i]  device array of n byte counts.
+ *   out128[i] device array of n results.
+ *
+ * n == 0 is a no-op.  A buffer of size 0 gets the empty-input fingerprint.
+ * Buffers may overlap or alias.  The result does not depend on the buffer's
+ * address, on the other buffers of the batch or on the launch schedule.
+ * Returns ODP_ERR_INVALID_ARG for null arrays with n > 0 and ODP_ERR_OOM /
+ * ODP_ERR_CUDA for allocation / launch failures.  A null ptrs[i] with
+ * sizes[i] > 0 is detected on the device: out128[i] is set to {0, 0} and
+ * ODP_ERR_INVALID_ARG is recorded in the device status word read by
+ * odp_fingerprint_status.
+ *
+ * FP128 v1 (all arithmetic modulo 2^64; C[i] = output i of SplitMix64
+ * seeded with 0x46503132385F7631, "FP128_v1"; Kodd(i) = C[i] | 1):
+ *   - split the input into 4096-byte chunks; the last one holds r valid
+ *     bytes and is zero-padded; a chunk is 256 little-endian 16-byte words
+ *     (lo, hi);
+ *   - lane l = 0..31 absorbs words l, l+32, ..., l+224 into two chains
+ *     a = C[32+2l], b = C[33+2l]:  a = S(a ^ lo; Kodd 0, 1),
+ *     b = S(b ^ hi; Kodd 2, 3) with S(v; k1, k2) = ((v*k1) ^ (v*k1) >> 32) * k2;
+ *     then a ^= b * Kodd(4); b ^= a * Kodd(5);
+ *   - the 32 lane states combine as a complete binary tree with
+ *     node = L ^ G(R), G(x, y) = (y, x ^ y);
+ *   - leaf = M_Q(root.x ^ r ^ C[18], root.y ^ C[19]);
+ *   - leaves combine in a left-balanced binary tree (split at the largest
+ *     power of two below the count) with node = M_P(L.x ^ G(R).x ^ count,
+ *     L.y ^ G(R).y ^ C[20]), count = leaves under the node;
+ *   - out = M_Z(root.x ^ len, root.y ^ nchunks ^ C[21]); the empty input
+ *     uses root = (C[22], C[23]);
+ *   - M_{Q,P,Z}(x, y) with four odd multipliers k0..k3 (Kodd 6-9, 10-13,
+ *     14-17): x*=k0; y^=x>>29; y*=k1; x^=y>>32; x*=k2; y^=x>>32; y*=k3;
+ *     x^=y>>29.
+ */
+int odp_fingerprint(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
+                    odp_fp128* out128, cudaStream_t stream);
+
+/* Reads (synchronising `stream`) and clears the device status word that
+ * odp_fingerprint writes for per-buffer errors; *status receives ODP_OK or
+ * the first error recorded. */
+int odp_fingerprint_status(cudaStream_t stream, int32_t* status);
+
+/* -------------------------------------------------------------- analysis */
+
+/* Event kinds (OMPT target data-op types plus target kernel launches). */
+enum {
+    ODP_ALLOC = 1,
+    ODP_TO_DEV = 2,      /* host -> device transfer */
+    ODP_FROM_DEV = 3,    /* device -> host transfer */
+    ODP_DEV_TO_DEV = 4,  /* device -> device transfer */
+    ODP_DELETE = 5,
+    ODP_KERNEL = 6
+};
+
+#define ODP_HOST_DEVICE (-1)
+#define ODP_MAX_SITES 65536u
+#define ODP_MAX_BYTES (1ull << 56)
+#define ODP_NO_EVENT (~0ull)
+
+/*
+ * One mapping event, 64 bytes, packed little-endian (the paper's log entry
+ * of Sec. 5: start/end time, hash of the transferred data, source and
+ * destination device, code location, bytes, operation type; Sec. 7.4 sizes
+ * it at 72 B -- this record replaces the code pointer by a site id).
+ *   - t_start_ns / t_end_ns: interval of the operation (kernels too).
+ *   - host_addr: host address of the mapped variable; dev_addr: device
+ *     address (alloc/delete pairing key together with dst_dev).
+ *   - fp_lo/fp_hi: FP128 of the transferred bytes (transfers only).
+ *   - src_dev/dst_dev: device numbers, host = -1.  ALLOC, DELETE and KERNEL
+ *     use dst_dev for their device.
+ *   - site_id: caller-assigned code-location id (< ODP_MAX_SITES).
+ */
+#pragma pack(push, 1)
+typedef struct odp_event {
+    uint64_t t_start_ns;
+    uint64_t t_end_ns;
+    uint64_t host_addr;
+    uint64_t dev_addr;
+    uint64_t bytes;
+    uint64_t fp_lo;
+    uint64_t fp_hi;
+    uint32_t site_id;
+    uint8_t kind;
+    int8_t src_dev;
+    int8_t dst_dev;
+    uint8_t flags;
+} odp_event;
+
+/* Finding kinds (Sec. 7.5 abbreviations). */
+enum { ODP_DD = 1, ODP_RT = 2, ODP_RA = 3, ODP_UA = 4, ODP_UT = 5 };
+
+/*
+ * One finding, 48 bytes.
+ *   DD: event = a transfer whose <fingerprint, destination> was received
+ *       before; partner = the first such transfer (Alg. 1).
+ *   RT: event = a transfer tx, partner = the reception rx it pairs with
+ *       (Alg. 2, literal peek/dequeue semantics); the wasted trip is rx.
+ *   RA: event = the alloc of a repeated <host_addr, device, bytes> pair,
+ *       partner = the first pair's alloc (Alg. 3).
+ *   UA: event = an unused allocation, partner = its delete or ODP_NO_EVENT
+ *       when it is never deleted (Alg. 4).
+ *   UT: event = an unused to-device transfer; partner = the transfer that
+ *       overwrote it, or ODP_NO_EVENT after the last kernel (Alg. 5).
+ *   wasted_bytes / wasted_ns: bytes and duration of the eliminable
+ *   operations (DD, UT: the event; RT: rx; RA, UA: alloc + delete).
+ */
+typedef struct odp_finding {
+    uint8_t kind;
+    uint8_t pad0[3];
+    uint32_t site;          /* site_id of `event` */
+    uint32_t partner_site;  /* site_id of `partner`, 0xFFFFFFFF if none */
+    uint32_t pad1;
+    uint64_t event;
+    uint64_t partner;
+    uint64_t wasted_bytes;
+    uint64_t wasted_ns;
+} odp_finding;
+
+/* Per (kind, site) totals, rows ordered by (kind, site). */
+typedef struct odp_site_row {
+    uint32_t site;
+    uint8_t kind;
+    uint8_t pad[3];
+    uint64_t count;
+    uint64_t wasted_bytes;
+    uint64_t wasted_ns;
+} odp_site_row;
+
+/* Trace totals and the Sec. 7.6 estimate: predicted time = span - saved,
+ * where saved sums the durations of the union of wasted events; the
+ * predicted speedup is speedup_num / speedup_den (den 0: unbounded). */
+typedef struct odp_summary {
+    uint64_t n_events, n_transfers, n_allocs, n_deletes, n_kernels;
+    uint64_t n_pairs, n_unpaired_allocs, n_unmatched_deletes;
+    uint64_t count[6];          /* indexed by finding kind */
+    uint64_t wasted_bytes[6];
+    uint64_t wasted_ns[6];
+    uint64_t trace_begin_ns, trace_end_ns, trace_span_ns;
+    uint64_t saved_ns;
+    uint64_t speedup_num, speedup_den;
+} odp_summary;
+#pragma pack(pop)
+
+/* Output description for odp_analyze.  All pointers are device pointers. */
+typedef struct odp_findings {
+    odp_finding* items;        /* capacity entries */
+    uint64_t capacity;
+    uint64_t* count;           /* total findings (may exceed capacity) */
+    odp_site_row* sites;       /* sites_capacity rows */
+    uint64_t sites_capacity;
+    uint64_t* sites_count;     /* total rows (may exceed sites_capacity) */
+    odp_summary* summary;
+    int32_t* status;           /* ODP_OK, ODP_WARN_TRUNCATED or an error */
+} odp_findings;
+
+/*
+ * odp_analyze -- Algorithms 1-5 of Sec. 5 over n events (device memory,
+ * chronological: t_start_ns nondecreasing, array index breaks ties).
+ *
+ * Findings are written ordered by (kind, event index).  If the total
+ * exceeds out->capacity the first `capacity` are written, *count still holds
+ * the total and *status is ODP_WARN_TRUNCATED; the summary and the site rows
+ * are always computed over all findings.  Validation errors (unknown kind,
+ * t_end < t_start, zero-byte transfer, inconsistent devices, site_id or
+ * bytes beyond the limits -> ODP_ERR_MALFORMED; decreasing t_start ->
+ * ODP_ERR_UNSORTED; the lowest offending index decides) zero the outputs and
+ * set *status.  n must be below 2^32 - 16 (ODP_ERR_UNSUPPORTED otherwise).
+ * Interpretations where the paper is silent: transfers only for Alg. 1/2,
+ * to-device transfers only for Alg. 5, a DELETE closes the nearest earlier
+ * open ALLOC of the same (device, dev_addr), never-deleted allocations end
+ * at the trace end for Alg. 4 and are excluded from Alg. 3.
+ */
+int odp_analyze(const odp_event* events, uint64_t n, const odp_findings* out,
+                cudaStream_t stream);
+
+/* ----------------------------------------------------------------- memory */
+
+typedef void* (*odp_alloc_fn)(size_t bytes, cudaStream_t stream, void* ctx);
+typedef void (*odp_free_fn)(void* ptr, cudaStream_t stream, void* ctx);
+
+/* Installs the scratch allocator (null restores cudaMallocAsync/FreeAsync).
+ * Frees every cached scratch block first (synchronising the device). */
+int odp_set_allocator(odp_alloc_fn alloc_fn, odp_free_fn free_fn, void* ctx);
+
+/* Releases all cached scratch memory and graphs (synchronises the device). */
+int odp_release_scratch(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ODP_H */

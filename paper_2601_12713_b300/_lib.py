@@ -1,0 +1,188 @@
+"""ctypes binding of libodp (argument marshalling only)."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libodp.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_2601_12713_b300.build` "
+        "(there is no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_vp = ctypes.c_void_p
+
+_lib.odp_status_string.argtypes = [ctypes.c_int]
+_lib.odp_status_string.restype = ctypes.c_char_p
+_lib.odp_fingerprint.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, _vp]
+_lib.odp_fingerprint.restype = ctypes.c_int
+_lib.odp_fingerprint_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+_lib.odp_fingerprint_status.restype = ctypes.c_int
+_lib.odp_analyze.argtypes = [_vp, ctypes.c_uint64, _vp, _vp]
+_lib.odp_analyze.restype = ctypes.c_int
+_lib.odp_release_scratch.argtypes = []
+_lib.odp_release_scratch.restype = ctypes.c_int
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_lib.odp_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, ctypes.c_void_p]
+_lib.odp_set_allocator.restype = ctypes.c_int
+
+
+def lib():
+    return _lib
+
+
+class OdpError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+def status_string(status: int) -> str:
+    return _lib.odp_status_string(int(status)).decode()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check(status: int, what: str) -> int:
+    if status < 0:
+        raise OdpError(status, what)
+    return status
+
+
+# ------------------------------------------------------------ fingerprint
+
+def fingerprint(ptrs: torch.Tensor, sizes: torch.Tensor, out: torch.Tensor, stream=None) -> None:
+    """FP128 of n buffers: ``ptrs``/``sizes`` int64 CUDA tensors of n entries,
+    ``out`` an (n, 2) int64 CUDA tensor receiving (lo, hi)."""
+    n = ptrs.numel()
+    assert sizes.numel() == n and out.numel() == 2 * n
+    for t in (ptrs, sizes, out):
+        assert t.is_cuda and t.is_contiguous()
+    _check(_lib.odp_fingerprint(ptrs.data_ptr() if n else None, sizes.data_ptr() if n else None,
+                                n, out.data_ptr() if n else None, _stream(stream)),
+           "odp_fingerprint")
+
+
+def fingerprint_tensors(tensors, stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """FP128 of the bytes of each CUDA tensor (any dtype, contiguous)."""
+    dev = tensors[0].device if tensors else torch.device("cuda")
+    n = len(tensors)
+    ptr_h = torch.tensor([t.data_ptr() for t in tensors], dtype=torch.int64)
+    size_h = torch.tensor([t.numel() * t.element_size() for t in tensors], dtype=torch.int64)
+    ptrs = ptr_h.to(dev, non_blocking=False)
+    sizes = size_h.to(dev, non_blocking=False)
+    if out is None:
+        out = torch.empty((n, 2), dtype=torch.int64, device=dev)
+    fingerprint(ptrs, sizes, out, stream)
+    return out
+
+
+def fingerprint_status(stream=None) -> int:
+    s = ctypes.c_int32(0)
+    _check(_lib.odp_fingerprint_status(_stream(stream), ctypes.byref(s)), "odp_fingerprint_status")
+    return int(s.value)
+
+
+# ---------------------------------------------------------------- analysis
+
+EVENT_DTYPE = np.dtype(
+    [("t_start_ns", "<u8"), ("t_end_ns", "<u8"), ("host_addr", "<u8"), ("dev_addr", "<u8"),
+     ("bytes", "<u8"), ("fp_lo", "<u8"), ("fp_hi", "<u8"), ("site_id", "<u4"), ("kind", "u1"),
+     ("src_dev", "i1"), ("dst_dev", "i1"), ("flags", "u1")])
+FINDING_DTYPE = np.dtype(
+    [("kind", "u1"), ("pad0", "u1", (3,)), ("site", "<u4"), ("partner_site", "<u4"),
+     ("pad1", "<u4"), ("event", "<u8"), ("partner", "<u8"), ("wasted_bytes", "<u8"),
+     ("wasted_ns", "<u8")])
+SITE_DTYPE = np.dtype(
+    [("site", "<u4"), ("kind", "u1"), ("pad", "u1", (3,)), ("count", "<u8"),
+     ("wasted_bytes", "<u8"), ("wasted_ns", "<u8")])
+SUMMARY_FIELDS = (
+    ["n_events", "n_transfers", "n_allocs", "n_deletes", "n_kernels", "n_pairs",
+     "n_unpaired_allocs", "n_unmatched_deletes"]
+    + [f"count{k}" for k in range(6)] + [f"wasted_bytes{k}" for k in range(6)]
+    + [f"wasted_ns{k}" for k in range(6)]
+    + ["trace_begin_ns", "trace_end_ns", "trace_span_ns", "saved_ns", "speedup_num",
+       "speedup_den"])
+assert EVENT_DTYPE.itemsize == 64 and FINDING_DTYPE.itemsize == 48 and SITE_DTYPE.itemsize == 32
+
+
+class _OdpFindings(ctypes.Structure):
+    _fields_ = [("items", _vp), ("capacity", ctypes.c_uint64), ("count", _vp), ("sites", _vp),
+                ("sites_capacity", ctypes.c_uint64), ("sites_count", _vp), ("summary", _vp),
+                ("status", _vp)]
+
+
+class Findings:
+    """Device-side output buffers of odp_analyze."""
+
+    def __init__(self, capacity: int, sites_capacity: int = 5 * 65536, device="cuda"):
+        self.capacity = int(capacity)
+        self.sites_capacity = int(sites_capacity)
+        self.items = torch.empty(max(1, self.capacity) * 48, dtype=torch.uint8, device=device)
+        self.sites = torch.empty(max(1, self.sites_capacity) * 32, dtype=torch.uint8, device=device)
+        # count, sites_count, status (+pad), summary
+        self.small = torch.zeros(4 + len(SUMMARY_FIELDS), dtype=torch.int64, device=device)
+        base = self.small.data_ptr()
+        self.struct = _OdpFindings(self.items.data_ptr(), self.capacity, base,
+                                   self.sites.data_ptr(), self.sites_capacity, base + 8,
+                                   base + 32, base + 16)
+
+    def to_host(self):
+        small = self.small.cpu().numpy().view(np.uint64)
+        count = int(small[0])
+        n_sites = int(small[1])
+        status = int(np.int32(np.uint32(small[2] & np.uint64(0xFFFFFFFF))))
+        summary = {k: int(v) for k, v in zip(SUMMARY_FIELDS, small[4:])}
+        k = min(count, self.capacity)
+        items = self.items[: k * 48].cpu().numpy().view(FINDING_DTYPE).copy()
+        s = min(n_sites, self.sites_capacity)
+        sites = self.sites[: s * 32].cpu().numpy().view(SITE_DTYPE).copy()
+        return {"status": status, "count": count, "findings": items, "summary": summary,
+                "sites": sites, "n_sites": n_sites}
+
+
+def analyze(events: torch.Tensor, n: int, out: Findings, stream=None) -> None:
+    """Algorithms 1-5 over ``n`` 64-byte events held in a CUDA byte tensor."""
+    assert events.is_cuda and events.numel() >= 64 * n
+    _check(_lib.odp_analyze(events.data_ptr() if n else None, n, ctypes.byref(out.struct),
+                            _stream(stream)), "odp_analyze")
+
+
+# ---------------------------------------------------------------- memory
+
+_keep = []
+
+
+def set_torch_allocator() -> None:
+    """Route libodp scratch through torch's caching allocator."""
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC_FN(_alloc), _FREE_FN(_free)
+    _keep[:] = [a, f]
+    _check(_lib.odp_set_allocator(a, f, None), "odp_set_allocator")
+
+
+def release_scratch() -> None:
+    _check(_lib.odp_release_scratch(), "odp_release_scratch")

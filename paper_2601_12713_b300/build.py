@@ -1,0 +1,67 @@
+"""Builds libodp.so (and the synthetic-input fill library) in-tree with nvcc
+for sm_103a.  Run ``python -m paper_2601_12713_b300.build``."""
+
+from __future__ import annotations
+
+import glob
+import os
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+LIB = os.path.join(PKG, "libodp.so")
+SYNTH_SRC = os.path.join(ROOT, "synth", "gen.cu")
+SYNTH_LIB = os.path.join(ROOT, "synth", "libsynth.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+         "--expt-relaxed-constexpr", "-Xptxas", "-v"]
+
+
+def _sources():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+
+
+def _deps():
+    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
+        os.path.join(INCLUDE, "odp.h")]
+
+
+def _stale(target, deps):
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def _nvcc(out, srcs, extra=(), log=None):
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = [NVCC, *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC, *extra, "-o", tmp, *srcs]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if log is not None:
+        with open(log, "w") as f:
+            f.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)
+    if res.returncode != 0:
+        sys.stderr.write(res.stdout + res.stderr)
+        raise RuntimeError(f"nvcc failed for {out}")
+    os.replace(tmp, out)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if force or _stale(LIB, _deps()):
+        _nvcc(LIB, _sources(), extra=["-lcuda"] if False else [],
+              log=os.path.join(PKG, "build.log"))
+        if verbose:
+            print(open(os.path.join(PKG, "build.log")).read())
+    if force or _stale(SYNTH_LIB, [SYNTH_SRC]):
+        _nvcc(SYNTH_LIB, [SYNTH_SRC])
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
+    print(LIB)

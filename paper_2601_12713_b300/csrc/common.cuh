@@ -1,0 +1,96 @@
+// common.cuh -- shared host/device helpers of libodp (status, scratch, SM
+// count, small warp/block primitives).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "odp.h"
+
+#define ODP_FULL_MASK 0xFFFFFFFFu
+
+namespace odp {
+
+// ------------------------------------------------------------------ host
+
+// Scratch blocks are cached per (device, stream, slot) and grow on demand.
+// Slots keep the fingerprint and analysis scratch apart.
+enum ScratchSlot {
+    SLOT_FP_PLAN = 0,
+    SLOT_AN_MAIN = 1,
+    SLOT_AN_TABLE = 2,
+    SLOT_AN_SORT = 3,
+    SLOT_AN_SITES = 4,
+    SLOT_SERVE = 5,
+    SLOT_COUNT = 8
+};
+
+// Returns a device block of at least `bytes` bytes for (current device,
+// stream, slot), or null with *status = ODP_ERR_OOM.
+void* scratch_get(int slot, size_t bytes, cudaStream_t stream, int* status);
+
+int device_sm_count();       // SMs of the current device
+int current_device();
+int32_t* device_status_word(int* status);  // per-device fingerprint status
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? ODP_OK : ODP_ERR_CUDA; }
+
+#define ODP_CHECK_CUDA(expr)                              \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) return ODP_ERR_CUDA;       \
+    } while (0)
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- device
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    return __shfl_sync(ODP_FULL_MASK, v, src);
+}
+__device__ __forceinline__ uint64_t shfl_down64(uint64_t v, int d) {
+    return __shfl_down_sync(ODP_FULL_MASK, v, d);
+}
+
+// Records the first (lowest-index) device error: packs (index, code) so that
+// atomicMin keeps the smallest index.  code is the negated status (1..127).
+__device__ __forceinline__ void record_error(unsigned long long* word, uint64_t index, int status) {
+    unsigned long long v = ((unsigned long long)index << 8) | (unsigned long long)(-status & 0xFF);
+    atomicMin(word, v);
+}
+
+// Block-wide exclusive scan of one u32 per thread (blockDim.x multiple of 32,
+// at most 1024).  Returns the exclusive prefix; *total gets the block sum.
+__device__ __forceinline__ uint32_t block_exclusive_scan_u32(uint32_t v, uint32_t* total,
+                                                             uint32_t* smem /*>=33*/) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(ODP_FULL_MASK, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) smem[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < nwarps ? smem[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(ODP_FULL_MASK, s, d);
+            if (lane >= d) s += y;
+        }
+        if (lane < nwarps) smem[lane] = s;  // inclusive per-warp sums
+        if (lane == nwarps - 1) smem[32] = s;
+    }
+    __syncthreads();
+    uint32_t base = warp > 0 ? smem[warp - 1] : 0;
+    *total = smem[32];
+    uint32_t r = base + x - v;
+    __syncthreads();
+    return r;
+}
+
+}  // namespace odp

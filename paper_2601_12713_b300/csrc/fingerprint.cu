@@ -1,0 +1,625 @@
+// fingerprint.cu -- odp_fingerprint: FP128 v1 of a ragged batch of buffers in
+// one persistent launch (paper Sec. 5.1 hashes every transferred buffer; this
+// is the data-parallel form of that step).
+//
+// Schedule (none of it changes the result; see the tree argument below):
+//   plan     per buffer: chunk count, tile size 2^m_b chunks, tile and node
+//            offsets (exclusive scans); tile -> buffer list.
+//   tiles    persistent warps take tiles from an atomic counter.  A warp
+//            hashes the tile's chunks (lane l loads 16-byte words l + 32j),
+//            reduces up to 32 leaves across lanes, folds groups of 32 with
+//            a small stack (tiles > 32 chunks), then either finalises the
+//            buffer (single-tile buffers) or climbs the upper tree: it
+//            stores the tile root, bumps the counter of its 32-node group and
+//            the warp that completes a group combines it, level by level.
+// An aligned block of 2^k leaves of a left-balanced tree is a complete
+// subtree, and the suffix after the last full block is one too, so tiles of
+// 2^m chunks and 32-aligned groups of tile roots give the same root as the
+// plain recursive split.
+#include <algorithm>
+
+#include "common.cuh"
+#include "fp128.cuh"
+
+namespace odp {
+namespace {
+
+using fp::U128;
+
+constexpr uint32_t CHUNK = 4096;
+constexpr int MAX_SMALL_PLAN = 8192;  // single-block plan up to this many buffers
+
+struct PlanHeader {
+    unsigned long long total_chunks;
+    unsigned long long err;  // packed (index, -status) of the first bad buffer
+    uint32_t m_floor;
+    uint32_t total_tiles;
+    uint32_t total_nodes;
+    uint32_t tile_counter;
+};
+
+struct FpArgs {
+    const void* const* ptrs;
+    const uint64_t* sizes;
+    odp_fp128* out;
+    uint32_t n;
+    uint32_t tmin;        // target tiles per buffer (launch-level knob)
+    uint32_t cap_tiles;   // tile capacity of the scratch
+    PlanHeader* hdr;
+    uint32_t* tile_off;   // n + 1
+    uint32_t* node_off;   // n + 1
+    uint32_t* block_sums; // 2 * plan blocks
+    uint32_t* tile_buf;   // cap_tiles
+    uint32_t* counters;   // 2 * cap_tiles
+    U128* nodes;          // 2 * cap_tiles
+    int32_t* status;      // per-device status word
+};
+
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ uint64_t n_chunks(uint64_t size) { return (size + CHUNK - 1) / CHUNK; }
+
+__device__ __forceinline__ int ceil_log2(uint64_t v) {
+    return v <= 1 ? 0 : 64 - __clzll((long long)(v - 1));
+}
+
+// Tile size exponent of a buffer: aim for `tmin` tiles, at most 32 chunks per
+// tile unless the scratch capacity forces larger tiles (m_floor).
+__device__ __forceinline__ int tile_log2(uint64_t nchunk, uint32_t tmin, uint32_t m_floor) {
+    uint64_t want = (nchunk + tmin - 1) / tmin;
+    int m = min(ceil_log2(want), 5);
+    return max(m, (int)m_floor);
+}
+
+__device__ __forceinline__ uint64_t n_tiles(uint64_t nchunk, int m) {
+    return (nchunk + (1ull << m) - 1) >> m;
+}
+
+// Nodes kept for the upper tree of a buffer with `nt` tiles (0 if nt <= 1):
+// every level down from the tiles, including the single top node.
+__device__ __forceinline__ uint64_t n_nodes(uint64_t nt) {
+    if (nt <= 1) return 0;
+    uint64_t s = 0;
+    for (uint64_t l = nt;; l = (l + 31) / 32) {
+        s += l;
+        if (l == 1) break;
+    }
+    return s;
+}
+
+// --------------------------------------------------------------- plan
+
+// Per-buffer work shared by the plan kernels: chunk count; empty buffers and
+// null pointers are finished here.
+__device__ __forceinline__ uint64_t plan_chunks(const FpArgs& a, uint32_t i) {
+    uint64_t size = a.sizes[i];
+    if (size == 0) {
+        U128 e = fp::empty_input();
+        a.out[i].lo = e.x;
+        a.out[i].hi = e.y;
+        return 0;
+    }
+    if (a.ptrs[i] == nullptr) {
+        a.out[i].lo = 0;
+        a.out[i].hi = 0;
+        record_error(&a.hdr->err, i, ODP_ERR_INVALID_ARG);
+        return 0;
+    }
+    return n_chunks(size);
+}
+
+__device__ __forceinline__ uint32_t floor_for(unsigned long long total_chunks, uint32_t budget) {
+    uint32_t m = 0;
+    while ((total_chunks >> m) > budget) ++m;
+    return m;
+}
+
+// Single-block plan for small n: reduce, choose m_floor, scan, write offsets.
+__global__ void __launch_bounds__(1024) fp_plan_small(FpArgs a) {
+    __shared__ uint32_t sm[40];
+    __shared__ unsigned long long s_total;
+    if (threadIdx.x == 0) s_total = 0;
+    __syncthreads();
+    unsigned long long local = 0;
+    for (uint32_t i = threadIdx.x; i < a.n; i += blockDim.x) local += plan_chunks(a, i);
+    atomicAdd(&s_total, local);
+    __syncthreads();
+    const uint32_t budget = a.cap_tiles - a.n;
+    const uint32_t m_floor = floor_for(s_total, budget);
+    uint32_t base_t = 0, base_n = 0;
+    for (uint32_t i0 = 0; i0 < a.n; i0 += blockDim.x) {
+        uint32_t i = i0 + threadIdx.x;
+        uint32_t nt = 0, nn = 0;
+        if (i < a.n) {
+            uint64_t size = a.sizes[i];
+            if (size != 0 && a.ptrs[i] != nullptr) {
+                uint64_t nc = n_chunks(size);
+                nt = (uint32_t)n_tiles(nc, tile_log2(nc, a.tmin, m_floor));
+                nn = (uint32_t)n_nodes(nt);
+            }
+        }
+        uint32_t tot_t, tot_n;
+        uint32_t et = block_exclusive_scan_u32(nt, &tot_t, sm);
+        uint32_t en = block_exclusive_scan_u32(nn, &tot_n, sm);
+        if (i < a.n) {
+            a.tile_off[i] = base_t + et;
+            a.node_off[i] = base_n + en;
+        }
+        base_t += tot_t;
+        base_n += tot_n;
+    }
+    if (threadIdx.x == 0) {
+        a.tile_off[a.n] = base_t;
+        a.node_off[a.n] = base_n;
+        a.hdr->total_chunks = s_total;
+        a.hdr->m_floor = m_floor;
+        a.hdr->total_tiles = base_t;
+        a.hdr->total_nodes = base_n;
+        a.hdr->tile_counter = 0;
+    }
+}
+
+// Multi-block plan, pass 1: total chunk count (and empty-buffer results).
+__global__ void __launch_bounds__(256) fp_plan_count(FpArgs a) {
+    __shared__ unsigned long long s_total;
+    if (threadIdx.x == 0) s_total = 0;
+    __syncthreads();
+    unsigned long long local = 0;
+    uint32_t base = blockIdx.x * 1024;
+    for (int k = 0; k < 4; ++k) {
+        uint32_t i = base + k * 256 + threadIdx.x;
+        if (i < a.n) local += plan_chunks(a, i);
+    }
+    atomicAdd(&s_total, local);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&a.hdr->total_chunks, s_total);
+}
+
+// Pass 2: per-buffer tiles/nodes, block-local exclusive offsets, block sums.
+__global__ void __launch_bounds__(256) fp_plan_scan(FpArgs a) {
+    __shared__ uint32_t sm[40];
+    const uint32_t m_floor = floor_for(a.hdr->total_chunks, a.cap_tiles - a.n);
+    uint32_t base = blockIdx.x * 1024 + threadIdx.x * 4;
+    uint32_t nt[4], nn[4], st = 0, sn = 0;
+    for (int k = 0; k < 4; ++k) {
+        uint32_t i = base + k;
+        nt[k] = nn[k] = 0;
+        if (i < a.n) {
+            uint64_t size = a.sizes[i];
+            if (size != 0 && a.ptrs[i] != nullptr) {
+                uint64_t nc = n_chunks(size);
+                nt[k] = (uint32_t)n_tiles(nc, tile_log2(nc, a.tmin, m_floor));
+                nn[k] = (uint32_t)n_nodes(nt[k]);
+            }
+        }
+        st += nt[k];
+        sn += nn[k];
+    }
+    uint32_t tot_t, tot_n;
+    uint32_t et = block_exclusive_scan_u32(st, &tot_t, sm);
+    uint32_t en = block_exclusive_scan_u32(sn, &tot_n, sm);
+    for (int k = 0; k < 4; ++k) {
+        uint32_t i = base + k;
+        if (i < a.n) {
+            a.tile_off[i] = et;
+            a.node_off[i] = en;
+        }
+        et += nt[k];
+        en += nn[k];
+    }
+    if (threadIdx.x == 0) {
+        a.block_sums[2 * blockIdx.x] = tot_t;
+        a.block_sums[2 * blockIdx.x + 1] = tot_n;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.hdr->m_floor = m_floor;
+}
+
+// Pass 3 (one block): exclusive scan of the block sums; totals.
+__global__ void __launch_bounds__(1024) fp_plan_blocks(FpArgs a, uint32_t nblocks) {
+    __shared__ uint32_t sm[40];
+    uint32_t base_t = 0, base_n = 0;
+    for (uint32_t b0 = 0; b0 < nblocks; b0 += blockDim.x) {
+        uint32_t b = b0 + threadIdx.x;
+        uint32_t vt = b < nblocks ? a.block_sums[2 * b] : 0;
+        uint32_t vn = b < nblocks ? a.block_sums[2 * b + 1] : 0;
+        uint32_t tt, tn;
+        uint32_t et = block_exclusive_scan_u32(vt, &tt, sm);
+        uint32_t en = block_exclusive_scan_u32(vn, &tn, sm);
+        if (b < nblocks) {
+            a.block_sums[2 * b] = base_t + et;
+            a.block_sums[2 * b + 1] = base_n + en;
+        }
+        base_t += tt;
+        base_n += tn;
+    }
+    if (threadIdx.x == 0) {
+        a.tile_off[a.n] = base_t;
+        a.node_off[a.n] = base_n;
+        a.hdr->total_tiles = base_t;
+        a.hdr->total_nodes = base_n;
+        a.hdr->tile_counter = 0;
+    }
+}
+
+// Pass 4: add the block offsets.
+__global__ void __launch_bounds__(256) fp_plan_add(FpArgs a) {
+    uint32_t bt = a.block_sums[2 * blockIdx.x], bn = a.block_sums[2 * blockIdx.x + 1];
+    uint32_t base = blockIdx.x * 1024 + threadIdx.x * 4;
+    for (int k = 0; k < 4; ++k) {
+        uint32_t i = base + k;
+        if (i < a.n) {
+            a.tile_off[i] += bt;
+            a.node_off[i] += bn;
+        }
+    }
+}
+
+// Tile -> buffer list (binary search over tile offsets) and counter reset.
+__global__ void __launch_bounds__(256) fp_plan_tiles(FpArgs a) {
+    const uint32_t T = a.hdr->total_tiles, N = a.hdr->total_nodes;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += stride) {
+        // largest i with tile_off[i] <= t and a non-empty range
+        uint32_t lo = 0, hi = a.n;  // invariant: tile_off[lo] <= t < tile_off[hi]
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (a.tile_off[mid] <= t) lo = mid; else hi = mid;
+        }
+        a.tile_buf[t] = lo;
+    }
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) a.counters[i] = 0;
+}
+
+// --------------------------------------------------------------- tiles
+
+__device__ __forceinline__ uint4 ld_stream(const uint8_t* p) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+
+// Keep the first v (0..16) bytes of a little-endian 16-byte word.
+__device__ __forceinline__ uint4 keep_bytes(uint4 w, uint32_t v) {
+    uint32_t m[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int k = (int)v - 4 * i;  // valid bytes in component i
+        m[i] = k >= 4 ? 0xFFFFFFFFu : (k <= 0 ? 0u : (0xFFFFFFFFu >> (32 - 8 * k)));
+    }
+    return make_uint4(w.x & m[0], w.y & m[1], w.z & m[2], w.w & m[3]);
+}
+
+// 16 bytes starting `off` (1..15) bytes into the 32-byte pair (lo, hi).
+__device__ __forceinline__ uint4 funnel16(uint4 lo, uint4 hi, uint32_t off) {
+    const uint32_t q = off >> 2, s = (off & 3) * 8;
+    uint32_t c0, c1, c2, c3, c4;
+    if (q == 0) { c0 = lo.x; c1 = lo.y; c2 = lo.z; c3 = lo.w; c4 = hi.x; }
+    else if (q == 1) { c0 = lo.y; c1 = lo.z; c2 = lo.w; c3 = hi.x; c4 = hi.y; }
+    else if (q == 2) { c0 = lo.z; c1 = lo.w; c2 = hi.x; c3 = hi.y; c4 = hi.z; }
+    else { c0 = lo.w; c1 = hi.x; c2 = hi.y; c3 = hi.z; c4 = hi.w; }
+    return make_uint4(__funnelshift_r(c0, c1, s), __funnelshift_r(c1, c2, s),
+                      __funnelshift_r(c2, c3, s), __funnelshift_r(c3, c4, s));
+}
+
+// Word `wi` of a chunk whose first byte is at `cp`, `r` valid bytes, general
+// alignment.  Only aligned 16-byte blocks that hold a valid byte are read.
+__device__ __forceinline__ uint4 load_word_general(const uint8_t* cp, uint32_t wi, uint32_t r) {
+    const uint32_t o = 16 * wi;
+    if (o >= r) return make_uint4(0, 0, 0, 0);
+    const uint32_t v = min(16u, r - o);
+    const uint8_t* p = cp + o;
+    const uint32_t off = (uint32_t)((uintptr_t)p & 15);
+    uint4 w;
+    if (off == 0) {
+        w = ld_stream(p);
+    } else {
+        const uint8_t* b0 = p - off;
+        uint4 lo = ld_stream(b0);
+        uint4 hi = make_uint4(0, 0, 0, 0);
+        if (off + v > 16) hi = ld_stream(b0 + 16);
+        w = funnel16(lo, hi, off);
+    }
+    return v < 16 ? keep_bytes(w, v) : w;
+}
+
+// Chain absorption, lane finish and the 32-lane combine.  Lane 0 ends with
+// the chunk root.
+__device__ __forceinline__ void absorb_and_combine(const uint4 (&w)[8], uint64_t a, uint64_t b,
+                                                   uint64_t& rx, uint64_t& ry) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint64_t lo = ((uint64_t)w[j].y << 32) | w[j].x;
+        uint64_t hi = ((uint64_t)w[j].w << 32) | w[j].z;
+        a = fp::chain(a ^ lo, fp::KA1, fp::KA2);
+        b = fp::chain(b ^ hi, fp::KB1, fp::KB2);
+    }
+    a ^= b * fp::KF1;
+    b ^= a * fp::KF2;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t ox = shfl_down64(a, d), oy = shfl_down64(b, d);
+        a ^= oy;
+        b ^= ox ^ oy;
+    }
+    rx = a;
+    ry = b;
+}
+
+// Left-balanced combine of `cnt` (1..32) nodes held by lanes 0..cnt-1, each
+// with its leaf count c.  Every lane returns the root and its count.
+__device__ __forceinline__ U128 warp_tree(U128 v, uint64_t& c, uint32_t cnt, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t rx = shfl_down64(v.x, d), ry = shfl_down64(v.y, d);
+        uint64_t rc = shfl_down64(c, d);
+        U128 nd = fp::node(v, U128{rx, ry}, c + rc);
+        if ((lane & (2 * d - 1)) == 0 && (uint32_t)(lane + d) < cnt) {
+            v = nd;
+            c += rc;
+        }
+    }
+    v.x = shfl64(v.x, 0);
+    v.y = shfl64(v.y, 0);
+    c = shfl64(c, 0);
+    return v;
+}
+
+struct WarpStack {
+    U128 node[40];
+    uint64_t count[40];
+};
+
+// Hash chunks [c0, c0 + cnt) of a buffer (`cnt` <= 2^m); returns the subtree
+// root in every lane.
+template <bool ALIGNED>
+__device__ __forceinline__ U128 hash_tile(const uint8_t* base, uint64_t size, uint64_t c0,
+                                          uint64_t cnt, int lane, uint64_t a0, uint64_t b0,
+                                          WarpStack* st) {
+    int depth = 0;
+    U128 root{0, 0};
+    uint64_t root_c = 0;
+    for (uint64_t g0 = 0; g0 < cnt; g0 += 32) {
+        const uint32_t gc = (uint32_t)umin64(32, cnt - g0);
+        uint64_t mx = 0, my = 0;
+        for (uint32_t k = 0; k < gc; ++k) {
+            const uint64_t c = c0 + g0 + k;
+            const uint8_t* cp = base + c * CHUNK;
+            const uint32_t r = (uint32_t)umin64(CHUNK, size - c * CHUNK);
+            uint4 w[8];
+            if (ALIGNED && r == CHUNK) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) w[j] = ld_stream(cp + 16 * (lane + 32 * j));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) w[j] = load_word_general(cp, lane + 32 * j, r);
+            }
+            uint64_t rx, ry;
+            absorb_and_combine(w, a0, b0, rx, ry);
+            rx = shfl64(rx, 0);
+            ry = shfl64(ry, 0);
+            if ((uint32_t)lane == k) {
+                mx = rx;
+                my = ry;
+            }
+        }
+        // leaves of this group, one per lane, then the group subtree
+        const uint64_t cl = c0 + g0 + (uint64_t)umin32(lane, gc - 1);
+        const uint64_t rl = umin64(CHUNK, size - cl * CHUNK);
+        U128 lf = fp::leaf(mx, my, rl);
+        uint64_t lc = 1;
+        U128 gr = warp_tree(lf, lc, gc, lane);
+        if (cnt <= 32) return gr;
+        // push the group root; merge equal-sized neighbours
+        if (lane == 0) {
+            st->node[depth] = gr;
+            st->count[depth] = lc;
+        }
+        ++depth;
+        __syncwarp();
+        while (depth >= 2 && st->count[depth - 2] == st->count[depth - 1]) {
+            U128 l = st->node[depth - 2], rr = st->node[depth - 1];
+            uint64_t cc = st->count[depth - 2] + st->count[depth - 1];
+            U128 nd = fp::node(l, rr, cc);
+            __syncwarp();
+            if (lane == 0) {
+                st->node[depth - 2] = nd;
+                st->count[depth - 2] = cc;
+            }
+            --depth;
+            __syncwarp();
+        }
+    }
+    // fold right to left
+    root = st->node[depth - 1];
+    root_c = st->count[depth - 1];
+    for (int i = depth - 2; i >= 0; --i) {
+        root_c += st->count[i];
+        root = fp::node(st->node[i], root, root_c);
+    }
+    __syncwarp();
+    return root;
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) fp_tiles(FpArgs a) {
+    __shared__ WarpStack stacks[WARPS];
+    const int lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    WarpStack* st = &stacks[warp];
+    uint64_t a0, b0;
+    fp::lane_init(lane, a0, b0);
+    const uint32_t T = a.hdr->total_tiles;
+    const uint32_t m_floor = a.hdr->m_floor;
+
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&a.hdr->tile_counter, 1u);
+    t = __shfl_sync(ODP_FULL_MASK, t, 0);
+    while (t < T) {
+        // fetch the next tile index early to hide the atomic's latency
+        uint32_t t_next = 0;
+        if (lane == 0) t_next = atomicAdd(&a.hdr->tile_counter, 1u);
+
+        const uint32_t b = a.n == 1 ? 0u : a.tile_buf[t];
+        const uint32_t tb = t - a.tile_off[b];
+        const uint64_t size = a.sizes[b];
+        const uint8_t* base = (const uint8_t*)a.ptrs[b];
+        const uint64_t nchunk = n_chunks(size);
+        const int m = tile_log2(nchunk, a.tmin, m_floor);
+        const uint64_t c0 = (uint64_t)tb << m;
+        const uint64_t cnt = umin64(1ull << m, nchunk - c0);
+
+        U128 root;
+        if (((uintptr_t)base & 15) == 0)
+            root = hash_tile<true>(base, size, c0, cnt, lane, a0, b0, st);
+        else
+            root = hash_tile<false>(base, size, c0, cnt, lane, a0, b0, st);
+
+        const uint64_t ntile = n_tiles(nchunk, m);
+        if (ntile == 1) {
+            if (lane == 0) {
+                U128 o = fp::finish(root, size, nchunk);
+                a.out[b].lo = o.x;
+                a.out[b].hi = o.y;
+            }
+        } else {
+            // climb: level L holds nodes covering span = 2^m * 32^L chunks
+            uint64_t nl = ntile, idx = tb, off = a.node_off[b];
+            uint64_t span = 1ull << m;
+            U128 node = root;
+            while (true) {
+                if (nl == 1) {
+                    if (lane == 0) {
+                        U128 o = fp::finish(node, size, nchunk);
+                        a.out[b].lo = o.x;
+                        a.out[b].hi = o.y;
+                    }
+                    break;
+                }
+                const uint64_t nup = (nl + 31) / 32;
+                const uint64_t g = idx / 32;
+                const uint32_t gsize = (uint32_t)umin64(32, nl - 32 * g);
+                uint32_t old = 0;
+                if (lane == 0) {
+                    a.nodes[off + idx] = node;
+                    __threadfence();
+                    old = atomicAdd(&a.counters[off + nl + g], 1u);
+                }
+                old = __shfl_sync(ODP_FULL_MASK, old, 0);
+                if (old != gsize - 1) break;  // another warp finishes this group
+                __threadfence();
+                U128 v{0, 0};
+                uint64_t c = 0;
+                if ((uint32_t)lane < gsize) {
+                    const U128* src = &a.nodes[off + 32 * g + lane];
+                    v.x = __ldcg((const unsigned long long*)&src->x);
+                    v.y = __ldcg((const unsigned long long*)&src->y);
+                    const uint64_t first = (32 * g + lane) * span;
+                    c = umin64(span, nchunk - first);
+                }
+                node = warp_tree(v, c, gsize, lane);
+                off += nl;
+                nl = nup;
+                idx = g;
+                span *= 32;
+            }
+        }
+        t = __shfl_sync(ODP_FULL_MASK, t_next, 0);
+    }
+}
+
+// Status word: the first error index is not kept; only the code.
+__global__ void fp_publish_status(const PlanHeader* hdr, int32_t* status) {
+    unsigned long long e = hdr->err;
+    if (e != ~0ull && *status == 0) *status = -(int32_t)(e & 0xFF);
+}
+
+constexpr int TILE_WARPS = 8;
+
+}  // namespace
+
+// Launch parameters picked per call (autotuned elsewhere; defaults here).
+struct FpLaunch {
+    int warps_per_cta = TILE_WARPS;
+    int ctas_per_sm = 0;     // 0: occupancy maximum
+    uint32_t tmin = 0;       // 0: derived from n and the warp count
+};
+
+static int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128* out,
+                  cudaStream_t stream, const FpLaunch& L) {
+    if (n == 0) return ODP_OK;
+    if (!ptrs || !sizes || !out) return ODP_ERR_INVALID_ARG;
+    if (n > (1ull << 28)) return ODP_ERR_UNSUPPORTED;
+    int st = ODP_OK;
+    int32_t* status = device_status_word(&st);
+    if (!status) return st;
+
+    const uint32_t nn = (uint32_t)n;
+    const uint32_t cap_tiles = nn + (1u << 20);
+    const uint32_t nblocks = (nn + 1023) / 1024;
+    size_t bytes = 0;
+    auto carve = [&](size_t sz) {
+        size_t o = bytes;
+        bytes = align_up(bytes + sz, 256);
+        return o;
+    };
+    size_t o_hdr = carve(sizeof(PlanHeader));
+    size_t o_toff = carve(sizeof(uint32_t) * (nn + 1));
+    size_t o_noff = carve(sizeof(uint32_t) * (nn + 1));
+    size_t o_bsum = carve(sizeof(uint32_t) * 2 * (nblocks + 1));
+    size_t o_tbuf = carve(sizeof(uint32_t) * (size_t)cap_tiles);
+    size_t o_cnt = carve(sizeof(uint32_t) * 2 * (size_t)cap_tiles);
+    size_t o_nodes = carve(sizeof(U128) * 2 * (size_t)cap_tiles);
+    uint8_t* s = (uint8_t*)scratch_get(SLOT_FP_PLAN, bytes, stream, &st);
+    if (!s) return st;
+
+    const int sms = device_sm_count();
+    FpArgs a;
+    a.ptrs = ptrs;
+    a.sizes = sizes;
+    a.out = out;
+    a.n = nn;
+    a.cap_tiles = cap_tiles;
+    a.hdr = (PlanHeader*)(s + o_hdr);
+    a.tile_off = (uint32_t*)(s + o_toff);
+    a.node_off = (uint32_t*)(s + o_noff);
+    a.block_sums = (uint32_t*)(s + o_bsum);
+    a.tile_buf = (uint32_t*)(s + o_tbuf);
+    a.counters = (uint32_t*)(s + o_cnt);
+    a.nodes = (U128*)(s + o_nodes);
+    a.status = status;
+
+    int ctas = L.ctas_per_sm;
+    if (ctas <= 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<TILE_WARPS>, TILE_WARPS * 32, 0);
+        ctas = std::max(1, occ);
+    }
+    const uint32_t total_warps = (uint32_t)(sms * ctas * TILE_WARPS);
+    a.tmin = L.tmin ? L.tmin : std::max<uint32_t>(1, (uint32_t)(2ull * total_warps / nn));
+
+    ODP_CHECK_CUDA(cudaMemsetAsync(a.hdr, 0, sizeof(PlanHeader), stream));
+    ODP_CHECK_CUDA(cudaMemsetAsync(&a.hdr->err, 0xFF, sizeof(unsigned long long), stream));
+    if (nn <= (uint32_t)MAX_SMALL_PLAN) {
+        fp_plan_small<<<1, 1024, 0, stream>>>(a);
+    } else {
+        fp_plan_count<<<nblocks, 256, 0, stream>>>(a);
+        fp_plan_scan<<<nblocks, 256, 0, stream>>>(a);
+        fp_plan_blocks<<<1, 1024, 0, stream>>>(a, nblocks);
+        fp_plan_add<<<nblocks, 256, 0, stream>>>(a);
+    }
+    fp_plan_tiles<<<sms * 4, 256, 0, stream>>>(a);
+    fp_tiles<TILE_WARPS><<<sms * ctas, TILE_WARPS * 32, 0, stream>>>(a);
+    fp_publish_status<<<1, 1, 0, stream>>>(a.hdr, status);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace odp
+
+extern "C" int odp_fingerprint(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
+                               odp_fp128* out128, cudaStream_t stream) {
+    odp::FpLaunch L;
+    return odp::fp_run(ptrs, sizes, n, out128, stream, L);
+}

@@ -1,0 +1,283 @@
+// prims.cuh -- device-wide primitives for the analysis pipeline: exclusive
+// scan of u32, stable LSD radix sort of (u32 key, u32 value) pairs, and an
+// open-addressing table of 128-bit keys keeping the minimum u32 value.
+//
+// Lengths that are only known on the device are passed as pointers; grids
+// are sized from a host-side upper bound and blocks past the device length
+// exit at once.
+#pragma once
+
+#include "common.cuh"
+
+namespace odp {
+namespace prim {
+
+constexpr uint32_t NONE32 = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t dev_len(const uint32_t* n_dev, uint32_t n_max) {
+    return n_dev ? min(*n_dev, n_max) : n_max;
+}
+
+// ------------------------------------------------------------------ scan
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr uint32_t SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Tile-local exclusive scan; block sums to `sums`.
+__global__ void __launch_bounds__(SCAN_THREADS)
+scan_local(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t n_max,
+           uint32_t* sums) {
+    __shared__ uint32_t sm[40];
+    const uint32_t n = dev_len(n_dev, n_max);
+    const uint32_t base = blockIdx.x * SCAN_TILE;
+    if (base >= n) return;
+    uint32_t v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    uint32_t tot;
+    uint32_t e = block_exclusive_scan_u32(s, &tot, sm);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
+        if (i < n) out[i] = e;
+        e += v[k];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// One block: exclusive scan of the tile sums; total to *total.
+__global__ void __launch_bounds__(SCAN_THREADS)
+scan_blocks(uint32_t* sums, const uint32_t* n_dev, uint32_t n_max, uint32_t* total) {
+    __shared__ uint32_t sm[40];
+    const uint32_t n = dev_len(n_dev, n_max);
+    const uint32_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    uint32_t run = 0;
+    for (uint32_t b0 = 0; b0 < nb; b0 += SCAN_THREADS) {
+        uint32_t b = b0 + threadIdx.x;
+        uint32_t v = b < nb ? sums[b] : 0, t;
+        uint32_t e = block_exclusive_scan_u32(v, &t, sm);
+        if (b < nb) sums[b] = run + e;
+        run += t;
+    }
+    if (threadIdx.x == 0 && total) *total = run;
+}
+
+__global__ void __launch_bounds__(256)
+scan_add(uint32_t* out, const uint32_t* n_dev, uint32_t n_max, const uint32_t* sums) {
+    const uint32_t n = dev_len(n_dev, n_max);
+    const uint32_t base = blockIdx.x * SCAN_TILE;
+    if (base >= n) return;
+    const uint32_t add = sums[blockIdx.x];
+    for (uint32_t i = base + threadIdx.x; i < min(base + SCAN_TILE, n); i += 256) out[i] += add;
+}
+
+inline size_t scan_tmp_words(uint32_t n_max) { return (n_max + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+// out[i] = sum of in[0..i) for i < n; *total = sum of all (may be null).
+inline void exclusive_scan(const uint32_t* in, uint32_t* out, const uint32_t* n_dev,
+                           uint32_t n_max, uint32_t* total, uint32_t* tmp, cudaStream_t s) {
+    if (n_max == 0) {
+        if (total) cudaMemsetAsync(total, 0, 4, s);
+        return;
+    }
+    const uint32_t nb = (n_max + SCAN_TILE - 1) / SCAN_TILE;
+    scan_local<<<nb, SCAN_THREADS, 0, s>>>(in, out, n_dev, n_max, tmp);
+    scan_blocks<<<1, SCAN_THREADS, 0, s>>>(tmp, n_dev, n_max, total);
+    scan_add<<<nb, 256, 0, s>>>(out, n_dev, n_max, tmp);
+}
+
+// ------------------------------------------------------------ radix sort
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ROUNDS = 16;
+constexpr uint32_t SORT_TILE = SORT_THREADS * SORT_ROUNDS;  // 4096 items per tile
+
+// Per-tile digit histogram, stored digit-major: hist[d * ntiles + tile].
+__global__ void __launch_bounds__(SORT_THREADS)
+sort_upsweep(const uint32_t* keys, const uint32_t* n_dev, uint32_t n_max, int shift, int bits,
+             uint32_t* hist, uint32_t ntiles) {
+    __shared__ uint32_t h[256];
+    const uint32_t n = dev_len(n_dev, n_max);
+    const uint32_t radix = 1u << bits;
+    for (uint32_t d = threadIdx.x; d < radix; d += SORT_THREADS) h[d] = 0;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * SORT_TILE;
+    if (base < n) {
+        for (uint32_t i = base + threadIdx.x; i < min(base + SORT_TILE, n); i += SORT_THREADS)
+            atomicAdd(&h[(keys[i] >> shift) & (radix - 1)], 1u);
+    }
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < radix; d += SORT_THREADS) hist[d * ntiles + blockIdx.x] = h[d];
+}
+
+// Stable scatter: items of a tile are ranked in index order (round-major,
+// then warp, then lane) with warp match_any and per-warp digit counts.
+__global__ void __launch_bounds__(SORT_THREADS)
+sort_downsweep(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
+               uint32_t* vals_out, const uint32_t* n_dev, uint32_t n_max, int shift, int bits,
+               const uint32_t* hist_scanned, uint32_t ntiles) {
+    constexpr int W = SORT_THREADS / 32;
+    __shared__ uint32_t base_d[256];
+    __shared__ uint32_t wcnt[W][256];
+    const uint32_t n = dev_len(n_dev, n_max);
+    const uint32_t tile0 = blockIdx.x * SORT_TILE;
+    if (tile0 >= n) return;
+    const uint32_t radix = 1u << bits;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t d = threadIdx.x; d < radix; d += SORT_THREADS) {
+        base_d[d] = hist_scanned[d * ntiles + blockIdx.x];
+        for (int w = 0; w < W; ++w) wcnt[w][d] = 0;
+    }
+    __syncthreads();
+    const uint32_t lt_mask = (1u << lane) - 1;
+    for (int r = 0; r < SORT_ROUNDS; ++r) {
+        const uint32_t i = tile0 + r * SORT_THREADS + threadIdx.x;
+        const bool valid = i < n;
+        uint32_t k = 0, v = 0, d = radix;  // invalid items use a digit no one shares
+        if (valid) {
+            k = keys[i];
+            v = vals[i];
+            d = (k >> shift) & (radix - 1);
+        }
+        const uint32_t peers = __match_any_sync(ODP_FULL_MASK, d);
+        const uint32_t rank_w = __popc(peers & lt_mask);
+        const int leader = __ffs(peers) - 1;
+        if (valid && lane == leader) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = base_d[d] + rank_w;
+            for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+            keys_out[pos] = k;
+            vals_out[pos] = v;
+        }
+        __syncthreads();
+        for (uint32_t dd = threadIdx.x; dd < radix; dd += SORT_THREADS) {
+            uint32_t s = 0;
+            for (int w = 0; w < W; ++w) {
+                s += wcnt[w][dd];
+                wcnt[w][dd] = 0;
+            }
+            base_d[dd] += s;
+        }
+        __syncthreads();
+    }
+}
+
+inline int bit_length(uint64_t v) {
+    int b = 0;
+    while (v) {
+        ++b;
+        v >>= 1;
+    }
+    return b;
+}
+
+struct SortTmp {
+    uint32_t* keys_alt;
+    uint32_t* vals_alt;
+    uint32_t* hist;      // 256 * ntiles_max
+    uint32_t* scan_tmp;  // scan_tmp_words(256 * ntiles_max)
+};
+
+inline size_t sort_hist_words(uint32_t n_max) {
+    return 256ull * ((n_max + SORT_TILE - 1) / SORT_TILE + 1);
+}
+
+// Stable sort of (keys, vals) by the low `key_bits` bits of the keys; the
+// result ends in (keys, vals) (ping-pong through the alternates).
+inline void radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, uint32_t n_max,
+                       int key_bits, const SortTmp& t, cudaStream_t s) {
+    if (n_max == 0 || key_bits <= 0) return;
+    const uint32_t ntiles = (n_max + SORT_TILE - 1) / SORT_TILE;
+    const int passes = (key_bits + 7) / 8;
+    // an even number of passes leaves the data in place
+    const int npass = passes + (passes & 1);
+    const int per = (key_bits + npass - 1) / npass;
+    uint32_t *k_in = keys, *v_in = vals, *k_out = t.keys_alt, *v_out = t.vals_alt;
+    int shift = 0;
+    for (int p = 0; p < npass; ++p) {
+        const int bits = std::max(1, std::min(per, key_bits - shift));
+        const uint32_t hn = (1u << bits) * ntiles;
+        sort_upsweep<<<ntiles, SORT_THREADS, 0, s>>>(k_in, n_dev, n_max, shift, bits, t.hist, ntiles);
+        exclusive_scan(t.hist, t.hist, nullptr, hn, nullptr, t.scan_tmp, s);
+        sort_downsweep<<<ntiles, SORT_THREADS, 0, s>>>(k_in, v_in, k_out, v_out, n_dev, n_max, shift,
+                                                       bits, t.hist, ntiles);
+        shift += bits;
+        std::swap(k_in, k_out);
+        std::swap(v_in, v_out);
+    }
+}
+
+// ---------------------------------------------------------------- table
+
+struct __align__(16) Key128 {
+    uint64_t lo, hi;
+};
+
+__device__ __forceinline__ bool key_eq(Key128 a, Key128 b) { return a.lo == b.lo && a.hi == b.hi; }
+
+constexpr uint64_t EMPTY_KEY = ~0ull;
+
+struct Table {
+    Key128* keys;       // capacity + 1 slots (the last one holds the all-ones key)
+    uint32_t* vals;
+    uint32_t cap_max;   // power of two
+    uint32_t* cap_dev;  // capacity in use (power of two, set on the device)
+};
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 33;
+    x *= 0xFF51AFD7ED558CCDull;
+    x ^= x >> 33;
+    x *= 0xC4CEB9FE1A85EC53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+// Set the capacity in use to the smallest power of two >= 2 * count (at
+// least 1024, at most cap_max) and clear it.
+__global__ void table_clear(Table t, const uint32_t* count_dev, uint32_t count_max) {
+    const uint32_t cnt = dev_len(count_dev, count_max);
+    uint32_t cap = 1024;
+    while (cap < 2ull * cnt && cap < t.cap_max) cap <<= 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t.cap_dev = cap;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= cap; i += stride) {
+        uint32_t slot = i == cap ? t.cap_max : i;
+        t.keys[slot].lo = EMPTY_KEY;
+        t.keys[slot].hi = EMPTY_KEY;
+        t.vals[slot] = NONE32;
+    }
+}
+
+// Inserts `k` and lowers the slot's value to v; returns the slot index, or
+// NONE32 if the probe sequence exhausted the table (cannot happen at <= 50%
+// load).
+__device__ __forceinline__ uint32_t table_insert_min(const Table& t, uint32_t cap, Key128 k,
+                                                     uint32_t v) {
+    if (k.lo == EMPTY_KEY && k.hi == EMPTY_KEY) {
+        atomicMin(&t.vals[t.cap_max], v);
+        return t.cap_max;
+    }
+    const uint32_t mask = cap - 1;
+    uint32_t slot = (uint32_t)mix64(k.lo ^ mix64(k.hi)) & mask;
+    const Key128 empty{EMPTY_KEY, EMPTY_KEY};
+    for (uint32_t probe = 0; probe < cap; ++probe) {
+        Key128 cur = t.keys[slot];
+        if (key_eq(cur, empty)) cur = atomicCAS(&t.keys[slot], empty, k);
+        if (key_eq(cur, empty) || key_eq(cur, k)) {
+            atomicMin(&t.vals[slot], v);
+            return slot;
+        }
+        slot = (slot + 1) & mask;
+    }
+    return NONE32;
+}
+
+}  // namespace prim
+}  // namespace odp

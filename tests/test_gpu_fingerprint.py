@@ -1,0 +1,133 @@
+"""GPU parity of odp_fingerprint against the oracle's FP128 (bit-exact).
+
+Calls go through the C ABI (ctypes binding); inputs are seeded synthetic
+contents materialised on the device by the fill kernels and, for the oracle,
+copied back or regenerated on the host.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from synth import content
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def odp():
+    import paper_2601_12713_b300 as odp
+
+    return odp
+
+
+def dev_buffer(nbytes, variant=content.RANDOM, seed=1, pad=64):
+    from synth import gpu
+
+    t = torch.zeros(nbytes + pad, dtype=torch.uint8, device="cuda")
+    if nbytes:
+        gpu.fill(t, variant, seed, nbytes=nbytes)
+    return t
+
+
+def gpu_fp(odp, views):
+    out = odp.fingerprint_tensors(views)
+    torch.cuda.synchronize()
+    return [tuple(int(v) & ((1 << 64) - 1) for v in row) for row in out.cpu().tolist()]
+
+
+SIZES = [1, 2, 15, 16, 17, 31, 100, 511, 512, 4095, 4096, 4097, 8191, 8192, 12293,
+         32 * 4096 - 1, 32 * 4096, 32 * 4096 + 1, 33 * 4096 + 17, (1 << 20) + 3, 5 << 20]
+
+
+@pytest.mark.parametrize("size", SIZES)
+@pytest.mark.parametrize("variant", [content.RANDOM, content.ZERO, content.PAGE])
+def test_single_buffer_matches_oracle(cuda_ok, orc, odp, size, variant):
+    t = dev_buffer(size, variant, seed=size)
+    host = t[:size].cpu().numpy()
+    assert np.array_equal(host, content.bytes_of(variant, size, size))
+    assert gpu_fp(odp, [t[:size]]) == [orc.fp128(host)]
+
+
+@pytest.mark.parametrize("off", list(range(1, 16)))
+def test_misaligned_views(cuda_ok, orc, odp, off):
+    size = 3 * 4096 + 77
+    t = dev_buffer(size + 32, seed=99 + off)
+    v = t[off:off + size]
+    assert gpu_fp(odp, [v]) == [orc.fp128(v.cpu().numpy())]
+
+
+def test_empty_and_zero_sized(cuda_ok, orc, odp):
+    t = dev_buffer(100)
+    assert gpu_fp(odp, [t[:0]]) == [orc.fp128(b"")]
+    # n == 0 is a no-op
+    z = torch.empty(0, dtype=torch.int64, device="cuda")
+    odp.fingerprint(z, z, torch.empty((0, 2), dtype=torch.int64, device="cuda"))
+
+
+def test_ragged_batch_mixed_alignment(cuda_ok, orc, odp):
+    rng = np.random.default_rng(5)
+    n = 3000
+    sizes = np.concatenate([rng.integers(0, 300, n // 3), rng.integers(1, 70_000, n // 3),
+                            rng.integers(4000, 4200, n - 2 * (n // 3))])
+    rng.shuffle(sizes)
+    offs = np.zeros(n, dtype=np.int64)
+    cur = 0
+    for i in range(n):
+        cur += int(rng.integers(0, 16))       # arbitrary byte alignment
+        offs[i] = cur
+        cur += int(sizes[i])
+    arena = dev_buffer(cur + 64, seed=7)
+    host = arena.cpu().numpy()
+    views = [arena[o:o + s] for o, s in zip(offs, sizes)]
+    got = gpu_fp(odp, views)
+    want = orc.fp128_many(host, offs, sizes)
+    assert got == [(int(a), int(b)) for a, b in want]
+
+
+def test_duplicates_and_aliases(cuda_ok, orc, odp):
+    t = dev_buffer(200_000, seed=3)
+    views = [t[:100_000], t[:100_000], t[5:100_005], t[:0], t[:100_000]]
+    got = gpu_fp(odp, views)
+    assert got[0] == got[1] == got[4]
+    assert got[2] != got[0]
+    assert got == [orc.fp128(v.cpu().numpy()) for v in views]
+
+
+def test_large_batch_multiblock_plan(cuda_ok, orc, odp):
+    # more buffers than the single-block plan handles
+    rng = np.random.default_rng(8)
+    n = 20_000
+    sizes = rng.integers(0, 9000, n)
+    offs = np.concatenate([[0], np.cumsum((sizes + 15) // 16 * 16)[:-1]])
+    arena = dev_buffer(int(offs[-1] + sizes[-1]) + 64, seed=11)
+    host = arena.cpu().numpy()
+    ptrs = torch.tensor(arena.data_ptr() + offs, dtype=torch.int64, device="cuda")
+    sz = torch.tensor(sizes, dtype=torch.int64, device="cuda")
+    out = torch.empty((n, 2), dtype=torch.int64, device="cuda")
+    odp.fingerprint(ptrs, sz, out)
+    got = out.cpu().numpy().view(np.uint64)
+    want = orc.fp128_many(host, offs, sizes)
+    assert np.array_equal(got, want)
+
+
+def test_null_pointer_reports_status(cuda_ok, odp):
+    ptrs = torch.zeros(2, dtype=torch.int64, device="cuda")
+    sizes = torch.tensor([0, 10], dtype=torch.int64, device="cuda")
+    out = torch.full((2, 2), 7, dtype=torch.int64, device="cuda")
+    odp.fingerprint(ptrs, sizes, out)
+    assert odp.fingerprint_status() == -1
+    assert out[1].tolist() == [0, 0]
+    assert odp.fingerprint_status() == 0
+
+
+def test_full_size_4gib_buffer(cuda_ok, orc, odp):
+    """The bandwidth sweep's largest buffer (4 GiB, random bytes) in the launch
+    configuration the benchmark times, checked against the oracle."""
+    size = 4 << 30
+    t = dev_buffer(size, seed=0x0DB2, pad=0)
+    got = gpu_fp(odp, [t])
+    host = t.cpu().numpy()
+    del t
+    torch.cuda.empty_cache()
+    assert got == [orc.fp128(host)]
