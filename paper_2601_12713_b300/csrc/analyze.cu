@@ -1,8 +1,1058 @@
-// analyze.cu -- odp_analyze (placeholder until the analysis kernels land).
+// analyze.cu -- odp_analyze: Algorithms 1-5 of the paper (Sec. 5) as
+// data-parallel GPU passes over the event log.
+//
+//   validate   record checks, order check, class of every event, lists of
+//              transfers (X), alloc/deletes (P), kernels (K), to-device (U)
+//   Alg. 1     table <fingerprint> -> content id (minimum event index), table
+//              <content id, destination> -> first receiver; every later
+//              transfer of a group is a duplicate of the first
+//   Alg. 2     stable sort of X by content id; with two endpoints in a
+//              content group the literal queue walk reduces to "the first
+//              later reception at the transfer's source", i.e. the start of
+//              the next run of equal destinations; other groups are walked
+//              literally, one thread per group
+//   pairs      table <device, device address> -> key id; stable sort of P;
+//              alternating groups pair each ALLOC with the next DELETE, other
+//              groups replay the nearest-open-ALLOC rule with a stack
+//   Alg. 3     table <host address, device, bytes> -> first pair's alloc
+//   kernels    stable sort of K by device; running maximum of kernel ends
+//   Alg. 4     binary search of the first kernel whose running-max end
+//              reaches the allocation's start (the literal monotone pointer)
+//   Alg. 5     same search per to-device transfer; transfers after the last
+//              kernel, barriers (overlapping the kernel) and candidates;
+//              candidate groups <segment, host address> sorted by group id,
+//              each member overwritten by the next one
+//   emit       per-kind ballot compaction in event order, wasted bytes/ns,
+//              per-site rows, union of wasted events, summary
+#include <algorithm>
+
 #include "common.cuh"
+#include "prims.cuh"
+
+namespace odp {
+namespace {
+
+using prim::Key128;
+using prim::NONE32;
+using prim::Table;
+
+constexpr uint32_t NOPART = 0xFFFFFFFEu;  // flagged without a partner
+constexpr unsigned long long NO_ERR = ~0ull;
+constexpr int NDEV = 129;                  // host + devices 0..127
+constexpr int TPB = 256;
+constexpr uint32_t VB = 1024;              // events per validate/emit block
+
+struct Hdr {
+    unsigned long long err;
+    unsigned long long t_end_max;
+    unsigned long long saved_ns;
+    unsigned long long unmatched;
+    unsigned long long n_allocs, n_deletes, n_pairs, n_unpaired;
+    unsigned long long count[6], bytes[6], ns[6];
+    uint32_t nX, nP, nK, nU;
+    uint32_t nseg, nrun, nseg2, nsegU;
+    uint32_t total_findings, n_site_rows;
+    uint32_t tcap;
+};
+
+// Event field access (64-byte records).
+struct Ev {
+    const uint8_t* p;
+    __device__ __forceinline__ uint64_t u64(uint32_t i, int off) const {
+        return *(const uint64_t*)(p + 64ull * i + off);
+    }
+    __device__ __forceinline__ uint64_t t0(uint32_t i) const { return u64(i, 0); }
+    __device__ __forceinline__ uint64_t t1(uint32_t i) const { return u64(i, 8); }
+    __device__ __forceinline__ uint64_t host(uint32_t i) const { return u64(i, 16); }
+    __device__ __forceinline__ uint64_t daddr(uint32_t i) const { return u64(i, 24); }
+    __device__ __forceinline__ uint64_t bytes(uint32_t i) const { return u64(i, 32); }
+    __device__ __forceinline__ uint64_t fplo(uint32_t i) const { return u64(i, 40); }
+    __device__ __forceinline__ uint64_t fphi(uint32_t i) const { return u64(i, 48); }
+    __device__ __forceinline__ uint32_t site(uint32_t i) const {
+        return *(const uint32_t*)(p + 64ull * i + 56);
+    }
+};
+
+// cls word: kind | (src + 1) << 8 | (dst + 1) << 16
+__device__ __forceinline__ uint32_t c_kind(uint32_t c) { return c & 0xFF; }
+__device__ __forceinline__ uint32_t c_src(uint32_t c) { return (c >> 8) & 0xFF; }
+__device__ __forceinline__ uint32_t c_dst(uint32_t c) { return (c >> 16) & 0xFF; }
+
+struct A {
+    Ev ev;
+    uint32_t n;
+    uint32_t nb;          // validate/emit blocks
+    Hdr* h;
+    uint32_t* cls;
+    uint32_t* bcnt;       // 5 * nb
+    uint32_t *X, *P, *K, *U;
+    uint32_t *dd, *rt, *ra, *ua, *ut, *del_of;
+    uint8_t* wasted;
+    uint8_t* bad;
+    uint32_t *slot, *sk, *sv, *k2, *v2, *f1, *f2, *id1, *id2, *H, *R, *stk;
+    uint32_t *pq;
+    uint8_t* uc;
+    uint64_t *ks, *ke;    // kernels sorted by device: start, running max of end
+    uint32_t *dstart, *dend;  // kernel ranges per device, indexed by device number + 1
+    unsigned long long* sites;  // [5][65536][3]
+    Table tab;
+    odp_findings out;
+};
+
+__device__ __forceinline__ bool failed(const A& a) { return a.h->err != NO_ERR; }
+
+#define GRID_STRIDE(i, n) \
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------ validate
+
+__device__ __forceinline__ bool record_ok(const Ev& ev, uint32_t i, uint32_t& cls) {
+    const uint64_t t0 = ev.t0(i), t1 = ev.t1(i), by = ev.bytes(i);
+    const uint32_t site = ev.site(i);
+    const uint32_t w = *(const uint32_t*)(ev.p + 64ull * i + 60);
+    const int kind = w & 0xFF;
+    const int src = (int8_t)((w >> 8) & 0xFF), dst = (int8_t)((w >> 16) & 0xFF);
+    cls = (uint32_t)kind | ((uint32_t)(src + 1) & 0xFF) << 8 | ((uint32_t)(dst + 1) & 0xFF) << 16;
+    if (t1 < t0 || site >= ODP_MAX_SITES || by >= ODP_MAX_BYTES) return false;
+    switch (kind) {
+        case ODP_TO_DEV: return by > 0 && src == -1 && dst >= 0;
+        case ODP_FROM_DEV: return by > 0 && src >= 0 && dst == -1;
+        case ODP_DEV_TO_DEV: return by > 0 && src >= 0 && dst >= 0 && src != dst;
+        case ODP_ALLOC:
+        case ODP_DELETE:
+        case ODP_KERNEL: return dst >= 0;
+        default: return false;
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_validate(A a) {
+    const uint32_t base = blockIdx.x * VB;
+    unsigned long long tmax = 0;
+    uint32_t nallocs = 0, ndels = 0;
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t i = base + k * TPB + threadIdx.x;
+        bool isX = false, isP = false, isK = false, isU = false;
+        if (i < a.n) {
+            uint32_t c;
+            bool ok = record_ok(a.ev, i, c);
+            if (!ok) {
+                record_error(&a.h->err, i, ODP_ERR_MALFORMED);
+                c = 0;
+            } else if (i > 0 && a.ev.t0(i) < a.ev.t0(i - 1)) {
+                record_error(&a.h->err, i, ODP_ERR_UNSORTED);
+            }
+            a.cls[i] = c;
+            const uint32_t kd = c_kind(c);
+            isX = kd == ODP_TO_DEV || kd == ODP_FROM_DEV || kd == ODP_DEV_TO_DEV;
+            isP = kd == ODP_ALLOC || kd == ODP_DELETE;
+            isK = kd == ODP_KERNEL;
+            isU = kd == ODP_TO_DEV;
+            nallocs += kd == ODP_ALLOC;
+            ndels += kd == ODP_DELETE;
+            tmax = max(tmax, (unsigned long long)a.ev.t1(i));
+        }
+        uint32_t cx = __syncthreads_count(isX), cp = __syncthreads_count(isP);
+        uint32_t ck = __syncthreads_count(isK), cu = __syncthreads_count(isU);
+        if (threadIdx.x == 0) {
+            if (k == 0) {
+                a.bcnt[0 * a.nb + blockIdx.x] = 0;
+                a.bcnt[1 * a.nb + blockIdx.x] = 0;
+                a.bcnt[2 * a.nb + blockIdx.x] = 0;
+                a.bcnt[3 * a.nb + blockIdx.x] = 0;
+            }
+            a.bcnt[0 * a.nb + blockIdx.x] += cx;
+            a.bcnt[1 * a.nb + blockIdx.x] += cp;
+            a.bcnt[2 * a.nb + blockIdx.x] += ck;
+            a.bcnt[3 * a.nb + blockIdx.x] += cu;
+        }
+    }
+    // block reductions of the max end time and alloc/delete counts
+    for (int d = 16; d > 0; d >>= 1) {
+        tmax = max(tmax, __shfl_xor_sync(ODP_FULL_MASK, tmax, d));
+        nallocs += __shfl_xor_sync(ODP_FULL_MASK, nallocs, d);
+        ndels += __shfl_xor_sync(ODP_FULL_MASK, ndels, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&a.h->t_end_max, tmax);
+        if (nallocs) atomicAdd(&a.h->n_allocs, (unsigned long long)nallocs);
+        if (ndels) atomicAdd(&a.h->n_deletes, (unsigned long long)ndels);
+    }
+}
+
+// list lengths from the scanned block counts (scan covers 4 * nb + 1)
+__global__ void k_list_lengths(A a, const uint32_t* scanned, const uint32_t* total) {
+    if (threadIdx.x != 0) return;
+    const uint32_t nb = a.nb;
+    a.h->nX = scanned[1 * nb] - scanned[0];
+    a.h->nP = scanned[2 * nb] - scanned[1 * nb];
+    a.h->nK = scanned[3 * nb] - scanned[2 * nb];
+    a.h->nU = *total - scanned[3 * nb];
+}
+
+// Stable compaction of event indices into the four lists.
+__global__ void __launch_bounds__(TPB) k_compact(A a, const uint32_t* scanned) {
+    __shared__ uint32_t wc[4][TPB / 32];
+    __shared__ uint32_t run[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t base = blockIdx.x * VB;
+    if (threadIdx.x < 4) run[threadIdx.x] = 0;
+    uint32_t* lists[4] = {a.X, a.P, a.K, a.U};
+    uint32_t list_base[4];
+    for (int L = 0; L < 4; ++L) list_base[L] = scanned[L * a.nb + blockIdx.x] - scanned[L * a.nb];
+    __syncthreads();
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t i = base + k * TPB + threadIdx.x;
+        uint32_t kd = i < a.n ? c_kind(a.cls[i]) : 0;
+        bool pred[4] = {kd == ODP_TO_DEV || kd == ODP_FROM_DEV || kd == ODP_DEV_TO_DEV,
+                        kd == ODP_ALLOC || kd == ODP_DELETE, kd == ODP_KERNEL, kd == ODP_TO_DEV};
+        uint32_t bal[4];
+        for (int L = 0; L < 4; ++L) {
+            bal[L] = __ballot_sync(ODP_FULL_MASK, pred[L]);
+            if (lane == 0) wc[L][warp] = __popc(bal[L]);
+        }
+        __syncthreads();
+        for (int L = 0; L < 4; ++L) {
+            if (pred[L]) {
+                uint32_t pos = run[L] + __popc(bal[L] & ((1u << lane) - 1));
+                for (int w = 0; w < warp; ++w) pos += wc[L][w];
+                lists[L][list_base[L] + pos] = i;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            uint32_t s = 0;
+            for (int w = 0; w < TPB / 32; ++w) s += wc[threadIdx.x][w];
+            run[threadIdx.x] += s;
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------- Alg. 1 (and ids)
+
+__global__ void k_x_insert_fp(A a) {
+    if (failed(a)) return;
+    const uint32_t cap = *a.tab.cap_dev;
+    GRID_STRIDE(j, a.h->nX) {
+        const uint32_t e = a.X[j];
+        Key128 key{a.ev.fplo(e), a.ev.fphi(e)};
+        a.slot[j] = prim::table_insert_min(a.tab, cap, key, e);
+    }
+}
+
+__global__ void k_x_cid(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(j, a.h->nX) {
+        const uint32_t s = a.slot[j];
+        a.sk[j] = s == NONE32 ? a.X[j] : a.tab.vals[s];
+        a.sv[j] = a.X[j];
+    }
+}
+
+__global__ void k_x_insert_dd(A a) {
+    if (failed(a)) return;
+    const uint32_t cap = *a.tab.cap_dev;
+    GRID_STRIDE(j, a.h->nX) {
+        const uint32_t e = a.sv[j];
+        const uint64_t dst1 = c_dst(a.cls[e]);
+        Key128 key{(uint64_t)a.sk[j] | (dst1 << 32), 0};
+        a.slot[j] = prim::table_insert_min(a.tab, cap, key, e);
+    }
+}
+
+__global__ void k_x_dd(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(j, a.h->nX) {
+        const uint32_t e = a.sv[j];
+        const uint32_t s = a.slot[j];
+        const uint32_t first = s == NONE32 ? e : a.tab.vals[s];
+        if (first != e) a.dd[e] = first;
+    }
+}
+
+// ------------------------------------------------------------- Alg. 2
+
+__global__ void k_rt_flags(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(q, a.h->nX) {
+        const bool head = q == 0 || a.sk[q] != a.sk[q - 1];
+        const uint32_t dst = c_dst(a.cls[a.sv[q]]);
+        const bool run = head || dst != c_dst(a.cls[a.sv[q - 1]]);
+        a.f1[q] = head;
+        a.f2[q] = run;
+    }
+}
+
+__global__ void k_rt_starts(A a) {
+    if (failed(a)) return;
+    const uint32_t n = a.h->nX;
+    GRID_STRIDE(q, n) {
+        if (a.f1[q]) a.H[a.id1[q]] = q;
+        if (a.f2[q]) a.R[a.id2[q]] = q;
+        a.bad[q] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.H[a.h->nseg] = n;
+        a.R[a.h->nrun] = n;
+    }
+}
+
+__device__ __forceinline__ bool same_endpoints(uint32_t c, uint32_t d) {
+    const uint32_t s1 = c_src(c), d1 = c_dst(c), s2 = c_src(d), d2 = c_dst(d);
+    return (s1 == s2 && d1 == d2) || (s1 == d2 && d1 == s2);
+}
+
+__global__ void k_rt_check(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(q, a.h->nX) {
+        const uint32_t s = a.id1[q] + a.f1[q] - 1;
+        const uint32_t h = a.H[s];
+        if (!same_endpoints(a.cls[a.sv[q]], a.cls[a.sv[h]])) a.bad[s] = 1;
+    }
+}
+
+// Two endpoints: a transfer pairs with the first event of the next run of
+// its content group (the next run receives at the other endpoint, which is
+// the transfer's source).
+__global__ void k_rt_partner(A a) {
+    if (failed(a)) return;
+    const uint32_t nrun = a.h->nrun;
+    GRID_STRIDE(q, a.h->nX) {
+        const uint32_t s = a.id1[q] + a.f1[q] - 1;
+        if (a.bad[s]) continue;
+        const uint32_t r = a.id2[q] + a.f2[q] - 1;
+        if (r + 1 < nrun) {
+            const uint32_t q2 = a.R[r + 1];
+            if (!a.f1[q2]) a.rt[a.sv[q]] = a.sv[q2];
+        }
+    }
+}
+
+// Groups with more than two endpoints: the queue walk of Alg. 2 verbatim,
+// one thread per group.  received[<h, d>] is the group's events with
+// destination d in order; front[d] is the position of its current front.
+__global__ void k_rt_literal(A a) {
+    if (failed(a)) return;
+    const uint32_t nseg = a.h->nseg;
+    GRID_STRIDE(s, nseg) {
+        if (!a.bad[s]) continue;
+        const uint32_t lo = a.H[s], hi = a.H[s + 1];
+        uint32_t cnt[NDEV], pops[NDEV], front[NDEV];
+        for (int d = 0; d < NDEV; ++d) {
+            cnt[d] = 0;
+            pops[d] = 0;
+            front[d] = NONE32;
+        }
+        for (uint32_t q = lo; q < hi; ++q) cnt[c_dst(a.cls[a.sv[q]])]++;
+        for (uint32_t q = lo; q < hi; ++q) {
+            const uint32_t e = a.sv[q];
+            const uint32_t c = a.cls[e];
+            const uint32_t A_ = c_src(c), B_ = c_dst(c);
+            if (pops[A_] >= cnt[A_]) continue;  // queue of the source is empty
+            if (front[A_] == NONE32) {
+                uint32_t f = lo;
+                while (f < hi && c_dst(a.cls[a.sv[f]]) != A_) ++f;
+                front[A_] = f;
+            }
+            if (front[A_] >= hi) continue;  // unreachable: cnt[A_] > pops[A_]
+            a.rt[e] = a.sv[front[A_]];
+            // dequeue received[<h, dest>]
+            if (front[B_] == NONE32) {
+                uint32_t f = lo;
+                while (f < hi && c_dst(a.cls[a.sv[f]]) != B_) ++f;
+                front[B_] = f;
+            }
+            pops[B_]++;
+            if (pops[B_] < cnt[B_]) {
+                uint32_t f = front[B_] + 1;
+                while (f < hi && c_dst(a.cls[a.sv[f]]) != B_) ++f;
+                front[B_] = f;
+            } else {
+                front[B_] = hi;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- pairs
+
+__global__ void k_p_insert(A a) {
+    if (failed(a)) return;
+    const uint32_t cap = *a.tab.cap_dev;
+    GRID_STRIDE(j, a.h->nP) {
+        const uint32_t e = a.P[j];
+        Key128 key{a.ev.daddr(e), (uint64_t)c_dst(a.cls[e])};
+        a.slot[j] = prim::table_insert_min(a.tab, cap, key, e);
+    }
+}
+
+__global__ void k_p_keys(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(j, a.h->nP) {
+        const uint32_t s = a.slot[j];
+        a.sk[j] = s == NONE32 ? a.P[j] : a.tab.vals[s];
+        a.sv[j] = a.P[j];
+    }
+}
+
+__global__ void k_seg_heads(A a, const uint32_t* count) {
+    if (failed(a)) return;
+    GRID_STRIDE(q, *count) a.f1[q] = q == 0 || a.sk[q] != a.sk[q - 1];
+}
+
+__global__ void k_seg_starts(A a, const uint32_t* count, const uint32_t* nseg) {
+    if (failed(a)) return;
+    const uint32_t n = *count;
+    GRID_STRIDE(q, n) {
+        if (a.f1[q]) a.H[a.id1[q]] = q;
+        a.bad[q] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.H[*nseg] = n;
+}
+
+__device__ __forceinline__ bool is_alloc(const A& a, uint32_t e) {
+    return c_kind(a.cls[e]) == ODP_ALLOC;
+}
+
+__global__ void k_p_check(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(q, a.h->nP) {
+        const uint32_t s = a.id1[q] + a.f1[q] - 1;
+        const uint32_t lo = a.H[s], hi = a.H[s + 1];
+        const bool al = is_alloc(a, a.sv[q]);
+        bool bad;
+        if (!al) bad = q == lo || !is_alloc(a, a.sv[q - 1]);
+        else bad = q + 1 < hi && is_alloc(a, a.sv[q + 1]);
+        if (bad) a.bad[s] = 1;
+    }
+}
+
+__global__ void k_p_match(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(q, a.h->nP) {
+        const uint32_t s = a.id1[q] + a.f1[q] - 1;
+        if (a.bad[s]) continue;
+        const uint32_t hi = a.H[s + 1];
+        const uint32_t e = a.sv[q];
+        if (is_alloc(a, e) && q + 1 < hi) a.del_of[e] = a.sv[q + 1];
+    }
+}
+
+// Non-alternating groups: a DELETE closes the nearest earlier open ALLOC.
+__global__ void k_p_literal(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(s, a.h->nseg2) {
+        if (!a.bad[s]) continue;
+        const uint32_t lo = a.H[s], hi = a.H[s + 1];
+        uint32_t depth = 0;
+        unsigned long long unmatched = 0;
+        for (uint32_t q = lo; q < hi; ++q) {
+            const uint32_t e = a.sv[q];
+            if (is_alloc(a, e)) {
+                a.stk[lo + depth++] = e;
+            } else if (depth > 0) {
+                a.del_of[a.stk[lo + --depth]] = e;
+            } else {
+                ++unmatched;
+            }
+        }
+        if (unmatched) atomicAdd(&a.h->unmatched, unmatched);
+    }
+}
+
+// ------------------------------------------------------------- Alg. 3
+
+__global__ void k_ra_insert(A a) {
+    if (failed(a)) return;
+    const uint32_t cap = *a.tab.cap_dev;
+    GRID_STRIDE(j, a.h->nP) {
+        const uint32_t e = a.P[j];
+        uint32_t s = NONE32;
+        if (is_alloc(a, e) && a.del_of[e] != NONE32) {
+            Key128 key{a.ev.host(e), a.ev.bytes(e) | ((uint64_t)c_dst(a.cls[e]) << 56)};
+            s = prim::table_insert_min(a.tab, cap, key, e);
+        }
+        a.slot[j] = s;
+    }
+}
+
+__global__ void k_ra_flag(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(j, a.h->nP) {
+        const uint32_t s = a.slot[j];
+        if (s == NONE32) continue;
+        const uint32_t e = a.P[j];
+        const uint32_t first = a.tab.vals[s];
+        if (first != e) a.ra[e] = first;
+    }
+}
+
+// ------------------------------------------------------------ kernels
+
+__global__ void k_dev_keys(A a, const uint32_t* list, const uint32_t* count) {
+    if (failed(a)) return;
+    GRID_STRIDE(j, *count) {
+        const uint32_t e = list[j];
+        a.sk[j] = c_dst(a.cls[e]);
+        a.sv[j] = e;
+    }
+}
+
+__global__ void k_k_bounds(A a) {
+    if (failed(a)) return;
+    const uint32_t n = a.h->nK;
+    GRID_STRIDE(q, n) {
+        const uint32_t d = a.sk[q];
+        if (q == 0 || a.sk[q - 1] != d) a.dstart[d] = q;
+        if (q + 1 == n || a.sk[q + 1] != d) a.dend[d] = q + 1;
+        a.ks[q] = a.ev.t0(a.sv[q]);
+        a.ke[q] = a.ev.t1(a.sv[q]);
+    }
+}
+
+// Running maximum of kernel ends within each device (sequential per device;
+// kernel events are few next to data operations).
+__global__ void k_k_pmax(A a) {
+    if (failed(a)) return;
+    for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < NDEV; d += gridDim.x * blockDim.x) {
+        uint64_t m = 0;
+        for (uint32_t q = a.dstart[d]; q < a.dend[d]; ++q) {
+            m = max(m, a.ke[q]);
+            a.ke[q] = m;
+        }
+    }
+}
+
+// First kernel position p in [dstart, dend) of device d with running-max
+// end >= t (dend if none): the monotone pointer of Alg. 4 and 5.
+__device__ __forceinline__ uint32_t first_kernel(const A& a, uint32_t d, uint64_t t) {
+    uint32_t lo = a.dstart[d], hi = a.dend[d];
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (a.ke[mid] >= t) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------- Alg. 4
+
+__global__ void k_ua(A a) {
+    if (failed(a)) return;
+    const uint64_t trace_end = a.h->t_end_max;
+    GRID_STRIDE(j, a.h->nP) {
+        const uint32_t e = a.P[j];
+        if (!is_alloc(a, e)) continue;
+        const uint32_t d = c_dst(a.cls[e]);  // device number + 1
+        const uint32_t del = a.del_of[e];
+        const uint64_t end = del != NONE32 ? a.ev.t1(del) : trace_end;
+        const uint32_t p = first_kernel(a, d, a.ev.t0(e));
+        if (p == a.dend[d] || a.ks[p] > end) a.ua[e] = del != NONE32 ? del : NOPART;
+    }
+}
+
+// ------------------------------------------------------------- Alg. 5
+
+__global__ void k_ut_class(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(q, a.h->nU) {
+        const uint32_t e = a.sv[q];
+        const uint32_t d = a.sk[q];  // device number + 1
+        const uint64_t t = a.ev.t0(e);
+        const uint32_t p = first_kernel(a, d, t);
+        uint8_t c;
+        if (p == a.dend[d]) {
+            c = 2;                       // after the last kernel
+            a.ut[e] = NOPART;
+        } else if (a.ks[p] <= t) {
+            c = 1;                       // overlaps kernel p: clears candidates
+        } else {
+            c = 0;                       // candidate
+        }
+        a.pq[q] = p;
+        a.uc[q] = c;
+    }
+}
+
+__global__ void k_ut_heads(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(q, a.h->nU) {
+        a.f1[q] = q == 0 || a.sk[q] != a.sk[q - 1] || a.pq[q] != a.pq[q - 1] || a.uc[q - 1] == 1;
+    }
+}
+
+__global__ void k_ut_insert(A a) {
+    if (failed(a)) return;
+    const uint32_t cap = *a.tab.cap_dev;
+    GRID_STRIDE(q, a.h->nU) {
+        uint32_t s = NONE32;
+        if (a.uc[q] == 0) {
+            const uint32_t seg = a.id1[q] + a.f1[q] - 1;
+            Key128 key{a.ev.host(a.sv[q]), (uint64_t)seg};
+            s = prim::table_insert_min(a.tab, cap, key, q);
+        }
+        a.slot[q] = s;
+    }
+}
+
+__global__ void k_ut_gid(A a) {
+    if (failed(a)) return;
+    const uint32_t nU = a.h->nU;
+    GRID_STRIDE(q, nU) {
+        const uint32_t s = a.slot[q];
+        a.k2[q] = s == NONE32 ? nU : a.tab.vals[s];
+        a.v2[q] = q;
+    }
+}
+
+__global__ void k_ut_next(A a) {
+    if (failed(a)) return;
+    const uint32_t nU = a.h->nU;
+    GRID_STRIDE(r, nU) {
+        if (a.k2[r] < nU && r + 1 < nU && a.k2[r + 1] == a.k2[r]) a.ut[a.sv[a.v2[r]]] = a.sv[a.v2[r + 1]];
+    }
+}
+
+// ------------------------------------------------------------ emission
+
+struct Fnd {
+    uint32_t partner;  // NONE32: not flagged
+    uint64_t bytes, ns;
+};
+
+__device__ __forceinline__ uint64_t dur(const A& a, uint32_t i) { return a.ev.t1(i) - a.ev.t0(i); }
+
+__device__ __forceinline__ Fnd finding_of(const A& a, int kind, uint32_t i) {
+    Fnd f{NONE32, 0, 0};
+    uint32_t p;
+    switch (kind) {
+        case ODP_DD:
+            p = a.dd[i];
+            if (p != NONE32) f = Fnd{p, a.ev.bytes(i), dur(a, i)};
+            break;
+        case ODP_RT:
+            p = a.rt[i];
+            if (p != NONE32) f = Fnd{p, a.ev.bytes(p), dur(a, p)};
+            break;
+        case ODP_RA:
+            p = a.ra[i];
+            if (p != NONE32) f = Fnd{p, a.ev.bytes(i), dur(a, i) + dur(a, a.del_of[i])};
+            break;
+        case ODP_UA:
+            p = a.ua[i];
+            if (p != NONE32) f = Fnd{p, a.ev.bytes(i), dur(a, i) + (p == NOPART ? 0 : dur(a, p))};
+            break;
+        case ODP_UT:
+            p = a.ut[i];
+            if (p != NONE32) f = Fnd{p, a.ev.bytes(i), dur(a, i)};
+            break;
+    }
+    return f;
+}
+
+// Counts per (kind, block); per-kind totals; site rows; wasted-event marks;
+// pair counts.
+__global__ void __launch_bounds__(TPB) k_em_count(A a) {
+    if (failed(a)) return;
+    const uint32_t base = blockIdx.x * VB;
+    unsigned long long cnt[5] = {0, 0, 0, 0, 0}, by[5] = {0, 0, 0, 0, 0}, ns[5] = {0, 0, 0, 0, 0};
+    unsigned long long pairs = 0, unpaired = 0;
+    uint32_t bc[5] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t i = base + k * TPB + threadIdx.x;
+        bool fl[5] = {false, false, false, false, false};
+        if (i < a.n) {
+            if (is_alloc(a, i)) {
+                if (a.del_of[i] != NONE32) ++pairs; else ++unpaired;
+            }
+            const uint32_t site = a.ev.site(i);
+            for (int kind = 1; kind <= 5; ++kind) {
+                Fnd f = finding_of(a, kind, i);
+                if (f.partner == NONE32) continue;
+                fl[kind - 1] = true;
+                cnt[kind - 1]++;
+                by[kind - 1] += f.bytes;
+                ns[kind - 1] += f.ns;
+                unsigned long long* row = a.sites + 3ull * ((uint64_t)(kind - 1) * ODP_MAX_SITES + site);
+                atomicAdd(row + 0, 1ull);
+                atomicAdd(row + 1, (unsigned long long)f.bytes);
+                atomicAdd(row + 2, (unsigned long long)f.ns);
+                switch (kind) {
+                    case ODP_DD:
+                    case ODP_UT: a.wasted[i] = 1; break;
+                    case ODP_RT: a.wasted[f.partner] = 1; break;
+                    case ODP_RA: a.wasted[i] = 1; a.wasted[a.del_of[i]] = 1; break;
+                    case ODP_UA:
+                        a.wasted[i] = 1;
+                        if (f.partner != NOPART) a.wasted[f.partner] = 1;
+                        break;
+                }
+            }
+        }
+        for (int kind = 0; kind < 5; ++kind) bc[kind] += __syncthreads_count(fl[kind]);
+    }
+    if (threadIdx.x == 0)
+        for (int kind = 0; kind < 5; ++kind) a.bcnt[kind * a.nb + blockIdx.x] = bc[kind];
+    for (int d = 16; d > 0; d >>= 1) {
+        for (int kind = 0; kind < 5; ++kind) {
+            cnt[kind] += __shfl_xor_sync(ODP_FULL_MASK, cnt[kind], d);
+            by[kind] += __shfl_xor_sync(ODP_FULL_MASK, by[kind], d);
+            ns[kind] += __shfl_xor_sync(ODP_FULL_MASK, ns[kind], d);
+        }
+        pairs += __shfl_xor_sync(ODP_FULL_MASK, pairs, d);
+        unpaired += __shfl_xor_sync(ODP_FULL_MASK, unpaired, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int kind = 0; kind < 5; ++kind) {
+            if (cnt[kind]) {
+                atomicAdd(&a.h->count[kind + 1], cnt[kind]);
+                atomicAdd(&a.h->bytes[kind + 1], by[kind]);
+                atomicAdd(&a.h->ns[kind + 1], ns[kind]);
+            }
+        }
+        if (pairs) atomicAdd(&a.h->n_pairs, pairs);
+        if (unpaired) atomicAdd(&a.h->n_unpaired, unpaired);
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_em_write(A a, const uint32_t* scanned) {
+    if (failed(a)) return;
+    __shared__ uint32_t wc[TPB / 32];
+    __shared__ uint32_t run;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t base = blockIdx.x * VB;
+    odp_finding* items = a.out.items;
+    const uint64_t cap = a.out.capacity;
+    for (int kind = 1; kind <= 5; ++kind) {
+        if (threadIdx.x == 0) run = 0;
+        __syncthreads();
+        const uint32_t off = scanned[(kind - 1) * a.nb + blockIdx.x];
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t i = base + k * TPB + threadIdx.x;
+            Fnd f{NONE32, 0, 0};
+            if (i < a.n) f = finding_of(a, kind, i);
+            const bool fl = f.partner != NONE32;
+            const uint32_t bal = __ballot_sync(ODP_FULL_MASK, fl);
+            if (lane == 0) wc[warp] = __popc(bal);
+            __syncthreads();
+            if (fl) {
+                uint64_t pos = (uint64_t)off + run + __popc(bal & ((1u << lane) - 1));
+                for (int w = 0; w < warp; ++w) pos += wc[w];
+                if (pos < cap) {
+                    odp_finding o;
+                    o.kind = (uint8_t)kind;
+                    o.pad0[0] = o.pad0[1] = o.pad0[2] = 0;
+                    o.site = a.ev.site(i);
+                    const bool np = f.partner == NOPART;
+                    o.partner_site = np ? 0xFFFFFFFFu : a.ev.site(f.partner);
+                    o.pad1 = 0;
+                    o.event = i;
+                    o.partner = np ? ODP_NO_EVENT : (uint64_t)f.partner;
+                    o.wasted_bytes = f.bytes;
+                    o.wasted_ns = f.ns;
+                    items[pos] = o;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t s = 0;
+                for (int w = 0; w < TPB / 32; ++w) s += wc[w];
+                run += s;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_em_saved(A a) {
+    if (failed(a)) return;
+    unsigned long long s = 0;
+    GRID_STRIDE(i, a.n) if (a.wasted[i]) s += dur(a, i);
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(ODP_FULL_MASK, s, d);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(&a.h->saved_ns, s);
+}
+
+// site rows: flags over the dense [kind][site] table, then compaction
+__global__ void k_site_flags(A a, uint32_t* flags) {
+    GRID_STRIDE(r, 5u * ODP_MAX_SITES) flags[r] = failed(a) ? 0 : a.sites[3ull * r] != 0;
+}
+
+__global__ void k_site_write(A a, const uint32_t* flags, const uint32_t* pos) {
+    if (failed(a)) return;
+    GRID_STRIDE(r, 5u * ODP_MAX_SITES) {
+        if (!flags[r] || pos[r] >= a.out.sites_capacity) continue;
+        odp_site_row row;
+        row.site = r % ODP_MAX_SITES;
+        row.kind = (uint8_t)(r / ODP_MAX_SITES + 1);
+        row.pad[0] = row.pad[1] = row.pad[2] = 0;
+        row.count = a.sites[3ull * r];
+        row.wasted_bytes = a.sites[3ull * r + 1];
+        row.wasted_ns = a.sites[3ull * r + 2];
+        a.out.sites[pos[r]] = row;
+    }
+}
+
+__global__ void k_finalize(A a, const uint32_t* n_findings, const uint32_t* n_rows) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    odp_summary* S = a.out.summary;
+    const Hdr* h = a.h;
+    if (h->err != NO_ERR) {
+        uint64_t* z = (uint64_t*)S;
+        for (size_t k = 0; k < sizeof(odp_summary) / 8; ++k) z[k] = 0;
+        *a.out.count = 0;
+        *a.out.sites_count = 0;
+        *a.out.status = -(int32_t)(h->err & 0xFF);
+        return;
+    }
+    S->n_events = a.n;
+    S->n_transfers = h->nX;
+    S->n_allocs = h->n_allocs;
+    S->n_deletes = h->n_deletes;
+    S->n_kernels = h->nK;
+    S->n_pairs = h->n_pairs;
+    S->n_unpaired_allocs = h->n_unpaired;
+    S->n_unmatched_deletes = h->unmatched;
+    for (int k = 0; k < 6; ++k) {
+        S->count[k] = h->count[k];
+        S->wasted_bytes[k] = h->bytes[k];
+        S->wasted_ns[k] = h->ns[k];
+    }
+    const uint64_t begin = a.n ? a.ev.t0(0) : 0;
+    const uint64_t end = h->t_end_max;
+    S->trace_begin_ns = begin;
+    S->trace_end_ns = end;
+    S->trace_span_ns = end - begin;
+    S->saved_ns = h->saved_ns;
+    S->speedup_num = end - begin;
+    S->speedup_den = (end - begin) > h->saved_ns ? (end - begin) - h->saved_ns : 0;
+    const uint64_t total = *n_findings, rows = *n_rows;
+    *a.out.count = total;
+    *a.out.sites_count = rows;
+    *a.out.status = (total > a.out.capacity || rows > a.out.sites_capacity) ? ODP_WARN_TRUNCATED : ODP_OK;
+}
+
+__global__ void k_empty_outputs(odp_findings out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint64_t* z = (uint64_t*)out.summary;
+    for (size_t k = 0; k < sizeof(odp_summary) / 8; ++k) z[k] = 0;
+    *out.count = 0;
+    *out.sites_count = 0;
+    *out.status = ODP_OK;
+}
+
+}  // namespace
+
+static int grid_for(uint64_t n, int sms) {
+    uint64_t g = (n + TPB - 1) / TPB;
+    uint64_t cap = (uint64_t)sms * 16;
+    return (int)std::max<uint64_t>(1, std::min(g, cap));
+}
+
+static int an_run(const odp_event* events, uint64_t n64, const odp_findings* outp,
+                  cudaStream_t s) {
+    if (!outp) return ODP_ERR_INVALID_ARG;
+    const odp_findings out = *outp;
+    if (!out.count || !out.sites_count || !out.summary || !out.status) return ODP_ERR_INVALID_ARG;
+    if (out.capacity > 0 && !out.items) return ODP_ERR_INVALID_ARG;
+    if (out.sites_capacity > 0 && !out.sites) return ODP_ERR_INVALID_ARG;
+    if (n64 > 0 && !events) return ODP_ERR_INVALID_ARG;
+    if (n64 >= 0xFFFFFFF0ull) return ODP_ERR_UNSUPPORTED;
+    if (n64 == 0) {
+        k_empty_outputs<<<1, 1, 0, s>>>(out);
+        return cuda_status(cudaGetLastError());
+    }
+    const uint32_t n = (uint32_t)n64;
+    const uint32_t nb = (n + VB - 1) / VB;
+    const int sms = device_sm_count();
+    int st = ODP_OK;
+
+    uint32_t cap_max = 1024;
+    while (cap_max < 2ull * n) cap_max <<= 1;
+
+    // ---- scratch layout
+    size_t bytes = 0;
+    auto carve = [&](size_t sz) {
+        size_t o = bytes;
+        bytes = align_up(bytes + std::max<size_t>(sz, 16), 256);
+        return o;
+    };
+    const size_t N4 = 4ull * (n + 2);
+    const size_t o_h = carve(sizeof(Hdr));
+    const size_t o_cls = carve(N4);
+    const size_t o_bcnt = carve(4ull * (5 * nb + 2));
+    const size_t o_bscan = carve(4ull * (5 * nb + 2));
+    const size_t o_X = carve(N4), o_P = carve(N4), o_K = carve(N4), o_U = carve(N4);
+    const size_t o_part = carve(6 * N4);  // dd rt ra ua ut del_of
+    const size_t o_wasted = carve(n + 16);
+    const size_t o_bad = carve(n + 16);
+    const size_t o_slot = carve(N4), o_sk = carve(N4), o_sv = carve(N4), o_k2 = carve(N4),
+                 o_v2 = carve(N4), o_f1 = carve(N4), o_f2 = carve(N4), o_id1 = carve(N4),
+                 o_id2 = carve(N4), o_H = carve(N4), o_R = carve(N4), o_stk = carve(N4),
+                 o_pq = carve(N4);
+    const size_t o_uc = carve(n + 16);
+    const size_t o_ks = carve(8ull * (n + 2)), o_ke = carve(8ull * (n + 2));
+    const size_t o_dev = carve(2 * 4 * NDEV);
+    const size_t o_sites = carve(8ull * 3 * 5 * ODP_MAX_SITES);
+    const size_t o_sflag = carve(4ull * 5 * ODP_MAX_SITES), o_spos = carve(4ull * 5 * ODP_MAX_SITES);
+    const size_t o_misc = carve(64);
+    const size_t o_keys_alt = carve(N4), o_vals_alt = carve(N4);
+    const size_t o_hist = carve(4 * prim::sort_hist_words(n));
+    const size_t scan_words = std::max(prim::scan_tmp_words(256u * ((n + prim::SORT_TILE - 1) / prim::SORT_TILE + 1)),
+                                       std::max(prim::scan_tmp_words(n), prim::scan_tmp_words(5 * ODP_MAX_SITES)));
+    const size_t o_scan = carve(4 * (scan_words + 16));
+    const size_t o_tkeys = carve(sizeof(Key128) * ((size_t)cap_max + 1));
+    const size_t o_tvals = carve(4ull * ((size_t)cap_max + 1));
+
+    uint8_t* b = (uint8_t*)scratch_get(SLOT_AN_MAIN, bytes, s, &st);
+    if (!b) return st;
+
+    A a;
+    a.ev.p = (const uint8_t*)events;
+    a.n = n;
+    a.nb = nb;
+    a.h = (Hdr*)(b + o_h);
+    a.cls = (uint32_t*)(b + o_cls);
+    a.bcnt = (uint32_t*)(b + o_bcnt);
+    a.X = (uint32_t*)(b + o_X);
+    a.P = (uint32_t*)(b + o_P);
+    a.K = (uint32_t*)(b + o_K);
+    a.U = (uint32_t*)(b + o_U);
+    uint32_t* part = (uint32_t*)(b + o_part);
+    a.dd = part;
+    a.rt = part + (n + 2);
+    a.ra = part + 2 * (n + 2);
+    a.ua = part + 3 * (n + 2);
+    a.ut = part + 4 * (n + 2);
+    a.del_of = part + 5 * (n + 2);
+    a.wasted = b + o_wasted;
+    a.bad = b + o_bad;
+    a.slot = (uint32_t*)(b + o_slot);
+    a.sk = (uint32_t*)(b + o_sk);
+    a.sv = (uint32_t*)(b + o_sv);
+    a.k2 = (uint32_t*)(b + o_k2);
+    a.v2 = (uint32_t*)(b + o_v2);
+    a.f1 = (uint32_t*)(b + o_f1);
+    a.f2 = (uint32_t*)(b + o_f2);
+    a.id1 = (uint32_t*)(b + o_id1);
+    a.id2 = (uint32_t*)(b + o_id2);
+    a.H = (uint32_t*)(b + o_H);
+    a.R = (uint32_t*)(b + o_R);
+    a.stk = (uint32_t*)(b + o_stk);
+    a.pq = (uint32_t*)(b + o_pq);
+    a.uc = b + o_uc;
+    a.ks = (uint64_t*)(b + o_ks);
+    a.ke = (uint64_t*)(b + o_ke);
+    a.dstart = (uint32_t*)(b + o_dev);
+    a.dend = a.dstart + NDEV;
+    a.sites = (unsigned long long*)(b + o_sites);
+    uint32_t* sflag = (uint32_t*)(b + o_sflag);
+    uint32_t* spos = (uint32_t*)(b + o_spos);
+    uint32_t* misc = (uint32_t*)(b + o_misc);  // [0] total findings, [1] site rows, [2] scan total
+    a.tab.keys = (Key128*)(b + o_tkeys);
+    a.tab.vals = (uint32_t*)(b + o_tvals);
+    a.tab.cap_max = cap_max;
+    a.tab.cap_dev = &a.h->tcap;
+    a.out = out;
+    prim::SortTmp srt;
+    srt.keys_alt = (uint32_t*)(b + o_keys_alt);
+    srt.vals_alt = (uint32_t*)(b + o_vals_alt);
+    srt.hist = (uint32_t*)(b + o_hist);
+    srt.scan_tmp = (uint32_t*)(b + o_scan);
+    uint32_t* scan_tmp = srt.scan_tmp;
+
+    const int bits_n = prim::bit_length(n);   // keys < n + 1
+    const int gX = grid_for(n, sms);
+    const int clear_grid = sms * 8;
+
+    // ---- init
+    ODP_CHECK_CUDA(cudaMemsetAsync(a.h, 0, sizeof(Hdr), s));
+    ODP_CHECK_CUDA(cudaMemsetAsync(&a.h->err, 0xFF, 8, s));
+    ODP_CHECK_CUDA(cudaMemsetAsync(part, 0xFF, 6 * N4, s));
+    ODP_CHECK_CUDA(cudaMemsetAsync(a.wasted, 0, n + 16, s));
+    ODP_CHECK_CUDA(cudaMemsetAsync(a.dstart, 0, 2 * 4 * NDEV, s));
+    ODP_CHECK_CUDA(cudaMemsetAsync(a.sites, 0, 8ull * 3 * 5 * ODP_MAX_SITES, s));
+
+    // ---- validate, lists
+    k_validate<<<nb, TPB, 0, s>>>(a);
+    prim::exclusive_scan(a.bcnt, (uint32_t*)(b + o_bscan), nullptr, 4 * nb, misc + 2, scan_tmp, s);
+    k_list_lengths<<<1, 32, 0, s>>>(a, (uint32_t*)(b + o_bscan), misc + 2);
+    k_compact<<<nb, TPB, 0, s>>>(a, (uint32_t*)(b + o_bscan));
+    uint32_t* nX = &a.h->nX;
+    uint32_t* nP = &a.h->nP;
+    uint32_t* nK = &a.h->nK;
+    uint32_t* nU = &a.h->nU;
+
+    // ---- Alg. 1: content ids, first receivers
+    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nX, n);
+    k_x_insert_fp<<<gX, TPB, 0, s>>>(a);
+    k_x_cid<<<gX, TPB, 0, s>>>(a);
+    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nX, n);
+    k_x_insert_dd<<<gX, TPB, 0, s>>>(a);
+    k_x_dd<<<gX, TPB, 0, s>>>(a);
+
+    // ---- Alg. 2
+    prim::radix_sort(a.sk, a.sv, nX, n, bits_n, srt, s);
+    k_rt_flags<<<gX, TPB, 0, s>>>(a);
+    prim::exclusive_scan(a.f1, a.id1, nX, n, &a.h->nseg, scan_tmp, s);
+    prim::exclusive_scan(a.f2, a.id2, nX, n, &a.h->nrun, scan_tmp, s);
+    k_rt_starts<<<gX, TPB, 0, s>>>(a);
+    k_rt_check<<<gX, TPB, 0, s>>>(a);
+    k_rt_partner<<<gX, TPB, 0, s>>>(a);
+    k_rt_literal<<<gX, TPB, 0, s>>>(a);
+
+    // ---- pairs
+    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nP, n);
+    k_p_insert<<<gX, TPB, 0, s>>>(a);
+    k_p_keys<<<gX, TPB, 0, s>>>(a);
+    prim::radix_sort(a.sk, a.sv, nP, n, bits_n, srt, s);
+    k_seg_heads<<<gX, TPB, 0, s>>>(a, nP);
+    prim::exclusive_scan(a.f1, a.id1, nP, n, &a.h->nseg2, scan_tmp, s);
+    k_seg_starts<<<gX, TPB, 0, s>>>(a, nP, &a.h->nseg2);
+    k_p_check<<<gX, TPB, 0, s>>>(a);
+    k_p_match<<<gX, TPB, 0, s>>>(a);
+    k_p_literal<<<gX, TPB, 0, s>>>(a);
+
+    // ---- Alg. 3
+    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nP, n);
+    k_ra_insert<<<gX, TPB, 0, s>>>(a);
+    k_ra_flag<<<gX, TPB, 0, s>>>(a);
+
+    // ---- kernels per device
+    k_dev_keys<<<gX, TPB, 0, s>>>(a, a.K, nK);
+    prim::radix_sort(a.sk, a.sv, nK, n, 8, srt, s);
+    k_k_bounds<<<gX, TPB, 0, s>>>(a);
+    k_k_pmax<<<1, 160, 0, s>>>(a);
+
+    // ---- Alg. 4
+    k_ua<<<gX, TPB, 0, s>>>(a);
+
+    // ---- Alg. 5
+    k_dev_keys<<<gX, TPB, 0, s>>>(a, a.U, nU);
+    prim::radix_sort(a.sk, a.sv, nU, n, 8, srt, s);
+    k_ut_class<<<gX, TPB, 0, s>>>(a);
+    k_ut_heads<<<gX, TPB, 0, s>>>(a);
+    prim::exclusive_scan(a.f1, a.id1, nU, n, &a.h->nsegU, scan_tmp, s);
+    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nU, n);
+    k_ut_insert<<<gX, TPB, 0, s>>>(a);
+    k_ut_gid<<<gX, TPB, 0, s>>>(a);
+    prim::radix_sort(a.k2, a.v2, nU, n, bits_n, srt, s);
+    k_ut_next<<<gX, TPB, 0, s>>>(a);
+
+    // ---- emission
+    k_em_count<<<nb, TPB, 0, s>>>(a);
+    uint32_t* escan = (uint32_t*)(b + o_bscan);
+    prim::exclusive_scan(a.bcnt, escan, nullptr, 5 * nb, misc + 0, scan_tmp, s);
+    k_em_write<<<nb, TPB, 0, s>>>(a, escan);
+    k_em_saved<<<gX, TPB, 0, s>>>(a);
+    k_site_flags<<<grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s>>>(a, sflag);
+    prim::exclusive_scan(sflag, spos, nullptr, 5u * ODP_MAX_SITES, misc + 1, scan_tmp, s);
+    k_site_write<<<grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s>>>(a, sflag, spos);
+    k_finalize<<<1, 32, 0, s>>>(a, misc + 0, misc + 1);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace odp
 
 extern "C" int odp_analyze(const odp_event* events, uint64_t n, const odp_findings* out,
                            cudaStream_t stream) {
-    (void)events; (void)n; (void)out; (void)stream;
-    return ODP_ERR_UNSUPPORTED;
+    return odp::an_run(events, n, out, stream);
 }

@@ -268,8 +268,8 @@ __device__ __forceinline__ uint32_t table_insert_min(const Table& t, uint32_t ca
     uint32_t slot = (uint32_t)mix64(k.lo ^ mix64(k.hi)) & mask;
     const Key128 empty{EMPTY_KEY, EMPTY_KEY};
     for (uint32_t probe = 0; probe < cap; ++probe) {
-        Key128 cur = t.keys[slot];
-        if (key_eq(cur, empty)) cur = atomicCAS(&t.keys[slot], empty, k);
+        // slots change only once (empty -> key), always through the 16-byte CAS
+        const Key128 cur = atomicCAS(&t.keys[slot], empty, k);
         if (key_eq(cur, empty) || key_eq(cur, k)) {
             atomicMin(&t.vals[slot], v);
             return slot;

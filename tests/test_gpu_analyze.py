@@ -1,0 +1,176 @@
+"""GPU parity of odp_analyze against the oracle (bit-exact findings, site
+rows, summary and status), through the C ABI."""
+
+import numpy as np
+import pytest
+import torch
+
+from synth import content, traces
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def odp():
+    import paper_2601_12713_b300 as odp
+
+    return odp
+
+
+def gpu_analyze(odp, events, capacity=None, site_capacity=5 * 65536):
+    n = events.size
+    if capacity is None:
+        capacity = max(16, 6 * n)
+    ev = torch.from_numpy(events.view(np.uint8).reshape(-1).copy()).cuda() if n else \
+        torch.empty(64, dtype=torch.uint8, device="cuda")
+    out = odp.Findings(capacity, site_capacity)
+    odp.analyze(ev, n, out)
+    torch.cuda.synchronize()
+    return out.to_host()
+
+
+def assert_same(g, o):
+    assert g["status"] == o.status
+    assert g["count"] == o.count
+    assert g["summary"] == o.summary
+    assert g["n_sites"] == o.n_sites
+    assert np.array_equal(g["findings"].view(np.uint8), o.findings.view(np.uint8)), \
+        first_diff(g["findings"], o.findings)
+    assert np.array_equal(g["sites"].view(np.uint8), o.sites.view(np.uint8))
+
+
+def first_diff(a, b):
+    for i in range(min(a.size, b.size)):
+        if a[i].tobytes() != b[i].tobytes():
+            return f"first difference at {i}: gpu {a[i]} oracle {b[i]}"
+    return f"sizes {a.size} vs {b.size}"
+
+
+def check(odp, orc, events, **kw):
+    g = gpu_analyze(odp, events, **kw)
+    o = orc.analyze(events, **{k: v for k, v in kw.items()})
+    assert_same(g, o)
+    return g
+
+
+def with_fp(bundle):
+    traces.fill_fp_from_content(bundle)
+    return bundle.events
+
+
+def test_listings(cuda_ok, orc, odp):
+    check(odp, orc, with_fp(traces.listing1()))
+    for n in (1, 2, 8, 50):
+        check(odp, orc, with_fp(traces.listing2(n)))
+    check(odp, orc, with_fp(traces.repeated_runs(500, 4096)))
+
+
+def test_empty_trace(cuda_ok, orc, odp):
+    ev = np.zeros(0, dtype=traces.EVENT_DTYPE)
+    g = gpu_analyze(odp, ev)
+    assert g["status"] == 0 and g["count"] == 0 and g["n_sites"] == 0
+    assert all(v == 0 for v in g["summary"].values())
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_small_traces(cuda_ok, orc, odp, seed):
+    n_dev = 1 + seed % 3
+    b = traces.random_small(seed, n_ops=10 + (seed * 7) % 60, n_devices=n_dev, d2d=seed % 2 == 0)
+    check(odp, orc, with_fp(b))
+
+
+def test_random_medium_traces(cuda_ok, orc, odp):
+    for seed in range(8):
+        b = traces.random_small(1000 + seed, n_ops=20_000, n_contents=50, n_hosts=40,
+                                n_devices=1 + seed % 4, d2d=True)
+        check(odp, orc, with_fp(b))
+
+
+def test_exhaustive_two_endpoint_rt(cuda_ok, orc, odp):
+    # every direction pattern of length 6 over 2 contents, concatenated with
+    # distinct content ids per pattern so the groups stay independent
+    import itertools
+
+    dirs_all, cont_all = [], []
+    for k, dirs in enumerate(itertools.product((0, 1), repeat=6)):
+        for cs in itertools.product((0, 1), repeat=6):
+            dirs_all += list(dirs)
+            cont_all += [2 * (k * 64 + int("".join(map(str, cs)), 2)) + c for c in cs]
+    b = traces.two_endpoint_sequence(dirs_all, cont_all)
+    check(odp, orc, with_fp(b))
+
+
+def test_plain_small_with_payload_fingerprints(cuda_ok, orc, odp):
+    """Plain small workload: every transfer fingerprinted on the GPU, one
+    buffer per launch, then the whole log analysed; fingerprints and findings
+    checked against the oracle."""
+    from synth import gpu
+
+    b = traces.plain_small()
+    ev = b.events
+    idx = np.flatnonzero(b.content >= 0)
+    fps_gpu = np.zeros((ev.size, 2), dtype=np.uint64)
+    for i in idx:
+        nbytes = int(ev["bytes"][i])
+        t = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        gpu.fill(t, content.RANDOM, int(b.payload_seed[i]))
+        out = odp.fingerprint_tensors([t])
+        fps_gpu[i] = out.cpu().numpy().view(np.uint64)[0]
+    for i in idx[::7]:
+        data = content.bytes_of(content.RANDOM, int(b.payload_seed[i]), int(ev["bytes"][i]))
+        assert tuple(int(x) for x in fps_gpu[i]) == orc.fp128(data)
+    ev_g = ev.copy()
+    ev_g["fp_lo"][idx] = fps_gpu[idx, 0]
+    ev_g["fp_hi"][idx] = fps_gpu[idx, 1]
+    g = check(odp, orc, ev_g)
+    assert g["summary"]["count1"] > 0 and g["summary"]["count3"] > 0
+
+
+@pytest.mark.parametrize("n_iter,n_arrays,per_iter", [(20, 400, 100), (60, 2000, 500)])
+def test_iterative_solver_reduced(cuda_ok, orc, odp, n_iter, n_arrays, per_iter):
+    b = traces.iterative_solver(n_iter=n_iter, n_arrays=n_arrays, per_iter=per_iter, n_sites=50)
+    check(odp, orc, with_fp(b))
+
+
+def test_validation_errors(cuda_ok, orc, odp):
+    b = traces.listing2(4)
+    base = with_fp(b)
+    cases = []
+    e = base.copy(); e["kind"][3] = 9; cases.append(e)
+    e = base.copy(); e["t_start_ns"][7] = e["t_start_ns"][6] - 1; cases.append(e)
+    e = base.copy(); e["t_end_ns"][2] = e["t_start_ns"][2] - 1; cases.append(e)
+    e = base.copy(); e["bytes"][1] = 0; cases.append(e)
+    e = base.copy(); e["site_id"][5] = 70000; cases.append(e)
+    e = base.copy(); e["src_dev"][1] = 0; cases.append(e)          # to-device from a device
+    e = base.copy(); e["t_start_ns"][3] = 0; e["kind"][8] = 0; cases.append(e)
+    for e in cases:
+        g = gpu_analyze(odp, e)
+        o = orc.analyze(e)
+        assert g["status"] == o.status < 0
+        assert g["count"] == 0 and g["n_sites"] == 0
+        assert all(v == 0 for v in g["summary"].values())
+
+
+def test_truncation(cuda_ok, orc, odp):
+    ev = with_fp(traces.repeated_runs(50, 64))
+    check(odp, orc, ev, capacity=10, site_capacity=1)
+
+
+def test_unmatched_and_nested_pairs(cuda_ok, orc, odp):
+    bld = traces._Builder()
+    D = traces.DELETE
+    A = traces.ALLOC
+    # nested allocations of one device address, an unmatched delete, a
+    # never-deleted allocation, and a kernel that overlaps only some lifetimes
+    bld.add(D, 10, dst=0, host_addr=0x10, dev_addr=0x100, nbytes=8)
+    bld.add(A, 10, dst=0, host_addr=0x10, dev_addr=0x100, nbytes=8)
+    bld.add(A, 10, dst=0, host_addr=0x10, dev_addr=0x100, nbytes=8)
+    bld.add(traces.KERNEL, 50, dst=0)
+    bld.add(D, 10, dst=0, host_addr=0x10, dev_addr=0x100, nbytes=8)
+    bld.add(D, 10, dst=0, host_addr=0x10, dev_addr=0x100, nbytes=8)
+    bld.add(A, 10, dst=0, host_addr=0x10, dev_addr=0x100, nbytes=8)
+    bld.add(A, 10, dst=1, host_addr=0x20, dev_addr=0x100, nbytes=8)
+    bld.add(D, 10, dst=0, host_addr=0x10, dev_addr=0x100, nbytes=8)
+    bld.add(A, 10, dst=0, host_addr=0x30, dev_addr=0x200, nbytes=8)
+    g = check(odp, orc, with_fp(bld.done()))
+    assert g["summary"]["n_unmatched_deletes"] == 1
