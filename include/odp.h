@@ -102,6 +102,30 @@ typedef struct odp_fp128 {
 int odp_fingerprint(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
                     odp_fp128* out128, cudaStream_t stream);
 
+/*
+ * odp_fingerprint_noalloc -- the same results as odp_fingerprint, computed
+ * without allocating any device memory.  The paper has no counterpart; this
+ * is for callers that cannot call cudaMalloc or an allocator at the moment
+ * they need a fingerprint (code running inside an allocator or an
+ * out-of-memory path, or a host program that forbids allocation after
+ * start-up).  Its scratch is one file-scope device array of about 0.9 MiB
+ * that every GPU loading the library keeps until the process exits.
+ *
+ *   ptrs, sizes, out128: as for odp_fingerprint (device arrays, n entries).
+ *   n: at most 4096 buffers; larger n returns ODP_ERR_UNSUPPORTED.  Buffers
+ *   of any size are accepted (large batches use larger tiles).
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and may return ODP_ERR_CUDA if that fails; make the
+ * first call on a device before capturing a stream.  Every call reuses the
+ * same array: calls whose work overlaps on the GPU (different streams, or
+ * another thread) race and give wrong results, so serialise them.  A null
+ * ptrs[i] with sizes[i] > 0 yields {0, 0} in out128[i]; this variant does
+ * not update the status word of odp_fingerprint_status.
+ */
+int odp_fingerprint_noalloc(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
+                            odp_fp128* out128, cudaStream_t stream);
+
 /* Reads (synchronising `stream`) and clears the device status word that
  * odp_fingerprint writes for per-buffer errors; *status receives ODP_OK or
  * the first error recorded. */

@@ -8,7 +8,8 @@ is no CPU fallback.  ``paper_2601_12713_b300.build`` compiles it.
 """
 
 _EXPORTS = (
-    "LIB_PATH", "lib", "status_string", "OdpError", "fingerprint", "fingerprint_tensors",
+    "LIB_PATH", "lib", "status_string", "OdpError", "fingerprint", "fingerprint_noalloc",
+    "fingerprint_tensors",
     "fingerprint_status", "analyze", "Findings", "EVENT_DTYPE", "FINDING_DTYPE", "SITE_DTYPE",
     "SUMMARY_FIELDS", "set_torch_allocator", "release_scratch",
 )

@@ -24,6 +24,8 @@ _lib.odp_status_string.argtypes = [ctypes.c_int]
 _lib.odp_status_string.restype = ctypes.c_char_p
 _lib.odp_fingerprint.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, _vp]
 _lib.odp_fingerprint.restype = ctypes.c_int
+_lib.odp_fingerprint_noalloc.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, _vp]
+_lib.odp_fingerprint_noalloc.restype = ctypes.c_int
 _lib.odp_fingerprint_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
 _lib.odp_fingerprint_status.restype = ctypes.c_int
 _lib.odp_analyze.argtypes = [_vp, ctypes.c_uint64, _vp, _vp]
@@ -75,6 +77,21 @@ def fingerprint(ptrs: torch.Tensor, sizes: torch.Tensor, out: torch.Tensor, stre
     _check(_lib.odp_fingerprint(ptrs.data_ptr() if n else None, sizes.data_ptr() if n else None,
                                 n, out.data_ptr() if n else None, _stream(stream)),
            "odp_fingerprint")
+
+
+def fingerprint_noalloc(ptrs: torch.Tensor, sizes: torch.Tensor, out: torch.Tensor,
+                        stream=None) -> None:
+    """Like :func:`fingerprint` but through odp_fingerprint_noalloc, which uses
+    a fixed device array instead of allocating scratch (at most 4096 buffers
+    per call; calls must not overlap on the GPU)."""
+    n = ptrs.numel()
+    assert sizes.numel() == n and out.numel() == 2 * n
+    for t in (ptrs, sizes, out):
+        assert t.is_cuda and t.is_contiguous()
+    _check(_lib.odp_fingerprint_noalloc(ptrs.data_ptr() if n else None,
+                                        sizes.data_ptr() if n else None, n,
+                                        out.data_ptr() if n else None, _stream(stream)),
+           "odp_fingerprint_noalloc")
 
 
 def fingerprint_tensors(tensors, stream=None, out: torch.Tensor | None = None) -> torch.Tensor:

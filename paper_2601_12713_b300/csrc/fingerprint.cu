@@ -623,3 +623,104 @@ extern "C" int odp_fingerprint(const void* const* ptrs, const uint64_t* sizes, u
     odp::FpLaunch L;
     return odp::fp_run(ptrs, sizes, n, out128, stream, L);
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of odp_fingerprint (no counterpart in the paper).
+//
+// For callers that cannot allocate device memory -- for example code running
+// inside a custom allocator or an out-of-memory handler, or an embedding
+// that forbids cudaMalloc after start-up.  The plan, tile list, tree nodes
+// and counters live in one file-scope device array of fixed size, which every
+// GPU that loads the library holds until the process exits.
+// ---------------------------------------------------------------------------
+#include <map>
+#include <mutex>
+
+namespace odp {
+namespace {
+
+constexpr uint32_t NA_MAX_BUFFERS = 4096;
+constexpr uint32_t NA_CAP_TILES = NA_MAX_BUFFERS + 16384;
+
+constexpr size_t na_up(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t NA_O_HDR = 0;
+constexpr size_t NA_O_TOFF = na_up(NA_O_HDR + sizeof(PlanHeader));
+constexpr size_t NA_O_NOFF = na_up(NA_O_TOFF + 4ull * (NA_MAX_BUFFERS + 1));
+constexpr size_t NA_O_BSUM = na_up(NA_O_NOFF + 4ull * (NA_MAX_BUFFERS + 1));
+constexpr size_t NA_O_TBUF = na_up(NA_O_BSUM + 4ull * 2 * 8);
+constexpr size_t NA_O_CNT = na_up(NA_O_TBUF + 4ull * NA_CAP_TILES);
+constexpr size_t NA_O_NODES = na_up(NA_O_CNT + 4ull * 2 * NA_CAP_TILES);
+constexpr size_t NA_BYTES = na_up(NA_O_NODES + sizeof(U128) * 2 * NA_CAP_TILES);
+
+__device__ __align__(256) uint8_t g_na_scratch[NA_BYTES];
+
+std::mutex g_na_mu;
+std::map<int, uint8_t*> g_na_base;  // device -> address of g_na_scratch
+
+// Device address of the array on the current device (looked up once per
+// device with that device current).
+uint8_t* na_base(int* status) {
+    int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    auto it = g_na_base.find(dev);
+    if (it != g_na_base.end()) return it->second;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        *status = ODP_ERR_CUDA;
+        return nullptr;
+    }
+    g_na_base[dev] = (uint8_t*)p;
+    return (uint8_t*)p;
+}
+
+}  // namespace
+
+static int fp_run_noalloc(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
+                          odp_fp128* out, cudaStream_t stream) {
+    if (n == 0) return ODP_OK;
+    if (!ptrs || !sizes || !out) return ODP_ERR_INVALID_ARG;
+    if (n > NA_MAX_BUFFERS) return ODP_ERR_UNSUPPORTED;
+    int st = ODP_OK;
+    uint8_t* s = na_base(&st);
+    if (!s) return st;
+
+    FpArgs a;
+    a.ptrs = ptrs;
+    a.sizes = sizes;
+    a.out = out;
+    a.n = (uint32_t)n;
+    a.cap_tiles = NA_CAP_TILES;
+    a.hdr = (PlanHeader*)(s + NA_O_HDR);
+    a.tile_off = (uint32_t*)(s + NA_O_TOFF);
+    a.node_off = (uint32_t*)(s + NA_O_NOFF);
+    a.block_sums = (uint32_t*)(s + NA_O_BSUM);
+    a.tile_buf = (uint32_t*)(s + NA_O_TBUF);
+    a.counters = (uint32_t*)(s + NA_O_CNT);
+    a.nodes = (U128*)(s + NA_O_NODES);
+    a.status = nullptr;
+
+    const int sms = device_sm_count();
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<TILE_WARPS>, TILE_WARPS * 32, 0);
+    const int ctas = std::max(1, occ);
+    const uint32_t total_warps = (uint32_t)(sms * ctas * TILE_WARPS);
+    a.tmin = std::max<uint32_t>(1, (uint32_t)(2ull * total_warps / a.n));
+
+    // the header (chunk total, error word, tile counter) must start cleared;
+    // the plan kernels rewrite every offset and zero the tree counters
+    ODP_CHECK_CUDA(cudaMemsetAsync(a.hdr, 0, sizeof(PlanHeader), stream));
+    ODP_CHECK_CUDA(cudaMemsetAsync(&a.hdr->err, 0xFF, sizeof(unsigned long long), stream));
+    fp_plan_small<<<1, 1024, 0, stream>>>(a);
+    fp_plan_tiles<<<sms * 4, 256, 0, stream>>>(a);
+    fp_tiles<TILE_WARPS><<<sms * ctas, TILE_WARPS * 32, 0, stream>>>(a);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace odp
+
+extern "C" int odp_fingerprint_noalloc(const void* const* ptrs, const uint64_t* sizes,
+                                       uint64_t n, odp_fp128* out128, cudaStream_t stream) {
+    return odp::fp_run_noalloc(ptrs, sizes, n, out128, stream);
+}
