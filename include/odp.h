@@ -45,7 +45,8 @@ enum {
     ODP_ERR_TIMEOUT = -4,       /* a bounded device-side wait ran out       */
     ODP_ERR_MALFORMED = -5,     /* an event record failed validation        */
     ODP_ERR_UNSORTED = -6,      /* event start times decrease               */
-    ODP_ERR_UNSUPPORTED = -7    /* input outside the implemented limits     */
+    ODP_ERR_UNSUPPORTED = -7,   /* input outside the implemented limits     */
+    ODP_ERR_MISMATCH = -8       /* autotune: schedules disagreed (a bug)    */
 };
 
 /* Human-readable name of a status code (static string, never null). */
@@ -125,6 +126,46 @@ int odp_fingerprint(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
  */
 int odp_fingerprint_noalloc(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
                             odp_fp128* out128, cudaStream_t stream);
+
+/*
+ * Launch schedule of the fingerprint kernels.  A schedule spreads the work
+ * differently over the GPU and never changes a fingerprint (tiles are
+ * aligned power-of-two blocks of chunks; the left-balanced tree gives the
+ * same root for any tile size).
+ *   warps_per_cta  4, 8 or 16
+ *   ctas_per_sm    0 = as many as fit, else at most this many
+ *   tmin_scale     >= 1; each buffer aims at tmin_scale * (resident warps) / n
+ *                  tiles of 1..32 chunks
+ */
+typedef struct odp_fp_schedule {
+    int32_t warps_per_cta;
+    int32_t ctas_per_sm;
+    int32_t tmin_scale;
+    int32_t reserved;
+} odp_fp_schedule;
+
+/* odp_fingerprint with an explicit schedule (ODP_ERR_INVALID_ARG for values
+ * outside the ranges above). */
+int odp_fingerprint_with(const odp_fp_schedule* sched, const void* const* ptrs,
+                         const uint64_t* sizes, uint64_t n, odp_fp128* out128,
+                         cudaStream_t stream);
+
+/*
+ * odp_autotune_fingerprint -- times every candidate schedule on this input
+ * (`reps` timed calls each after one warm-up; synchronises `stream`), checks
+ * that all candidates give identical fingerprints (ODP_ERR_MISMATCH if not),
+ * and records the fastest for n's size class (bit length of n).  Later
+ * odp_fingerprint calls of that class use it.  When the environment variable
+ * ODP_AUTOTUNE_CACHE names a file, the table is read from it on first use and
+ * rewritten after each tuning.  out128 ends with the fingerprints; *best and
+ * *best_ms (optional) receive the choice and its time per call.
+ */
+int odp_autotune_fingerprint(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
+                             odp_fp128* out128, cudaStream_t stream, int reps,
+                             odp_fp_schedule* best, float* best_ms);
+
+/* Forgets every tuned schedule (in memory; the cache file is left alone). */
+int odp_autotune_clear(void);
 
 /* Reads (synchronising `stream`) and clears the device status word that
  * odp_fingerprint writes for per-buffer errors; *status receives ODP_OK or
@@ -263,6 +304,79 @@ typedef struct odp_findings {
  */
 int odp_analyze(const odp_event* events, uint64_t n, const odp_findings* out,
                 cudaStream_t stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/*
+ * A serving loop (no counterpart in the paper, which analyses its log after
+ * the program exits): many host threads submit mapping events as they
+ * happen; the server merges them in start-time order behind a watermark,
+ * forms batches continuously, fingerprints every transfer's payload on the
+ * GPU, appends the events to a log resident in device memory and updates
+ * Algorithm 1 (duplicate transfers) and Algorithm 2 (round trips) state
+ * kept on the device, so those findings are reported while the program
+ * runs.  The complete Algorithms 1-5 run over the resident log with
+ * odp_analyze after odp_server_flush (odp_server_log gives the log).
+ */
+typedef struct odp_server odp_server;
+
+typedef struct odp_server_cfg {
+    int32_t device;                 /* CUDA device of the server */
+    int32_t n_slots;                /* batches in flight at most (>= 1) */
+    uint64_t device_budget_bytes;   /* device memory the server may use */
+    uint64_t max_events;            /* capacity of the resident log */
+    uint32_t max_batch_events;      /* events per batch at most */
+    uint32_t max_producers;         /* distinct submitting threads at most */
+    uint32_t watermark_timeout_us;  /* a thread silent this long stops holding
+                                       back the merge watermark */
+    uint32_t batch_interval_us;     /* batcher polling period */
+} odp_server_cfg;
+
+/* Per-server counters and latency percentiles (ns, from the submit call of
+ * the event that completes a finding to the moment the server hands the
+ * finding to the poll queue). */
+typedef struct odp_server_stats {
+    uint64_t events_submitted, events_processed, batches, findings_streamed;
+    uint64_t late_events;           /* events behind the released watermark */
+    uint64_t latency_p50_ns, latency_p99_ns, latency_max_ns;
+    uint64_t first_submit_ns, last_done_ns;  /* steady-clock stamps */
+    uint64_t rt_groups_unstreamed;  /* content groups with > 2 endpoints */
+} odp_server_stats;
+
+/* Creates a server and allocates all of its device memory up front
+ * (ODP_ERR_OOM if that exceeds device_budget_bytes or the device). */
+int odp_server_create(const odp_server_cfg* cfg, odp_server** out);
+
+/*
+ * Thread-safe.  Submits n events (host memory, 64-byte records).  For
+ * transfers, dev_payloads[i] is the device address of the transferred bytes
+ * (event.bytes of them); the server computes fp_lo/fp_hi.  Events of one
+ * calling thread must have nondecreasing t_start_ns.  Returns
+ * ODP_ERR_INVALID_ARG for null arrays, ODP_ERR_UNSUPPORTED when the log
+ * capacity or the producer limit would be exceeded.
+ */
+int odp_server_submit(odp_server* s, const odp_event* host_events,
+                      const void* const* dev_payloads, uint64_t n);
+
+/* Moves up to cap streamed findings (DD and RT, event indices in the merged
+ * log order) to host_out; *n_out receives the number moved. */
+int odp_server_poll(odp_server* s, odp_finding* host_out, uint64_t cap, uint64_t* n_out);
+
+/* Releases every submitted event (the watermark no longer waits) and blocks
+ * until all batches are done. */
+int odp_server_flush(odp_server* s);
+
+/* The resident merged log (device pointer) and its length; valid until the
+ * next submit or destroy.  Pass it to odp_analyze for Algorithms 1-5. */
+int odp_server_log(odp_server* s, const odp_event** dev_log, uint64_t* n);
+
+/* Maps merged-log positions to (submitting thread index, sequence number of
+ * the event within that thread's submissions); host arrays of n entries. */
+int odp_server_origin(odp_server* s, uint32_t* producer, uint64_t* seq, uint64_t n);
+
+int odp_server_stats_get(odp_server* s, odp_server_stats* st);
+
+int odp_server_destroy(odp_server* s);
 
 /* ----------------------------------------------------------------- memory */
 

@@ -26,6 +26,20 @@ _lib.odp_fingerprint.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, _vp]
 _lib.odp_fingerprint.restype = ctypes.c_int
 _lib.odp_fingerprint_noalloc.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, _vp]
 _lib.odp_fingerprint_noalloc.restype = ctypes.c_int
+class FpSchedule(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("tmin_scale", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib.odp_fingerprint_with.argtypes = [ctypes.POINTER(FpSchedule), _vp, _vp, ctypes.c_uint64, _vp,
+                                      _vp]
+_lib.odp_fingerprint_with.restype = ctypes.c_int
+_lib.odp_autotune_fingerprint.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, _vp, ctypes.c_int,
+                                          ctypes.POINTER(FpSchedule),
+                                          ctypes.POINTER(ctypes.c_float)]
+_lib.odp_autotune_fingerprint.restype = ctypes.c_int
+_lib.odp_autotune_clear.argtypes = []
+_lib.odp_autotune_clear.restype = ctypes.c_int
 _lib.odp_fingerprint_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
 _lib.odp_fingerprint_status.restype = ctypes.c_int
 _lib.odp_analyze.argtypes = [_vp, ctypes.c_uint64, _vp, _vp]
@@ -77,6 +91,40 @@ def fingerprint(ptrs: torch.Tensor, sizes: torch.Tensor, out: torch.Tensor, stre
     _check(_lib.odp_fingerprint(ptrs.data_ptr() if n else None, sizes.data_ptr() if n else None,
                                 n, out.data_ptr() if n else None, _stream(stream)),
            "odp_fingerprint")
+
+
+def _fp_args(ptrs, sizes, out):
+    n = ptrs.numel()
+    assert sizes.numel() == n and out.numel() == 2 * n
+    for t in (ptrs, sizes, out):
+        assert t.is_cuda and t.is_contiguous()
+    return (ptrs.data_ptr() if n else None, sizes.data_ptr() if n else None, n,
+            out.data_ptr() if n else None)
+
+
+def fingerprint_with(schedule, ptrs: torch.Tensor, sizes: torch.Tensor, out: torch.Tensor,
+                     stream=None) -> None:
+    """odp_fingerprint with an explicit (warps_per_cta, ctas_per_sm, tmin_scale)."""
+    w, c, t = schedule
+    sch = FpSchedule(w, c, t, 0)
+    _check(_lib.odp_fingerprint_with(ctypes.byref(sch), *_fp_args(ptrs, sizes, out),
+                                     _stream(stream)), "odp_fingerprint_with")
+
+
+def autotune_fingerprint(ptrs: torch.Tensor, sizes: torch.Tensor, out: torch.Tensor, reps=3,
+                         stream=None):
+    """Times every schedule on this batch, keeps the fastest for its size class;
+    returns ((warps_per_cta, ctas_per_sm, tmin_scale), ms per call)."""
+    sch = FpSchedule()
+    ms = ctypes.c_float(0)
+    _check(_lib.odp_autotune_fingerprint(*_fp_args(ptrs, sizes, out), _stream(stream), reps,
+                                         ctypes.byref(sch), ctypes.byref(ms)),
+           "odp_autotune_fingerprint")
+    return (sch.warps_per_cta, sch.ctas_per_sm, sch.tmin_scale), float(ms.value)
+
+
+def autotune_clear() -> None:
+    _check(_lib.odp_autotune_clear(), "odp_autotune_clear")
 
 
 def fingerprint_noalloc(ptrs: torch.Tensor, sizes: torch.Tensor, out: torch.Tensor,
@@ -177,6 +225,116 @@ def analyze(events: torch.Tensor, n: int, out: Findings, stream=None) -> None:
     assert events.is_cuda and events.numel() >= 64 * n
     _check(_lib.odp_analyze(events.data_ptr() if n else None, n, ctypes.byref(out.struct),
                             _stream(stream)), "odp_analyze")
+
+
+# ---------------------------------------------------------------- serving
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("n_slots", ctypes.c_int32),
+                ("device_budget_bytes", ctypes.c_uint64), ("max_events", ctypes.c_uint64),
+                ("max_batch_events", ctypes.c_uint32), ("max_producers", ctypes.c_uint32),
+                ("watermark_timeout_us", ctypes.c_uint32), ("batch_interval_us", ctypes.c_uint32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "events_submitted", "events_processed", "batches", "findings_streamed", "late_events",
+        "latency_p50_ns", "latency_p99_ns", "latency_max_ns", "first_submit_ns", "last_done_ns",
+        "rt_groups_unstreamed")]
+
+
+_lib.odp_server_create.argtypes = [ctypes.POINTER(ServerCfg), ctypes.POINTER(_vp)]
+_lib.odp_server_create.restype = ctypes.c_int
+_lib.odp_server_submit.argtypes = [_vp, _vp, _vp, ctypes.c_uint64]
+_lib.odp_server_submit.restype = ctypes.c_int
+_lib.odp_server_poll.argtypes = [_vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+_lib.odp_server_poll.restype = ctypes.c_int
+_lib.odp_server_flush.argtypes = [_vp]
+_lib.odp_server_flush.restype = ctypes.c_int
+_lib.odp_server_log.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64)]
+_lib.odp_server_log.restype = ctypes.c_int
+_lib.odp_server_origin.argtypes = [_vp, _vp, _vp, ctypes.c_uint64]
+_lib.odp_server_origin.restype = ctypes.c_int
+_lib.odp_server_stats_get.argtypes = [_vp, ctypes.POINTER(ServerStats)]
+_lib.odp_server_stats_get.restype = ctypes.c_int
+_lib.odp_server_destroy.argtypes = [_vp]
+_lib.odp_server_destroy.restype = ctypes.c_int
+
+
+class Server:
+    """Continuous-batching serving loop (odp_server_*)."""
+
+    def __init__(self, device=0, n_slots=4, device_budget_bytes=8 << 30, max_events=1 << 23,
+                 max_batch_events=4096, max_producers=128, watermark_timeout_us=50_000,
+                 batch_interval_us=50):
+        cfg = ServerCfg(device, n_slots, device_budget_bytes, max_events, max_batch_events,
+                        max_producers, watermark_timeout_us, batch_interval_us)
+        h = _vp()
+        _check(_lib.odp_server_create(ctypes.byref(cfg), ctypes.byref(h)), "odp_server_create")
+        self.h = h
+        self.submit_fn = ctypes.cast(_lib.odp_server_submit, _vp).value
+
+    def submit(self, events: np.ndarray, payload_ptrs) -> None:
+        ev = np.ascontiguousarray(events)
+        n = ev.size
+        ptrs = np.ascontiguousarray(np.asarray(payload_ptrs, dtype=np.uint64))
+        _check(_lib.odp_server_submit(self.h, ev.ctypes.data, ptrs.ctypes.data, n),
+               "odp_server_submit")
+
+    def poll(self, cap=1 << 20) -> np.ndarray:
+        out = np.zeros(cap, dtype=FINDING_DTYPE)
+        k = ctypes.c_uint64(0)
+        _check(_lib.odp_server_poll(self.h, out.ctypes.data, cap, ctypes.byref(k)), "odp_server_poll")
+        return out[: k.value].copy()
+
+    def flush(self) -> None:
+        _check(_lib.odp_server_flush(self.h), "odp_server_flush")
+
+    def log(self):
+        p = _vp()
+        n = ctypes.c_uint64(0)
+        _check(_lib.odp_server_log(self.h, ctypes.byref(p), ctypes.byref(n)), "odp_server_log")
+        return int(p.value or 0), int(n.value)
+
+    def origin(self, n):
+        prod = np.zeros(n, dtype=np.uint32)
+        seq = np.zeros(n, dtype=np.uint64)
+        _check(_lib.odp_server_origin(self.h, prod.ctypes.data, seq.ctypes.data, n),
+               "odp_server_origin")
+        return prod, seq
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib.odp_server_stats_get(self.h, ctypes.byref(st)), "odp_server_stats_get")
+        return {k: int(getattr(st, k)) for k, _ in ServerStats._fields_}
+
+    def close(self) -> None:
+        if self.h:
+            _lib.odp_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def log_tensor(server: Server, n: int | None = None) -> torch.Tensor:
+    """The server's resident log as a CUDA byte tensor view (no copy)."""
+    ptr, m = server.log()
+    n = m if n is None else n
+    if n == 0:
+        return torch.empty(64, dtype=torch.uint8, device="cuda")
+    return _wrap_device(ptr, 64 * n)
+
+
+def _wrap_device(ptr: int, nbytes: int) -> torch.Tensor:
+    class _Holder:
+        __cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False),
+                                    "version": 3, "strides": None}
+
+    return torch.as_tensor(_Holder(), device="cuda")
 
 
 # ---------------------------------------------------------------- memory

@@ -15,6 +15,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libodp.so")
 SYNTH_SRC = os.path.join(ROOT, "synth", "gen.cu")
 SYNTH_LIB = os.path.join(ROOT, "synth", "libsynth.so")
+LOADGEN_SRC = os.path.join(ROOT, "synth", "loadgen.cpp")
+LOADGEN_LIB = os.path.join(ROOT, "synth", "libsynth_load.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
@@ -59,6 +61,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(open(os.path.join(PKG, "build.log")).read())
     if force or _stale(SYNTH_LIB, [SYNTH_SRC]):
         _nvcc(SYNTH_LIB, [SYNTH_SRC])
+    if force or _stale(LOADGEN_LIB, [LOADGEN_SRC]):
+        tmp = LOADGEN_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o",
+                               tmp, LOADGEN_SRC])
+        os.replace(tmp, LOADGEN_LIB)
     return LIB
 
 

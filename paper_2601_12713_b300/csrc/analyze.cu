@@ -614,78 +614,31 @@ __global__ void k_ut_next(A a) {
 
 // ------------------------------------------------------------ emission
 
-struct Fnd {
-    uint32_t partner;  // NONE32: not flagged
-    uint64_t bytes, ns;
-};
-
 __device__ __forceinline__ uint64_t dur(const A& a, uint32_t i) { return a.ev.t1(i) - a.ev.t0(i); }
 
-__device__ __forceinline__ Fnd finding_of(const A& a, int kind, uint32_t i) {
-    Fnd f{NONE32, 0, 0};
-    uint32_t p;
+__device__ __forceinline__ uint32_t partner_of(const A& a, int kind, uint32_t i) {
     switch (kind) {
-        case ODP_DD:
-            p = a.dd[i];
-            if (p != NONE32) f = Fnd{p, a.ev.bytes(i), dur(a, i)};
-            break;
-        case ODP_RT:
-            p = a.rt[i];
-            if (p != NONE32) f = Fnd{p, a.ev.bytes(p), dur(a, p)};
-            break;
-        case ODP_RA:
-            p = a.ra[i];
-            if (p != NONE32) f = Fnd{p, a.ev.bytes(i), dur(a, i) + dur(a, a.del_of[i])};
-            break;
-        case ODP_UA:
-            p = a.ua[i];
-            if (p != NONE32) f = Fnd{p, a.ev.bytes(i), dur(a, i) + (p == NOPART ? 0 : dur(a, p))};
-            break;
-        case ODP_UT:
-            p = a.ut[i];
-            if (p != NONE32) f = Fnd{p, a.ev.bytes(i), dur(a, i)};
-            break;
+        case ODP_DD: return a.dd[i];
+        case ODP_RT: return a.rt[i];
+        case ODP_RA: return a.ra[i];
+        case ODP_UA: return a.ua[i];
+        default: return a.ut[i];
     }
-    return f;
 }
 
-// Counts per (kind, block); per-kind totals; site rows; wasted-event marks;
-// pair counts.
+// Counts per (kind, block) from the partner arrays alone, and pair counts.
 __global__ void __launch_bounds__(TPB) k_em_count(A a) {
     if (failed(a)) return;
     const uint32_t base = blockIdx.x * VB;
-    unsigned long long cnt[5] = {0, 0, 0, 0, 0}, by[5] = {0, 0, 0, 0, 0}, ns[5] = {0, 0, 0, 0, 0};
     unsigned long long pairs = 0, unpaired = 0;
     uint32_t bc[5] = {0, 0, 0, 0, 0};
     for (int k = 0; k < 4; ++k) {
         const uint32_t i = base + k * TPB + threadIdx.x;
         bool fl[5] = {false, false, false, false, false};
         if (i < a.n) {
-            if (is_alloc(a, i)) {
+            for (int kind = 1; kind <= 5; ++kind) fl[kind - 1] = partner_of(a, kind, i) != NONE32;
+            if (c_kind(a.cls[i]) == ODP_ALLOC) {
                 if (a.del_of[i] != NONE32) ++pairs; else ++unpaired;
-            }
-            const uint32_t site = a.ev.site(i);
-            for (int kind = 1; kind <= 5; ++kind) {
-                Fnd f = finding_of(a, kind, i);
-                if (f.partner == NONE32) continue;
-                fl[kind - 1] = true;
-                cnt[kind - 1]++;
-                by[kind - 1] += f.bytes;
-                ns[kind - 1] += f.ns;
-                unsigned long long* row = a.sites + 3ull * ((uint64_t)(kind - 1) * ODP_MAX_SITES + site);
-                atomicAdd(row + 0, 1ull);
-                atomicAdd(row + 1, (unsigned long long)f.bytes);
-                atomicAdd(row + 2, (unsigned long long)f.ns);
-                switch (kind) {
-                    case ODP_DD:
-                    case ODP_UT: a.wasted[i] = 1; break;
-                    case ODP_RT: a.wasted[f.partner] = 1; break;
-                    case ODP_RA: a.wasted[i] = 1; a.wasted[a.del_of[i]] = 1; break;
-                    case ODP_UA:
-                        a.wasted[i] = 1;
-                        if (f.partner != NOPART) a.wasted[f.partner] = 1;
-                        break;
-                }
             }
         }
         for (int kind = 0; kind < 5; ++kind) bc[kind] += __syncthreads_count(fl[kind]);
@@ -693,72 +646,170 @@ __global__ void __launch_bounds__(TPB) k_em_count(A a) {
     if (threadIdx.x == 0)
         for (int kind = 0; kind < 5; ++kind) a.bcnt[kind * a.nb + blockIdx.x] = bc[kind];
     for (int d = 16; d > 0; d >>= 1) {
+        pairs += __shfl_xor_sync(ODP_FULL_MASK, pairs, d);
+        unpaired += __shfl_xor_sync(ODP_FULL_MASK, unpaired, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (pairs) atomicAdd(&a.h->n_pairs, pairs);
+        if (unpaired) atomicAdd(&a.h->n_unpaired, unpaired);
+    }
+}
+
+// Site rows are accumulated per block in a shared-memory hash table of
+// (kind, site) keys and flushed to the dense global table once per block;
+// keys that do not fit go straight to global atomics.
+constexpr int SITE_SLOTS = 4096;
+constexpr uint32_t SITE_EMPTY = 0xFFFFFFFFu;
+
+struct SiteSmem {
+    uint32_t key[SITE_SLOTS];
+    uint32_t cnt[SITE_SLOTS];
+    unsigned long long bytes[SITE_SLOTS];
+    unsigned long long ns[SITE_SLOTS];
+};
+
+__device__ __forceinline__ void site_add(SiteSmem& t, const A& a, uint32_t kind0, uint32_t site,
+                                         uint64_t wb, uint64_t wn) {
+    const uint32_t key = kind0 * ODP_MAX_SITES + site;
+    uint32_t slot = (key * 2654435761u) >> (32 - 12);
+    for (int probe = 0; probe < 32; ++probe) {
+        const uint32_t old = atomicCAS(&t.key[slot], SITE_EMPTY, key);
+        if (old == SITE_EMPTY || old == key) {
+            atomicAdd(&t.cnt[slot], 1u);
+            atomicAdd(&t.bytes[slot], (unsigned long long)wb);
+            atomicAdd(&t.ns[slot], (unsigned long long)wn);
+            return;
+        }
+        slot = (slot + 1) & (SITE_SLOTS - 1);
+    }
+    unsigned long long* row = a.sites + 3ull * key;
+    atomicAdd(row + 0, 1ull);
+    atomicAdd(row + 1, (unsigned long long)wb);
+    atomicAdd(row + 2, (unsigned long long)wn);
+}
+
+// Persistent blocks walk event ranges of VB events: every finding is
+// computed once, placed at (kind offset + range offset + rank in event
+// order), added to its site row and to the per-kind totals, and its wasted
+// events are marked.
+__global__ void __launch_bounds__(TPB) k_em_write(A a, const uint32_t* scanned) {
+    if (failed(a)) return;
+    constexpr int W = TPB / 32;
+    __shared__ uint32_t wc[5][W];
+    __shared__ uint32_t run[5];
+    extern __shared__ __align__(16) unsigned char em_dyn[];
+    SiteSmem& st = *reinterpret_cast<SiteSmem*>(em_dyn);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1;
+    odp_finding* items = a.out.items;
+    const uint64_t cap = a.out.capacity;
+    for (int i = threadIdx.x; i < SITE_SLOTS; i += TPB) {
+        st.key[i] = SITE_EMPTY;
+        st.cnt[i] = 0;
+        st.bytes[i] = 0;
+        st.ns[i] = 0;
+    }
+    unsigned long long cnt[5] = {0, 0, 0, 0, 0}, by[5] = {0, 0, 0, 0, 0}, ns[5] = {0, 0, 0, 0, 0};
+    for (uint32_t rg = blockIdx.x; rg < a.nb; rg += gridDim.x) {
+        const uint32_t base = rg * VB;
+        uint32_t off[5];
+        for (int kind = 0; kind < 5; ++kind) off[kind] = scanned[kind * a.nb + rg];
+        if (threadIdx.x < 5) run[threadIdx.x] = 0;
+        __syncthreads();
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t i = base + k * TPB + threadIdx.x;
+            const bool valid = i < a.n;
+            uint32_t part[5];
+            uint32_t bal[5];
+            for (int kind = 0; kind < 5; ++kind) {
+                part[kind] = valid ? partner_of(a, kind + 1, i) : NONE32;
+                bal[kind] = __ballot_sync(ODP_FULL_MASK, part[kind] != NONE32);
+                if (lane == 0) wc[kind][warp] = __popc(bal[kind]);
+            }
+            __syncthreads();
+            if (valid && (bal[0] | bal[1] | bal[2] | bal[3] | bal[4]) & (1u << lane)) {
+                const uint64_t t0 = a.ev.t0(i), t1 = a.ev.t1(i), own_bytes = a.ev.bytes(i);
+                const uint32_t site = a.ev.site(i);
+                for (int kind = 0; kind < 5; ++kind) {
+                    const uint32_t p = part[kind];
+                    if (p == NONE32) continue;
+                    const bool np = p == NOPART;
+                    uint64_t wb = own_bytes, wn = t1 - t0;
+                    switch (kind + 1) {
+                        case ODP_RT:
+                            wb = a.ev.bytes(p);
+                            wn = dur(a, p);
+                            a.wasted[p] = 1;
+                            break;
+                        case ODP_RA: {
+                            const uint32_t d = a.del_of[i];
+                            wn += dur(a, d);
+                            a.wasted[i] = 1;
+                            a.wasted[d] = 1;
+                            break;
+                        }
+                        case ODP_UA:
+                            if (!np) {
+                                wn += dur(a, p);
+                                a.wasted[p] = 1;
+                            }
+                            a.wasted[i] = 1;
+                            break;
+                        default:  // DD, UT
+                            a.wasted[i] = 1;
+                            break;
+                    }
+                    cnt[kind]++;
+                    by[kind] += wb;
+                    ns[kind] += wn;
+                    site_add(st, a, kind, site, wb, wn);
+                    uint64_t pos = (uint64_t)off[kind] + run[kind] + __popc(bal[kind] & lt);
+                    for (int w = 0; w < warp; ++w) pos += wc[kind][w];
+                    if (pos < cap) {
+                        odp_finding o;
+                        o.kind = (uint8_t)(kind + 1);
+                        o.pad0[0] = o.pad0[1] = o.pad0[2] = 0;
+                        o.site = site;
+                        o.partner_site = np ? 0xFFFFFFFFu : a.ev.site(p);
+                        o.pad1 = 0;
+                        o.event = i;
+                        o.partner = np ? ODP_NO_EVENT : (uint64_t)p;
+                        o.wasted_bytes = wb;
+                        o.wasted_ns = wn;
+                        items[pos] = o;
+                    }
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < 5) {
+                uint32_t sum = 0;
+                for (int w = 0; w < W; ++w) sum += wc[threadIdx.x][w];
+                run[threadIdx.x] += sum;
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < SITE_SLOTS; i += TPB) {
+        if (st.key[i] == SITE_EMPTY) continue;
+        unsigned long long* row = a.sites + 3ull * st.key[i];
+        atomicAdd(row + 0, (unsigned long long)st.cnt[i]);
+        atomicAdd(row + 1, st.bytes[i]);
+        atomicAdd(row + 2, st.ns[i]);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
         for (int kind = 0; kind < 5; ++kind) {
             cnt[kind] += __shfl_xor_sync(ODP_FULL_MASK, cnt[kind], d);
             by[kind] += __shfl_xor_sync(ODP_FULL_MASK, by[kind], d);
             ns[kind] += __shfl_xor_sync(ODP_FULL_MASK, ns[kind], d);
         }
-        pairs += __shfl_xor_sync(ODP_FULL_MASK, pairs, d);
-        unpaired += __shfl_xor_sync(ODP_FULL_MASK, unpaired, d);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         for (int kind = 0; kind < 5; ++kind) {
             if (cnt[kind]) {
                 atomicAdd(&a.h->count[kind + 1], cnt[kind]);
                 atomicAdd(&a.h->bytes[kind + 1], by[kind]);
                 atomicAdd(&a.h->ns[kind + 1], ns[kind]);
             }
-        }
-        if (pairs) atomicAdd(&a.h->n_pairs, pairs);
-        if (unpaired) atomicAdd(&a.h->n_unpaired, unpaired);
-    }
-}
-
-__global__ void __launch_bounds__(TPB) k_em_write(A a, const uint32_t* scanned) {
-    if (failed(a)) return;
-    __shared__ uint32_t wc[TPB / 32];
-    __shared__ uint32_t run;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t base = blockIdx.x * VB;
-    odp_finding* items = a.out.items;
-    const uint64_t cap = a.out.capacity;
-    for (int kind = 1; kind <= 5; ++kind) {
-        if (threadIdx.x == 0) run = 0;
-        __syncthreads();
-        const uint32_t off = scanned[(kind - 1) * a.nb + blockIdx.x];
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t i = base + k * TPB + threadIdx.x;
-            Fnd f{NONE32, 0, 0};
-            if (i < a.n) f = finding_of(a, kind, i);
-            const bool fl = f.partner != NONE32;
-            const uint32_t bal = __ballot_sync(ODP_FULL_MASK, fl);
-            if (lane == 0) wc[warp] = __popc(bal);
-            __syncthreads();
-            if (fl) {
-                uint64_t pos = (uint64_t)off + run + __popc(bal & ((1u << lane) - 1));
-                for (int w = 0; w < warp; ++w) pos += wc[w];
-                if (pos < cap) {
-                    odp_finding o;
-                    o.kind = (uint8_t)kind;
-                    o.pad0[0] = o.pad0[1] = o.pad0[2] = 0;
-                    o.site = a.ev.site(i);
-                    const bool np = f.partner == NOPART;
-                    o.partner_site = np ? 0xFFFFFFFFu : a.ev.site(f.partner);
-                    o.pad1 = 0;
-                    o.event = i;
-                    o.partner = np ? ODP_NO_EVENT : (uint64_t)f.partner;
-                    o.wasted_bytes = f.bytes;
-                    o.wasted_ns = f.ns;
-                    items[pos] = o;
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                uint32_t s = 0;
-                for (int w = 0; w < TPB / 32; ++w) s += wc[w];
-                run += s;
-            }
-            __syncthreads();
         }
     }
 }
@@ -1041,7 +1092,14 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     k_em_count<<<nb, TPB, 0, s>>>(a);
     uint32_t* escan = (uint32_t*)(b + o_bscan);
     prim::exclusive_scan(a.bcnt, escan, nullptr, 5 * nb, misc + 0, scan_tmp, s);
-    k_em_write<<<nb, TPB, 0, s>>>(a, escan);
+    static bool em_attr[256] = {};
+    const int dev = current_device();
+    if (dev < 256 && !em_attr[dev]) {
+        ODP_CHECK_CUDA(cudaFuncSetAttribute(k_em_write, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sizeof(SiteSmem)));
+        em_attr[dev] = true;
+    }
+    k_em_write<<<std::min<uint32_t>(nb, (uint32_t)sms * 2), TPB, sizeof(SiteSmem), s>>>(a, escan);
     k_em_saved<<<gX, TPB, 0, s>>>(a);
     k_site_flags<<<grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s>>>(a, sflag);
     prim::exclusive_scan(sflag, spos, nullptr, 5u * ODP_MAX_SITES, misc + 1, scan_tmp, s);

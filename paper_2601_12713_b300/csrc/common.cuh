@@ -26,8 +26,13 @@ enum ScratchSlot {
 };
 
 // Returns a device block of at least `bytes` bytes for (current device,
-// stream, slot), or null with *status = ODP_ERR_OOM.
-void* scratch_get(int slot, size_t bytes, cudaStream_t stream, int* status);
+// stream, slot), or null with *status = ODP_ERR_OOM.  *fresh (if given) is
+// set when the block was just allocated (its contents are undefined).
+void* scratch_get(int slot, size_t bytes, cudaStream_t stream, int* status,
+                  bool* fresh = nullptr);
+
+// Frees the (current device, stream, slot) block (stream-ordered).
+void release_slot(int slot, cudaStream_t stream);
 
 int device_sm_count();       // SMs of the current device
 int current_device();

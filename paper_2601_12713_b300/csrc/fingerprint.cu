@@ -17,8 +17,11 @@
 // 2^m chunks and 32-aligned groups of tile roots give the same root as the
 // plain recursive split.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
+#include "fingerprint.cuh"
 #include "fp128.cuh"
 
 namespace odp {
@@ -36,6 +39,8 @@ struct PlanHeader {
     uint32_t total_tiles;
     uint32_t total_nodes;
     uint32_t tile_counter;
+    uint32_t warps_done;   // warps that left the tile loop (reset by the last one)
+    uint32_t pad;
 };
 
 struct FpArgs {
@@ -52,7 +57,8 @@ struct FpArgs {
     uint32_t* tile_buf;   // cap_tiles
     uint32_t* counters;   // 2 * cap_tiles
     U128* nodes;          // 2 * cap_tiles
-    int32_t* status;      // per-device status word
+    int32_t* status;      // per-device status word (null: not published)
+    uint32_t single;      // 1: one buffer, planned inside fp_tiles
 };
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
@@ -255,9 +261,10 @@ __global__ void __launch_bounds__(256) fp_plan_add(FpArgs a) {
     }
 }
 
-// Tile -> buffer list (binary search over tile offsets) and counter reset.
+// Tile -> buffer list (binary search over tile offsets).  The tree counters
+// need no reset: each group's last arriver sets its counter back to zero.
 __global__ void __launch_bounds__(256) fp_plan_tiles(FpArgs a) {
-    const uint32_t T = a.hdr->total_tiles, N = a.hdr->total_nodes;
+    const uint32_t T = a.hdr->total_tiles;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += stride) {
         // largest i with tile_off[i] <= t and a non-empty range
@@ -268,7 +275,6 @@ __global__ void __launch_bounds__(256) fp_plan_tiles(FpArgs a) {
         }
         a.tile_buf[t] = lo;
     }
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) a.counters[i] = 0;
 }
 
 // --------------------------------------------------------------- tiles
@@ -451,8 +457,29 @@ __global__ void __launch_bounds__(WARPS * 32) fp_tiles(FpArgs a) {
     WarpStack* st = &stacks[warp];
     uint64_t a0, b0;
     fp::lane_init(lane, a0, b0);
-    const uint32_t T = a.hdr->total_tiles;
-    const uint32_t m_floor = a.hdr->m_floor;
+    uint32_t T, m_floor;
+    if (a.single) {
+        // one buffer: the plan is a few integer operations, done by every warp
+        const uint64_t size = a.sizes[0];
+        const bool null_ptr = a.ptrs[0] == nullptr;
+        if (size == 0 || null_ptr) {
+            T = 0;
+            m_floor = 0;
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                U128 e = size == 0 ? fp::empty_input() : U128{0, 0};
+                a.out[0].lo = e.x;
+                a.out[0].hi = e.y;
+                if (size != 0 && a.status) atomicCAS((int*)a.status, 0, ODP_ERR_INVALID_ARG);
+            }
+        } else {
+            const uint64_t nc = n_chunks(size);
+            m_floor = floor_for(nc, a.cap_tiles - 1);
+            T = (uint32_t)n_tiles(nc, tile_log2(nc, a.tmin, m_floor));
+        }
+    } else {
+        T = a.hdr->total_tiles;
+        m_floor = a.hdr->m_floor;
+    }
 
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(&a.hdr->tile_counter, 1u);
@@ -463,7 +490,7 @@ __global__ void __launch_bounds__(WARPS * 32) fp_tiles(FpArgs a) {
         if (lane == 0) t_next = atomicAdd(&a.hdr->tile_counter, 1u);
 
         const uint32_t b = a.n == 1 ? 0u : a.tile_buf[t];
-        const uint32_t tb = t - a.tile_off[b];
+        const uint32_t tb = a.single ? t : t - a.tile_off[b];
         const uint64_t size = a.sizes[b];
         const uint8_t* base = (const uint8_t*)a.ptrs[b];
         const uint64_t nchunk = n_chunks(size);
@@ -486,7 +513,7 @@ __global__ void __launch_bounds__(WARPS * 32) fp_tiles(FpArgs a) {
             }
         } else {
             // climb: level L holds nodes covering span = 2^m * 32^L chunks
-            uint64_t nl = ntile, idx = tb, off = a.node_off[b];
+            uint64_t nl = ntile, idx = tb, off = a.single ? 0 : a.node_off[b];
             uint64_t span = 1ull << m;
             U128 node = root;
             while (true) {
@@ -519,6 +546,7 @@ __global__ void __launch_bounds__(WARPS * 32) fp_tiles(FpArgs a) {
                     const uint64_t first = (32 * g + lane) * span;
                     c = umin64(span, nchunk - first);
                 }
+                if (lane == 0) a.counters[off + nl + g] = 0;  // ready for the next call
                 node = warp_tree(v, c, gsize, lane);
                 off += nl;
                 nl = nup;
@@ -528,27 +556,47 @@ __global__ void __launch_bounds__(WARPS * 32) fp_tiles(FpArgs a) {
         }
         t = __shfl_sync(ODP_FULL_MASK, t_next, 0);
     }
+    // The last warp out resets the tile counter for the next call and
+    // publishes the plan's error code (the first error index is not kept).
+    if (lane == 0) {
+        __threadfence();
+        const uint32_t total = gridDim.x * WARPS;
+        if (atomicAdd(&a.hdr->warps_done, 1u) == total - 1) {
+            a.hdr->tile_counter = 0;
+            a.hdr->warps_done = 0;
+            if (!a.single && a.status) {
+                const unsigned long long e = a.hdr->err;
+                if (e != ~0ull) atomicCAS((int*)a.status, 0, -(int)(e & 0xFF));
+            }
+        }
+    }
 }
-
-// Status word: the first error index is not kept; only the code.
-__global__ void fp_publish_status(const PlanHeader* hdr, int32_t* status) {
-    unsigned long long e = hdr->err;
-    if (e != ~0ull && *status == 0) *status = -(int32_t)(e & 0xFF);
-}
-
-constexpr int TILE_WARPS = 8;
 
 }  // namespace
 
-// Launch parameters picked per call (autotuned elsewhere; defaults here).
-struct FpLaunch {
-    int warps_per_cta = TILE_WARPS;
-    int ctas_per_sm = 0;     // 0: occupancy maximum
-    uint32_t tmin = 0;       // 0: derived from n and the warp count
-};
+template <int W>
+static void fp_tiles_launch(const FpArgs& a, int ctas_per_sm, int sms, cudaStream_t stream) {
+    fp_tiles<W><<<sms * ctas_per_sm, W * 32, 0, stream>>>(a);
+}
 
-static int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128* out,
-                  cudaStream_t stream, const FpLaunch& L) {
+static int fp_occupancy(int warps) {
+    int occ = 0;
+    if (warps == 4)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<4>, 128, 0);
+    else if (warps == 16)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<16>, 512, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<8>, 256, 0);
+    return std::max(1, occ);
+}
+
+// Bytes at the start of each plan scratch block known to be zero (header +
+// tree counters), per block address.
+static std::mutex g_zero_mu;
+static std::map<void*, size_t> g_zeroed;
+
+int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128* out,
+           cudaStream_t stream, const FpLaunch& L) {
     if (n == 0) return ODP_OK;
     if (!ptrs || !sizes || !out) return ODP_ERR_INVALID_ARG;
     if (n > (1ull << 28)) return ODP_ERR_UNSUPPORTED;
@@ -565,15 +613,30 @@ static int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, od
         bytes = align_up(bytes + sz, 256);
         return o;
     };
+    // The header and the tree counters sit at fixed places in front, so a
+    // call with another n finds its counters inside the region earlier calls
+    // left at zero (the last arriver of every group resets its counter).
     size_t o_hdr = carve(sizeof(PlanHeader));
+    size_t o_cnt = carve(sizeof(uint32_t) * 2 * (size_t)cap_tiles);
+    const size_t zero_needed = bytes;
     size_t o_toff = carve(sizeof(uint32_t) * (nn + 1));
     size_t o_noff = carve(sizeof(uint32_t) * (nn + 1));
     size_t o_bsum = carve(sizeof(uint32_t) * 2 * (nblocks + 1));
     size_t o_tbuf = carve(sizeof(uint32_t) * (size_t)cap_tiles);
-    size_t o_cnt = carve(sizeof(uint32_t) * 2 * (size_t)cap_tiles);
     size_t o_nodes = carve(sizeof(U128) * 2 * (size_t)cap_tiles);
-    uint8_t* s = (uint8_t*)scratch_get(SLOT_FP_PLAN, bytes, stream, &st);
+    bool fresh = false;
+    uint8_t* s = (uint8_t*)scratch_get(SLOT_FP_PLAN, bytes, stream, &st, &fresh);
     if (!s) return st;
+    {
+        // extend the zeroed prefix (header + counters) when this call needs more
+        std::lock_guard<std::mutex> lk(g_zero_mu);
+        size_t& z = g_zeroed[s];
+        if (fresh) z = 0;
+        if (z < zero_needed) {
+            ODP_CHECK_CUDA(cudaMemsetAsync(s + z, 0, zero_needed - z, stream));
+            z = zero_needed;
+        }
+    }
 
     const int sms = device_sm_count();
     FpArgs a;
@@ -590,37 +653,48 @@ static int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, od
     a.counters = (uint32_t*)(s + o_cnt);
     a.nodes = (U128*)(s + o_nodes);
     a.status = status;
+    a.single = nn == 1;
 
-    int ctas = L.ctas_per_sm;
-    if (ctas <= 0) {
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<TILE_WARPS>, TILE_WARPS * 32, 0);
-        ctas = std::max(1, occ);
-    }
-    const uint32_t total_warps = (uint32_t)(sms * ctas * TILE_WARPS);
-    a.tmin = L.tmin ? L.tmin : std::max<uint32_t>(1, (uint32_t)(2ull * total_warps / nn));
+    const int W = (L.warps_per_cta == 4 || L.warps_per_cta == 16) ? L.warps_per_cta : TILE_WARPS;
+    const int occ = fp_occupancy(W);
+    const int ctas = L.ctas_per_sm > 0 ? std::min(L.ctas_per_sm, occ) : occ;
+    const uint64_t total_warps = (uint64_t)sms * ctas * W;
+    a.tmin = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(1u << 30,
+                                          (uint64_t)L.tmin_scale * total_warps / nn));
 
-    ODP_CHECK_CUDA(cudaMemsetAsync(a.hdr, 0, sizeof(PlanHeader), stream));
-    ODP_CHECK_CUDA(cudaMemsetAsync(&a.hdr->err, 0xFF, sizeof(unsigned long long), stream));
-    if (nn <= (uint32_t)MAX_SMALL_PLAN) {
-        fp_plan_small<<<1, 1024, 0, stream>>>(a);
-    } else {
-        fp_plan_count<<<nblocks, 256, 0, stream>>>(a);
-        fp_plan_scan<<<nblocks, 256, 0, stream>>>(a);
-        fp_plan_blocks<<<1, 1024, 0, stream>>>(a, nblocks);
-        fp_plan_add<<<nblocks, 256, 0, stream>>>(a);
+    if (!a.single) {
+        ODP_CHECK_CUDA(cudaMemsetAsync(a.hdr, 0, sizeof(PlanHeader), stream));
+        ODP_CHECK_CUDA(cudaMemsetAsync(&a.hdr->err, 0xFF, sizeof(unsigned long long), stream));
+        if (nn <= (uint32_t)MAX_SMALL_PLAN) {
+            fp_plan_small<<<1, 1024, 0, stream>>>(a);
+        } else {
+            fp_plan_count<<<nblocks, 256, 0, stream>>>(a);
+            fp_plan_scan<<<nblocks, 256, 0, stream>>>(a);
+            fp_plan_blocks<<<1, 1024, 0, stream>>>(a, nblocks);
+            fp_plan_add<<<nblocks, 256, 0, stream>>>(a);
+        }
+        fp_plan_tiles<<<sms * 4, 256, 0, stream>>>(a);
     }
-    fp_plan_tiles<<<sms * 4, 256, 0, stream>>>(a);
-    fp_tiles<TILE_WARPS><<<sms * ctas, TILE_WARPS * 32, 0, stream>>>(a);
-    fp_publish_status<<<1, 1, 0, stream>>>(a.hdr, status);
-    return cuda_status(cudaGetLastError());
+    if (W == 4) fp_tiles_launch<4>(a, ctas, sms, stream);
+    else if (W == 16) fp_tiles_launch<16>(a, ctas, sms, stream);
+    else fp_tiles_launch<8>(a, ctas, sms, stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        {
+            std::lock_guard<std::mutex> lk(g_zero_mu);
+            g_zeroed.erase(s);
+        }
+        release_slot(SLOT_FP_PLAN, stream);  // counters may be left set
+        return ODP_ERR_CUDA;
+    }
+    return ODP_OK;
 }
 
 }  // namespace odp
 
 extern "C" int odp_fingerprint(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
                                odp_fp128* out128, cudaStream_t stream) {
-    odp::FpLaunch L;
+    odp::FpLaunch L = odp::fp_schedule_for(n);
     return odp::fp_run(ptrs, sizes, n, out128, stream, L);
 }
 
@@ -700,6 +774,7 @@ static int fp_run_noalloc(const void* const* ptrs, const uint64_t* sizes, uint64
     a.counters = (uint32_t*)(s + NA_O_CNT);
     a.nodes = (U128*)(s + NA_O_NODES);
     a.status = nullptr;
+    a.single = 0;
 
     const int sms = device_sm_count();
     int occ = 0;

@@ -11,6 +11,9 @@
 
 namespace odp {
 namespace prim {
+// Every translation unit that includes this header gets its own copy of the
+// kernels (internal linkage).
+namespace {
 
 constexpr uint32_t NONE32 = 0xFFFFFFFFu;
 
@@ -279,5 +282,6 @@ __device__ __forceinline__ uint32_t table_insert_min(const Table& t, uint32_t ca
     return NONE32;
 }
 
+}  // namespace
 }  // namespace prim
 }  // namespace odp

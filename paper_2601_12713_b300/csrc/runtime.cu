@@ -77,11 +77,13 @@ int device_sm_count() {
     return n;
 }
 
-void* scratch_get(int slot, size_t bytes, cudaStream_t stream, int* status) {
+void* scratch_get(int slot, size_t bytes, cudaStream_t stream, int* status, bool* fresh) {
     int d = current_device();
     std::lock_guard<std::mutex> lk(g_mu);
     Block& b = g_blocks[std::make_tuple(d, stream, slot)];
+    if (fresh) *fresh = false;
     if (b.ptr && b.bytes >= bytes) return b.ptr;
+    if (fresh) *fresh = true;
     if (b.ptr) raw_free(b.ptr, stream);  // stream-ordered after earlier uses
     b.ptr = nullptr;
     b.bytes = 0;
@@ -94,6 +96,15 @@ void* scratch_get(int slot, size_t bytes, cudaStream_t stream, int* status) {
     b.ptr = p;
     b.bytes = want;
     return p;
+}
+
+void release_slot(int slot, cudaStream_t stream) {
+    int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_blocks.find(std::make_tuple(d, stream, slot));
+    if (it == g_blocks.end()) return;
+    raw_free(it->second.ptr, stream);
+    g_blocks.erase(it);
 }
 
 int32_t* device_status_word(int* status) {
@@ -127,6 +138,7 @@ const char* odp_status_string(int status) {
         case ODP_ERR_MALFORMED: return "ODP_ERR_MALFORMED";
         case ODP_ERR_UNSORTED: return "ODP_ERR_UNSORTED";
         case ODP_ERR_UNSUPPORTED: return "ODP_ERR_UNSUPPORTED";
+        case ODP_ERR_MISMATCH: return "ODP_ERR_MISMATCH";
         default: return "ODP_UNKNOWN_STATUS";
     }
 }

@@ -1,0 +1,707 @@
+// server.cu -- continuous-batching serving loop over mapping events.
+//
+// Producers (any host threads) submit events as they happen.  A batcher
+// thread merges them in start-time order behind a watermark (the smallest
+// last start time among producers that submitted recently), cuts batches and
+// runs each through a slot: the payloads of its transfers are fingerprinted
+// on the slot's own stream (slots overlap), then, in order on the analysis
+// stream, the batch is appended to the log resident in device memory and the
+// duplicate-transfer (Alg. 1) and round-trip (Alg. 2) state kept in device
+// tables is updated.  Findings are copied to pinned host memory and handed to
+// the poll queue with their latency.
+//
+// Streaming Alg. 1: table <fingerprint> -> first log index (content id) and
+// table <content id, destination> -> first receiver persist across batches;
+// log indices grow with time, so the minimum is the first ever.
+// Streaming Alg. 2 (content groups with at most two endpoints): a transfer
+// from A pairs with the first later reception of its content at A.  Inside
+// a batch that is the next run of destinations in the batch's content-sorted
+// transfers; transfers left unpaired wait in a per-<content id, endpoint>
+// list, which the first reception at that endpoint in a later batch closes.
+// Groups that ever show a third endpoint stop streaming round trips; their
+// exact result comes from odp_analyze over the log.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "fingerprint.cuh"
+#include "prims.cuh"
+
+namespace odp {
+namespace {
+
+using prim::Key128;
+using prim::NONE32;
+using prim::Table;
+
+uint64_t now_ns() {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+constexpr uint32_t EP_MORE = 1u << 16;  // endpoint set: more than two endpoints
+
+struct SrvDev {
+    odp_event* log;
+    uint32_t* cid;     // per log index (transfers)
+    uint32_t* next;    // pending-list links, per log index
+    Table t_fp, t_dd, t_pend, t_ep, t_b;
+};
+
+struct SlotDev {
+    odp_event* ev;         // batch events (staged from host)
+    const void** ptrs;     // payload pointers of the batch's transfers
+    uint64_t* sizes;
+    odp_fp128* fp;
+    uint32_t* xpos;        // batch position of each transfer
+    uint32_t* nx;          // number of transfers (device copy)
+    uint32_t* sfp;         // per batch position: slot in t_fp / t_dd / t_b
+    uint32_t* sdd;
+    uint32_t* sb;
+    uint32_t* skeys;       // content-sorted transfers (key, value) + alternates
+    uint32_t* svals;
+    prim::SortTmp sort;
+    odp_finding* find;     // streamed findings of the batch
+    uint64_t* complete;    // log index of the event that completed each finding
+    uint32_t* nfind;
+};
+
+__device__ __forceinline__ uint32_t ep_of(int8_t dev) { return (uint32_t)(dev + 1) & 0xFF; }
+
+__device__ __forceinline__ bool is_xfer(uint8_t k) {
+    return k == ODP_TO_DEV || k == ODP_FROM_DEV || k == ODP_DEV_TO_DEV;
+}
+
+__device__ __forceinline__ void emit(const SlotDev& s, uint32_t cap, const odp_event* log,
+                                     uint8_t kind, uint64_t e, uint64_t p, uint64_t wasted_of,
+                                     uint64_t completing) {
+    const uint32_t j = atomicAdd(s.nfind, 1u);
+    if (j >= cap) return;
+    odp_finding f;
+    f.kind = kind;
+    f.pad0[0] = f.pad0[1] = f.pad0[2] = 0;
+    f.site = log[e].site_id;
+    f.partner_site = log[p].site_id;
+    f.pad1 = 0;
+    f.event = e;
+    f.partner = p;
+    f.wasted_bytes = log[wasted_of].bytes;
+    f.wasted_ns = log[wasted_of].t_end_ns - log[wasted_of].t_start_ns;
+    s.find[j] = f;
+    s.complete[j] = completing;
+}
+
+// Fingerprints into the batch's transfer records.
+__global__ void srv_scatter_fp(SlotDev s) {
+    const uint32_t nx = *s.nx;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nx; j += gridDim.x * blockDim.x) {
+        odp_event& e = s.ev[s.xpos[j]];
+        e.fp_lo = s.fp[j].lo;
+        e.fp_hi = s.fp[j].hi;
+    }
+}
+
+// Content ids: insert <fingerprint> with the log index.
+__global__ void srv_insert_fp(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
+    const uint32_t cap = *d.t_fp.cap_dev;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+        const odp_event& e = d.log[g0 + q];
+        s.sfp[q] = is_xfer(e.kind) ? prim::table_insert_min(d.t_fp, cap, Key128{e.fp_lo, e.fp_hi},
+                                                            (uint32_t)(g0 + q))
+                                   : NONE32;
+    }
+}
+
+// cid; first-receiver and batch-first-receiver tables; endpoint sets.
+__global__ void srv_insert_dd(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
+    const uint32_t cap_dd = *d.t_dd.cap_dev, cap_b = *d.t_b.cap_dev, cap_ep = *d.t_ep.cap_dev;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+        const uint64_t g = g0 + q;
+        const odp_event& e = d.log[g];
+        if (!is_xfer(e.kind) || s.sfp[q] == NONE32) {
+            s.sdd[q] = s.sb[q] = NONE32;
+            continue;
+        }
+        const uint32_t cid = d.t_fp.vals[s.sfp[q]];
+        d.cid[g] = cid;
+        const Key128 k{(uint64_t)cid | ((uint64_t)ep_of(e.dst_dev) << 32), 0};
+        s.sdd[q] = prim::table_insert_min(d.t_dd, cap_dd, k, (uint32_t)g);
+        s.sb[q] = prim::table_insert_min(d.t_b, cap_b, k, (uint32_t)g);
+        // endpoint set of the content group: up to two endpoints, then "more"
+        const uint32_t es = prim::table_insert_min(d.t_ep, cap_ep, Key128{cid, 1}, NONE32);
+        if (es == NONE32) continue;
+        for (uint32_t ep : {ep_of(e.src_dev), ep_of(e.dst_dev)}) {
+            uint32_t cur = d.t_ep.vals[es];
+            for (int it = 0; it < 64; ++it) {  // bounded CAS loop
+                uint32_t a = cur == NONE32 ? 0 : cur;
+                const uint32_t e1 = a & 0xFF, e2 = (a >> 8) & 0xFF;
+                const uint32_t v = ep + 1;
+                uint32_t nxt;
+                if (a & EP_MORE || e1 == v || e2 == v) break;
+                if (e1 == 0) nxt = a | v;
+                else if (e2 == 0) nxt = a | (v << 8);
+                else nxt = a | EP_MORE;
+                const uint32_t old = atomicCAS(&d.t_ep.vals[es], cur, nxt);
+                if (old == cur) break;
+                cur = old;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ bool complex_group(const SrvDev& d, uint32_t cid) {
+    const uint32_t cap = *d.t_ep.cap_dev;
+    const uint32_t es = prim::table_insert_min(d.t_ep, cap, Key128{cid, 1}, NONE32);
+    const uint32_t v = es == NONE32 ? EP_MORE : d.t_ep.vals[es];
+    return v != NONE32 && (v & EP_MORE);
+}
+
+// Duplicate transfers, and the first reception of each group at each
+// endpoint in this batch closes the round trips waiting for it.
+__global__ void srv_dd_resolve(SrvDev d, SlotDev s, uint64_t g0, uint32_t m, uint32_t cap,
+                               uint64_t max_events) {
+    const uint32_t cap_pend = *d.t_pend.cap_dev;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+        if (s.sdd[q] == NONE32) continue;
+        const uint64_t g = g0 + q;
+        const uint32_t first = d.t_dd.vals[s.sdd[q]];
+        if (first != (uint32_t)g) emit(s, cap, d.log, ODP_DD, g, first, g, g);
+        if (d.t_b.vals[s.sb[q]] != (uint32_t)g) continue;  // not the batch's first here
+        const uint32_t cid = d.cid[g];
+        if (complex_group(d, cid)) continue;
+        const Key128 k{(uint64_t)cid | ((uint64_t)ep_of(d.log[g].dst_dev) << 32), 2};
+        const uint32_t ps = prim::table_insert_min(d.t_pend, cap_pend, k, NONE32);
+        if (ps == NONE32) continue;
+        uint32_t e = atomicExch(&d.t_pend.vals[ps], NONE32);
+        for (uint64_t guard = 0; e != NONE32 && guard < max_events; ++guard) {
+            emit(s, cap, d.log, ODP_RT, e, g, g, g);
+            e = d.next[e];
+        }
+    }
+}
+
+// Sort keys: content id of each transfer, value = batch position.
+__global__ void srv_sort_keys(SrvDev d, SlotDev s, uint64_t g0) {
+    const uint32_t nx = *s.nx;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nx; j += gridDim.x * blockDim.x) {
+        const uint32_t q = s.xpos[j];
+        s.skeys[j] = d.cid[g0 + q];
+        s.svals[j] = q;
+    }
+}
+
+// In-batch round trips on the content-sorted transfers: the partner of a
+// transfer is the first event of the next destination run of its group;
+// transfers without one wait in the group's list for their source.
+__global__ void srv_rt_batch(SrvDev d, SlotDev s, uint64_t g0, uint32_t cap) {
+    const uint32_t nx = *s.nx;
+    const uint32_t cap_pend = *d.t_pend.cap_dev;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nx; r += gridDim.x * blockDim.x) {
+        const uint32_t cid = s.skeys[r];
+        if (complex_group(d, cid)) continue;
+        const uint64_t g = g0 + s.svals[r];
+        const uint32_t dst = ep_of(d.log[g].dst_dev);
+        uint32_t t = r + 1;
+        while (t < nx && s.skeys[t] == cid && ep_of(d.log[g0 + s.svals[t]].dst_dev) == dst) ++t;
+        if (t < nx && s.skeys[t] == cid) {
+            const uint64_t p = g0 + s.svals[t];
+            emit(s, cap, d.log, ODP_RT, g, p, p, p);
+        } else {
+            const Key128 k{(uint64_t)cid | ((uint64_t)ep_of(d.log[g].src_dev) << 32), 2};
+            const uint32_t ps = prim::table_insert_min(d.t_pend, cap_pend, k, NONE32);
+            if (ps == NONE32) continue;
+            const uint32_t old = atomicExch(&d.t_pend.vals[ps], (uint32_t)g);
+            d.next[g] = old;
+        }
+    }
+}
+
+__global__ void srv_zero(uint32_t* p) { *p = 0; }
+
+struct Pending {
+    odp_event ev;
+    const void* payload;
+    uint64_t submit_ns;
+    uint64_t seq;
+};
+
+struct Producer {
+    std::deque<Pending> q;
+    uint64_t last_t = 0;
+    uint64_t last_seen = 0;
+    uint64_t seq = 0;
+};
+
+struct Slot {
+    SlotDev d;
+    odp_event* h_ev = nullptr;
+    const void** h_ptrs = nullptr;
+    uint64_t* h_sizes = nullptr;
+    uint32_t* h_xpos = nullptr;
+    uint32_t* h_nx = nullptr;
+    odp_finding* h_find = nullptr;
+    uint64_t* h_complete = nullptr;
+    uint32_t* h_nfind = nullptr;
+    cudaStream_t fp_stream = nullptr;
+    cudaEvent_t fp_done = nullptr, an_done = nullptr;
+    bool busy = false;
+    uint64_t g0 = 0;
+    uint32_t m = 0;
+};
+
+}  // namespace
+}  // namespace odp
+
+struct odp_server {
+    odp_server_cfg cfg;
+    std::mutex mu;
+    std::map<std::thread::id, uint32_t> producer_of;
+    std::vector<odp::Producer> producers;
+    std::thread batcher;
+    std::atomic<bool> stop{false};
+    std::atomic<bool> flushing{false};
+    std::condition_variable cv_done;
+    uint64_t submitted = 0;
+    uint64_t released_t = 0;
+    // device
+    odp::SrvDev d;
+    std::vector<void*> dev_blocks;
+    cudaStream_t an_stream = nullptr;
+    std::vector<odp::Slot> slots;
+    uint32_t find_cap = 0;
+    // host bookkeeping (guarded by mu)
+    uint64_t n_log = 0;       // events released into the log
+    uint64_t n_done = 0;      // events whose batch completed
+    std::vector<uint64_t> submit_ns;
+    std::vector<uint32_t> origin_prod;
+    std::vector<uint64_t> origin_seq;
+    std::deque<odp::Pending> ready;
+    std::deque<uint32_t> ready_prod;
+    std::deque<odp_finding> outq;
+    std::vector<uint64_t> latencies;
+    uint64_t batches = 0, streamed = 0, late = 0, first_submit = 0, last_done = 0;
+    int error = ODP_OK;
+};
+
+namespace odp {
+namespace {
+
+uint32_t pow2_at_least(uint64_t v) {
+    uint64_t c = 1024;
+    while (c < v) c <<= 1;
+    return (uint32_t)c;
+}
+
+int alloc_dev(odp_server* s, void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return ODP_ERR_OOM;
+    }
+    s->dev_blocks.push_back(*p);
+    return ODP_OK;
+}
+
+int make_table(odp_server* s, Table& t, uint32_t cap, uint32_t* cap_dev, cudaStream_t st) {
+    t.cap_max = cap;
+    t.cap_dev = cap_dev;
+    int rc = alloc_dev(s, (void**)&t.keys, sizeof(Key128) * ((size_t)cap + 1));
+    if (rc) return rc;
+    rc = alloc_dev(s, (void**)&t.vals, 4ull * ((size_t)cap + 1));
+    if (rc) return rc;
+    prim::table_clear<<<256, 256, 0, st>>>(t, nullptr, cap / 2);
+    return ODP_OK;
+}
+
+void launch_batch(odp_server* S, Slot& sl) {
+    const uint32_t m = sl.m;
+    cudaStream_t fs = sl.fp_stream, as = S->an_stream;
+    uint32_t nx = 0;
+    for (uint32_t q = 0; q < m; ++q) {
+        const uint8_t k = sl.h_ev[q].kind;
+        if (k == ODP_TO_DEV || k == ODP_FROM_DEV || k == ODP_DEV_TO_DEV) sl.h_xpos[nx++] = q;
+    }
+    for (uint32_t j = 0; j < nx; ++j) {
+        sl.h_sizes[j] = sl.h_ev[sl.h_xpos[j]].bytes;
+    }
+    *sl.h_nx = nx;
+    cudaMemcpyAsync(sl.d.ev, sl.h_ev, sizeof(odp_event) * m, cudaMemcpyHostToDevice, fs);
+    cudaMemcpyAsync(sl.d.ptrs, sl.h_ptrs, sizeof(void*) * nx, cudaMemcpyHostToDevice, fs);
+    cudaMemcpyAsync(sl.d.sizes, sl.h_sizes, 8ull * nx, cudaMemcpyHostToDevice, fs);
+    cudaMemcpyAsync(sl.d.xpos, sl.h_xpos, 4ull * nx, cudaMemcpyHostToDevice, fs);
+    cudaMemcpyAsync(sl.d.nx, sl.h_nx, 4, cudaMemcpyHostToDevice, fs);
+    if (nx) {
+        FpLaunch L = fp_schedule_for(nx);
+        if (fp_run((const void* const*)sl.d.ptrs, sl.d.sizes, nx, sl.d.fp, fs, L) != ODP_OK)
+            S->error = ODP_ERR_CUDA;
+        srv_scatter_fp<<<64, 256, 0, fs>>>(sl.d);
+    }
+    cudaEventRecord(sl.fp_done, fs);
+
+    // analysis, in batch order on one stream
+    cudaStreamWaitEvent(as, sl.fp_done, 0);
+    const uint64_t g0 = sl.g0;
+    cudaMemcpyAsync(S->d.log + g0, sl.d.ev, sizeof(odp_event) * m, cudaMemcpyDeviceToDevice, as);
+    srv_zero<<<1, 1, 0, as>>>(sl.d.nfind);
+    const int grid = (int)std::min<uint32_t>(1024, (m + 255) / 256);
+    prim::table_clear<<<64, 256, 0, as>>>(S->d.t_b, nullptr, m);
+    srv_insert_fp<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
+    srv_insert_dd<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
+    srv_dd_resolve<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m, S->find_cap, S->cfg.max_events);
+    srv_sort_keys<<<grid, 256, 0, as>>>(S->d, sl.d, g0);
+    prim::radix_sort(sl.d.skeys, sl.d.svals, sl.d.nx, S->cfg.max_batch_events,
+                     prim::bit_length(S->cfg.max_events), sl.d.sort, as);
+    srv_rt_batch<<<grid, 256, 0, as>>>(S->d, sl.d, g0, S->find_cap);
+    cudaMemcpyAsync(sl.h_nfind, sl.d.nfind, 4, cudaMemcpyDeviceToHost, as);
+    cudaMemcpyAsync(sl.h_find, sl.d.find, sizeof(odp_finding) * S->find_cap,
+                    cudaMemcpyDeviceToHost, as);
+    cudaMemcpyAsync(sl.h_complete, sl.d.complete, 8ull * S->find_cap, cudaMemcpyDeviceToHost, as);
+    cudaEventRecord(sl.an_done, as);
+    if (cudaGetLastError() != cudaSuccess) S->error = ODP_ERR_CUDA;
+}
+
+// Moves releasable events into the ready queue in merged order (mu held).
+void release_locked(odp_server* S, uint64_t now) {
+    uint64_t wm = ~0ull;
+    const bool all = S->flushing.load();
+    const uint64_t timeout = (uint64_t)S->cfg.watermark_timeout_us * 1000ull;
+    if (!all) {
+        for (auto& p : S->producers) {
+            if (now - p.last_seen > timeout && p.q.empty()) continue;  // silent producer
+            wm = std::min(wm, p.last_t);
+        }
+    }
+    // k-way merge of the queue prefixes with t_start <= wm
+    while (true) {
+        int best = -1;
+        uint64_t bt = 0;
+        for (size_t i = 0; i < S->producers.size(); ++i) {
+            auto& q = S->producers[i].q;
+            if (q.empty() || q.front().ev.t_start_ns > wm) continue;
+            if (best < 0 || q.front().ev.t_start_ns < bt) {
+                best = (int)i;
+                bt = q.front().ev.t_start_ns;
+            }
+        }
+        if (best < 0) break;
+        Pending p = S->producers[best].q.front();
+        S->producers[best].q.pop_front();
+        if (p.ev.t_start_ns < S->released_t) ++S->late;
+        S->released_t = std::max(S->released_t, p.ev.t_start_ns);
+        S->ready.push_back(p);
+        S->ready_prod.push_back((uint32_t)best);
+    }
+}
+
+void harvest(odp_server* S, Slot& sl) {
+    const uint64_t t = now_ns();
+    const uint32_t n = std::min(*sl.h_nfind, S->find_cap);
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (uint32_t j = 0; j < n; ++j) {
+        S->outq.push_back(sl.h_find[j]);
+        const uint64_t c = sl.h_complete[j];
+        if (c < S->submit_ns.size()) S->latencies.push_back(t - S->submit_ns[c]);
+    }
+    S->streamed += n;
+    S->n_done += sl.m;
+    S->last_done = t;
+    ++S->batches;
+    sl.busy = false;
+    S->cv_done.notify_all();
+}
+
+void batcher_main(odp_server* S) {
+    cudaSetDevice(S->cfg.device);
+    const uint32_t B = S->cfg.max_batch_events;
+    while (true) {
+        bool idle = true;
+        for (auto& sl : S->slots) {
+            if (sl.busy && cudaEventQuery(sl.an_done) == cudaSuccess) {
+                harvest(S, sl);
+                idle = false;
+            }
+        }
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            release_locked(S, now_ns());
+            for (auto& sl : S->slots) {
+                if (S->ready.empty()) break;
+                if (sl.busy) continue;
+                const uint32_t m = (uint32_t)std::min<size_t>(B, S->ready.size());
+                sl.g0 = S->n_log;
+                sl.m = m;
+                uint32_t nx = 0;
+                for (uint32_t q = 0; q < m; ++q) {
+                    const Pending& p = S->ready.front();
+                    sl.h_ev[q] = p.ev;
+                    const uint8_t k = p.ev.kind;
+                    if (k == ODP_TO_DEV || k == ODP_FROM_DEV || k == ODP_DEV_TO_DEV)
+                        sl.h_ptrs[nx++] = p.payload;
+                    S->submit_ns[S->n_log] = p.submit_ns;
+                    S->origin_prod[S->n_log] = S->ready_prod.front();
+                    S->origin_seq[S->n_log] = p.seq;
+                    ++S->n_log;
+                    S->ready.pop_front();
+                    S->ready_prod.pop_front();
+                }
+                sl.busy = true;
+                lk.unlock();
+                launch_batch(S, sl);
+                lk.lock();
+                idle = false;
+            }
+            if (S->stop.load() && S->ready.empty()) {
+                bool any = false;
+                for (auto& sl : S->slots) any |= sl.busy;
+                bool queued = false;
+                for (auto& p : S->producers) queued |= !p.q.empty();
+                if (!any && !queued) break;
+            }
+        }
+        if (idle) std::this_thread::sleep_for(std::chrono::microseconds(S->cfg.batch_interval_us));
+    }
+}
+
+}  // namespace
+}  // namespace odp
+
+extern "C" {
+
+int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
+    using namespace odp;
+    if (!cfg || !out) return ODP_ERR_INVALID_ARG;
+    if (cfg->n_slots < 1 || cfg->max_events == 0 || cfg->max_batch_events == 0 ||
+        cfg->max_producers == 0 || cfg->max_events >= 0xFFFFFFF0ull)
+        return ODP_ERR_INVALID_ARG;
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return ODP_ERR_CUDA;
+    const uint64_t E = cfg->max_events, B = cfg->max_batch_events;
+    const uint32_t cap_p = pow2_at_least(2 * E), cap_b = pow2_at_least(2 * B);
+    const uint64_t find_cap = 2 * B + 64;
+    // device bytes: log + per-event arrays + four persistent tables + slots
+    const uint64_t per_table = (16 + 4) * ((uint64_t)cap_p + 1);
+    const uint64_t slot_bytes = B * (64 + 8 + 8 + 16 + 4 + 12 + 16 + 16) + 256ull * (B / 4096 + 2) * 4 +
+                                find_cap * (48 + 8) + (20ull << 20) + (46ull << 20);
+    const uint64_t need = E * (64 + 8) + 4 * per_table + (16 + 4) * ((uint64_t)cap_b + 1) +
+                          (uint64_t)cfg->n_slots * slot_bytes;
+    if (cfg->device_budget_bytes && need > cfg->device_budget_bytes) return ODP_ERR_OOM;
+
+    odp_server* S = new odp_server();
+    S->cfg = *cfg;
+    S->find_cap = (uint32_t)find_cap;
+    auto fail = [&](int rc) {
+        odp_server_destroy(S);
+        return rc;
+    };
+    if (cudaStreamCreateWithFlags(&S->an_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(ODP_ERR_CUDA);
+    uint32_t* caps = nullptr;
+    int rc = alloc_dev(S, (void**)&caps, 64);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.log, sizeof(odp_event) * E);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.cid, 4 * E);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.next, 4 * E);
+    if (!rc) rc = make_table(S, S->d.t_fp, cap_p, caps + 0, S->an_stream);
+    if (!rc) rc = make_table(S, S->d.t_dd, cap_p, caps + 1, S->an_stream);
+    if (!rc) rc = make_table(S, S->d.t_pend, cap_p, caps + 2, S->an_stream);
+    if (!rc) rc = make_table(S, S->d.t_ep, cap_p, caps + 3, S->an_stream);
+    if (!rc) rc = make_table(S, S->d.t_b, cap_b, caps + 4, S->an_stream);
+    if (rc) return fail(rc);
+    S->slots.resize(cfg->n_slots);
+    for (auto& sl : S->slots) {
+        SlotDev& d = sl.d;
+        rc = alloc_dev(S, (void**)&d.ev, sizeof(odp_event) * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.ptrs, 8 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.sizes, 8 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.fp, 16 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.xpos, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.nx, 16);
+        if (!rc) rc = alloc_dev(S, (void**)&d.sfp, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.sdd, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.sb, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.skeys, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.svals, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.sort.keys_alt, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.sort.vals_alt, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.sort.hist, 4 * prim::sort_hist_words((uint32_t)B));
+        if (!rc)
+            rc = alloc_dev(S, (void**)&d.sort.scan_tmp,
+                           4 * (prim::scan_tmp_words(256u * ((uint32_t)B / prim::SORT_TILE + 2)) + 16));
+        if (!rc) rc = alloc_dev(S, (void**)&d.find, sizeof(odp_finding) * find_cap);
+        if (!rc) rc = alloc_dev(S, (void**)&d.complete, 8 * find_cap);
+        if (!rc) rc = alloc_dev(S, (void**)&d.nfind, 16);
+        if (rc) return fail(rc);
+        if (cudaHostAlloc((void**)&sl.h_ev, sizeof(odp_event) * B, 0) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.h_ptrs, 8 * B, 0) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.h_sizes, 8 * B, 0) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.h_xpos, 4 * B, 0) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.h_nx, 16, 0) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.h_find, sizeof(odp_finding) * find_cap, 0) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.h_complete, 8 * find_cap, 0) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.h_nfind, 16, 0) != cudaSuccess)
+            return fail(ODP_ERR_OOM);
+        if (cudaStreamCreateWithFlags(&sl.fp_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.fp_done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.an_done, cudaEventDisableTiming) != cudaSuccess)
+            return fail(ODP_ERR_CUDA);
+    }
+    if (cudaStreamSynchronize(S->an_stream) != cudaSuccess) return fail(ODP_ERR_CUDA);
+    S->submit_ns.assign(E, 0);
+    S->origin_prod.assign(E, 0);
+    S->origin_seq.assign(E, 0);
+    S->batcher = std::thread(odp::batcher_main, S);
+    *out = S;
+    return ODP_OK;
+}
+
+int odp_server_submit(odp_server* S, const odp_event* ev, const void* const* payloads,
+                      uint64_t n) {
+    if (!S || (n && (!ev || !payloads))) return ODP_ERR_INVALID_ARG;
+    if (n == 0) return ODP_OK;
+    const uint64_t t = odp::now_ns();
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->submitted + n > S->cfg.max_events) return ODP_ERR_UNSUPPORTED;
+    auto id = std::this_thread::get_id();
+    auto it = S->producer_of.find(id);
+    uint32_t p;
+    if (it == S->producer_of.end()) {
+        if (S->producers.size() >= S->cfg.max_producers) return ODP_ERR_UNSUPPORTED;
+        p = (uint32_t)S->producers.size();
+        S->producer_of[id] = p;
+        S->producers.emplace_back();
+    } else {
+        p = it->second;
+    }
+    odp::Producer& pr = S->producers[p];
+    if (!S->first_submit) S->first_submit = t;
+    for (uint64_t i = 0; i < n; ++i) {
+        odp::Pending q;
+        q.ev = ev[i];
+        q.payload = payloads[i];
+        q.submit_ns = t;
+        q.seq = pr.seq++;
+        pr.last_t = std::max(pr.last_t, ev[i].t_start_ns);
+        pr.q.push_back(q);
+    }
+    pr.last_seen = t;
+    S->submitted += n;
+    return ODP_OK;
+}
+
+int odp_server_poll(odp_server* S, odp_finding* out, uint64_t cap, uint64_t* n_out) {
+    if (!S || !n_out || (cap && !out)) return ODP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    uint64_t k = 0;
+    while (k < cap && !S->outq.empty()) {
+        out[k++] = S->outq.front();
+        S->outq.pop_front();
+    }
+    *n_out = k;
+    return S->error;
+}
+
+int odp_server_flush(odp_server* S) {
+    if (!S) return ODP_ERR_INVALID_ARG;
+    S->flushing = true;
+    std::unique_lock<std::mutex> lk(S->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::minutes(10);
+    while (S->n_done < S->submitted) {
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+            S->flushing = false;
+            return ODP_ERR_TIMEOUT;
+        }
+    }
+    S->flushing = false;
+    return S->error;
+}
+
+int odp_server_log(odp_server* S, const odp_event** dev_log, uint64_t* n) {
+    if (!S || !dev_log || !n) return ODP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *dev_log = S->d.log;
+    *n = S->n_done;
+    return ODP_OK;
+}
+
+int odp_server_origin(odp_server* S, uint32_t* producer, uint64_t* seq, uint64_t n) {
+    if (!S || !producer || !seq) return ODP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (n > S->n_log) return ODP_ERR_INVALID_ARG;
+    for (uint64_t i = 0; i < n; ++i) {
+        producer[i] = S->origin_prod[i];
+        seq[i] = S->origin_seq[i];
+    }
+    return ODP_OK;
+}
+
+int odp_server_stats_get(odp_server* S, odp_server_stats* st) {
+    if (!S || !st) return ODP_ERR_INVALID_ARG;
+    std::vector<uint64_t> lat;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        st->events_submitted = S->submitted;
+        st->events_processed = S->n_done;
+        st->batches = S->batches;
+        st->findings_streamed = S->streamed;
+        st->late_events = S->late;
+        st->first_submit_ns = S->first_submit;
+        st->last_done_ns = S->last_done;
+        lat = S->latencies;
+    }
+    std::sort(lat.begin(), lat.end());
+    auto pct = [&](double q) -> uint64_t {
+        if (lat.empty()) return 0;
+        size_t i = (size_t)(q * (double)(lat.size() - 1) + 0.5);
+        return lat[std::min(i, lat.size() - 1)];
+    };
+    st->latency_p50_ns = pct(0.50);
+    st->latency_p99_ns = pct(0.99);
+    st->latency_max_ns = lat.empty() ? 0 : lat.back();
+    // groups with more than two endpoints (counted on the device table)
+    st->rt_groups_unstreamed = 0;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->n_done > 0 && S->d.t_ep.vals) {
+            const uint32_t cap = S->d.t_ep.cap_max;
+            std::vector<uint32_t> v((size_t)cap + 1);
+            if (cudaMemcpy(v.data(), S->d.t_ep.vals, 4ull * (cap + 1), cudaMemcpyDeviceToHost) ==
+                cudaSuccess)
+                for (uint32_t x : v)
+                    if (x != odp::prim::NONE32 && (x & odp::EP_MORE)) ++st->rt_groups_unstreamed;
+        }
+    }
+    return ODP_OK;
+}
+
+int odp_server_destroy(odp_server* S) {
+    if (!S) return ODP_ERR_INVALID_ARG;
+    S->stop = true;
+    S->flushing = true;
+    if (S->batcher.joinable()) S->batcher.join();
+    cudaSetDevice(S->cfg.device);
+    if (S->an_stream) cudaStreamSynchronize(S->an_stream);
+    for (auto& sl : S->slots) {
+        if (sl.fp_stream) {
+            cudaStreamSynchronize(sl.fp_stream);
+            odp::release_slot(odp::SLOT_FP_PLAN, sl.fp_stream);
+            cudaStreamSynchronize(sl.fp_stream);
+            cudaStreamDestroy(sl.fp_stream);
+        }
+        if (sl.fp_done) cudaEventDestroy(sl.fp_done);
+        if (sl.an_done) cudaEventDestroy(sl.an_done);
+        for (void* h : {(void*)sl.h_ev, (void*)sl.h_ptrs, (void*)sl.h_sizes, (void*)sl.h_xpos,
+                        (void*)sl.h_nx, (void*)sl.h_find, (void*)sl.h_complete, (void*)sl.h_nfind})
+            if (h) cudaFreeHost(h);
+    }
+    for (void* p : S->dev_blocks) cudaFree(p);
+    if (S->an_stream) cudaStreamDestroy(S->an_stream);
+    delete S;
+    return ODP_OK;
+}
+
+}  // extern "C"
