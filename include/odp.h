@@ -275,7 +275,7 @@ typedef struct odp_summary {
 
 /* Output description for odp_analyze.  All pointers are device pointers. */
 typedef struct odp_findings {
-    odp_finding* items;        /* capacity entries */
+    odp_finding* items;        /* capacity entries, 16-byte aligned */
     uint64_t capacity;
     uint64_t* count;           /* total findings (may exceed capacity) */
     odp_site_row* sites;       /* sites_capacity rows */
@@ -287,7 +287,8 @@ typedef struct odp_findings {
 
 /*
  * odp_analyze -- Algorithms 1-5 of Sec. 5 over n events (device memory,
- * chronological: t_start_ns nondecreasing, array index breaks ties).
+ * 16-byte aligned, else ODP_ERR_INVALID_ARG; chronological: t_start_ns
+ * nondecreasing, array index breaks ties).
  *
  * Findings are written ordered by (kind, event index).  If the total
  * exceeds out->capacity the first `capacity` are written, *count still holds
@@ -337,7 +338,8 @@ typedef struct odp_server_cfg {
  * finding to the poll queue). */
 typedef struct odp_server_stats {
     uint64_t events_submitted, events_processed, batches, findings_streamed;
-    uint64_t late_events;           /* events behind the released watermark */
+    uint64_t late_events;           /* events behind the released watermark
+                                       (they break the log's order) */
     uint64_t latency_p50_ns, latency_p99_ns, latency_max_ns;
     uint64_t first_submit_ns, last_done_ns;  /* steady-clock stamps */
     uint64_t rt_groups_unstreamed;  /* content groups with > 2 endpoints */
@@ -346,6 +348,15 @@ typedef struct odp_server_stats {
 /* Creates a server and allocates all of its device memory up front
  * (ODP_ERR_OOM if that exceeds device_budget_bytes or the device). */
 int odp_server_create(const odp_server_cfg* cfg, odp_server** out);
+
+/*
+ * Registers the calling thread as a producer before its first event.  Until
+ * the thread submits, the merge watermark does not pass start_t_ns, so its
+ * first events cannot fall behind events already released from other
+ * threads.  A thread that submits without attaching is registered by its
+ * first submit (and may then see its first events counted as late).
+ */
+int odp_server_attach(odp_server* s, uint64_t start_t_ns);
 
 /*
  * Thread-safe.  Submits n events (host memory, 64-byte records).  For

@@ -247,6 +247,8 @@ _lib.odp_server_create.argtypes = [ctypes.POINTER(ServerCfg), ctypes.POINTER(_vp
 _lib.odp_server_create.restype = ctypes.c_int
 _lib.odp_server_submit.argtypes = [_vp, _vp, _vp, ctypes.c_uint64]
 _lib.odp_server_submit.restype = ctypes.c_int
+_lib.odp_server_attach.argtypes = [_vp, ctypes.c_uint64]
+_lib.odp_server_attach.restype = ctypes.c_int
 _lib.odp_server_poll.argtypes = [_vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
 _lib.odp_server_poll.restype = ctypes.c_int
 _lib.odp_server_flush.argtypes = [_vp]
@@ -273,6 +275,10 @@ class Server:
         _check(_lib.odp_server_create(ctypes.byref(cfg), ctypes.byref(h)), "odp_server_create")
         self.h = h
         self.submit_fn = ctypes.cast(_lib.odp_server_submit, _vp).value
+        self.attach_fn = ctypes.cast(_lib.odp_server_attach, _vp).value
+
+    def attach(self, start_t_ns: int = 0) -> None:
+        _check(_lib.odp_server_attach(self.h, start_t_ns), "odp_server_attach")
 
     def submit(self, events: np.ndarray, payload_ptrs) -> None:
         ev = np.ascontiguousarray(events)

@@ -106,10 +106,9 @@ __device__ __forceinline__ bool failed(const A& a) { return a.h->err != NO_ERR; 
 
 // ------------------------------------------------------------ validate
 
-__device__ __forceinline__ bool record_ok(const Ev& ev, uint32_t i, uint32_t& cls) {
-    const uint64_t t0 = ev.t0(i), t1 = ev.t1(i), by = ev.bytes(i);
-    const uint32_t site = ev.site(i);
-    const uint32_t w = *(const uint32_t*)(ev.p + 64ull * i + 60);
+// Record checks on the fields of one event (loaded as three 16-byte words).
+__device__ __forceinline__ bool record_ok(uint64_t t0, uint64_t t1, uint64_t by, uint32_t site,
+                                          uint32_t w, uint32_t& cls) {
     const int kind = w & 0xFF;
     const int src = (int8_t)((w >> 8) & 0xFF), dst = (int8_t)((w >> 16) & 0xFF);
     cls = (uint32_t)kind | ((uint32_t)(src + 1) & 0xFF) << 8 | ((uint32_t)(dst + 1) & 0xFF) << 16;
@@ -127,18 +126,32 @@ __device__ __forceinline__ bool record_ok(const Ev& ev, uint32_t i, uint32_t& cl
 
 __global__ void __launch_bounds__(TPB) k_validate(A a) {
     const uint32_t base = blockIdx.x * VB;
+    const int lane = threadIdx.x & 31;
     unsigned long long tmax = 0;
     uint32_t nallocs = 0, ndels = 0;
     for (int k = 0; k < 4; ++k) {
         const uint32_t i = base + k * TPB + threadIdx.x;
         bool isX = false, isP = false, isK = false, isU = false;
+        uint64_t t0 = 0;
+        uint4 q0 = make_uint4(0, 0, 0, 0), q2 = q0, q3 = q0;
         if (i < a.n) {
+            const uint4* r = reinterpret_cast<const uint4*>(a.ev.p + 64ull * i);
+            q0 = __ldg(r);
+            q2 = __ldg(r + 2);
+            q3 = __ldg(r + 3);
+            t0 = ((uint64_t)q0.y << 32) | q0.x;
+        }
+        // start time of the previous event: the neighbour lane's, or a load
+        uint64_t prev = __shfl_up_sync(ODP_FULL_MASK, t0, 1);
+        if (i < a.n) {
+            if (lane == 0 && i > 0) prev = a.ev.t0(i - 1);
+            const uint64_t t1 = ((uint64_t)q0.w << 32) | q0.z;
+            const uint64_t by = ((uint64_t)q2.y << 32) | q2.x;
             uint32_t c;
-            bool ok = record_ok(a.ev, i, c);
-            if (!ok) {
+            if (!record_ok(t0, t1, by, q3.z, q3.w, c)) {
                 record_error(&a.h->err, i, ODP_ERR_MALFORMED);
                 c = 0;
-            } else if (i > 0 && a.ev.t0(i) < a.ev.t0(i - 1)) {
+            } else if (i > 0 && t0 < prev) {
                 record_error(&a.h->err, i, ODP_ERR_UNSORTED);
             }
             a.cls[i] = c;
@@ -149,7 +162,7 @@ __global__ void __launch_bounds__(TPB) k_validate(A a) {
             isU = kd == ODP_TO_DEV;
             nallocs += kd == ODP_ALLOC;
             ndels += kd == ODP_DELETE;
-            tmax = max(tmax, (unsigned long long)a.ev.t1(i));
+            tmax = max(tmax, (unsigned long long)t1);
         }
         uint32_t cx = __syncthreads_count(isX), cp = __syncthreads_count(isP);
         uint32_t ck = __syncthreads_count(isK), cu = __syncthreads_count(isU);
@@ -249,27 +262,6 @@ __global__ void k_x_cid(A a) {
     }
 }
 
-__global__ void k_x_insert_dd(A a) {
-    if (failed(a)) return;
-    const uint32_t cap = *a.tab.cap_dev;
-    GRID_STRIDE(j, a.h->nX) {
-        const uint32_t e = a.sv[j];
-        const uint64_t dst1 = c_dst(a.cls[e]);
-        Key128 key{(uint64_t)a.sk[j] | (dst1 << 32), 0};
-        a.slot[j] = prim::table_insert_min(a.tab, cap, key, e);
-    }
-}
-
-__global__ void k_x_dd(A a) {
-    if (failed(a)) return;
-    GRID_STRIDE(j, a.h->nX) {
-        const uint32_t e = a.sv[j];
-        const uint32_t s = a.slot[j];
-        const uint32_t first = s == NONE32 ? e : a.tab.vals[s];
-        if (first != e) a.dd[e] = first;
-    }
-}
-
 // ------------------------------------------------------------- Alg. 2
 
 __global__ void k_rt_flags(A a) {
@@ -313,18 +305,26 @@ __global__ void k_rt_check(A a) {
 
 // Two endpoints: a transfer pairs with the first event of the next run of
 // its content group (the next run receives at the other endpoint, which is
-// the transfer's source).
+// the transfer's source).  Alg. 1 comes from the same order: the first
+// receiver of <content, destination> is the group head when the destination
+// matches the head's, else the start of the group's second run.
 __global__ void k_rt_partner(A a) {
     if (failed(a)) return;
     const uint32_t nrun = a.h->nrun;
     GRID_STRIDE(q, a.h->nX) {
         const uint32_t s = a.id1[q] + a.f1[q] - 1;
         if (a.bad[s]) continue;
+        const uint32_t e = a.sv[q];
         const uint32_t r = a.id2[q] + a.f2[q] - 1;
         if (r + 1 < nrun) {
             const uint32_t q2 = a.R[r + 1];
-            if (!a.f1[q2]) a.rt[a.sv[q]] = a.sv[q2];
+            if (!a.f1[q2]) a.rt[e] = a.sv[q2];
         }
+        const uint32_t h = a.H[s];
+        uint32_t first;
+        if (c_dst(a.cls[e]) == c_dst(a.cls[a.sv[h]])) first = a.sv[h];
+        else first = a.sv[a.R[a.id2[h] + 1]];
+        if (first != e) a.dd[e] = first;
     }
 }
 
@@ -337,13 +337,20 @@ __global__ void k_rt_literal(A a) {
     GRID_STRIDE(s, nseg) {
         if (!a.bad[s]) continue;
         const uint32_t lo = a.H[s], hi = a.H[s + 1];
-        uint32_t cnt[NDEV], pops[NDEV], front[NDEV];
+        uint32_t cnt[NDEV], pops[NDEV], front[NDEV], first_rx[NDEV];
         for (int d = 0; d < NDEV; ++d) {
             cnt[d] = 0;
             pops[d] = 0;
             front[d] = NONE32;
+            first_rx[d] = NONE32;
         }
-        for (uint32_t q = lo; q < hi; ++q) cnt[c_dst(a.cls[a.sv[q]])]++;
+        for (uint32_t q = lo; q < hi; ++q) {
+            // Alg. 1 for this group: the first receiver of each destination
+            const uint32_t e = a.sv[q], d = c_dst(a.cls[e]);
+            cnt[d]++;
+            if (first_rx[d] == NONE32) first_rx[d] = e;
+            else a.dd[e] = first_rx[d];
+        }
         for (uint32_t q = lo; q < hi; ++q) {
             const uint32_t e = a.sv[q];
             const uint32_t c = a.cls[e];
@@ -626,30 +633,30 @@ __device__ __forceinline__ uint32_t partner_of(const A& a, int kind, uint32_t i)
     }
 }
 
-// Counts per (kind, block) from the partner arrays alone, and pair counts.
-__global__ void __launch_bounds__(TPB) k_em_count(A a) {
+// Findings per (kind, 32-event chunk) from the partner arrays alone, and
+// pair counts; one warp per chunk.
+__global__ void k_em_count(A a, uint32_t* wcnt, uint32_t nch) {
     if (failed(a)) return;
-    const uint32_t base = blockIdx.x * VB;
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     unsigned long long pairs = 0, unpaired = 0;
-    uint32_t bc[5] = {0, 0, 0, 0, 0};
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t i = base + k * TPB + threadIdx.x;
-        bool fl[5] = {false, false, false, false, false};
-        if (i < a.n) {
-            for (int kind = 1; kind <= 5; ++kind) fl[kind - 1] = partner_of(a, kind, i) != NONE32;
-            if (c_kind(a.cls[i]) == ODP_ALLOC) {
-                if (a.del_of[i] != NONE32) ++pairs; else ++unpaired;
-            }
+    for (uint32_t c = gw; c < nch; c += nw) {
+        const uint32_t i = c * 32 + lane;
+        const bool valid = i < a.n;
+        for (int kind = 1; kind <= 5; ++kind) {
+            const uint32_t bal = __ballot_sync(ODP_FULL_MASK, valid && partner_of(a, kind, i) != NONE32);
+            if (lane == 0) wcnt[(kind - 1) * nch + c] = __popc(bal);
         }
-        for (int kind = 0; kind < 5; ++kind) bc[kind] += __syncthreads_count(fl[kind]);
+        if (valid && c_kind(a.cls[i]) == ODP_ALLOC) {
+            if (a.del_of[i] != NONE32) ++pairs; else ++unpaired;
+        }
     }
-    if (threadIdx.x == 0)
-        for (int kind = 0; kind < 5; ++kind) a.bcnt[kind * a.nb + blockIdx.x] = bc[kind];
     for (int d = 16; d > 0; d >>= 1) {
         pairs += __shfl_xor_sync(ODP_FULL_MASK, pairs, d);
         unpaired += __shfl_xor_sync(ODP_FULL_MASK, unpaired, d);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         if (pairs) atomicAdd(&a.h->n_pairs, pairs);
         if (unpaired) atomicAdd(&a.h->n_unpaired, unpaired);
     }
@@ -688,108 +695,85 @@ __device__ __forceinline__ void site_add(SiteSmem& t, const A& a, uint32_t kind0
     atomicAdd(row + 2, (unsigned long long)wn);
 }
 
-// Persistent blocks walk event ranges of VB events: every finding is
-// computed once, placed at (kind offset + range offset + rank in event
-// order), added to its site row and to the per-kind totals, and its wasted
-// events are marked.
-__global__ void __launch_bounds__(TPB) k_em_write(A a, const uint32_t* scanned) {
+// Persistent blocks; each warp walks 32-event chunks on its own: every
+// finding is computed once, placed at (scanned chunk offset of its kind +
+// rank in the chunk), added to the block's site table and the per-kind
+// totals, and its wasted events are marked.  No block barrier inside the loop.
+constexpr int EMW_THREADS = 512;
+
+__global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* wscan, uint32_t nch) {
     if (failed(a)) return;
-    constexpr int W = TPB / 32;
-    __shared__ uint32_t wc[5][W];
-    __shared__ uint32_t run[5];
     extern __shared__ __align__(16) unsigned char em_dyn[];
     SiteSmem& st = *reinterpret_cast<SiteSmem*>(em_dyn);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1;
     odp_finding* items = a.out.items;
     const uint64_t cap = a.out.capacity;
-    for (int i = threadIdx.x; i < SITE_SLOTS; i += TPB) {
+    for (int i = threadIdx.x; i < SITE_SLOTS; i += blockDim.x) {
         st.key[i] = SITE_EMPTY;
         st.cnt[i] = 0;
         st.bytes[i] = 0;
         st.ns[i] = 0;
     }
+    __syncthreads();
     unsigned long long cnt[5] = {0, 0, 0, 0, 0}, by[5] = {0, 0, 0, 0, 0}, ns[5] = {0, 0, 0, 0, 0};
-    for (uint32_t rg = blockIdx.x; rg < a.nb; rg += gridDim.x) {
-        const uint32_t base = rg * VB;
-        uint32_t off[5];
-        for (int kind = 0; kind < 5; ++kind) off[kind] = scanned[kind * a.nb + rg];
-        if (threadIdx.x < 5) run[threadIdx.x] = 0;
-        __syncthreads();
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t i = base + k * TPB + threadIdx.x;
-            const bool valid = i < a.n;
-            uint32_t part[5];
-            uint32_t bal[5];
-            for (int kind = 0; kind < 5; ++kind) {
-                part[kind] = valid ? partner_of(a, kind + 1, i) : NONE32;
-                bal[kind] = __ballot_sync(ODP_FULL_MASK, part[kind] != NONE32);
-                if (lane == 0) wc[kind][warp] = __popc(bal[kind]);
-            }
-            __syncthreads();
-            if (valid && (bal[0] | bal[1] | bal[2] | bal[3] | bal[4]) & (1u << lane)) {
-                const uint64_t t0 = a.ev.t0(i), t1 = a.ev.t1(i), own_bytes = a.ev.bytes(i);
-                const uint32_t site = a.ev.site(i);
-                for (int kind = 0; kind < 5; ++kind) {
-                    const uint32_t p = part[kind];
-                    if (p == NONE32) continue;
-                    const bool np = p == NOPART;
-                    uint64_t wb = own_bytes, wn = t1 - t0;
-                    switch (kind + 1) {
-                        case ODP_RT:
-                            wb = a.ev.bytes(p);
-                            wn = dur(a, p);
-                            a.wasted[p] = 1;
-                            break;
-                        case ODP_RA: {
-                            const uint32_t d = a.del_of[i];
-                            wn += dur(a, d);
-                            a.wasted[i] = 1;
-                            a.wasted[d] = 1;
-                            break;
-                        }
-                        case ODP_UA:
-                            if (!np) {
-                                wn += dur(a, p);
-                                a.wasted[p] = 1;
-                            }
-                            a.wasted[i] = 1;
-                            break;
-                        default:  // DD, UT
-                            a.wasted[i] = 1;
-                            break;
-                    }
-                    cnt[kind]++;
-                    by[kind] += wb;
-                    ns[kind] += wn;
-                    site_add(st, a, kind, site, wb, wn);
-                    uint64_t pos = (uint64_t)off[kind] + run[kind] + __popc(bal[kind] & lt);
-                    for (int w = 0; w < warp; ++w) pos += wc[kind][w];
-                    if (pos < cap) {
-                        odp_finding o;
-                        o.kind = (uint8_t)(kind + 1);
-                        o.pad0[0] = o.pad0[1] = o.pad0[2] = 0;
-                        o.site = site;
-                        o.partner_site = np ? 0xFFFFFFFFu : a.ev.site(p);
-                        o.pad1 = 0;
-                        o.event = i;
-                        o.partner = np ? ODP_NO_EVENT : (uint64_t)p;
-                        o.wasted_bytes = wb;
-                        o.wasted_ns = wn;
-                        items[pos] = o;
-                    }
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = gw; c < nch; c += nw) {
+        const uint32_t i = c * 32 + lane;
+        const bool valid = i < a.n;
+        uint32_t part[5];
+        uint32_t bal[5];
+        uint32_t any = 0;
+        for (int kind = 0; kind < 5; ++kind) {
+            part[kind] = valid ? partner_of(a, kind + 1, i) : NONE32;
+            bal[kind] = __ballot_sync(ODP_FULL_MASK, part[kind] != NONE32);
+            any |= bal[kind];
+        }
+        if (!(any & (1u << lane))) continue;
+        const uint64_t t0 = a.ev.t0(i), t1 = a.ev.t1(i), own_bytes = a.ev.bytes(i);
+        const uint32_t site = a.ev.site(i);
+        for (int kind = 0; kind < 5; ++kind) {
+            const uint32_t p = part[kind];
+            if (p == NONE32) continue;
+            const bool np = p == NOPART;
+            uint64_t wb = own_bytes, wn = t1 - t0;
+            switch (kind + 1) {
+                case ODP_RT:
+                    wb = a.ev.bytes(p);
+                    wn = dur(a, p);
+                    a.wasted[p] = 1;
+                    break;
+                case ODP_RA: {
+                    const uint32_t d = a.del_of[i];
+                    wn += dur(a, d);
+                    a.wasted[i] = 1;
+                    a.wasted[d] = 1;
+                    break;
                 }
+                case ODP_UA:
+                    if (!np) {
+                        wn += dur(a, p);
+                        a.wasted[p] = 1;
+                    }
+                    a.wasted[i] = 1;
+                    break;
+                default:  // DD, UT
+                    a.wasted[i] = 1;
+                    break;
             }
-            __syncthreads();
-            if (threadIdx.x < 5) {
-                uint32_t sum = 0;
-                for (int w = 0; w < W; ++w) sum += wc[threadIdx.x][w];
-                run[threadIdx.x] += sum;
-            }
-            __syncthreads();
+            cnt[kind]++;
+            by[kind] += wb;
+            ns[kind] += wn;
+            site_add(st, a, kind, site, wb, wn);
+            const uint64_t pos = (uint64_t)wscan[kind * nch + c] + __popc(bal[kind] & lt);
+            if (pos < cap)
+                store_finding(items, pos, kind + 1, site, np ? 0xFFFFFFFFu : a.ev.site(p), i,
+                              np ? ODP_NO_EVENT : (uint64_t)p, wb, wn);
         }
     }
-    for (int i = threadIdx.x; i < SITE_SLOTS; i += TPB) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < SITE_SLOTS; i += blockDim.x) {
         if (st.key[i] == SITE_EMPTY) continue;
         unsigned long long* row = a.sites + 3ull * st.key[i];
         atomicAdd(row + 0, (unsigned long long)st.cnt[i]);
@@ -904,8 +888,10 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     const odp_findings out = *outp;
     if (!out.count || !out.sites_count || !out.summary || !out.status) return ODP_ERR_INVALID_ARG;
     if (out.capacity > 0 && !out.items) return ODP_ERR_INVALID_ARG;
+    if (((uintptr_t)out.items & 15) != 0) return ODP_ERR_INVALID_ARG;  // 16-byte stores
     if (out.sites_capacity > 0 && !out.sites) return ODP_ERR_INVALID_ARG;
     if (n64 > 0 && !events) return ODP_ERR_INVALID_ARG;
+    if (((uintptr_t)events & 15) != 0) return ODP_ERR_INVALID_ARG;  // records are read as 16-byte words
     if (n64 >= 0xFFFFFFF0ull) return ODP_ERR_UNSUPPORTED;
     if (n64 == 0) {
         k_empty_outputs<<<1, 1, 0, s>>>(out);
@@ -931,6 +917,9 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     const size_t o_cls = carve(N4);
     const size_t o_bcnt = carve(4ull * (5 * nb + 2));
     const size_t o_bscan = carve(4ull * (5 * nb + 2));
+    const uint32_t nch = (n + 31) / 32;
+    const size_t o_wcnt = carve(4ull * (5ull * nch + 2));
+    const size_t o_wscan = carve(4ull * (5ull * nch + 2));
     const size_t o_X = carve(N4), o_P = carve(N4), o_K = carve(N4), o_U = carve(N4);
     const size_t o_part = carve(6 * N4);  // dd rt ra ua ut del_of
     const size_t o_wasted = carve(n + 16);
@@ -1036,9 +1025,6 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nX, n);
     k_x_insert_fp<<<gX, TPB, 0, s>>>(a);
     k_x_cid<<<gX, TPB, 0, s>>>(a);
-    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nX, n);
-    k_x_insert_dd<<<gX, TPB, 0, s>>>(a);
-    k_x_dd<<<gX, TPB, 0, s>>>(a);
 
     // ---- Alg. 2
     prim::radix_sort(a.sk, a.sv, nX, n, bits_n, srt, s);
@@ -1089,9 +1075,10 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     k_ut_next<<<gX, TPB, 0, s>>>(a);
 
     // ---- emission
-    k_em_count<<<nb, TPB, 0, s>>>(a);
-    uint32_t* escan = (uint32_t*)(b + o_bscan);
-    prim::exclusive_scan(a.bcnt, escan, nullptr, 5 * nb, misc + 0, scan_tmp, s);
+    uint32_t* wcnt = (uint32_t*)(b + o_wcnt);
+    uint32_t* wscan = (uint32_t*)(b + o_wscan);
+    k_em_count<<<sms * 8, 256, 0, s>>>(a, wcnt, nch);
+    prim::exclusive_scan(wcnt, wscan, nullptr, 5 * nch, misc + 0, scan_tmp, s);
     static bool em_attr[256] = {};
     const int dev = current_device();
     if (dev < 256 && !em_attr[dev]) {
@@ -1099,7 +1086,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
                                             (int)sizeof(SiteSmem)));
         em_attr[dev] = true;
     }
-    k_em_write<<<std::min<uint32_t>(nb, (uint32_t)sms * 2), TPB, sizeof(SiteSmem), s>>>(a, escan);
+    k_em_write<<<sms * 2, EMW_THREADS, sizeof(SiteSmem), s>>>(a, wscan, nch);
     k_em_saved<<<gX, TPB, 0, s>>>(a);
     k_site_flags<<<grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s>>>(a, sflag);
     prim::exclusive_scan(sflag, spos, nullptr, 5u * ODP_MAX_SITES, misc + 1, scan_tmp, s);

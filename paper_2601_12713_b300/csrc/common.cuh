@@ -59,6 +59,21 @@ __device__ __forceinline__ uint64_t shfl_down64(uint64_t v, int d) {
     return __shfl_down_sync(ODP_FULL_MASK, v, d);
 }
 
+// A finding record written as three aligned 16-byte words (the record type
+// is byte-packed, so a plain struct store would be split into byte stores).
+// `items` must be 16-byte aligned.
+__device__ __forceinline__ void store_finding(odp_finding* items, uint64_t pos, uint32_t kind,
+                                              uint32_t site, uint32_t partner_site,
+                                              uint64_t event, uint64_t partner,
+                                              uint64_t wasted_bytes, uint64_t wasted_ns) {
+    uint4* d = reinterpret_cast<uint4*>(items) + 3 * pos;
+    d[0] = make_uint4(kind, site, partner_site, 0u);
+    d[1] = make_uint4((uint32_t)event, (uint32_t)(event >> 32), (uint32_t)partner,
+                      (uint32_t)(partner >> 32));
+    d[2] = make_uint4((uint32_t)wasted_bytes, (uint32_t)(wasted_bytes >> 32),
+                      (uint32_t)wasted_ns, (uint32_t)(wasted_ns >> 32));
+}
+
 // Records the first (lowest-index) device error: packs (index, code) so that
 // atomicMin keeps the smallest index.  code is the negated status (1..127).
 __device__ __forceinline__ void record_error(unsigned long long* word, uint64_t index, int status) {

@@ -85,17 +85,8 @@ __device__ __forceinline__ void emit(const SlotDev& s, uint32_t cap, const odp_e
                                      uint64_t completing) {
     const uint32_t j = atomicAdd(s.nfind, 1u);
     if (j >= cap) return;
-    odp_finding f;
-    f.kind = kind;
-    f.pad0[0] = f.pad0[1] = f.pad0[2] = 0;
-    f.site = log[e].site_id;
-    f.partner_site = log[p].site_id;
-    f.pad1 = 0;
-    f.event = e;
-    f.partner = p;
-    f.wasted_bytes = log[wasted_of].bytes;
-    f.wasted_ns = log[wasted_of].t_end_ns - log[wasted_of].t_start_ns;
-    s.find[j] = f;
+    store_finding(s.find, j, kind, log[e].site_id, log[p].site_id, e, p, log[wasted_of].bytes,
+                  log[wasted_of].t_end_ns - log[wasted_of].t_start_ns);
     s.complete[j] = completing;
 }
 
@@ -559,6 +550,35 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     return ODP_OK;
 }
 
+namespace {
+// Index of the calling thread's producer, registering it if needed (mu held).
+int producer_index_locked(odp_server* S, uint32_t* p) {
+    auto id = std::this_thread::get_id();
+    auto it = S->producer_of.find(id);
+    if (it != S->producer_of.end()) {
+        *p = it->second;
+        return ODP_OK;
+    }
+    if (S->producers.size() >= S->cfg.max_producers) return ODP_ERR_UNSUPPORTED;
+    *p = (uint32_t)S->producers.size();
+    S->producer_of[id] = *p;
+    S->producers.emplace_back();
+    return ODP_OK;
+}
+}  // namespace
+
+int odp_server_attach(odp_server* S, uint64_t start_t_ns) {
+    if (!S) return ODP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    uint32_t p;
+    int rc = producer_index_locked(S, &p);
+    if (rc) return rc;
+    odp::Producer& pr = S->producers[p];
+    pr.last_t = std::max(pr.last_t, start_t_ns);
+    pr.last_seen = odp::now_ns();
+    return ODP_OK;
+}
+
 int odp_server_submit(odp_server* S, const odp_event* ev, const void* const* payloads,
                       uint64_t n) {
     if (!S || (n && (!ev || !payloads))) return ODP_ERR_INVALID_ARG;
@@ -566,17 +586,9 @@ int odp_server_submit(odp_server* S, const odp_event* ev, const void* const* pay
     const uint64_t t = odp::now_ns();
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->submitted + n > S->cfg.max_events) return ODP_ERR_UNSUPPORTED;
-    auto id = std::this_thread::get_id();
-    auto it = S->producer_of.find(id);
     uint32_t p;
-    if (it == S->producer_of.end()) {
-        if (S->producers.size() >= S->cfg.max_producers) return ODP_ERR_UNSUPPORTED;
-        p = (uint32_t)S->producers.size();
-        S->producer_of[id] = p;
-        S->producers.emplace_back();
-    } else {
-        p = it->second;
-    }
+    int rc = producer_index_locked(S, &p);
+    if (rc) return rc;
     odp::Producer& pr = S->producers[p];
     if (!S->first_submit) S->first_submit = t;
     for (uint64_t i = 0; i < n; ++i) {

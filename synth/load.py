@@ -20,7 +20,8 @@ def lib():
                                          ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
                                          ctypes.c_uint64, ctypes.c_uint64]
         so.synth_load_create.restype = ctypes.c_void_p
-        so.synth_load_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        so.synth_load_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]
         so.synth_load_run.restype = ctypes.c_int64
         so.synth_load_payload.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
                                           ctypes.POINTER(ctypes.c_uint64),
@@ -44,7 +45,7 @@ class Load:
                                          pool_bytes, min_payload, max_payload)
 
     def run(self, server) -> int:
-        return int(lib().synth_load_run(self.h, server.h, server.submit_fn))
+        return int(lib().synth_load_run(self.h, server.h, server.submit_fn, server.attach_fn))
 
     def payload(self, thread, seq):
         off, size = ctypes.c_uint64(), ctypes.c_uint64()

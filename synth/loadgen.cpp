@@ -29,6 +29,7 @@ static_assert(sizeof(Event) == 64, "64-byte record");
 enum { ALLOC = 1, TO_DEV = 2, FROM_DEV = 3, DELETE = 5, KERNEL = 6 };
 
 typedef int (*submit_fn)(void* server, const void* events, const void* const* payloads, uint64_t n);
+typedef int (*attach_fn)(void* server, uint64_t start_t_ns);
 
 struct Rng {
     uint64_t s, i = 0;
@@ -73,7 +74,8 @@ struct Gen {
     std::vector<Thread> th;
 };
 
-void producer(Gen* g, uint32_t k, void* server, submit_fn submit, std::atomic<bool>* go) {
+void producer(Gen* g, uint32_t k, void* server, submit_fn submit, attach_fn attach,
+              std::atomic<bool>* go, std::atomic<uint32_t>* ready) {
     const Cfg& c = g->cfg;
     Thread& T = g->th[k];
     Rng r(c.seed ^ (0x5EED0000ull + k) * 0xD1342543DE82EF95ull);
@@ -92,6 +94,9 @@ void producer(Gen* g, uint32_t k, void* server, submit_fn submit, std::atomic<bo
         uint64_t off = (uint64_t)(r.uniform() * (double)span) & ~15ull;
         return View{off, size};
     };
+    // register before the first event so the server's merge waits for us
+    if (attach && attach(server, 0) < 0) T.rc = -1;
+    ready->fetch_add(1);
     while (!go->load()) std::this_thread::yield();
     const uint64_t t_begin = now_ns();
     const uint64_t t_stop = t_begin + (uint64_t)(c.seconds * 1e9);
@@ -186,12 +191,14 @@ void* synth_load_create(uint32_t n_threads, double events_per_s, double seconds,
 
 // Runs all producer threads to completion; returns the number of events
 // submitted, or a negative submit status.
-int64_t synth_load_run(void* h, void* server, void* submit) {
+int64_t synth_load_run(void* h, void* server, void* submit, void* attach) {
     Gen* g = (Gen*)h;
     std::atomic<bool> go{false};
+    std::atomic<uint32_t> ready{0};
     std::vector<std::thread> ts;
     for (uint32_t k = 0; k < g->cfg.n_threads; ++k)
-        ts.emplace_back(producer, g, k, server, (submit_fn)submit, &go);
+        ts.emplace_back(producer, g, k, server, (submit_fn)submit, (attach_fn)attach, &go, &ready);
+    while (ready.load() < g->cfg.n_threads) std::this_thread::yield();
     go = true;
     for (auto& t : ts) t.join();
     int64_t total = 0;

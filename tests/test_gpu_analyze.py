@@ -174,3 +174,13 @@ def test_unmatched_and_nested_pairs(cuda_ok, orc, odp):
     bld.add(A, 10, dst=0, host_addr=0x30, dev_addr=0x200, nbytes=8)
     g = check(odp, orc, with_fp(bld.done()))
     assert g["summary"]["n_unmatched_deletes"] == 1
+
+
+def test_misaligned_events_rejected(cuda_ok, odp):
+    ev = with_fp(traces.listing2(3))
+    raw = torch.zeros(ev.size * 64 + 16, dtype=torch.uint8, device="cuda")
+    raw[8:8 + ev.size * 64] = torch.from_numpy(ev.view(np.uint8).reshape(-1).copy()).cuda()
+    out = odp.Findings(64)
+    with pytest.raises(odp.OdpError) as e:
+        odp.analyze(raw[8:], ev.size, out)
+    assert e.value.status == -1
