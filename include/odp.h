@@ -389,6 +389,29 @@ int odp_server_stats_get(odp_server* s, odp_server_stats* st);
 
 int odp_server_destroy(odp_server* s);
 
+/* ------------------------------------------------------- collision check */
+
+/*
+ * odp_verify_fingerprints -- the collision check of the paper's App. B:
+ * where two transfers carry the same fingerprint, compare the transferred
+ * bytes.  Every transfer of the log is compared with the first transfer
+ * (lowest index) that has its fingerprint; a different length or any
+ * different byte is a collision, i.e. a duplicate or round trip the
+ * fingerprint would report falsely (the paper observed none).
+ *
+ *   events       device, n 64-byte records, 16-byte aligned
+ *   payloads     device array of n device pointers: the bytes of each
+ *                transfer (event.bytes of them, any alignment); entries of
+ *                other events are ignored
+ *   n_collisions device u64: number of colliding transfers
+ *   flags        device, n bytes, or null: 1 for a colliding transfer, 0 for
+ *                a verified one; other events' bytes are left unchanged
+ * Asynchronous on `stream`; scratch from the library's allocator.
+ */
+int odp_verify_fingerprints(const odp_event* events, const void* const* payloads, uint64_t n,
+                            unsigned long long* n_collisions, uint8_t* flags,
+                            cudaStream_t stream);
+
 /* ----------------------------------------------------------------- memory */
 
 typedef void* (*odp_alloc_fn)(size_t bytes, cudaStream_t stream, void* ctx);

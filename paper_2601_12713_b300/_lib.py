@@ -44,6 +44,8 @@ _lib.odp_fingerprint_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
 _lib.odp_fingerprint_status.restype = ctypes.c_int
 _lib.odp_analyze.argtypes = [_vp, ctypes.c_uint64, _vp, _vp]
 _lib.odp_analyze.restype = ctypes.c_int
+_lib.odp_verify_fingerprints.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, _vp, _vp]
+_lib.odp_verify_fingerprints.restype = ctypes.c_int
 _lib.odp_release_scratch.argtypes = []
 _lib.odp_release_scratch.restype = ctypes.c_int
 
@@ -225,6 +227,19 @@ def analyze(events: torch.Tensor, n: int, out: Findings, stream=None) -> None:
     assert events.is_cuda and events.numel() >= 64 * n
     _check(_lib.odp_analyze(events.data_ptr() if n else None, n, ctypes.byref(out.struct),
                             _stream(stream)), "odp_analyze")
+
+
+def verify_fingerprints(events: torch.Tensor, n: int, payload_ptrs: torch.Tensor,
+                        flags: torch.Tensor | None = None, stream=None) -> int:
+    """Collision check: returns the number of transfers whose bytes differ
+    from the first transfer with the same fingerprint (synchronises)."""
+    count = torch.zeros(1, dtype=torch.int64, device=events.device)
+    _check(_lib.odp_verify_fingerprints(events.data_ptr() if n else None,
+                                        payload_ptrs.data_ptr() if n else None, n,
+                                        count.data_ptr(),
+                                        flags.data_ptr() if flags is not None else None,
+                                        _stream(stream)), "odp_verify_fingerprints")
+    return int(count.item())
 
 
 # ---------------------------------------------------------------- serving

@@ -184,3 +184,25 @@ def test_misaligned_events_rejected(cuda_ok, odp):
     with pytest.raises(odp.OdpError) as e:
         odp.analyze(raw[8:], ev.size, out)
     assert e.value.status == -1
+
+
+def test_full_scale_iterative_solver(cuda_ok, orc, odp):
+    """The 5·10^7-event trace at full size, as the benchmark times it: the GPU
+    output equals the oracle's bit for bit (the oracle takes minutes)."""
+    b = traces.iterative_solver()
+    traces.fill_fp_from_content(b)
+    n = b.events.size
+    assert n == 50_002_000
+    ev = torch.from_numpy(b.events.view(np.uint8).reshape(-1)).cuda()
+    out = odp.Findings(n)
+    odp.analyze(ev, n, out)
+    torch.cuda.synchronize()
+    del ev
+    g = out.to_host()
+    del out
+    torch.cuda.empty_cache()
+    o = orc.analyze(b.events, capacity=n)
+    assert g["status"] == o.status == 0
+    assert g["count"] == o.count and g["summary"] == o.summary and g["n_sites"] == o.n_sites
+    assert np.array_equal(g["sites"].view(np.uint8), o.sites.view(np.uint8))
+    assert np.array_equal(g["findings"].view(np.uint8), o.findings.view(np.uint8))

@@ -131,3 +131,31 @@ def test_full_size_4gib_buffer(cuda_ok, orc, odp):
     del t
     torch.cuda.empty_cache()
     assert got == [orc.fp128(host)]
+
+
+def test_full_scale_batched_ragged(cuda_ok, orc, odp):
+    """The 10^6-buffer, 16 GiB ragged batch in one call (as benchmarked):
+    sampled buffers equal the oracle, duplicates share fingerprints, and
+    distinct contents get distinct fingerprints."""
+    from synth import gpu
+
+    sizes, offs, seeds, dup_of = content.batched_ragged(seed=0x0DB3)
+    n = sizes.size
+    arena = torch.empty(int(offs[-1] + sizes[-1]) + 64, dtype=torch.uint8, device="cuda")
+    gpu.fill_many(arena, offs, sizes, seeds)
+    ptrs = torch.from_numpy(arena.data_ptr() + offs).cuda()
+    sz = torch.from_numpy(sizes).cuda()
+    out = torch.empty((n, 2), dtype=torch.int64, device="cuda")
+    odp.fingerprint(ptrs, sz, out)
+    fps = out.cpu().numpy().view(np.uint64)
+    del arena
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(99)
+    sample = np.concatenate([rng.choice(n, 300, replace=False), np.argsort(sizes)[-4:]])
+    for i in sample:
+        data = content.bytes_of(content.RANDOM, int(seeds[i]), int(sizes[i]))
+        assert orc.fp128(data) == (int(fps[i, 0]), int(fps[i, 1])), i
+    d = np.flatnonzero(dup_of >= 0)
+    assert np.array_equal(fps[d], fps[dup_of[d]])
+    orig = fps[dup_of < 0]
+    assert np.unique(orig, axis=0).shape[0] == orig.shape[0]
