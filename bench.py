@@ -155,9 +155,11 @@ def dist_setup(n_gpus):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
 
-        backend = "nccl"
+        backend = os.environ.get("ODP_BENCH_BACKEND",
+                                 "nccl" if torch.cuda.is_available() else "gloo")
         dist.init_process_group(backend)
         return rank, world, local, dist
     return rank, world, local, None
@@ -168,12 +170,16 @@ def barrier(dist):
         dist.barrier()
 
 
+def _reduce_device(dist):
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def max_over_ranks(dist, v):
     if dist is None:
         return v
     import torch
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -183,7 +189,7 @@ def sum_over_ranks(dist, v):
         return v
     import torch
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 

@@ -363,6 +363,19 @@ def _wrap_device(ptr: int, nbytes: int) -> torch.Tensor:
 _keep = []
 
 
+def _install(a, f) -> None:
+    # odp_set_allocator frees the cached blocks through the previous
+    # callbacks, so they must stay alive until it returns
+    old = list(_keep)
+    try:
+        _check(_lib.odp_set_allocator(a if a is not None else _ALLOC_FN(),
+                                      f if f is not None else _FREE_FN(), None),
+               "odp_set_allocator")
+        _keep[:] = [a, f] if a is not None else []
+    finally:
+        del old
+
+
 def set_torch_allocator() -> None:
     """Route libodp scratch through torch's caching allocator."""
 
@@ -376,8 +389,19 @@ def set_torch_allocator() -> None:
         torch.cuda.caching_allocator_delete(int(ptr))
 
     a, f = _ALLOC_FN(_alloc), _FREE_FN(_free)
-    _keep[:] = [a, f]
-    _check(_lib.odp_set_allocator(a, f, None), "odp_set_allocator")
+    _install(a, f)
+
+
+def set_allocator(alloc, free) -> None:
+    """Route libodp scratch through Python callables alloc(nbytes, stream) ->
+    device pointer (0/None on failure) and free(ptr, stream); None, None
+    restores cudaMallocAsync."""
+    if alloc is None:
+        _install(None, None)
+        return
+    a = _ALLOC_FN(lambda nbytes, stream, ctx: alloc(int(nbytes), stream))
+    f = _FREE_FN(lambda ptr, stream, ctx: free(int(ptr or 0), stream))
+    _install(a, f)
 
 
 def release_scratch() -> None:

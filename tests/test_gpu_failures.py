@@ -1,0 +1,88 @@
+"""Failure paths without faulting the GPU: an allocator that fails, the torch
+caching allocator as scratch source, and a producer that stalls in serving."""
+
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from synth import content
+
+pytestmark = pytest.mark.gpu
+
+
+def test_failing_allocator_reports_oom(cuda_ok):
+    import paper_2601_12713_b300 as odp
+
+    t = torch.ones(1 << 20, dtype=torch.uint8, device="cuda")
+    calls = []
+    try:
+        odp.set_allocator(lambda nbytes, stream: calls.append(nbytes) or 0, lambda p, s: None)
+        with pytest.raises(odp.OdpError) as e:
+            odp.fingerprint_tensors([t[:1000], t[:5000]])
+        assert e.value.status == -3 and calls
+    finally:
+        odp.set_allocator(None, None)
+    out = odp.fingerprint_tensors([t[:1000], t[:5000]])  # default allocator works again
+    assert out.shape == (2, 2)
+
+
+def test_torch_allocator_gives_same_results(cuda_ok, orc):
+    import paper_2601_12713_b300 as odp
+    from synth import gpu, traces
+
+    t = torch.empty(3 << 20, dtype=torch.uint8, device="cuda")
+    gpu.fill(t, content.RANDOM, 4)
+    views = [t[:100], t[7:1 << 20], t[:3 << 20]]
+    ref = odp.fingerprint_tensors(views).cpu()
+    b = traces.listing2(5)
+    traces.fill_fp_from_content(b)
+    ev = torch.from_numpy(b.events.view(np.uint8).reshape(-1).copy()).cuda()
+    try:
+        odp.set_torch_allocator()
+        assert torch.equal(odp.fingerprint_tensors(views).cpu(), ref)
+        out = odp.Findings(64)
+        odp.analyze(ev, b.events.size, out)
+        r = out.to_host()
+        assert r["count"] == orc.analyze(b.events).count
+    finally:
+        odp.set_allocator(None, None)
+
+
+def test_stalled_producer_does_not_block_serving(cuda_ok):
+    """A thread that attaches and never submits holds the merge only for the
+    watermark timeout; the other producers' events are processed without a
+    flush."""
+    import paper_2601_12713_b300 as odp
+    from synth import gpu, load
+
+    pool = torch.empty(16 << 20, dtype=torch.uint8, device="cuda")
+    gpu.fill(pool, content.RANDOM, 8)
+    torch.cuda.synchronize()
+    srv = odp.Server(n_slots=2, max_events=1 << 18, max_batch_events=1024,
+                     device_budget_bytes=2 << 30, watermark_timeout_us=100_000)
+    stop = threading.Event()
+
+    def stalled():
+        srv.attach(0)
+        stop.wait(30)
+
+    th = threading.Thread(target=stalled)
+    th.start()
+    lg = load.Load(4, 8000, 1.0, 3, pool.data_ptr(), 16 << 20, 256, 1 << 16)
+    try:
+        time.sleep(0.05)
+        n = lg.run(srv)
+        deadline = time.time() + 10
+        while time.time() < deadline and srv.stats()["events_processed"] < n:
+            time.sleep(0.02)
+        s = srv.stats()
+        assert s["events_processed"] == n, s
+        srv.flush()
+    finally:
+        stop.set()
+        th.join()
+        srv.close()
+        lg.close()
