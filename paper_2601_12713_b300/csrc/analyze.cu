@@ -124,17 +124,20 @@ __device__ __forceinline__ bool record_ok(uint64_t t0, uint64_t t1, uint64_t by,
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_validate(A a) {
-    const uint32_t base = blockIdx.x * VB;
+// One warp per 32-event chunk: record checks, order check, class word,
+// per-(list, chunk) counts for the four lists.
+__global__ void __launch_bounds__(TPB) k_validate(A a, uint32_t* ccnt, uint32_t nch) {
     const int lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     unsigned long long tmax = 0;
     uint32_t nallocs = 0, ndels = 0;
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t i = base + k * TPB + threadIdx.x;
-        bool isX = false, isP = false, isK = false, isU = false;
+    for (uint32_t c = gw; c < nch; c += nw) {
+        const uint32_t i = c * 32 + lane;
+        const bool valid = i < a.n;
         uint64_t t0 = 0;
         uint4 q0 = make_uint4(0, 0, 0, 0), q2 = q0, q3 = q0;
-        if (i < a.n) {
+        if (valid) {
             const uint4* r = reinterpret_cast<const uint4*>(a.ev.p + 64ull * i);
             q0 = __ldg(r);
             q2 = __ldg(r + 2);
@@ -143,101 +146,76 @@ __global__ void __launch_bounds__(TPB) k_validate(A a) {
         }
         // start time of the previous event: the neighbour lane's, or a load
         uint64_t prev = __shfl_up_sync(ODP_FULL_MASK, t0, 1);
-        if (i < a.n) {
+        uint32_t kd = 0;
+        if (valid) {
             if (lane == 0 && i > 0) prev = a.ev.t0(i - 1);
             const uint64_t t1 = ((uint64_t)q0.w << 32) | q0.z;
             const uint64_t by = ((uint64_t)q2.y << 32) | q2.x;
-            uint32_t c;
-            if (!record_ok(t0, t1, by, q3.z, q3.w, c)) {
+            uint32_t cl;
+            if (!record_ok(t0, t1, by, q3.z, q3.w, cl)) {
                 record_error(&a.h->err, i, ODP_ERR_MALFORMED);
-                c = 0;
+                cl = 0;
             } else if (i > 0 && t0 < prev) {
                 record_error(&a.h->err, i, ODP_ERR_UNSORTED);
             }
-            a.cls[i] = c;
-            const uint32_t kd = c_kind(c);
-            isX = kd == ODP_TO_DEV || kd == ODP_FROM_DEV || kd == ODP_DEV_TO_DEV;
-            isP = kd == ODP_ALLOC || kd == ODP_DELETE;
-            isK = kd == ODP_KERNEL;
-            isU = kd == ODP_TO_DEV;
+            a.cls[i] = cl;
+            kd = c_kind(cl);
             nallocs += kd == ODP_ALLOC;
             ndels += kd == ODP_DELETE;
             tmax = max(tmax, (unsigned long long)t1);
         }
-        uint32_t cx = __syncthreads_count(isX), cp = __syncthreads_count(isP);
-        uint32_t ck = __syncthreads_count(isK), cu = __syncthreads_count(isU);
-        if (threadIdx.x == 0) {
-            if (k == 0) {
-                a.bcnt[0 * a.nb + blockIdx.x] = 0;
-                a.bcnt[1 * a.nb + blockIdx.x] = 0;
-                a.bcnt[2 * a.nb + blockIdx.x] = 0;
-                a.bcnt[3 * a.nb + blockIdx.x] = 0;
-            }
-            a.bcnt[0 * a.nb + blockIdx.x] += cx;
-            a.bcnt[1 * a.nb + blockIdx.x] += cp;
-            a.bcnt[2 * a.nb + blockIdx.x] += ck;
-            a.bcnt[3 * a.nb + blockIdx.x] += cu;
+        const uint32_t bx = __ballot_sync(ODP_FULL_MASK, kd == ODP_TO_DEV || kd == ODP_FROM_DEV ||
+                                                             kd == ODP_DEV_TO_DEV);
+        const uint32_t bp = __ballot_sync(ODP_FULL_MASK, kd == ODP_ALLOC || kd == ODP_DELETE);
+        const uint32_t bk = __ballot_sync(ODP_FULL_MASK, kd == ODP_KERNEL);
+        const uint32_t bu = __ballot_sync(ODP_FULL_MASK, kd == ODP_TO_DEV);
+        if (lane == 0) {
+            ccnt[0 * nch + c] = __popc(bx);
+            ccnt[1 * nch + c] = __popc(bp);
+            ccnt[2 * nch + c] = __popc(bk);
+            ccnt[3 * nch + c] = __popc(bu);
         }
     }
-    // block reductions of the max end time and alloc/delete counts
     for (int d = 16; d > 0; d >>= 1) {
         tmax = max(tmax, __shfl_xor_sync(ODP_FULL_MASK, tmax, d));
         nallocs += __shfl_xor_sync(ODP_FULL_MASK, nallocs, d);
         ndels += __shfl_xor_sync(ODP_FULL_MASK, ndels, d);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         atomicMax(&a.h->t_end_max, tmax);
         if (nallocs) atomicAdd(&a.h->n_allocs, (unsigned long long)nallocs);
         if (ndels) atomicAdd(&a.h->n_deletes, (unsigned long long)ndels);
     }
 }
 
-// list lengths from the scanned block counts (scan covers 4 * nb + 1)
-__global__ void k_list_lengths(A a, const uint32_t* scanned, const uint32_t* total) {
+// list lengths from the scanned chunk counts (scan covers 4 * nch)
+__global__ void k_list_lengths(A a, const uint32_t* scanned, const uint32_t* total, uint32_t nch) {
     if (threadIdx.x != 0) return;
-    const uint32_t nb = a.nb;
-    a.h->nX = scanned[1 * nb] - scanned[0];
-    a.h->nP = scanned[2 * nb] - scanned[1 * nb];
-    a.h->nK = scanned[3 * nb] - scanned[2 * nb];
-    a.h->nU = *total - scanned[3 * nb];
+    a.h->nX = scanned[1 * nch] - scanned[0];
+    a.h->nP = scanned[2 * nch] - scanned[1 * nch];
+    a.h->nK = scanned[3 * nch] - scanned[2 * nch];
+    a.h->nU = *total - scanned[3 * nch];
 }
 
-// Stable compaction of event indices into the four lists.
-__global__ void __launch_bounds__(TPB) k_compact(A a, const uint32_t* scanned) {
-    __shared__ uint32_t wc[4][TPB / 32];
-    __shared__ uint32_t run[4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t base = blockIdx.x * VB;
-    if (threadIdx.x < 4) run[threadIdx.x] = 0;
+// Stable compaction of event indices into the four lists, a warp per chunk.
+__global__ void __launch_bounds__(TPB) k_compact(A a, const uint32_t* scanned, uint32_t nch) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     uint32_t* lists[4] = {a.X, a.P, a.K, a.U};
-    uint32_t list_base[4];
-    for (int L = 0; L < 4; ++L) list_base[L] = scanned[L * a.nb + blockIdx.x] - scanned[L * a.nb];
-    __syncthreads();
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t i = base + k * TPB + threadIdx.x;
-        uint32_t kd = i < a.n ? c_kind(a.cls[i]) : 0;
-        bool pred[4] = {kd == ODP_TO_DEV || kd == ODP_FROM_DEV || kd == ODP_DEV_TO_DEV,
-                        kd == ODP_ALLOC || kd == ODP_DELETE, kd == ODP_KERNEL, kd == ODP_TO_DEV};
-        uint32_t bal[4];
+    for (uint32_t c = gw; c < nch; c += nw) {
+        const uint32_t i = c * 32 + lane;
+        const uint32_t kd = i < a.n ? c_kind(a.cls[i]) : 0;
+        const bool pred[4] = {kd == ODP_TO_DEV || kd == ODP_FROM_DEV || kd == ODP_DEV_TO_DEV,
+                              kd == ODP_ALLOC || kd == ODP_DELETE, kd == ODP_KERNEL,
+                              kd == ODP_TO_DEV};
+#pragma unroll
         for (int L = 0; L < 4; ++L) {
-            bal[L] = __ballot_sync(ODP_FULL_MASK, pred[L]);
-            if (lane == 0) wc[L][warp] = __popc(bal[L]);
+            const uint32_t bal = __ballot_sync(ODP_FULL_MASK, pred[L]);
+            if (pred[L])
+                lists[L][scanned[L * nch + c] - scanned[L * nch] + __popc(bal & lt)] = i;
         }
-        __syncthreads();
-        for (int L = 0; L < 4; ++L) {
-            if (pred[L]) {
-                uint32_t pos = run[L] + __popc(bal[L] & ((1u << lane) - 1));
-                for (int w = 0; w < warp; ++w) pos += wc[L][w];
-                lists[L][list_base[L] + pos] = i;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x < 4) {
-            uint32_t s = 0;
-            for (int w = 0; w < TPB / 32; ++w) s += wc[threadIdx.x][w];
-            run[threadIdx.x] += s;
-        }
-        __syncthreads();
     }
 }
 
@@ -257,7 +235,7 @@ __global__ void k_x_cid(A a) {
     if (failed(a)) return;
     GRID_STRIDE(j, a.h->nX) {
         const uint32_t s = a.slot[j];
-        a.sk[j] = s == NONE32 ? a.X[j] : a.tab.vals[s];
+        a.sk[j] = s == NONE32 ? a.X[j] : a.tab.slots[s].v;
         a.sv[j] = a.X[j];
     }
 }
@@ -397,7 +375,7 @@ __global__ void k_p_keys(A a) {
     if (failed(a)) return;
     GRID_STRIDE(j, a.h->nP) {
         const uint32_t s = a.slot[j];
-        a.sk[j] = s == NONE32 ? a.P[j] : a.tab.vals[s];
+        a.sk[j] = s == NONE32 ? a.P[j] : a.tab.slots[s].v;
         a.sv[j] = a.P[j];
     }
 }
@@ -489,7 +467,7 @@ __global__ void k_ra_flag(A a) {
         const uint32_t s = a.slot[j];
         if (s == NONE32) continue;
         const uint32_t e = a.P[j];
-        const uint32_t first = a.tab.vals[s];
+        const uint32_t first = a.tab.slots[s].v;
         if (first != e) a.ra[e] = first;
     }
 }
@@ -587,14 +565,15 @@ __global__ void k_ut_heads(A a) {
     }
 }
 
+// Candidates grouped by host address (few distinct addresses: the table
+// stays in L2); the group id is the group's smallest position.
 __global__ void k_ut_insert(A a) {
     if (failed(a)) return;
     const uint32_t cap = *a.tab.cap_dev;
     GRID_STRIDE(q, a.h->nU) {
         uint32_t s = NONE32;
         if (a.uc[q] == 0) {
-            const uint32_t seg = a.id1[q] + a.f1[q] - 1;
-            Key128 key{a.ev.host(a.sv[q]), (uint64_t)seg};
+            Key128 key{a.ev.host(a.sv[q]), 1};
             s = prim::table_insert_min(a.tab, cap, key, q);
         }
         a.slot[q] = s;
@@ -606,16 +585,21 @@ __global__ void k_ut_gid(A a) {
     const uint32_t nU = a.h->nU;
     GRID_STRIDE(q, nU) {
         const uint32_t s = a.slot[q];
-        a.k2[q] = s == NONE32 ? nU : a.tab.vals[s];
+        a.k2[q] = s == NONE32 ? nU : a.tab.slots[s].v;
         a.v2[q] = q;
     }
 }
 
+// After the stable sort by host group, a candidate is overwritten by the
+// next candidate of its group when both lie in the same segment.
 __global__ void k_ut_next(A a) {
     if (failed(a)) return;
     const uint32_t nU = a.h->nU;
     GRID_STRIDE(r, nU) {
-        if (a.k2[r] < nU && r + 1 < nU && a.k2[r + 1] == a.k2[r]) a.ut[a.sv[a.v2[r]]] = a.sv[a.v2[r + 1]];
+        if (a.k2[r] >= nU || r + 1 >= nU || a.k2[r + 1] != a.k2[r]) continue;
+        const uint32_t q = a.v2[r], q2 = a.v2[r + 1];
+        const uint32_t s1 = a.id1[q] + a.f1[q] - 1, s2 = a.id1[q2] + a.f1[q2] - 1;
+        if (s1 == s2) a.ut[a.sv[q]] = a.sv[q2];
     }
 }
 
@@ -903,7 +887,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     int st = ODP_OK;
 
     uint32_t cap_max = 1024;
-    while (cap_max < 2ull * n) cap_max <<= 1;
+    while (cap_max < (uint64_t)n + n / 4) cap_max <<= 1;
 
     // ---- scratch layout
     size_t bytes = 0;
@@ -939,8 +923,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     const size_t scan_words = std::max(prim::scan_tmp_words(256u * ((n + prim::SORT_TILE - 1) / prim::SORT_TILE + 1)),
                                        std::max(prim::scan_tmp_words(n), prim::scan_tmp_words(5 * ODP_MAX_SITES)));
     const size_t o_scan = carve(4 * (scan_words + 16));
-    const size_t o_tkeys = carve(sizeof(Key128) * ((size_t)cap_max + 1));
-    const size_t o_tvals = carve(4ull * ((size_t)cap_max + 1));
+    const size_t o_tslots = carve(sizeof(prim::Slot) * ((size_t)cap_max + 1));
 
     uint8_t* b = (uint8_t*)scratch_get(SLOT_AN_MAIN, bytes, s, &st);
     if (!b) return st;
@@ -987,8 +970,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     uint32_t* sflag = (uint32_t*)(b + o_sflag);
     uint32_t* spos = (uint32_t*)(b + o_spos);
     uint32_t* misc = (uint32_t*)(b + o_misc);  // [0] total findings, [1] site rows, [2] scan total
-    a.tab.keys = (Key128*)(b + o_tkeys);
-    a.tab.vals = (uint32_t*)(b + o_tvals);
+    a.tab.slots = (prim::Slot*)(b + o_tslots);
     a.tab.cap_max = cap_max;
     a.tab.cap_dev = &a.h->tcap;
     a.out = out;
@@ -1012,10 +994,12 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     ODP_CHECK_CUDA(cudaMemsetAsync(a.sites, 0, 8ull * 3 * 5 * ODP_MAX_SITES, s));
 
     // ---- validate, lists
-    k_validate<<<nb, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.bcnt, (uint32_t*)(b + o_bscan), nullptr, 4 * nb, misc + 2, scan_tmp, s);
-    k_list_lengths<<<1, 32, 0, s>>>(a, (uint32_t*)(b + o_bscan), misc + 2);
-    k_compact<<<nb, TPB, 0, s>>>(a, (uint32_t*)(b + o_bscan));
+    uint32_t* ccnt = (uint32_t*)(b + o_wcnt);
+    uint32_t* cscan = (uint32_t*)(b + o_wscan);
+    k_validate<<<sms * 16, TPB, 0, s>>>(a, ccnt, nch);
+    prim::exclusive_scan(ccnt, cscan, nullptr, 4 * nch, misc + 2, scan_tmp, s);
+    k_list_lengths<<<1, 32, 0, s>>>(a, cscan, misc + 2, nch);
+    k_compact<<<sms * 16, TPB, 0, s>>>(a, cscan, nch);
     uint32_t* nX = &a.h->nX;
     uint32_t* nP = &a.h->nP;
     uint32_t* nK = &a.h->nK;

@@ -119,55 +119,87 @@ sort_upsweep(const uint32_t* keys, const uint32_t* n_dev, uint32_t n_max, int sh
 }
 
 // Stable scatter: items of a tile are ranked in index order (round-major,
-// then warp, then lane) with warp match_any and per-warp digit counts.
+// then warp, then lane) with warp match_any and per-warp digit counts, placed
+// in shared memory in digit order, and written out so that each digit's run
+// of the tile lands contiguously in the output.
 __global__ void __launch_bounds__(SORT_THREADS)
 sort_downsweep(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
                uint32_t* vals_out, const uint32_t* n_dev, uint32_t n_max, int shift, int bits,
                const uint32_t* hist_scanned, uint32_t ntiles) {
     constexpr int W = SORT_THREADS / 32;
-    __shared__ uint32_t base_d[256];
+    __shared__ uint32_t base_d[256];   // global start of each digit for this tile
+    __shared__ uint32_t loc_d[256];    // local start of each digit in the tile
+    __shared__ uint32_t run_d[256];    // items of each digit placed so far
     __shared__ uint32_t wcnt[W][256];
+    __shared__ uint32_t ks[SORT_TILE];
+    __shared__ uint32_t vs[SORT_TILE];
+    __shared__ uint32_t scan_tmp[40];
     const uint32_t n = dev_len(n_dev, n_max);
     const uint32_t tile0 = blockIdx.x * SORT_TILE;
     if (tile0 >= n) return;
+    const uint32_t tile_n = min(SORT_TILE, n - tile0);
     const uint32_t radix = 1u << bits;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t d = threadIdx.x; d < radix; d += SORT_THREADS) {
-        base_d[d] = hist_scanned[d * ntiles + blockIdx.x];
+    for (uint32_t d = threadIdx.x; d < 256; d += SORT_THREADS) {
+        base_d[d] = d < radix ? hist_scanned[d * ntiles + blockIdx.x] : 0;
+        run_d[d] = 0;
         for (int w = 0; w < W; ++w) wcnt[w][d] = 0;
     }
     __syncthreads();
+    // the tile's own digit histogram and its exclusive scan
+    uint32_t k_r[SORT_ROUNDS], v_r[SORT_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < SORT_ROUNDS; ++r) {
+        const uint32_t i = tile0 + r * SORT_THREADS + threadIdx.x;
+        k_r[r] = i < n ? keys[i] : 0;
+        v_r[r] = i < n ? vals[i] : 0;
+        if (i < n) atomicAdd(&run_d[(k_r[r] >> shift) & (radix - 1)], 1u);
+    }
+    __syncthreads();
+    {
+        uint32_t tot;
+        const uint32_t c = threadIdx.x < 256 ? run_d[threadIdx.x] : 0;
+        const uint32_t e = block_exclusive_scan_u32(c, &tot, scan_tmp);
+        if (threadIdx.x < 256) {
+            loc_d[threadIdx.x] = e;
+            run_d[threadIdx.x] = 0;
+        }
+    }
+    __syncthreads();
     const uint32_t lt_mask = (1u << lane) - 1;
+#pragma unroll
     for (int r = 0; r < SORT_ROUNDS; ++r) {
         const uint32_t i = tile0 + r * SORT_THREADS + threadIdx.x;
         const bool valid = i < n;
-        uint32_t k = 0, v = 0, d = radix;  // invalid items use a digit no one shares
-        if (valid) {
-            k = keys[i];
-            v = vals[i];
-            d = (k >> shift) & (radix - 1);
-        }
+        const uint32_t d = valid ? (k_r[r] >> shift) & (radix - 1) : radix;
         const uint32_t peers = __match_any_sync(ODP_FULL_MASK, d);
         const uint32_t rank_w = __popc(peers & lt_mask);
         const int leader = __ffs(peers) - 1;
         if (valid && lane == leader) wcnt[warp][d] = __popc(peers);
         __syncthreads();
         if (valid) {
-            uint32_t pos = base_d[d] + rank_w;
+            uint32_t pos = loc_d[d] + run_d[d] + rank_w;
             for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
-            keys_out[pos] = k;
-            vals_out[pos] = v;
+            ks[pos] = k_r[r];
+            vs[pos] = v_r[r];
         }
         __syncthreads();
         for (uint32_t dd = threadIdx.x; dd < radix; dd += SORT_THREADS) {
-            uint32_t s = 0;
+            uint32_t sum = 0;
             for (int w = 0; w < W; ++w) {
-                s += wcnt[w][dd];
+                sum += wcnt[w][dd];
                 wcnt[w][dd] = 0;
             }
-            base_d[dd] += s;
+            run_d[dd] += sum;
         }
         __syncthreads();
+    }
+    for (uint32_t j = threadIdx.x; j < tile_n; j += SORT_THREADS) {
+        const uint32_t k = ks[j];
+        const uint32_t d = (k >> shift) & (radix - 1);
+        const uint32_t g = base_d[d] + (j - loc_d[d]);
+        keys_out[g] = k;
+        vals_out[g] = vs[j];
     }
 }
 
@@ -226,9 +258,16 @@ __device__ __forceinline__ bool key_eq(Key128 a, Key128 b) { return a.lo == b.lo
 
 constexpr uint64_t EMPTY_KEY = ~0ull;
 
+// One slot per 32-byte sector: the key and its value are touched by one
+// random access.
+struct __align__(32) Slot {
+    Key128 k;
+    uint32_t v;
+    uint32_t pad[3];
+};
+
 struct Table {
-    Key128* keys;       // capacity + 1 slots (the last one holds the all-ones key)
-    uint32_t* vals;
+    Slot* slots;        // capacity + 1 slots (the last one holds the all-ones key)
     uint32_t cap_max;   // power of two
     uint32_t* cap_dev;  // capacity in use (power of two, set on the device)
 };
@@ -242,19 +281,22 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     return x;
 }
 
-// Set the capacity in use to the smallest power of two >= 2 * count (at
-// least 1024, at most cap_max) and clear it.
+// Set the capacity in use to the smallest power of two >= 1.25 * count (at
+// least 1024, at most cap_max; load stays <= 0.8) and clear it with whole
+// 32-byte slot writes.
 __global__ void table_clear(Table t, const uint32_t* count_dev, uint32_t count_max) {
     const uint32_t cnt = dev_len(count_dev, count_max);
     uint32_t cap = 1024;
-    while (cap < 2ull * cnt && cap < t.cap_max) cap <<= 1;
+    while (cap < (uint64_t)cnt + cnt / 4 && cap < t.cap_max) cap <<= 1;
     if (blockIdx.x == 0 && threadIdx.x == 0) *t.cap_dev = cap;
     const uint32_t stride = gridDim.x * blockDim.x;
+    uint4* w = reinterpret_cast<uint4*>(t.slots);
+    const uint4 empty_key = make_uint4(~0u, ~0u, ~0u, ~0u);
+    const uint4 empty_val = make_uint4(NONE32, 0u, 0u, 0u);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= cap; i += stride) {
-        uint32_t slot = i == cap ? t.cap_max : i;
-        t.keys[slot].lo = EMPTY_KEY;
-        t.keys[slot].hi = EMPTY_KEY;
-        t.vals[slot] = NONE32;
+        const uint32_t slot = i == cap ? t.cap_max : i;
+        w[2 * (size_t)slot] = empty_key;
+        w[2 * (size_t)slot + 1] = empty_val;
     }
 }
 
@@ -264,7 +306,7 @@ __global__ void table_clear(Table t, const uint32_t* count_dev, uint32_t count_m
 __device__ __forceinline__ uint32_t table_insert_min(const Table& t, uint32_t cap, Key128 k,
                                                      uint32_t v) {
     if (k.lo == EMPTY_KEY && k.hi == EMPTY_KEY) {
-        atomicMin(&t.vals[t.cap_max], v);
+        atomicMin(&t.slots[t.cap_max].v, v);
         return t.cap_max;
     }
     const uint32_t mask = cap - 1;
@@ -272,9 +314,9 @@ __device__ __forceinline__ uint32_t table_insert_min(const Table& t, uint32_t ca
     const Key128 empty{EMPTY_KEY, EMPTY_KEY};
     for (uint32_t probe = 0; probe < cap; ++probe) {
         // slots change only once (empty -> key), always through the 16-byte CAS
-        const Key128 cur = atomicCAS(&t.keys[slot], empty, k);
+        const Key128 cur = atomicCAS(&t.slots[slot].k, empty, k);
         if (key_eq(cur, empty) || key_eq(cur, k)) {
-            atomicMin(&t.vals[slot], v);
+            atomicMin(&t.slots[slot].v, v);
             return slot;
         }
         slot = (slot + 1) & mask;

@@ -121,7 +121,7 @@ __global__ void srv_insert_dd(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
             s.sdd[q] = s.sb[q] = NONE32;
             continue;
         }
-        const uint32_t cid = d.t_fp.vals[s.sfp[q]];
+        const uint32_t cid = d.t_fp.slots[s.sfp[q]].v;
         d.cid[g] = cid;
         const Key128 k{(uint64_t)cid | ((uint64_t)ep_of(e.dst_dev) << 32), 0};
         s.sdd[q] = prim::table_insert_min(d.t_dd, cap_dd, k, (uint32_t)g);
@@ -130,7 +130,7 @@ __global__ void srv_insert_dd(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
         const uint32_t es = prim::table_insert_min(d.t_ep, cap_ep, Key128{cid, 1}, NONE32);
         if (es == NONE32) continue;
         for (uint32_t ep : {ep_of(e.src_dev), ep_of(e.dst_dev)}) {
-            uint32_t cur = d.t_ep.vals[es];
+            uint32_t cur = d.t_ep.slots[es].v;
             for (int it = 0; it < 64; ++it) {  // bounded CAS loop
                 uint32_t a = cur == NONE32 ? 0 : cur;
                 const uint32_t e1 = a & 0xFF, e2 = (a >> 8) & 0xFF;
@@ -140,7 +140,7 @@ __global__ void srv_insert_dd(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
                 if (e1 == 0) nxt = a | v;
                 else if (e2 == 0) nxt = a | (v << 8);
                 else nxt = a | EP_MORE;
-                const uint32_t old = atomicCAS(&d.t_ep.vals[es], cur, nxt);
+                const uint32_t old = atomicCAS(&d.t_ep.slots[es].v, cur, nxt);
                 if (old == cur) break;
                 cur = old;
             }
@@ -151,7 +151,7 @@ __global__ void srv_insert_dd(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
 __device__ __forceinline__ bool complex_group(const SrvDev& d, uint32_t cid) {
     const uint32_t cap = *d.t_ep.cap_dev;
     const uint32_t es = prim::table_insert_min(d.t_ep, cap, Key128{cid, 1}, NONE32);
-    const uint32_t v = es == NONE32 ? EP_MORE : d.t_ep.vals[es];
+    const uint32_t v = es == NONE32 ? EP_MORE : d.t_ep.slots[es].v;
     return v != NONE32 && (v & EP_MORE);
 }
 
@@ -163,15 +163,15 @@ __global__ void srv_dd_resolve(SrvDev d, SlotDev s, uint64_t g0, uint32_t m, uin
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
         if (s.sdd[q] == NONE32) continue;
         const uint64_t g = g0 + q;
-        const uint32_t first = d.t_dd.vals[s.sdd[q]];
+        const uint32_t first = d.t_dd.slots[s.sdd[q]].v;
         if (first != (uint32_t)g) emit(s, cap, d.log, ODP_DD, g, first, g, g);
-        if (d.t_b.vals[s.sb[q]] != (uint32_t)g) continue;  // not the batch's first here
+        if (d.t_b.slots[s.sb[q]].v != (uint32_t)g) continue;  // not the batch's first here
         const uint32_t cid = d.cid[g];
         if (complex_group(d, cid)) continue;
         const Key128 k{(uint64_t)cid | ((uint64_t)ep_of(d.log[g].dst_dev) << 32), 2};
         const uint32_t ps = prim::table_insert_min(d.t_pend, cap_pend, k, NONE32);
         if (ps == NONE32) continue;
-        uint32_t e = atomicExch(&d.t_pend.vals[ps], NONE32);
+        uint32_t e = atomicExch(&d.t_pend.slots[ps].v, NONE32);
         for (uint64_t guard = 0; e != NONE32 && guard < max_events; ++guard) {
             emit(s, cap, d.log, ODP_RT, e, g, g, g);
             e = d.next[e];
@@ -209,7 +209,7 @@ __global__ void srv_rt_batch(SrvDev d, SlotDev s, uint64_t g0, uint32_t cap) {
             const Key128 k{(uint64_t)cid | ((uint64_t)ep_of(d.log[g].src_dev) << 32), 2};
             const uint32_t ps = prim::table_insert_min(d.t_pend, cap_pend, k, NONE32);
             if (ps == NONE32) continue;
-            const uint32_t old = atomicExch(&d.t_pend.vals[ps], (uint32_t)g);
+            const uint32_t old = atomicExch(&d.t_pend.slots[ps].v, (uint32_t)g);
             d.next[g] = old;
         }
     }
@@ -303,9 +303,7 @@ int alloc_dev(odp_server* s, void** p, size_t bytes) {
 int make_table(odp_server* s, Table& t, uint32_t cap, uint32_t* cap_dev, cudaStream_t st) {
     t.cap_max = cap;
     t.cap_dev = cap_dev;
-    int rc = alloc_dev(s, (void**)&t.keys, sizeof(Key128) * ((size_t)cap + 1));
-    if (rc) return rc;
-    rc = alloc_dev(s, (void**)&t.vals, 4ull * ((size_t)cap + 1));
+    int rc = alloc_dev(s, (void**)&t.slots, sizeof(prim::Slot) * ((size_t)cap + 1));
     if (rc) return rc;
     prim::table_clear<<<256, 256, 0, st>>>(t, nullptr, cap / 2);
     return ODP_OK;
@@ -476,10 +474,10 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     const uint32_t cap_p = pow2_at_least(2 * E), cap_b = pow2_at_least(2 * B);
     const uint64_t find_cap = 2 * B + 64;
     // device bytes: log + per-event arrays + four persistent tables + slots
-    const uint64_t per_table = (16 + 4) * ((uint64_t)cap_p + 1);
+    const uint64_t per_table = 32 * ((uint64_t)cap_p + 1);
     const uint64_t slot_bytes = B * (64 + 8 + 8 + 16 + 4 + 12 + 16 + 16) + 256ull * (B / 4096 + 2) * 4 +
                                 find_cap * (48 + 8) + (20ull << 20) + (46ull << 20);
-    const uint64_t need = E * (64 + 8) + 4 * per_table + (16 + 4) * ((uint64_t)cap_b + 1) +
+    const uint64_t need = E * (64 + 8) + 4 * per_table + 32 * ((uint64_t)cap_b + 1) +
                           (uint64_t)cfg->n_slots * slot_bytes;
     if (cfg->device_budget_bytes && need > cfg->device_budget_bytes) return ODP_ERR_OOM;
 
@@ -678,13 +676,13 @@ int odp_server_stats_get(odp_server* S, odp_server_stats* st) {
     st->rt_groups_unstreamed = 0;
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        if (S->n_done > 0 && S->d.t_ep.vals) {
+        if (S->n_done > 0 && S->d.t_ep.slots) {
             const uint32_t cap = S->d.t_ep.cap_max;
-            std::vector<uint32_t> v((size_t)cap + 1);
-            if (cudaMemcpy(v.data(), S->d.t_ep.vals, 4ull * (cap + 1), cudaMemcpyDeviceToHost) ==
-                cudaSuccess)
-                for (uint32_t x : v)
-                    if (x != odp::prim::NONE32 && (x & odp::EP_MORE)) ++st->rt_groups_unstreamed;
+            std::vector<odp::prim::Slot> v((size_t)cap + 1);
+            if (cudaMemcpy(v.data(), S->d.t_ep.slots, sizeof(odp::prim::Slot) * (cap + 1),
+                           cudaMemcpyDeviceToHost) == cudaSuccess)
+                for (const auto& x : v)
+                    if (x.v != odp::prim::NONE32 && (x.v & odp::EP_MORE)) ++st->rt_groups_unstreamed;
         }
     }
     return ODP_OK;

@@ -54,7 +54,7 @@ __global__ void v_compare(VArgs a) {
     for (uint32_t i = gw; i < a.n; i += nw) {
         const uint32_t s = a.slot[i];
         if (s == NONE32) continue;
-        const uint32_t rep = a.tab.vals[s];
+        const uint32_t rep = a.tab.slots[s].v;
         if (rep == i) {
             if (a.flags && lane == 0) a.flags[i] = 0;
             continue;
@@ -117,8 +117,8 @@ extern "C" int odp_verify_fingerprints(const odp_event* events, const void* cons
         bytes = align_up(bytes + sz, 256);
         return o;
     };
-    const size_t o_slot = carve(4ull * nn), o_keys = carve(sizeof(prim::Key128) * ((size_t)cap + 1)),
-                 o_vals = carve(4ull * ((size_t)cap + 1)), o_cap = carve(16);
+    const size_t o_slot = carve(4ull * nn), o_slots = carve(sizeof(prim::Slot) * ((size_t)cap + 1)),
+                 o_cap = carve(16);
     int st = ODP_OK;
     uint8_t* s = (uint8_t*)scratch_get(SLOT_AN_TABLE, bytes, stream, &st);
     if (!s) return st;
@@ -127,8 +127,7 @@ extern "C" int odp_verify_fingerprints(const odp_event* events, const void* cons
     a.payloads = payloads;
     a.n = nn;
     a.slot = (uint32_t*)(s + o_slot);
-    a.tab.keys = (prim::Key128*)(s + o_keys);
-    a.tab.vals = (uint32_t*)(s + o_vals);
+    a.tab.slots = (prim::Slot*)(s + o_slots);
     a.tab.cap_max = cap;
     a.tab.cap_dev = (uint32_t*)(s + o_cap);
     a.n_collisions = n_collisions;
