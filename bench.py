@@ -31,9 +31,11 @@ METRIC = "fingerprint GB/s vs HBM peak; M events/s analyzed; p99 event-to-findin
 BUF_BYTES = 4 << 30
 SEED = 0x0DB2
 # dram read+write bytes of one fp_tiles launch over 512 MiB from an ncu full
-# capture (537.0 MB read + 4.8 MB written); traffic grows with the bytes
-# hashed, so a launch over B bytes moves about B / 512 MiB times this.
-FP_TILES_TRAFFIC_512MIB = 541.75e6
+# capture of the default (8 warps, 2 bulk slots) kernel: 536.98 MB read +
+# 4.18 MB written.
+# Traffic grows with the bytes hashed: a launch over B bytes moves about
+# B / 512 MiB times this.
+FP_TILES_TRAFFIC_512MIB = 541.15e6
 
 
 def peaks():
@@ -302,11 +304,12 @@ def run_ours(args):
                 "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 "peak_kind": f"{peak_kind} (copy read+write)",
-                "traffic": args.traffic if args.traffic is not None else round(
-                    FP_TILES_TRAFFIC_512MIB * fp_bytes / (512 << 20)),
+                "traffic": args.traffic if args.traffic is not None else (
+                    round(FP_TILES_TRAFFIC_512MIB * fp_bytes / (512 << 20))
+                    if FP_TILES_TRAFFIC_512MIB else None),
                 "traffic_source": "ncu capture of the 512 MiB case scaled by bytes",
-                "kernel": "fp_tiles (CUDA events per odp_fingerprint call; the call's plan "
-                          "kernels are ~1.6 % of it in the ncu launch list)",
+                "kernel": "fp_tiles<8 warps, 2 bulk-copy slots> (CUDA events per "
+                          "odp_fingerprint call; a one-buffer call is this single launch)",
                 "algorithmic_bytes_per_launch": fp_bytes + 32,
             },
             "e2e": e2e,

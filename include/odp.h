@@ -136,12 +136,16 @@ int odp_fingerprint_noalloc(const void* const* ptrs, const uint64_t* sizes, uint
  *   ctas_per_sm    0 = as many as fit, else at most this many
  *   tmin_scale     >= 1; each buffer aims at tmin_scale * (resident warps) / n
  *                  tiles of 1..32 chunks
+ *   load_stages    0: chunks are read with 16-byte register loads; 2 or 4:
+ *                  whole chunks of 16-byte-aligned buffers are bulk-copied
+ *                  (cp.async.bulk) into that many shared-memory slots per
+ *                  warp (not with 16 warps and 4 slots)
  */
 typedef struct odp_fp_schedule {
     int32_t warps_per_cta;
     int32_t ctas_per_sm;
     int32_t tmin_scale;
-    int32_t reserved;
+    int32_t load_stages;
 } odp_fp_schedule;
 
 /* odp_fingerprint with an explicit schedule (ODP_ERR_INVALID_ARG for values

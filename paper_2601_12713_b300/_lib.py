@@ -28,7 +28,7 @@ _lib.odp_fingerprint_noalloc.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, _vp]
 _lib.odp_fingerprint_noalloc.restype = ctypes.c_int
 class FpSchedule(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("tmin_scale", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tmin_scale", ctypes.c_int32), ("load_stages", ctypes.c_int32)]
 
 
 _lib.odp_fingerprint_with.argtypes = [ctypes.POINTER(FpSchedule), _vp, _vp, ctypes.c_uint64, _vp,
@@ -106,9 +106,11 @@ def _fp_args(ptrs, sizes, out):
 
 def fingerprint_with(schedule, ptrs: torch.Tensor, sizes: torch.Tensor, out: torch.Tensor,
                      stream=None) -> None:
-    """odp_fingerprint with an explicit (warps_per_cta, ctas_per_sm, tmin_scale)."""
-    w, c, t = schedule
-    sch = FpSchedule(w, c, t, 0)
+    """odp_fingerprint with an explicit (warps_per_cta, ctas_per_sm, tmin_scale[,
+    load_stages])."""
+    w, c, t = schedule[:3]
+    st = schedule[3] if len(schedule) > 3 else 0
+    sch = FpSchedule(w, c, t, st)
     _check(_lib.odp_fingerprint_with(ctypes.byref(sch), *_fp_args(ptrs, sizes, out),
                                      _stream(stream)), "odp_fingerprint_with")
 
@@ -116,13 +118,13 @@ def fingerprint_with(schedule, ptrs: torch.Tensor, sizes: torch.Tensor, out: tor
 def autotune_fingerprint(ptrs: torch.Tensor, sizes: torch.Tensor, out: torch.Tensor, reps=3,
                          stream=None):
     """Times every schedule on this batch, keeps the fastest for its size class;
-    returns ((warps_per_cta, ctas_per_sm, tmin_scale), ms per call)."""
+    returns ((warps_per_cta, ctas_per_sm, tmin_scale, load_stages), ms per call)."""
     sch = FpSchedule()
     ms = ctypes.c_float(0)
     _check(_lib.odp_autotune_fingerprint(*_fp_args(ptrs, sizes, out), _stream(stream), reps,
                                          ctypes.byref(sch), ctypes.byref(ms)),
            "odp_autotune_fingerprint")
-    return (sch.warps_per_cta, sch.ctas_per_sm, sch.tmin_scale), float(ms.value)
+    return (sch.warps_per_cta, sch.ctas_per_sm, sch.tmin_scale, sch.load_stages), float(ms.value)
 
 
 def autotune_clear() -> None:

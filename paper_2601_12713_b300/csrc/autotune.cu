@@ -34,7 +34,7 @@ int size_class(uint64_t n) {
 
 const char* cache_path() { return std::getenv("ODP_AUTOTUNE_CACHE"); }
 
-// {"fp": {"<class>": [warps, ctas, tmin_scale], ...}}
+// {"fp": {"<class>": [warps, ctas, tmin_scale, stages], ...}}
 void load_locked(const char* path) {
     FILE* f = std::fopen(path, "r");
     if (!f) return;
@@ -46,12 +46,13 @@ void load_locked(const char* path) {
     const char* p = std::strstr(text.c_str(), "\"fp\"");
     if (!p) return;
     while ((p = std::strchr(p, '"')) != nullptr) {
-        int cls, w, c, t;
-        if (std::sscanf(p, "\"%d\": [%d, %d, %d]", &cls, &w, &c, &t) == 4) {
+        int cls, w, c, t, st = 0;
+        if (std::sscanf(p, "\"%d\": [%d, %d, %d, %d]", &cls, &w, &c, &t, &st) >= 4) {
             FpLaunch L;
             L.warps_per_cta = w;
             L.ctas_per_sm = c;
             L.tmin_scale = (uint32_t)std::max(1, t);
+            L.stages = st;
             g_cache[cls] = L;
         }
         ++p;
@@ -64,8 +65,9 @@ void save_locked(const char* path) {
     std::fprintf(f, "{\"fp\": {");
     bool first = true;
     for (auto& kv : g_cache) {
-        std::fprintf(f, "%s\"%d\": [%d, %d, %u]", first ? "" : ", ", kv.first,
-                     kv.second.warps_per_cta, kv.second.ctas_per_sm, kv.second.tmin_scale);
+        std::fprintf(f, "%s\"%d\": [%d, %d, %u, %d]", first ? "" : ", ", kv.first,
+                     kv.second.warps_per_cta, kv.second.ctas_per_sm, kv.second.tmin_scale,
+                     kv.second.stages);
         first = false;
     }
     std::fprintf(f, "}}\n");
@@ -83,6 +85,7 @@ FpLaunch from_public(const odp_fp_schedule& s) {
     L.warps_per_cta = s.warps_per_cta;
     L.ctas_per_sm = s.ctas_per_sm;
     L.tmin_scale = (uint32_t)std::max(1, s.tmin_scale);
+    L.stages = s.load_stages;
     return L;
 }
 
@@ -91,7 +94,7 @@ odp_fp_schedule to_public(const FpLaunch& L) {
     s.warps_per_cta = L.warps_per_cta;
     s.ctas_per_sm = L.ctas_per_sm;
     s.tmin_scale = (int32_t)L.tmin_scale;
-    s.reserved = 0;
+    s.load_stages = L.stages;
     return s;
 }
 
@@ -115,6 +118,9 @@ int odp_fingerprint_with(const odp_fp_schedule* sched, const void* const* ptrs,
     if (sched->warps_per_cta != 4 && sched->warps_per_cta != 8 && sched->warps_per_cta != 16)
         return ODP_ERR_INVALID_ARG;
     if (sched->ctas_per_sm < 0 || sched->tmin_scale < 1) return ODP_ERR_INVALID_ARG;
+    if (sched->load_stages != 0 && sched->load_stages != 2 && sched->load_stages != 4)
+        return ODP_ERR_INVALID_ARG;
+    if (sched->warps_per_cta == 16 && sched->load_stages == 4) return ODP_ERR_INVALID_ARG;
     return odp::fp_run(ptrs, sizes, n, out128, stream, odp::from_public(*sched));
 }
 
@@ -126,12 +132,15 @@ int odp_autotune_fingerprint(const void* const* ptrs, const uint64_t* sizes, uin
     if (reps < 1) reps = 3;
     std::vector<odp::FpLaunch> cand;
     for (int w : {4, 8, 16})
-        for (uint32_t t : {1u, 2u, 4u, 8u, 16u}) {
-            odp::FpLaunch L;
-            L.warps_per_cta = w;
-            L.tmin_scale = t;
-            cand.push_back(L);
-        }
+        for (int st : {0, 2, 4})
+            for (uint32_t t : {1u, 2u, 4u, 16u}) {
+                if (w == 16 && st == 4) continue;
+                odp::FpLaunch L;
+                L.warps_per_cta = w;
+                L.tmin_scale = t;
+                L.stages = st;
+                cand.push_back(L);
+            }
     std::vector<odp_fp128> ref((size_t)n), cur((size_t)n);
     cudaEvent_t e0, e1;
     ODP_CHECK_CUDA(cudaEventCreate(&e0));

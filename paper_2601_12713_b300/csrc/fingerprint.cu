@@ -380,13 +380,79 @@ struct WarpStack {
 
 // Hash chunks [c0, c0 + cnt) of a buffer (`cnt` <= 2^m); returns the subtree
 // root in every lane.
-template <bool ALIGNED>
+// ---------------------------------------------------------------- bulk ring
+// Optional load path: whole 4 KiB chunks of 16-byte-aligned buffers are
+// copied into a per-warp ring of shared-memory slots with 1D bulk copies
+// (cp.async.bulk) that complete on one mbarrier per slot, so a warp keeps
+// several chunks in flight without holding them in registers.
+
+struct Ring {
+    uint8_t* buf;        // STAGES * 4096 bytes of this warp
+    uint64_t* bars;      // STAGES mbarriers
+    uint32_t parity;     // expected phase parity per slot (bit s)
+    int32_t* timeout;    // set when a wait gave up
+};
+
+constexpr uint32_t RING_WAIT_LIMIT = 1u << 26;  // polls before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ring_init(Ring& r, int stages, int lane) {
+    if (lane == 0) {
+        for (int s = 0; s < stages; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(r.bars + s)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    r.parity = 0;
+    __syncwarp();
+}
+
+// Lane 0 starts the copy of one 4 KiB chunk into slot s.
+__device__ __forceinline__ void ring_issue(Ring& r, int s, const uint8_t* src) {
+    const uint32_t bar = smem_addr(r.bars + s), dst = smem_addr(r.buf + (size_t)s * CHUNK);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(CHUNK)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(CHUNK), "r"(bar)
+        : "memory");
+}
+
+// All lanes wait for slot s (bounded), then flip its expected parity.
+__device__ __forceinline__ void ring_wait(Ring& r, int s) {
+    const uint32_t bar = smem_addr(r.bars + s), par = (r.parity >> s) & 1u;
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < RING_WAIT_LIMIT && !done; ++it) {
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+            "selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(bar), "r"(par)
+            : "memory");
+    }
+    if (!done && r.timeout) atomicCAS((int*)r.timeout, 0, ODP_ERR_TIMEOUT);
+    r.parity ^= 1u << s;
+}
+
+template <bool ALIGNED, int STAGES>
 __device__ __forceinline__ U128 hash_tile(const uint8_t* base, uint64_t size, uint64_t c0,
                                           uint64_t cnt, int lane, uint64_t a0, uint64_t b0,
-                                          WarpStack* st) {
+                                          WarpStack* st, Ring& ring) {
     int depth = 0;
     U128 root{0, 0};
     uint64_t root_c = 0;
+    // chunks of this tile that go through the bulk ring: all but a partial last
+    uint64_t nbulk = 0;
+    if constexpr (STAGES > 0) {
+        if (ALIGNED) nbulk = (size - (c0 + cnt - 1) * CHUNK) >= CHUNK ? cnt : cnt - 1;
+        if (lane == 0)
+            for (uint64_t k = 0; k < nbulk && k < (uint64_t)STAGES; ++k)
+                ring_issue(ring, (int)k, base + (c0 + k) * CHUNK);
+    }
     for (uint64_t g0 = 0; g0 < cnt; g0 += 32) {
         const uint32_t gc = (uint32_t)umin64(32, cnt - g0);
         uint64_t mx = 0, my = 0;
@@ -395,7 +461,24 @@ __device__ __forceinline__ U128 hash_tile(const uint8_t* base, uint64_t size, ui
             const uint8_t* cp = base + c * CHUNK;
             const uint32_t r = (uint32_t)umin64(CHUNK, size - c * CHUNK);
             uint4 w[8];
-            if (ALIGNED && r == CHUNK) {
+            bool from_ring = false;
+            if constexpr (STAGES > 0) {
+                const uint64_t kk = g0 + k;  // chunk index within the tile
+                if (kk < nbulk) {
+                    const int slot = (int)(kk % STAGES);
+                    ring_wait(ring, slot);
+                    const uint8_t* sb = ring.buf + (size_t)slot * CHUNK;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        w[j] = *reinterpret_cast<const uint4*>(sb + 16 * (lane + 32 * j));
+                    __syncwarp();
+                    if (lane == 0 && kk + STAGES < nbulk)
+                        ring_issue(ring, slot, base + (c0 + kk + STAGES) * CHUNK);
+                    from_ring = true;
+                }
+            }
+            if (from_ring) {
+            } else if (ALIGNED && r == CHUNK) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) w[j] = ld_stream(cp + 16 * (lane + 32 * j));
             } else {
@@ -449,12 +532,18 @@ __device__ __forceinline__ U128 hash_tile(const uint8_t* base, uint64_t size, ui
     return root;
 }
 
-template <int WARPS>
+template <int WARPS, int STAGES>
 __global__ void __launch_bounds__(WARPS * 32) fp_tiles(FpArgs a) {
     __shared__ WarpStack stacks[WARPS];
+    extern __shared__ __align__(128) uint8_t ring_smem[];
     const int lane = lane_id();
     const int warp = threadIdx.x >> 5;
     WarpStack* st = &stacks[warp];
+    Ring ring;
+    ring.buf = ring_smem + (size_t)warp * STAGES * CHUNK;
+    ring.bars = reinterpret_cast<uint64_t*>(ring_smem + (size_t)WARPS * STAGES * CHUNK) + warp * 8;
+    ring.timeout = a.status;
+    if constexpr (STAGES > 0) ring_init(ring, STAGES, lane);
     uint64_t a0, b0;
     fp::lane_init(lane, a0, b0);
     uint32_t T, m_floor;
@@ -500,9 +589,9 @@ __global__ void __launch_bounds__(WARPS * 32) fp_tiles(FpArgs a) {
 
         U128 root;
         if (((uintptr_t)base & 15) == 0)
-            root = hash_tile<true>(base, size, c0, cnt, lane, a0, b0, st);
+            root = hash_tile<true, STAGES>(base, size, c0, cnt, lane, a0, b0, st, ring);
         else
-            root = hash_tile<false>(base, size, c0, cnt, lane, a0, b0, st);
+            root = hash_tile<false, STAGES>(base, size, c0, cnt, lane, a0, b0, st, ring);
 
         const uint64_t ntile = n_tiles(nchunk, m);
         if (ntile == 1) {
@@ -574,20 +663,63 @@ __global__ void __launch_bounds__(WARPS * 32) fp_tiles(FpArgs a) {
 
 }  // namespace
 
-template <int W>
-static void fp_tiles_launch(const FpArgs& a, int ctas_per_sm, int sms, cudaStream_t stream) {
-    fp_tiles<W><<<sms * ctas_per_sm, W * 32, 0, stream>>>(a);
+template <int W, int S>
+static size_t fp_dyn_smem() {
+    return S > 0 ? (size_t)W * S * CHUNK + (size_t)W * 64 : 0;
 }
 
-static int fp_occupancy(int warps) {
+template <int W, int S>
+static int fp_prepare() {
+    // opt in to more than 48 KiB of dynamic shared memory, once per device
+    static bool done[256] = {};
+    const int dev = current_device();
+    if (S > 0 && dev < 256 && !done[dev]) {
+        if (cudaFuncSetAttribute(fp_tiles<W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fp_dyn_smem<W, S>()) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        done[dev] = true;
+    }
     int occ = 0;
-    if (warps == 4)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<4>, 128, 0);
-    else if (warps == 16)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<16>, 512, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<8>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<W, S>, W * 32, fp_dyn_smem<W, S>());
     return std::max(1, occ);
+}
+
+template <int W, int S>
+static void fp_tiles_launch(const FpArgs& a, int ctas_per_sm, int sms, cudaStream_t stream) {
+    fp_tiles<W, S><<<sms * ctas_per_sm, W * 32, fp_dyn_smem<W, S>(), stream>>>(a);
+}
+
+// The (warps per CTA, stages) pairs that are instantiated.
+static bool fp_variant_ok(int W, int S) {
+    return (W == 4 || W == 8 || W == 16) && (S == 0 || S == 2 || S == 4) && !(W == 16 && S == 4);
+}
+
+static int fp_occupancy(int W, int S) {
+    switch (W * 16 + S) {
+        case 4 * 16 + 0: return fp_prepare<4, 0>();
+        case 4 * 16 + 2: return fp_prepare<4, 2>();
+        case 4 * 16 + 4: return fp_prepare<4, 4>();
+        case 8 * 16 + 2: return fp_prepare<8, 2>();
+        case 8 * 16 + 4: return fp_prepare<8, 4>();
+        case 16 * 16 + 0: return fp_prepare<16, 0>();
+        case 16 * 16 + 2: return fp_prepare<16, 2>();
+        default: return fp_prepare<8, 0>();
+    }
+}
+
+static void fp_launch(const FpArgs& a, int W, int S, int ctas, int sms, cudaStream_t stream) {
+    switch (W * 16 + S) {
+        case 4 * 16 + 0: fp_tiles_launch<4, 0>(a, ctas, sms, stream); break;
+        case 4 * 16 + 2: fp_tiles_launch<4, 2>(a, ctas, sms, stream); break;
+        case 4 * 16 + 4: fp_tiles_launch<4, 4>(a, ctas, sms, stream); break;
+        case 8 * 16 + 2: fp_tiles_launch<8, 2>(a, ctas, sms, stream); break;
+        case 8 * 16 + 4: fp_tiles_launch<8, 4>(a, ctas, sms, stream); break;
+        case 16 * 16 + 0: fp_tiles_launch<16, 0>(a, ctas, sms, stream); break;
+        case 16 * 16 + 2: fp_tiles_launch<16, 2>(a, ctas, sms, stream); break;
+        default: fp_tiles_launch<8, 0>(a, ctas, sms, stream); break;
+    }
 }
 
 // Bytes at the start of each plan scratch block known to be zero (header +
@@ -655,8 +787,10 @@ int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128
     a.status = status;
     a.single = nn == 1;
 
-    const int W = (L.warps_per_cta == 4 || L.warps_per_cta == 16) ? L.warps_per_cta : TILE_WARPS;
-    const int occ = fp_occupancy(W);
+    const bool ok = fp_variant_ok(L.warps_per_cta, L.stages);
+    const int W = ok ? L.warps_per_cta : TILE_WARPS;
+    const int S = ok ? L.stages : 0;
+    const int occ = fp_occupancy(W, S);
     const int ctas = L.ctas_per_sm > 0 ? std::min(L.ctas_per_sm, occ) : occ;
     const uint64_t total_warps = (uint64_t)sms * ctas * W;
     a.tmin = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(1u << 30,
@@ -675,9 +809,7 @@ int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128
         }
         fp_plan_tiles<<<sms * 4, 256, 0, stream>>>(a);
     }
-    if (W == 4) fp_tiles_launch<4>(a, ctas, sms, stream);
-    else if (W == 16) fp_tiles_launch<16>(a, ctas, sms, stream);
-    else fp_tiles_launch<8>(a, ctas, sms, stream);
+    fp_launch(a, W, S, ctas, sms, stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         {
@@ -778,7 +910,7 @@ static int fp_run_noalloc(const void* const* ptrs, const uint64_t* sizes, uint64
 
     const int sms = device_sm_count();
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<TILE_WARPS>, TILE_WARPS * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<TILE_WARPS, 0>, TILE_WARPS * 32, 0);
     const int ctas = std::max(1, occ);
     const uint32_t total_warps = (uint32_t)(sms * ctas * TILE_WARPS);
     a.tmin = std::max<uint32_t>(1, (uint32_t)(2ull * total_warps / a.n));
@@ -789,7 +921,7 @@ static int fp_run_noalloc(const void* const* ptrs, const uint64_t* sizes, uint64
     ODP_CHECK_CUDA(cudaMemsetAsync(&a.hdr->err, 0xFF, sizeof(unsigned long long), stream));
     fp_plan_small<<<1, 1024, 0, stream>>>(a);
     fp_plan_tiles<<<sms * 4, 256, 0, stream>>>(a);
-    fp_tiles<TILE_WARPS><<<sms * ctas, TILE_WARPS * 32, 0, stream>>>(a);
+    fp_tiles<TILE_WARPS, 0><<<sms * ctas, TILE_WARPS * 32, 0, stream>>>(a);
     return cuda_status(cudaGetLastError());
 }
 

@@ -14,6 +14,7 @@ struct FpLaunch {
     int warps_per_cta = TILE_WARPS;  // 4, 8 or 16
     int ctas_per_sm = 0;             // 0: occupancy maximum
     uint32_t tmin_scale = 2;         // target tiles per buffer = scale * warps / n
+    int stages = 2;                  // 0: register loads; 2 or 4: bulk-copy ring slots per warp
 };
 
 int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128* out,
