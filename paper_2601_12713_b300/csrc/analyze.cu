@@ -9,8 +9,10 @@
 //   Alg. 2     stable sort of X by content id; with two endpoints in a
 //              content group the literal queue walk reduces to "the first
 //              later reception at the transfer's source", i.e. the start of
-//              the next run of equal destinations; other groups are walked
-//              literally, one thread per group
+//              the next run of equal destinations; groups with more
+//              endpoints: sort by (group, destination), per-endpoint
+//              "all receptions succeeded" in order of last reception, partners
+//              by binary search
 //   pairs      table <device, device address> -> key id; stable sort of P;
 //              alternating groups pair each ALLOC with the next DELETE, other
 //              groups replay the nearest-open-ALLOC rule with a stack
@@ -51,6 +53,7 @@ struct Hdr {
     unsigned long long count[6], bytes[6], ns[6];
     uint32_t nX, nP, nK, nU;
     uint32_t nseg, nrun, nseg2, nsegU;
+    uint32_t nB, nsegB;  // transfers / endpoint segments of groups with > 2 endpoints
     uint32_t total_findings, n_site_rows;
     uint32_t tcap;
 };
@@ -306,56 +309,208 @@ __global__ void k_rt_partner(A a) {
     }
 }
 
-// Groups with more than two endpoints: the queue walk of Alg. 2 verbatim,
-// one thread per group.  received[<h, d>] is the group's events with
-// destination d in order; front[d] is the position of its current front.
-__global__ void k_rt_literal(A a) {
+// ------------------------------------ Alg. 2 with more than two endpoints
+//
+// A content group (transfers of one content id, in time order) with three or
+// more endpoints.  Alg. 2 keeps one queue per endpoint holding the group's
+// receptions there; a transfer from A reports the front of A's queue if it is
+// non-empty and then pops the queue of its own destination.  Without the
+// queues: let last_A be A's last reception and allOK_A say that every
+// reception at A succeeded (produced a finding).  Pops of A's queue before
+// time t equal the successful receptions at A before t, so
+//   * a transfer from A at t succeeds iff t < last_A or not allOK_A (a source
+//     that never receives has an empty queue: last = -1, allOK = true);
+//   * its partner is the k-th reception at A, k = successful receptions at A
+//     before t;
+//   * a reception r from X is "late" when r > last_X, and it fails iff it is
+//     late and allOK_X; so allOK_D = no late reception at D comes from an
+//     endpoint X with allOK_X.  A late reception from X at D has
+//     last_X < r <= last_D, so allOK is settled endpoint by endpoint in
+//     increasing order of last.
+// The passes: compact the groups' transfers, sort them stably by (group,
+// destination) so each endpoint's receptions are one segment in time order;
+// per reception, the source's segment (binary search) and the late flag,
+// folded into a per-segment set of late sources; per group, the allOK
+// recursion over its segments (endpoints <= 129, independent of the group's
+// length); per reception, success; a scan of successes; per transfer, the
+// partner by two binary searches.  Alg. 1 in these groups: the first element
+// of each segment is the first receiver, the others are duplicates of it.
+
+__device__ __forceinline__ uint32_t group_of(const A& a, uint32_t q) { return a.id1[q] + a.f1[q] - 1; }
+
+// flags of the transfers in groups with more than two endpoints
+__global__ void k_mx_flag(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(q, a.h->nX) a.f2[q] = a.bad[group_of(a, q)];
+}
+
+// compacted list: key = destination, value = position in content order
+__global__ void k_mx_scatter(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(q, a.h->nX) {
+        if (!a.f2[q]) continue;
+        const uint32_t j = a.id2[q];
+        a.k2[j] = c_dst(a.cls[a.sv[q]]);
+        a.v2[j] = q;
+    }
+}
+
+__global__ void k_mx_gkey(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(i, a.h->nB) a.k2[i] = group_of(a, a.v2[i]);
+}
+
+// Ld[i] = destination (in a.slot), segment heads (in a.f2), group starts.
+__global__ void k_mx_heads(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(i, a.h->nB) {
+        const uint32_t s = a.k2[i];
+        const uint32_t d = c_dst(a.cls[a.sv[a.v2[i]]]);
+        a.slot[i] = d;
+        const bool ghead = i == 0 || a.k2[i - 1] != s;
+        if (ghead) a.pq[s] = i;
+        a.f2[i] = ghead || c_dst(a.cls[a.sv[a.v2[i - 1]]]) != d;
+    }
+}
+
+// Segment starts (in a.R) and cleared per-segment late-source sets: a.ks/a.ke
+// hold one 128-bit set per segment (endpoint codes 0..127); a.uc holds per
+// segment bit 0 = late from code 128, bit 1 = allOK, bit 2 = late from an
+// endpoint that never receives.
+__global__ void k_mx_starts(A a) {
+    if (failed(a)) return;
+    const uint32_t nB = a.h->nB;
+    uint4* mask = reinterpret_cast<uint4*>(a.ks);
+    GRID_STRIDE(i, nB) {
+        if (!a.f2[i]) continue;
+        const uint32_t g = a.id2[i];
+        a.R[g] = i;
+        mask[g] = make_uint4(0, 0, 0, 0);
+        a.uc[g] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.R[a.h->nsegB] = nB;
+}
+
+// Segment of endpoint x in group s (NONE32 if x never receives there).
+__device__ __forceinline__ uint32_t mx_find(const A& a, uint32_t s, uint32_t x) {
+    uint32_t lo = a.pq[s], hi = lo + (a.H[s + 1] - a.H[s]);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a.slot[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    if (lo < a.pq[s] + (a.H[s + 1] - a.H[s]) && a.slot[lo] == x) return a.id2[lo];
+    return NONE32;
+}
+
+__device__ __forceinline__ uint32_t mx_last(const A& a, uint32_t g) { return a.v2[a.R[g + 1] - 1]; }
+
+// Per reception: source segment (in a.stk) and the late flag, folded into the
+// destination segment's set (one atomic per distinct (segment, source) of a
+// warp).
+__global__ void k_mx_late(A a) {
+    if (failed(a)) return;
+    const uint32_t nB = a.h->nB;
+    const int lane = threadIdx.x & 31;
+    uint32_t* mask = reinterpret_cast<uint32_t*>(a.ks);
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < nB;
+         base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + lane;
+        unsigned long long key = ~0ull;
+        uint32_t x = 0, g = 0;
+        bool late = false;
+        if (i < nB) {
+            const uint32_t q = a.v2[i];
+            x = c_src(a.cls[a.sv[q]]);
+            const uint32_t xs = mx_find(a, a.k2[i], x);
+            a.stk[i] = xs;
+            g = a.id2[i] + a.f2[i] - 1;
+            late = xs == NONE32 || q > mx_last(a, xs);
+            if (late) key = ((unsigned long long)g << 9) | (xs == NONE32 ? 256u : x);
+        }
+        const uint32_t peers = __match_any_sync(ODP_FULL_MASK, key);
+        if (late && lane == __ffs(peers) - 1) {
+            if ((key & 511u) == 256u) {
+                atomicOr(reinterpret_cast<unsigned int*>(a.uc + (g & ~3u)), 4u << (8 * (g & 3u)));
+            } else if (x == 128) {
+                atomicOr(reinterpret_cast<unsigned int*>(a.uc + (g & ~3u)), 1u << (8 * (g & 3u)));
+            } else {
+                atomicOr(&mask[4ull * g + (x >> 5)], 1u << (x & 31));
+            }
+        }
+    }
+}
+
+// Per group: allOK of its endpoints in increasing order of last reception.
+__global__ void k_mx_ok(A a) {
     if (failed(a)) return;
     const uint32_t nseg = a.h->nseg;
+    const uint4* mask = reinterpret_cast<const uint4*>(a.ks);
     GRID_STRIDE(s, nseg) {
         if (!a.bad[s]) continue;
-        const uint32_t lo = a.H[s], hi = a.H[s + 1];
-        uint32_t cnt[NDEV], pops[NDEV], front[NDEV], first_rx[NDEV];
-        for (int d = 0; d < NDEV; ++d) {
-            cnt[d] = 0;
-            pops[d] = 0;
-            front[d] = NONE32;
-            first_rx[d] = NONE32;
-        }
-        for (uint32_t q = lo; q < hi; ++q) {
-            // Alg. 1 for this group: the first receiver of each destination
-            const uint32_t e = a.sv[q], d = c_dst(a.cls[e]);
-            cnt[d]++;
-            if (first_rx[d] == NONE32) first_rx[d] = e;
-            else a.dd[e] = first_rx[d];
-        }
-        for (uint32_t q = lo; q < hi; ++q) {
-            const uint32_t e = a.sv[q];
-            const uint32_t c = a.cls[e];
-            const uint32_t A_ = c_src(c), B_ = c_dst(c);
-            if (pops[A_] >= cnt[A_]) continue;  // queue of the source is empty
-            if (front[A_] == NONE32) {
-                uint32_t f = lo;
-                while (f < hi && c_dst(a.cls[a.sv[f]]) != A_) ++f;
-                front[A_] = f;
+        const uint32_t lo = a.pq[s], hi = lo + (a.H[s + 1] - a.H[s]);
+        // segments [g0, g1): lo is a segment head, hi - 1 is in the last one
+        const uint32_t g0 = a.id2[lo], g1 = a.id2[hi - 1] + a.f2[hi - 1];
+        uint32_t ok[4] = {0, 0, 0, 0};
+        bool ok128 = false;
+        uint32_t done_below = 0;  // last position already processed
+        bool any = false;
+        for (uint32_t it = g0; it < g1; ++it) {
+            // next segment: smallest last above the previous one (lasts are distinct)
+            uint32_t best = NONE32, best_last = NONE32;
+            for (uint32_t g = g0; g < g1; ++g) {
+                const uint32_t l = mx_last(a, g);
+                if ((!any || l > done_below) && l < best_last) {
+                    best_last = l;
+                    best = g;
+                }
             }
-            if (front[A_] >= hi) continue;  // unreachable: cnt[A_] > pops[A_]
-            a.rt[e] = a.sv[front[A_]];
-            // dequeue received[<h, dest>]
-            if (front[B_] == NONE32) {
-                uint32_t f = lo;
-                while (f < hi && c_dst(a.cls[a.sv[f]]) != B_) ++f;
-                front[B_] = f;
-            }
-            pops[B_]++;
-            if (pops[B_] < cnt[B_]) {
-                uint32_t f = front[B_] + 1;
-                while (f < hi && c_dst(a.cls[a.sv[f]]) != B_) ++f;
-                front[B_] = f;
-            } else {
-                front[B_] = hi;
+            any = true;
+            done_below = best_last;
+            const uint4 m = mask[best];
+            const uint32_t fl = a.uc[best];
+            const bool all_ok = !(fl & 4u) && !((fl & 1u) && ok128) && !(m.x & ok[0]) &&
+                                !(m.y & ok[1]) && !(m.z & ok[2]) && !(m.w & ok[3]);
+            if (all_ok) {
+                const uint32_t d = a.slot[a.R[best]];
+                if (d == 128) ok128 = true;
+                else ok[d >> 5] |= 1u << (d & 31);
+                a.uc[best] = (uint8_t)(fl | 2u);
             }
         }
+    }
+}
+
+// Per reception: success (in a.k2, scanned into a.sk next).
+__global__ void k_mx_succ(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(i, a.h->nB) {
+        const uint32_t xs = a.stk[i];
+        bool fail = true;
+        if (xs != NONE32) fail = a.v2[i] > mx_last(a, xs) && (a.uc[xs] & 2u);
+        a.k2[i] = !fail;
+    }
+}
+
+// Per transfer: Alg. 1 inside its segment, Alg. 2 partner.
+__global__ void k_mx_partner(A a) {
+    if (failed(a)) return;
+    GRID_STRIDE(i, a.h->nB) {
+        const uint32_t q = a.v2[i];
+        const uint32_t e = a.sv[q];
+        const uint32_t head = a.R[a.id2[i] + a.f2[i] - 1];
+        if (head != i) a.dd[e] = a.sv[a.v2[head]];
+        const uint32_t xs = a.stk[i];
+        if (xs == NONE32) continue;
+        const uint32_t st = a.R[xs], en = a.R[xs + 1];
+        if (!(q < a.v2[en - 1] || !(a.uc[xs] & 2u))) continue;
+        uint32_t lo = st, hi = en;  // receptions at the source before q
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.v2[mid] < q) lo = mid + 1; else hi = mid;
+        }
+        // successes among [st, lo): a.k2 = success flags, a.sk = their exclusive scan
+        const uint32_t k = lo == st ? 0 : a.sk[lo - 1] + a.k2[lo - 1] - a.sk[st];
+        if (st + k < en) a.rt[e] = a.sv[a.v2[st + k]];
     }
 }
 
@@ -913,7 +1068,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
                  o_id2 = carve(N4), o_H = carve(N4), o_R = carve(N4), o_stk = carve(N4),
                  o_pq = carve(N4);
     const size_t o_uc = carve(n + 16);
-    const size_t o_ks = carve(8ull * (n + 2)), o_ke = carve(8ull * (n + 2));
+    const size_t o_kse = carve(16ull * (n + 2));  // ks | ke (also 16 B per endpoint segment)
     const size_t o_dev = carve(2 * 4 * NDEV);
     const size_t o_sites = carve(8ull * 3 * 5 * ODP_MAX_SITES);
     const size_t o_sflag = carve(4ull * 5 * ODP_MAX_SITES), o_spos = carve(4ull * 5 * ODP_MAX_SITES);
@@ -962,14 +1117,14 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     a.stk = (uint32_t*)(b + o_stk);
     a.pq = (uint32_t*)(b + o_pq);
     a.uc = b + o_uc;
-    a.ks = (uint64_t*)(b + o_ks);
-    a.ke = (uint64_t*)(b + o_ke);
+    a.ks = (uint64_t*)(b + o_kse);
+    a.ke = a.ks + (n + 2);
     a.dstart = (uint32_t*)(b + o_dev);
     a.dend = a.dstart + NDEV;
     a.sites = (unsigned long long*)(b + o_sites);
     uint32_t* sflag = (uint32_t*)(b + o_sflag);
     uint32_t* spos = (uint32_t*)(b + o_spos);
-    uint32_t* misc = (uint32_t*)(b + o_misc);  // [0] total findings, [1] site rows, [2] scan total
+    uint32_t* misc = (uint32_t*)(b + o_misc);  // [0] total findings, [1] site rows, [2] scan total, [3] sort histogram length
     a.tab.slots = (prim::Slot*)(b + o_tslots);
     a.tab.cap_max = cap_max;
     a.tab.cap_dev = &a.h->tcap;
@@ -979,6 +1134,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     srt.vals_alt = (uint32_t*)(b + o_vals_alt);
     srt.hist = (uint32_t*)(b + o_hist);
     srt.scan_tmp = (uint32_t*)(b + o_scan);
+    srt.hlen = misc + 3;
     uint32_t* scan_tmp = srt.scan_tmp;
 
     const int bits_n = prim::bit_length(n);   // keys < n + 1
@@ -1018,7 +1174,22 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     k_rt_starts<<<gX, TPB, 0, s>>>(a);
     k_rt_check<<<gX, TPB, 0, s>>>(a);
     k_rt_partner<<<gX, TPB, 0, s>>>(a);
-    k_rt_literal<<<gX, TPB, 0, s>>>(a);
+    // groups with more than two endpoints
+    uint32_t* nB = &a.h->nB;
+    k_mx_flag<<<gX, TPB, 0, s>>>(a);
+    prim::exclusive_scan(a.f2, a.id2, nX, n, nB, scan_tmp, s);
+    k_mx_scatter<<<gX, TPB, 0, s>>>(a);
+    prim::radix_sort(a.k2, a.v2, nB, n, 8, srt, s);
+    k_mx_gkey<<<gX, TPB, 0, s>>>(a);
+    prim::radix_sort(a.k2, a.v2, nB, n, bits_n, srt, s);
+    k_mx_heads<<<gX, TPB, 0, s>>>(a);
+    prim::exclusive_scan(a.f2, a.id2, nB, n, &a.h->nsegB, scan_tmp, s);
+    k_mx_starts<<<gX, TPB, 0, s>>>(a);
+    k_mx_late<<<gX, TPB, 0, s>>>(a);
+    k_mx_ok<<<gX, TPB, 0, s>>>(a);
+    k_mx_succ<<<gX, TPB, 0, s>>>(a);
+    prim::exclusive_scan(a.k2, a.sk, nB, n, nullptr, scan_tmp, s);
+    k_mx_partner<<<gX, TPB, 0, s>>>(a);
 
     // ---- pairs
     prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nP, n);

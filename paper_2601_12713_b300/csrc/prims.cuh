@@ -7,6 +7,8 @@
 // exit at once.
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace odp {
@@ -27,30 +29,32 @@ constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr uint32_t SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
-// Tile-local exclusive scan; block sums to `sums`.
+// Tile-local exclusive scan; tile sums to `sums`.  Blocks loop over tiles,
+// so the grid can be capped and a short device length costs little.
 __global__ void __launch_bounds__(SCAN_THREADS)
 scan_local(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t n_max,
            uint32_t* sums) {
     __shared__ uint32_t sm[40];
     const uint32_t n = dev_len(n_dev, n_max);
-    const uint32_t base = blockIdx.x * SCAN_TILE;
-    if (base >= n) return;
-    uint32_t v[SCAN_ITEMS], s = 0;
+    for (uint32_t base = blockIdx.x * SCAN_TILE; base < n; base += gridDim.x * SCAN_TILE) {
+        uint32_t v[SCAN_ITEMS], s = 0;
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
-        v[k] = i < n ? in[i] : 0;
-        s += v[k];
-    }
-    uint32_t tot;
-    uint32_t e = block_exclusive_scan_u32(s, &tot, sm);
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
+            v[k] = i < n ? in[i] : 0;
+            s += v[k];
+        }
+        uint32_t tot;
+        uint32_t e = block_exclusive_scan_u32(s, &tot, sm);
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
-        if (i < n) out[i] = e;
-        e += v[k];
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
+            if (i < n) out[i] = e;
+            e += v[k];
+        }
+        if (threadIdx.x == 0) sums[base / SCAN_TILE] = tot;
+        __syncthreads();  // sm is reused by the next tile
     }
-    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
 // One block: exclusive scan of the tile sums; total to *total.
@@ -66,6 +70,7 @@ scan_blocks(uint32_t* sums, const uint32_t* n_dev, uint32_t n_max, uint32_t* tot
         uint32_t e = block_exclusive_scan_u32(v, &t, sm);
         if (b < nb) sums[b] = run + e;
         run += t;
+        __syncthreads();
     }
     if (threadIdx.x == 0 && total) *total = run;
 }
@@ -73,15 +78,22 @@ scan_blocks(uint32_t* sums, const uint32_t* n_dev, uint32_t n_max, uint32_t* tot
 __global__ void __launch_bounds__(256)
 scan_add(uint32_t* out, const uint32_t* n_dev, uint32_t n_max, const uint32_t* sums) {
     const uint32_t n = dev_len(n_dev, n_max);
-    const uint32_t base = blockIdx.x * SCAN_TILE;
-    if (base >= n) return;
-    const uint32_t add = sums[blockIdx.x];
-    for (uint32_t i = base + threadIdx.x; i < min(base + SCAN_TILE, n); i += 256) out[i] += add;
+    for (uint32_t base = blockIdx.x * SCAN_TILE; base < n; base += gridDim.x * SCAN_TILE) {
+        const uint32_t add = sums[base / SCAN_TILE];
+        for (uint32_t i = base + threadIdx.x; i < min(base + SCAN_TILE, n); i += 256) out[i] += add;
+    }
 }
 
 inline size_t scan_tmp_words(uint32_t n_max) { return (n_max + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
+// Grid for a loop over `tiles` tiles: at most `per_sm` blocks per SM.
+inline uint32_t tile_grid(uint32_t tiles, int per_sm) {
+    const uint32_t cap = (uint32_t)std::max(1, device_sm_count() * per_sm);
+    return std::max(1u, std::min(tiles, cap));
+}
+
 // out[i] = sum of in[0..i) for i < n; *total = sum of all (may be null).
+// In place (in == out) is allowed.
 inline void exclusive_scan(const uint32_t* in, uint32_t* out, const uint32_t* n_dev,
                            uint32_t n_max, uint32_t* total, uint32_t* tmp, cudaStream_t s) {
     if (n_max == 0) {
@@ -89,9 +101,9 @@ inline void exclusive_scan(const uint32_t* in, uint32_t* out, const uint32_t* n_
         return;
     }
     const uint32_t nb = (n_max + SCAN_TILE - 1) / SCAN_TILE;
-    scan_local<<<nb, SCAN_THREADS, 0, s>>>(in, out, n_dev, n_max, tmp);
+    scan_local<<<tile_grid(nb, 2), SCAN_THREADS, 0, s>>>(in, out, n_dev, n_max, tmp);
     scan_blocks<<<1, SCAN_THREADS, 0, s>>>(tmp, n_dev, n_max, total);
-    scan_add<<<nb, 256, 0, s>>>(out, n_dev, n_max, tmp);
+    scan_add<<<tile_grid(nb, 8), 256, 0, s>>>(out, n_dev, n_max, tmp);
 }
 
 // ------------------------------------------------------------ radix sort
@@ -100,32 +112,40 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_ROUNDS = 16;
 constexpr uint32_t SORT_TILE = SORT_THREADS * SORT_ROUNDS;  // 4096 items per tile
 
-// Per-tile digit histogram, stored digit-major: hist[d * ntiles + tile].
+// Tiles of the device length n: ntd = ceil(n / SORT_TILE).  Histograms are
+// stored digit-major over the device tile count, hist[d * ntd + tile], so
+// the scan between the sweeps covers radix * ntd words (written to *hlen).
+__device__ __forceinline__ uint32_t sort_tiles(uint32_t n) { return (n + SORT_TILE - 1) / SORT_TILE; }
+
+// Per-tile digit histograms; blocks loop over tiles.
 __global__ void __launch_bounds__(SORT_THREADS)
 sort_upsweep(const uint32_t* keys, const uint32_t* n_dev, uint32_t n_max, int shift, int bits,
-             uint32_t* hist, uint32_t ntiles) {
+             uint32_t* hist, uint32_t* hlen) {
     __shared__ uint32_t h[256];
     const uint32_t n = dev_len(n_dev, n_max);
+    const uint32_t ntd = sort_tiles(n);
     const uint32_t radix = 1u << bits;
-    for (uint32_t d = threadIdx.x; d < radix; d += SORT_THREADS) h[d] = 0;
-    __syncthreads();
-    const uint32_t base = blockIdx.x * SORT_TILE;
-    if (base < n) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *hlen = radix * ntd;
+    for (uint32_t t = blockIdx.x; t < ntd; t += gridDim.x) {
+        for (uint32_t d = threadIdx.x; d < radix; d += SORT_THREADS) h[d] = 0;
+        __syncthreads();
+        const uint32_t base = t * SORT_TILE;
         for (uint32_t i = base + threadIdx.x; i < min(base + SORT_TILE, n); i += SORT_THREADS)
             atomicAdd(&h[(keys[i] >> shift) & (radix - 1)], 1u);
+        __syncthreads();
+        for (uint32_t d = threadIdx.x; d < radix; d += SORT_THREADS) hist[d * ntd + t] = h[d];
+        __syncthreads();
     }
-    __syncthreads();
-    for (uint32_t d = threadIdx.x; d < radix; d += SORT_THREADS) hist[d * ntiles + blockIdx.x] = h[d];
 }
 
 // Stable scatter: items of a tile are ranked in index order (round-major,
 // then warp, then lane) with warp match_any and per-warp digit counts, placed
 // in shared memory in digit order, and written out so that each digit's run
-// of the tile lands contiguously in the output.
+// of the tile lands contiguously in the output.  Blocks loop over tiles.
 __global__ void __launch_bounds__(SORT_THREADS)
 sort_downsweep(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
                uint32_t* vals_out, const uint32_t* n_dev, uint32_t n_max, int shift, int bits,
-               const uint32_t* hist_scanned, uint32_t ntiles) {
+               const uint32_t* hist_scanned) {
     constexpr int W = SORT_THREADS / 32;
     __shared__ uint32_t base_d[256];   // global start of each digit for this tile
     __shared__ uint32_t loc_d[256];    // local start of each digit in the tile
@@ -135,71 +155,74 @@ sort_downsweep(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
     __shared__ uint32_t vs[SORT_TILE];
     __shared__ uint32_t scan_tmp[40];
     const uint32_t n = dev_len(n_dev, n_max);
-    const uint32_t tile0 = blockIdx.x * SORT_TILE;
-    if (tile0 >= n) return;
-    const uint32_t tile_n = min(SORT_TILE, n - tile0);
+    const uint32_t ntd = sort_tiles(n);
     const uint32_t radix = 1u << bits;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t d = threadIdx.x; d < 256; d += SORT_THREADS) {
-        base_d[d] = d < radix ? hist_scanned[d * ntiles + blockIdx.x] : 0;
-        run_d[d] = 0;
-        for (int w = 0; w < W; ++w) wcnt[w][d] = 0;
-    }
-    __syncthreads();
-    // the tile's own digit histogram and its exclusive scan
-    uint32_t k_r[SORT_ROUNDS], v_r[SORT_ROUNDS];
-#pragma unroll
-    for (int r = 0; r < SORT_ROUNDS; ++r) {
-        const uint32_t i = tile0 + r * SORT_THREADS + threadIdx.x;
-        k_r[r] = i < n ? keys[i] : 0;
-        v_r[r] = i < n ? vals[i] : 0;
-        if (i < n) atomicAdd(&run_d[(k_r[r] >> shift) & (radix - 1)], 1u);
-    }
-    __syncthreads();
-    {
-        uint32_t tot;
-        const uint32_t c = threadIdx.x < 256 ? run_d[threadIdx.x] : 0;
-        const uint32_t e = block_exclusive_scan_u32(c, &tot, scan_tmp);
-        if (threadIdx.x < 256) {
-            loc_d[threadIdx.x] = e;
-            run_d[threadIdx.x] = 0;
-        }
-    }
-    __syncthreads();
     const uint32_t lt_mask = (1u << lane) - 1;
+    for (uint32_t t = blockIdx.x; t < ntd; t += gridDim.x) {
+        const uint32_t tile0 = t * SORT_TILE;
+        const uint32_t tile_n = min(SORT_TILE, n - tile0);
+        for (uint32_t d = threadIdx.x; d < 256; d += SORT_THREADS) {
+            base_d[d] = d < radix ? hist_scanned[d * ntd + t] : 0;
+            run_d[d] = 0;
+            for (int w = 0; w < W; ++w) wcnt[w][d] = 0;
+        }
+        __syncthreads();
+        // the tile's own digit histogram and its exclusive scan
+        uint32_t k_r[SORT_ROUNDS], v_r[SORT_ROUNDS];
 #pragma unroll
-    for (int r = 0; r < SORT_ROUNDS; ++r) {
-        const uint32_t i = tile0 + r * SORT_THREADS + threadIdx.x;
-        const bool valid = i < n;
-        const uint32_t d = valid ? (k_r[r] >> shift) & (radix - 1) : radix;
-        const uint32_t peers = __match_any_sync(ODP_FULL_MASK, d);
-        const uint32_t rank_w = __popc(peers & lt_mask);
-        const int leader = __ffs(peers) - 1;
-        if (valid && lane == leader) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = loc_d[d] + run_d[d] + rank_w;
-            for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
-            ks[pos] = k_r[r];
-            vs[pos] = v_r[r];
+        for (int r = 0; r < SORT_ROUNDS; ++r) {
+            const uint32_t i = tile0 + r * SORT_THREADS + threadIdx.x;
+            k_r[r] = i < n ? keys[i] : 0;
+            v_r[r] = i < n ? vals[i] : 0;
+            if (i < n) atomicAdd(&run_d[(k_r[r] >> shift) & (radix - 1)], 1u);
         }
         __syncthreads();
-        for (uint32_t dd = threadIdx.x; dd < radix; dd += SORT_THREADS) {
-            uint32_t sum = 0;
-            for (int w = 0; w < W; ++w) {
-                sum += wcnt[w][dd];
-                wcnt[w][dd] = 0;
+        {
+            uint32_t tot;
+            const uint32_t c = threadIdx.x < 256 ? run_d[threadIdx.x] : 0;
+            const uint32_t e = block_exclusive_scan_u32(c, &tot, scan_tmp);
+            if (threadIdx.x < 256) {
+                loc_d[threadIdx.x] = e;
+                run_d[threadIdx.x] = 0;
             }
-            run_d[dd] += sum;
         }
         __syncthreads();
-    }
-    for (uint32_t j = threadIdx.x; j < tile_n; j += SORT_THREADS) {
-        const uint32_t k = ks[j];
-        const uint32_t d = (k >> shift) & (radix - 1);
-        const uint32_t g = base_d[d] + (j - loc_d[d]);
-        keys_out[g] = k;
-        vals_out[g] = vs[j];
+#pragma unroll
+        for (int r = 0; r < SORT_ROUNDS; ++r) {
+            const uint32_t i = tile0 + r * SORT_THREADS + threadIdx.x;
+            const bool valid = i < n;
+            const uint32_t d = valid ? (k_r[r] >> shift) & (radix - 1) : radix;
+            const uint32_t peers = __match_any_sync(ODP_FULL_MASK, d);
+            const uint32_t rank_w = __popc(peers & lt_mask);
+            const int leader = __ffs(peers) - 1;
+            if (valid && lane == leader) wcnt[warp][d] = __popc(peers);
+            __syncthreads();
+            if (valid) {
+                uint32_t pos = loc_d[d] + run_d[d] + rank_w;
+                for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+                ks[pos] = k_r[r];
+                vs[pos] = v_r[r];
+            }
+            __syncthreads();
+            for (uint32_t dd = threadIdx.x; dd < radix; dd += SORT_THREADS) {
+                uint32_t sum = 0;
+                for (int w = 0; w < W; ++w) {
+                    sum += wcnt[w][dd];
+                    wcnt[w][dd] = 0;
+                }
+                run_d[dd] += sum;
+            }
+            __syncthreads();
+        }
+        for (uint32_t j = threadIdx.x; j < tile_n; j += SORT_THREADS) {
+            const uint32_t k = ks[j];
+            const uint32_t d = (k >> shift) & (radix - 1);
+            const uint32_t g = base_d[d] + (j - loc_d[d]);
+            keys_out[g] = k;
+            vals_out[g] = vs[j];
+        }
+        __syncthreads();  // shared arrays are reused by the next tile
     }
 }
 
@@ -217,10 +240,26 @@ struct SortTmp {
     uint32_t* vals_alt;
     uint32_t* hist;      // 256 * ntiles_max
     uint32_t* scan_tmp;  // scan_tmp_words(256 * ntiles_max)
+    uint32_t* hlen;      // one device word: histogram length of the current pass
 };
 
 inline size_t sort_hist_words(uint32_t n_max) {
     return 256ull * ((n_max + SORT_TILE - 1) / SORT_TILE + 1);
+}
+
+// Resident sort_downsweep blocks per SM (queried once per device).
+inline int downsweep_per_sm() {
+    static int cache[256] = {};
+    const int dev = current_device();
+    if (dev < 0 || dev >= 256) return 4;
+    if (!cache[dev]) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sort_downsweep, SORT_THREADS, 0) !=
+                cudaSuccess || b < 1)
+            b = 4;
+        cache[dev] = b;
+    }
+    return cache[dev];
 }
 
 // Stable sort of (keys, vals) by the low `key_bits` bits of the keys; the
@@ -238,10 +277,11 @@ inline void radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, ui
     for (int p = 0; p < npass; ++p) {
         const int bits = std::max(1, std::min(per, key_bits - shift));
         const uint32_t hn = (1u << bits) * ntiles;
-        sort_upsweep<<<ntiles, SORT_THREADS, 0, s>>>(k_in, n_dev, n_max, shift, bits, t.hist, ntiles);
-        exclusive_scan(t.hist, t.hist, nullptr, hn, nullptr, t.scan_tmp, s);
-        sort_downsweep<<<ntiles, SORT_THREADS, 0, s>>>(k_in, v_in, k_out, v_out, n_dev, n_max, shift,
-                                                       bits, t.hist, ntiles);
+        sort_upsweep<<<tile_grid(ntiles, 8), SORT_THREADS, 0, s>>>(k_in, n_dev, n_max, shift, bits,
+                                                                   t.hist, t.hlen);
+        exclusive_scan(t.hist, t.hist, t.hlen, hn, nullptr, t.scan_tmp, s);
+        sort_downsweep<<<tile_grid(ntiles, downsweep_per_sm()), SORT_THREADS, 0, s>>>(k_in, v_in, k_out, v_out, n_dev,
+                                                                     n_max, shift, bits, t.hist);
         shift += bits;
         std::swap(k_in, k_out);
         std::swap(v_in, v_out);

@@ -510,6 +510,7 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
         if (!rc) rc = alloc_dev(S, (void**)&d.fp, 16 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.xpos, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.nx, 16);
+        if (!rc) d.sort.hlen = d.nx + 2;  // words 2-3 of the 16-byte count block
         if (!rc) rc = alloc_dev(S, (void**)&d.sfp, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.sdd, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.sb, 4 * B);

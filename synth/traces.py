@@ -229,6 +229,42 @@ def two_endpoint_sequence(dirs, contents, host_addr=0x1000) -> TraceBundle:
     return b.done()
 
 
+def endpoint_sequence(pairs, contents, host_addr=0x1000) -> TraceBundle:
+    """Transfers only: pairs[i] = (src, dst) with the host as -1 (host->device,
+    device->host or device->device by the endpoints); contents[i] the content
+    id."""
+    b = _Builder(gap_ns=1)
+    for (src, dst), c in zip(pairs, contents):
+        kind = TO_DEV if src == HOST else FROM_DEV if dst == HOST else DEV_TO_DEV
+        b.add(kind, 10, src=src, dst=dst, host_addr=host_addr, nbytes=64, site=kind, content=c)
+    return b.done()
+
+
+def multi_endpoint(seed: int, n_transfers: int, n_contents: int, n_devices: int,
+                   hot: float = 0.3, follow: float = 0.7) -> TraceBundle:
+    """Transfers among the host and ``n_devices`` devices.  A fraction ``hot``
+    of the transfers moves content 0 (one long content group), the rest pick
+    one of ``n_contents`` contents uniformly; with probability ``follow`` a
+    transfer starts where the content last arrived (data moving along a chain
+    of devices), else at a random endpoint."""
+    r = prng.Rng(prng.derive(seed, 91))
+    u = r.uniform(2 * n_transfers).reshape(2, -1)
+    pick = r.integers(1, max(2, n_contents), n_transfers)
+    e_src = r.integers(0, n_devices + 1, n_transfers) - 1
+    e_off = r.integers(1, n_devices + 1, n_transfers)
+    last = {}
+    pairs, contents = [], []
+    for i in range(n_transfers):
+        c = 0 if u[0, i] < hot else int(pick[i])
+        src = last[c] if (c in last and u[1, i] < follow) else int(e_src[i])
+        # a destination other than src among the n_devices + 1 endpoints
+        dst = ((src + 1) + int(e_off[i])) % (n_devices + 1) - 1
+        pairs.append((src, dst))
+        contents.append(c)
+        last[c] = dst
+    return endpoint_sequence(pairs, contents)
+
+
 # ---------------------------------------------------------------------------
 # Plain small workload: 128 host buffers, 1,000 map cycles, 4,000 data ops
 # ---------------------------------------------------------------------------

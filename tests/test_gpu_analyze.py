@@ -1,6 +1,8 @@
 """GPU parity of odp_analyze against the oracle (bit-exact findings, site
 rows, summary and status), through the C ABI."""
 
+import itertools
+
 import numpy as np
 import pytest
 import torch
@@ -98,6 +100,44 @@ def test_exhaustive_two_endpoint_rt(cuda_ok, orc, odp):
             cont_all += [2 * (k * 64 + int("".join(map(str, cs)), 2)) + c for c in cs]
     b = traces.two_endpoint_sequence(dirs_all, cont_all)
     check(odp, orc, with_fp(b))
+
+
+def _all_sequences(endpoints, max_len):
+    pairs = [(a, b) for a in endpoints for b in endpoints if a != b]
+    seqs, conts = [], []
+    k = 0
+    for length in range(1, max_len + 1):
+        for seq in itertools.product(pairs, repeat=length):
+            seqs += list(seq)
+            conts += [k] * length
+            k += 1
+    return seqs, conts
+
+
+def test_exhaustive_three_endpoint_rt(cuda_ok, orc, odp):
+    # every transfer sequence of length <= 6 among the host and devices 0, 1,
+    # and of length <= 5 among devices 1, 2 and 127 (endpoint codes across
+    # 32-bit words of the per-segment source sets); one content per sequence
+    for endpoints, max_len in (((-1, 0, 1), 6), ((1, 2, 127), 5)):
+        seqs, conts = _all_sequences(endpoints, max_len)
+        check(odp, orc, with_fp(traces.endpoint_sequence(seqs, conts)))
+
+
+@pytest.mark.parametrize("n_devices", [2, 3, 4, 8, 128])
+def test_multi_endpoint_random(cuda_ok, orc, odp, n_devices):
+    for seed in range(3):
+        b = traces.multi_endpoint(7000 + seed, 40_000 + 30_000 * seed, n_contents=200 * (seed + 1),
+                                  n_devices=n_devices)
+        check(odp, orc, with_fp(b))
+
+
+def test_multi_endpoint_one_long_group(cuda_ok, orc, odp):
+    # one content moved 300,000 times among the host and 128 devices (129
+    # endpoints, the most the record allows), with and without chains
+    for follow in (0.9, 0.0):
+        b = traces.multi_endpoint(7100, 300_000, n_contents=1, n_devices=128, hot=1.0,
+                                  follow=follow)
+        check(odp, orc, with_fp(b))
 
 
 def test_plain_small_with_payload_fingerprints(cuda_ok, orc, odp):

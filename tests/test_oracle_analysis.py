@@ -377,3 +377,96 @@ def test_site_rows(orc):
     assert got == rows
     keys = [(int(s["kind"]), int(s["site"])) for s in r.sites]
     assert keys == sorted(keys)
+
+
+# --- more than two endpoints ------------------------------------------------
+
+def closed_form_rt_general(events):
+    """Alg. 2 restated without queues, for any number of endpoints, on one
+    content group given as (src, dst) pairs in order.  With n_A receptions at
+    A and last_A the index of the last one:
+      * a transfer from A at t succeeds iff t < last_A or some reception at A
+        failed (if all A-receptions lie before t, the queue of A is non-empty
+        exactly when not every one of them was popped);
+      * a reception r from X fails iff r > last_X and every reception at X
+        succeeded (allOK_X) -- so allOK is settled endpoint by endpoint in
+        increasing order of last;
+      * the partner is the k-th reception at A, k = receptions at A before t
+        that succeeded."""
+    rec = {}
+    for t, (s, d) in enumerate(events):
+        rec.setdefault(d, []).append(t)
+    last = {d: v[-1] for d, v in rec.items()}
+    all_ok = {}
+    failed = [False] * len(events)
+    for d in sorted(rec, key=lambda x: last[x]):
+        ok = True
+        for r in rec[d]:
+            x = events[r][0]
+            f = x in last and r > last[x] and all_ok[x]
+            if x not in last:
+                f = True  # the source never receives: its queue is empty
+            failed[r] = f
+            ok &= not f
+        all_ok[d] = ok
+    out = []
+    for t, (a, _d) in enumerate(events):
+        if a not in rec:
+            continue
+        if not (t < last[a] or not all_ok[a]):
+            continue
+        k = sum(1 for r in rec[a] if r < t and not failed[r])
+        out.append((t, rec[a][k]))
+    return out
+
+
+def literal_rt(events):
+    """Alg. 2 on one content group with the queues, for comparison."""
+    from collections import deque
+    q = {}
+    for t, (s, d) in enumerate(events):
+        q.setdefault(d, deque()).append(t)
+    out = []
+    for t, (a, b) in enumerate(events):
+        if a not in q or not q[a]:
+            continue
+        out.append((t, q[a][0]))
+        q[b].popleft()
+    return out
+
+
+def test_general_closed_form_three_endpoints(orc):
+    """Every sequence of up to 6 transfers among three endpoints: the queue
+    walk, the oracle and the closed form agree."""
+    eps = (-1, 0, 1)
+    pairs = [(a, b) for a in eps for b in eps if a != b]
+    n = 0
+    for length in range(1, 7):
+        for seq in itertools.product(pairs, repeat=length):
+            want = literal_rt(seq)
+            assert closed_form_rt_general(seq) == want, seq
+            n += 1
+            if length <= 4:
+                b = traces._Builder(gap_ns=1)
+                for s, d in seq:
+                    kind = traces.TO_DEV if s == -1 else traces.FROM_DEV if d == -1 else traces.DEV_TO_DEV
+                    b.add(kind, 5, src=s, dst=d, nbytes=8, content=0)
+                r = run(orc, b.done())
+                assert by_kind(r, RT) == want, seq
+    assert n > 50_000
+
+
+def test_oracle_rt_many_endpoints(orc):
+    """The oracle's Alg. 2 on traces over the host and 128 devices (129
+    endpoints) against the queue-free closed form, group by group."""
+    for seed, follow in ((1, 0.7), (2, 0.0)):
+        b = traces.multi_endpoint(seed, 3000, n_contents=5, n_devices=128, follow=follow)
+        r = run(orc, b)
+        got = by_kind(r, RT)
+        want = []
+        for c in np.unique(b.content):
+            idx = np.nonzero(b.content == c)[0]
+            seq = [(int(b.events["src_dev"][i]), int(b.events["dst_dev"][i])) for i in idx]
+            want += [(int(idx[t]), int(idx[p])) for t, p in closed_form_rt_general(seq)]
+        assert sorted(got) == sorted(want)
+        assert len(want) > 100
