@@ -3,17 +3,17 @@
 //
 //   validate   record checks, order check, class of every event, lists of
 //              transfers (X), alloc/deletes (P), kernels (K), to-device (U)
-//   Alg. 1     table <fingerprint> -> content id (minimum event index), table
-//              <content id, destination> -> first receiver; every later
-//              transfer of a group is a duplicate of the first
-//   Alg. 2     stable sort of X by content id; with two endpoints in a
-//              content group the literal queue walk reduces to "the first
-//              later reception at the transfer's source", i.e. the start of
-//              the next run of equal destinations; groups with more
-//              endpoints: sort by (group, destination), per-endpoint
-//              "all receptions succeeded" in order of last reception, partners
-//              by binary search
-//   pairs      table <device, device address> -> key id; stable sort of P;
+//   Alg. 1/2   table <fingerprint> -> content id (the content's first
+//              transfer); stable sort of X by content id.  The group
+//              head and the start of the group's second run give each
+//              destination's first receiver; every later transfer to it is a
+//              duplicate.  With two endpoints in a content group the literal
+//              queue walk reduces to "the first later reception at the
+//              transfer's source", i.e. the start of the next run of equal
+//              destinations; groups with more endpoints: sort by (group,
+//              destination), per-endpoint "all receptions succeeded" in order
+//              of last reception, partners by binary search
+//   pairs      table <device, device address> -> slot; stable sort of P;
 //              alternating groups pair each ALLOC with the next DELETE, other
 //              groups replay the nearest-open-ALLOC rule with a stack
 //   Alg. 3     table <host address, device, bytes> -> first pair's alloc
@@ -22,8 +22,8 @@
 //              reaches the allocation's start (the literal monotone pointer)
 //   Alg. 5     same search per to-device transfer; transfers after the last
 //              kernel, barriers (overlapping the kernel) and candidates;
-//              candidate groups <segment, host address> sorted by group id,
-//              each member overwritten by the next one
+//              candidates sorted stably by host-address slot, each member
+//              overwritten by the next one of its segment
 //   emit       per-kind ballot compaction in event order, wasted bytes/ns,
 //              per-site rows, union of wasted events, summary
 #include <algorithm>
@@ -90,7 +90,7 @@ struct A {
     uint32_t* bcnt;       // 5 * nb
     uint32_t *X, *P, *K, *U;
     uint32_t *dd, *rt, *ra, *ua, *ut, *del_of;
-    uint8_t* wasted;
+    uint32_t* wbits;      // wasted events, one bit per event
     uint8_t* bad;
     uint32_t *slot, *sk, *sv, *k2, *v2, *f1, *f2, *id1, *id2, *H, *R, *stk;
     uint32_t *pq;
@@ -224,21 +224,32 @@ __global__ void __launch_bounds__(TPB) k_compact(A a, const uint32_t* scanned, u
 
 // ----------------------------------------------------- Alg. 1 (and ids)
 
+// Group keys are table slot indices: one slot per distinct key, so sorting
+// by slot groups equal keys (in an order of groups that nothing depends on)
+// without a second pass that reads each slot's value.  A full table cannot
+// occur (capacity >= 1.25 x count); it would be reported, not mis-grouped.
+__device__ __forceinline__ uint32_t slot_key(const A& a, uint32_t s, uint32_t e) {
+    if (s == NONE32) record_error(&a.h->err, e, ODP_ERR_UNSUPPORTED);
+    return s;
+}
+
+// Content groups are keyed by their first transfer (the slot's minimum event
+// index), not by slot: groups then sort in time order, and the passes that
+// follow the sorted order touch the event-indexed arrays nearly sequentially.
 __global__ void k_x_insert_fp(A a) {
     if (failed(a)) return;
     const uint32_t cap = *a.tab.cap_dev;
     GRID_STRIDE(j, a.h->nX) {
         const uint32_t e = a.X[j];
         Key128 key{a.ev.fplo(e), a.ev.fphi(e)};
-        a.slot[j] = prim::table_insert_min(a.tab, cap, key, e);
+        a.slot[j] = slot_key(a, prim::table_insert_min(a.tab, cap, key, e), e);
     }
 }
 
 __global__ void k_x_cid(A a) {
     if (failed(a)) return;
     GRID_STRIDE(j, a.h->nX) {
-        const uint32_t s = a.slot[j];
-        a.sk[j] = s == NONE32 ? a.X[j] : a.tab.slots[s].v;
+        a.sk[j] = a.tab.slots[a.slot[j]].v;
         a.sv[j] = a.X[j];
     }
 }
@@ -522,16 +533,8 @@ __global__ void k_p_insert(A a) {
     GRID_STRIDE(j, a.h->nP) {
         const uint32_t e = a.P[j];
         Key128 key{a.ev.daddr(e), (uint64_t)c_dst(a.cls[e])};
-        a.slot[j] = prim::table_insert_min(a.tab, cap, key, e);
-    }
-}
-
-__global__ void k_p_keys(A a) {
-    if (failed(a)) return;
-    GRID_STRIDE(j, a.h->nP) {
-        const uint32_t s = a.slot[j];
-        a.sk[j] = s == NONE32 ? a.P[j] : a.tab.slots[s].v;
-        a.sv[j] = a.P[j];
+        a.sk[j] = slot_key(a, prim::table_insert(a.tab, cap, key), e);
+        a.sv[j] = e;
     }
 }
 
@@ -721,26 +724,18 @@ __global__ void k_ut_heads(A a) {
 }
 
 // Candidates grouped by host address (few distinct addresses: the table
-// stays in L2); the group id is the group's smallest position.
+// stays in L2); the group key is the address's slot, non-candidates get
+// cap_max + 1 (above every slot).
 __global__ void k_ut_insert(A a) {
     if (failed(a)) return;
     const uint32_t cap = *a.tab.cap_dev;
     GRID_STRIDE(q, a.h->nU) {
-        uint32_t s = NONE32;
+        uint32_t k = a.tab.cap_max + 1;
         if (a.uc[q] == 0) {
             Key128 key{a.ev.host(a.sv[q]), 1};
-            s = prim::table_insert_min(a.tab, cap, key, q);
+            k = slot_key(a, prim::table_insert(a.tab, cap, key), a.sv[q]);
         }
-        a.slot[q] = s;
-    }
-}
-
-__global__ void k_ut_gid(A a) {
-    if (failed(a)) return;
-    const uint32_t nU = a.h->nU;
-    GRID_STRIDE(q, nU) {
-        const uint32_t s = a.slot[q];
-        a.k2[q] = s == NONE32 ? nU : a.tab.slots[s].v;
+        a.k2[q] = k;
         a.v2[q] = q;
     }
 }
@@ -751,7 +746,7 @@ __global__ void k_ut_next(A a) {
     if (failed(a)) return;
     const uint32_t nU = a.h->nU;
     GRID_STRIDE(r, nU) {
-        if (a.k2[r] >= nU || r + 1 >= nU || a.k2[r + 1] != a.k2[r]) continue;
+        if (a.k2[r] > a.tab.cap_max || r + 1 >= nU || a.k2[r + 1] != a.k2[r]) continue;
         const uint32_t q = a.v2[r], q2 = a.v2[r + 1];
         const uint32_t s1 = a.id1[q] + a.f1[q] - 1, s2 = a.id1[q2] + a.f1[q2] - 1;
         if (s1 == s2) a.ut[a.sv[q]] = a.sv[q2];
@@ -761,6 +756,7 @@ __global__ void k_ut_next(A a) {
 // ------------------------------------------------------------ emission
 
 __device__ __forceinline__ uint64_t dur(const A& a, uint32_t i) { return a.ev.t1(i) - a.ev.t0(i); }
+__device__ __forceinline__ uint64_t lohi(uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; }
 
 __device__ __forceinline__ uint32_t partner_of(const A& a, int kind, uint32_t i) {
     switch (kind) {
@@ -772,23 +768,57 @@ __device__ __forceinline__ uint32_t partner_of(const A& a, int kind, uint32_t i)
     }
 }
 
+__device__ __forceinline__ const uint32_t* partner_array(const A& a, int kind) {
+    switch (kind) {
+        case ODP_DD: return a.dd;
+        case ODP_RT: return a.rt;
+        case ODP_RA: return a.ra;
+        case ODP_UA: return a.ua;
+        default: return a.ut;
+    }
+}
+
+// Four consecutive u32 from a 16-byte-aligned array (i0 % 4 == 0); entries at
+// or past n read as `fill`.
+__device__ __forceinline__ uint4 load4(const uint32_t* p, uint32_t i0, uint32_t n, uint32_t fill) {
+    if (i0 + 4 <= n) return __ldg(reinterpret_cast<const uint4*>(p + i0));
+    uint4 v = make_uint4(fill, fill, fill, fill);
+    if (i0 < n) v.x = p[i0];
+    if (i0 + 1 < n) v.y = p[i0 + 1];
+    if (i0 + 2 < n) v.z = p[i0 + 2];
+    return v;
+}
+
 // Findings per (kind, 32-event chunk) from the partner arrays alone, and
-// pair counts; one warp per chunk.
+// pair counts.  A warp takes 128 events (four chunks), four per lane with
+// 16-byte loads; lanes 8k..8k+7 sum chunk k.
 __global__ void k_em_count(A a, uint32_t* wcnt, uint32_t nch) {
     if (failed(a)) return;
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nq = (nch + 3) / 4;
     unsigned long long pairs = 0, unpaired = 0;
-    for (uint32_t c = gw; c < nch; c += nw) {
-        const uint32_t i = c * 32 + lane;
-        const bool valid = i < a.n;
+    for (uint32_t g = gw; g < nq; g += nw) {
+        const uint32_t i0 = g * 128 + lane * 4;
+        const uint32_t c = g * 4 + (lane >> 3);
+#pragma unroll
         for (int kind = 1; kind <= 5; ++kind) {
-            const uint32_t bal = __ballot_sync(ODP_FULL_MASK, valid && partner_of(a, kind, i) != NONE32);
-            if (lane == 0) wcnt[(kind - 1) * nch + c] = __popc(bal);
+            const uint4 v = load4(partner_array(a, kind), i0, a.n, NONE32);
+            uint32_t k = (v.x != NONE32) + (v.y != NONE32) + (v.z != NONE32) + (v.w != NONE32);
+            k += __shfl_xor_sync(ODP_FULL_MASK, k, 1);
+            k += __shfl_xor_sync(ODP_FULL_MASK, k, 2);
+            k += __shfl_xor_sync(ODP_FULL_MASK, k, 4);
+            if ((lane & 7) == 0 && c < nch) wcnt[(kind - 1) * nch + c] = k;
         }
-        if (valid && c_kind(a.cls[i]) == ODP_ALLOC) {
-            if (a.del_of[i] != NONE32) ++pairs; else ++unpaired;
+        const uint4 cl = load4(a.cls, i0, a.n, 0);
+        const uint4 dl = load4(a.del_of, i0, a.n, NONE32);
+        const uint32_t cv[4] = {cl.x, cl.y, cl.z, cl.w}, dv[4] = {dl.x, dl.y, dl.z, dl.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (c_kind(cv[j]) == ODP_ALLOC) {
+                if (dv[j] != NONE32) ++pairs; else ++unpaired;
+            }
         }
     }
     for (int d = 16; d > 0; d >>= 1) {
@@ -840,6 +870,12 @@ __device__ __forceinline__ void site_add(SiteSmem& t, const A& a, uint32_t kind0
 // totals, and its wasted events are marked.  No block barrier inside the loop.
 constexpr int EMW_THREADS = 512;
 
+// Sets event e's wasted bit; returns its duration if this call set it.
+__device__ __forceinline__ uint64_t mark_wasted(const A& a, uint32_t e, uint64_t duration) {
+    const uint32_t bit = 1u << (e & 31);
+    return (atomicOr(a.wbits + (e >> 5), bit) & bit) ? 0 : duration;
+}
+
 __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* wscan, uint32_t nch) {
     if (failed(a)) return;
     extern __shared__ __align__(16) unsigned char em_dyn[];
@@ -855,9 +891,9 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
         st.ns[i] = 0;
     }
     __syncthreads();
-    unsigned long long cnt[5] = {0, 0, 0, 0, 0}, by[5] = {0, 0, 0, 0, 0}, ns[5] = {0, 0, 0, 0, 0};
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long saved = 0;
     for (uint32_t c = gw; c < nch; c += nw) {
         const uint32_t i = c * 32 + lane;
         const bool valid = i < a.n;
@@ -869,9 +905,45 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
             bal[kind] = __ballot_sync(ODP_FULL_MASK, part[kind] != NONE32);
             any |= bal[kind];
         }
+        // Wasted events: the event itself for DD, RA, UA and UT findings (one
+        // atomic per chunk), the partner for RT, the delete for RA and UA.
+        // Whoever sets an event's bit adds its duration to the saved time, so
+        // the union is summed once.
+        const uint32_t own = bal[ODP_DD - 1] | bal[ODP_RA - 1] | bal[ODP_UA - 1] | bal[ODP_UT - 1];
+        uint32_t own_old = 0;
+        if (lane == 0 && own) own_old = atomicOr(a.wbits + c, own);
+        own_old = __shfl_sync(ODP_FULL_MASK, own_old, 0);
         if (!(any & (1u << lane))) continue;
-        const uint64_t t0 = a.ev.t0(i), t1 = a.ev.t1(i), own_bytes = a.ev.bytes(i);
-        const uint32_t site = a.ev.site(i);
+        // All global loads of the chunk are issued before any store, in two
+        // dependent rounds, so a warp waits for memory twice per chunk.
+        // Round 1: the event's own record, the delete closing an RA alloc.
+        const uint4* rec = reinterpret_cast<const uint4*>(a.ev.p) + 4ull * i;
+        const uint4 o0 = __ldg(rec), o2 = __ldg(rec + 2), o3 = __ldg(rec + 3);
+        const uint32_t d = part[ODP_RA - 1] != NONE32 ? __ldg(a.del_of + i) : NONE32;
+        // Round 2: partner sites, the RT partner's times and bytes, the UA
+        // partner's and the RA delete's times.
+        uint32_t psite[5];
+#pragma unroll
+        for (int kind = 0; kind < 5; ++kind) {
+            const uint32_t p = part[kind];
+            psite[kind] = (p != NONE32 && p != NOPART)
+                              ? __ldg(reinterpret_cast<const uint32_t*>(a.ev.p + 64ull * p + 56))
+                              : 0xFFFFFFFFu;
+        }
+        const uint32_t p_rt = part[ODP_RT - 1], p_ua = part[ODP_UA - 1];
+        const uint4* rrt = reinterpret_cast<const uint4*>(a.ev.p) + 4ull * p_rt;
+        const uint4 z4 = make_uint4(0, 0, 0, 0);
+        const uint4 rt0 = p_rt != NONE32 ? __ldg(rrt) : z4;
+        const uint4 rt2 = p_rt != NONE32 ? __ldg(rrt + 2) : z4;
+        const uint4 ua0 = (p_ua != NONE32 && p_ua != NOPART)
+                              ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * p_ua)
+                              : z4;
+        const uint4 d0 = d != NONE32 ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * d) : z4;
+        // Stores.
+        const uint64_t t0 = lohi(o0.x, o0.y), t1 = lohi(o0.z, o0.w), own_bytes = lohi(o2.x, o2.y);
+        const uint32_t site = o3.z;
+        if ((own >> lane) & 1 & ~(own_old >> lane)) saved += t1 - t0;
+#pragma unroll
         for (int kind = 0; kind < 5; ++kind) {
             const uint32_t p = part[kind];
             if (p == NONE32) continue;
@@ -879,35 +951,31 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
             uint64_t wb = own_bytes, wn = t1 - t0;
             switch (kind + 1) {
                 case ODP_RT:
-                    wb = a.ev.bytes(p);
-                    wn = dur(a, p);
-                    a.wasted[p] = 1;
+                    wb = lohi(rt2.x, rt2.y);
+                    wn = lohi(rt0.z, rt0.w) - lohi(rt0.x, rt0.y);
+                    saved += mark_wasted(a, p, wn);
                     break;
-                case ODP_RA: {
-                    const uint32_t d = a.del_of[i];
-                    wn += dur(a, d);
-                    a.wasted[i] = 1;
-                    a.wasted[d] = 1;
+                case ODP_RA:
+                    if (d != NONE32) {
+                        const uint64_t dd = lohi(d0.z, d0.w) - lohi(d0.x, d0.y);
+                        wn += dd;
+                        saved += mark_wasted(a, d, dd);
+                    }
                     break;
-                }
                 case ODP_UA:
                     if (!np) {
-                        wn += dur(a, p);
-                        a.wasted[p] = 1;
+                        const uint64_t dp = lohi(ua0.z, ua0.w) - lohi(ua0.x, ua0.y);
+                        wn += dp;
+                        saved += mark_wasted(a, p, dp);
                     }
-                    a.wasted[i] = 1;
                     break;
-                default:  // DD, UT
-                    a.wasted[i] = 1;
+                default:  // DD, UT: the event itself (marked above)
                     break;
             }
-            cnt[kind]++;
-            by[kind] += wb;
-            ns[kind] += wn;
             site_add(st, a, kind, site, wb, wn);
             const uint64_t pos = (uint64_t)wscan[kind * nch + c] + __popc(bal[kind] & lt);
             if (pos < cap)
-                store_finding(items, pos, kind + 1, site, np ? 0xFFFFFFFFu : a.ev.site(p), i,
+                store_finding(items, pos, kind + 1, site, psite[kind], i,
                               np ? ODP_NO_EVENT : (uint64_t)p, wb, wn);
         }
     }
@@ -919,35 +987,31 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
         atomicAdd(row + 1, st.bytes[i]);
         atomicAdd(row + 2, st.ns[i]);
     }
-    for (int d = 16; d > 0; d >>= 1) {
-        for (int kind = 0; kind < 5; ++kind) {
-            cnt[kind] += __shfl_xor_sync(ODP_FULL_MASK, cnt[kind], d);
-            by[kind] += __shfl_xor_sync(ODP_FULL_MASK, by[kind], d);
-            ns[kind] += __shfl_xor_sync(ODP_FULL_MASK, ns[kind], d);
-        }
-    }
-    if (lane == 0) {
-        for (int kind = 0; kind < 5; ++kind) {
-            if (cnt[kind]) {
-                atomicAdd(&a.h->count[kind + 1], cnt[kind]);
-                atomicAdd(&a.h->bytes[kind + 1], by[kind]);
-                atomicAdd(&a.h->ns[kind + 1], ns[kind]);
-            }
-        }
-    }
+    for (int d = 16; d > 0; d >>= 1) saved += __shfl_xor_sync(ODP_FULL_MASK, saved, d);
+    if (lane == 0 && saved) atomicAdd(&a.h->saved_ns, saved);
 }
 
-__global__ void __launch_bounds__(TPB) k_em_saved(A a) {
-    if (failed(a)) return;
-    unsigned long long s = 0;
-    GRID_STRIDE(i, a.n) if (a.wasted[i]) s += dur(a, i);
-    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(ODP_FULL_MASK, s, d);
-    if ((threadIdx.x & 31) == 0 && s) atomicAdd(&a.h->saved_ns, s);
-}
-
-// site rows: flags over the dense [kind][site] table, then compaction
+// site rows: flags over the dense [kind][site] table (then compaction), and
+// the per-kind totals of the summary as sums of the rows (every finding was
+// added to exactly one row).  A warp's 32 rows share one kind.
 __global__ void k_site_flags(A a, uint32_t* flags) {
-    GRID_STRIDE(r, 5u * ODP_MAX_SITES) flags[r] = failed(a) ? 0 : a.sites[3ull * r] != 0;
+    const bool bad = failed(a);
+    GRID_STRIDE(r, 5u * ODP_MAX_SITES) {
+        const unsigned long long* row = a.sites + 3ull * r;
+        unsigned long long c = bad ? 0 : row[0], wb = bad ? 0 : row[1], wn = bad ? 0 : row[2];
+        flags[r] = c != 0;
+        for (int d = 16; d > 0; d >>= 1) {
+            c += __shfl_xor_sync(ODP_FULL_MASK, c, d);
+            wb += __shfl_xor_sync(ODP_FULL_MASK, wb, d);
+            wn += __shfl_xor_sync(ODP_FULL_MASK, wn, d);
+        }
+        if ((threadIdx.x & 31) == 0 && c) {
+            const uint32_t kind = r / ODP_MAX_SITES + 1;
+            atomicAdd(&a.h->count[kind], c);
+            atomicAdd(&a.h->bytes[kind], wb);
+            atomicAdd(&a.h->ns[kind], wn);
+        }
+    }
 }
 
 __global__ void k_site_write(A a, const uint32_t* flags, const uint32_t* pos) {
@@ -1060,8 +1124,9 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     const size_t o_wcnt = carve(4ull * (5ull * nch + 2));
     const size_t o_wscan = carve(4ull * (5ull * nch + 2));
     const size_t o_X = carve(N4), o_P = carve(N4), o_K = carve(N4), o_U = carve(N4);
-    const size_t o_part = carve(6 * N4);  // dd rt ra ua ut del_of
-    const size_t o_wasted = carve(n + 16);
+    const size_t PS = (n + 2 + 3) & ~size_t(3);  // partner array stride: 16-byte aligned rows
+    const size_t o_part = carve(6 * 4 * PS);  // dd rt ra ua ut del_of
+    const size_t o_wasted = carve(4ull * ((n + 31) / 32) + 16);
     const size_t o_bad = carve(n + 16);
     const size_t o_slot = carve(N4), o_sk = carve(N4), o_sv = carve(N4), o_k2 = carve(N4),
                  o_v2 = carve(N4), o_f1 = carve(N4), o_f2 = carve(N4), o_id1 = carve(N4),
@@ -1096,12 +1161,12 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     a.U = (uint32_t*)(b + o_U);
     uint32_t* part = (uint32_t*)(b + o_part);
     a.dd = part;
-    a.rt = part + (n + 2);
-    a.ra = part + 2 * (n + 2);
-    a.ua = part + 3 * (n + 2);
-    a.ut = part + 4 * (n + 2);
-    a.del_of = part + 5 * (n + 2);
-    a.wasted = b + o_wasted;
+    a.rt = part + PS;
+    a.ra = part + 2 * PS;
+    a.ua = part + 3 * PS;
+    a.ut = part + 4 * PS;
+    a.del_of = part + 5 * PS;
+    a.wbits = (uint32_t*)(b + o_wasted);
     a.bad = b + o_bad;
     a.slot = (uint32_t*)(b + o_slot);
     a.sk = (uint32_t*)(b + o_sk);
@@ -1137,15 +1202,16 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     srt.hlen = misc + 3;
     uint32_t* scan_tmp = srt.scan_tmp;
 
-    const int bits_n = prim::bit_length(n);   // keys < n + 1
+    const int bits_n = prim::bit_length(n);              // keys < n + 1
+    const int bits_slot = prim::bit_length(cap_max + 1);  // slot keys <= cap_max + 1
     const int gX = grid_for(n, sms);
     const int clear_grid = sms * 8;
 
     // ---- init
     ODP_CHECK_CUDA(cudaMemsetAsync(a.h, 0, sizeof(Hdr), s));
     ODP_CHECK_CUDA(cudaMemsetAsync(&a.h->err, 0xFF, 8, s));
-    ODP_CHECK_CUDA(cudaMemsetAsync(part, 0xFF, 6 * N4, s));
-    ODP_CHECK_CUDA(cudaMemsetAsync(a.wasted, 0, n + 16, s));
+    ODP_CHECK_CUDA(cudaMemsetAsync(part, 0xFF, 6 * 4 * PS, s));
+    ODP_CHECK_CUDA(cudaMemsetAsync(a.wbits, 0, 4ull * ((n + 31) / 32) + 16, s));
     ODP_CHECK_CUDA(cudaMemsetAsync(a.dstart, 0, 2 * 4 * NDEV, s));
     ODP_CHECK_CUDA(cudaMemsetAsync(a.sites, 0, 8ull * 3 * 5 * ODP_MAX_SITES, s));
 
@@ -1194,8 +1260,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     // ---- pairs
     prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nP, n);
     k_p_insert<<<gX, TPB, 0, s>>>(a);
-    k_p_keys<<<gX, TPB, 0, s>>>(a);
-    prim::radix_sort(a.sk, a.sv, nP, n, bits_n, srt, s);
+    prim::radix_sort(a.sk, a.sv, nP, n, bits_slot, srt, s);
     k_seg_heads<<<gX, TPB, 0, s>>>(a, nP);
     prim::exclusive_scan(a.f1, a.id1, nP, n, &a.h->nseg2, scan_tmp, s);
     k_seg_starts<<<gX, TPB, 0, s>>>(a, nP, &a.h->nseg2);
@@ -1225,8 +1290,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     prim::exclusive_scan(a.f1, a.id1, nU, n, &a.h->nsegU, scan_tmp, s);
     prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nU, n);
     k_ut_insert<<<gX, TPB, 0, s>>>(a);
-    k_ut_gid<<<gX, TPB, 0, s>>>(a);
-    prim::radix_sort(a.k2, a.v2, nU, n, bits_n, srt, s);
+    prim::radix_sort(a.k2, a.v2, nU, n, bits_slot, srt, s);
     k_ut_next<<<gX, TPB, 0, s>>>(a);
 
     // ---- emission
@@ -1242,7 +1306,6 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
         em_attr[dev] = true;
     }
     k_em_write<<<sms * 2, EMW_THREADS, sizeof(SiteSmem), s>>>(a, wscan, nch);
-    k_em_saved<<<gX, TPB, 0, s>>>(a);
     k_site_flags<<<grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s>>>(a, sflag);
     prim::exclusive_scan(sflag, spos, nullptr, 5u * ODP_MAX_SITES, misc + 1, scan_tmp, s);
     k_site_write<<<grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s>>>(a, sflag, spos);

@@ -364,6 +364,21 @@ __device__ __forceinline__ uint32_t table_insert_min(const Table& t, uint32_t ca
     return NONE32;
 }
 
+// Inserts `k` without touching the slot's value; returns the slot index (one
+// per distinct key), or NONE32 if the probe sequence exhausted the table.
+__device__ __forceinline__ uint32_t table_insert(const Table& t, uint32_t cap, Key128 k) {
+    if (k.lo == EMPTY_KEY && k.hi == EMPTY_KEY) return t.cap_max;
+    const uint32_t mask = cap - 1;
+    uint32_t slot = (uint32_t)mix64(k.lo ^ mix64(k.hi)) & mask;
+    const Key128 empty{EMPTY_KEY, EMPTY_KEY};
+    for (uint32_t probe = 0; probe < cap; ++probe) {
+        const Key128 cur = atomicCAS(&t.slots[slot].k, empty, k);
+        if (key_eq(cur, empty) || key_eq(cur, k)) return slot;
+        slot = (slot + 1) & mask;
+    }
+    return NONE32;
+}
+
 }  // namespace
 }  // namespace prim
 }  // namespace odp
