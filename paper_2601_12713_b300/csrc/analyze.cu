@@ -42,7 +42,6 @@ constexpr uint32_t NOPART = 0xFFFFFFFEu;  // flagged without a partner
 constexpr unsigned long long NO_ERR = ~0ull;
 constexpr int NDEV = 129;                  // host + devices 0..127
 constexpr int TPB = 256;
-constexpr uint32_t VB = 1024;              // events per validate/emit block
 
 struct Hdr {
     unsigned long long err;
@@ -84,10 +83,8 @@ __device__ __forceinline__ uint32_t c_dst(uint32_t c) { return (c >> 16) & 0xFF;
 struct A {
     Ev ev;
     uint32_t n;
-    uint32_t nb;          // validate/emit blocks
     Hdr* h;
     uint32_t* cls;
-    uint32_t* bcnt;       // 5 * nb
     uint32_t *X, *P, *K, *U;
     uint32_t *dd, *rt, *ra, *ua, *ut, *del_of;
     uint32_t* wbits;      // wasted events, one bit per event
@@ -653,16 +650,38 @@ __global__ void k_k_bounds(A a) {
     }
 }
 
-// Running maximum of kernel ends within each device (sequential per device;
-// kernel events are few next to data operations).
-__global__ void k_k_pmax(A a) {
+// Running maximum of kernel ends within each device: one block per device,
+// an inclusive max-scan per 1024-kernel tile with a carry between tiles.
+constexpr int PMAX_THREADS = 1024;
+
+__global__ void __launch_bounds__(PMAX_THREADS) k_k_pmax(A a) {
     if (failed(a)) return;
-    for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < NDEV; d += gridDim.x * blockDim.x) {
-        uint64_t m = 0;
-        for (uint32_t q = a.dstart[d]; q < a.dend[d]; ++q) {
-            m = max(m, a.ke[q]);
-            a.ke[q] = m;
+    __shared__ unsigned long long wmax[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lo = a.dstart[blockIdx.x], hi = a.dend[blockIdx.x];
+    unsigned long long carry = 0;
+    for (uint32_t base = lo; base < hi; base += PMAX_THREADS) {
+        const uint32_t q = base + threadIdx.x;
+        unsigned long long v = q < hi ? a.ke[q] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(ODP_FULL_MASK, v, o);
+            if (lane >= o) v = max(v, y);
         }
+        if (lane == 31) wmax[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = wmax[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(ODP_FULL_MASK, w, o);
+                if (lane >= o) w = max(w, y);
+            }
+            wmax[lane] = w;
+        }
+        __syncthreads();
+        if (warp > 0) v = max(v, wmax[warp - 1]);
+        if (q < hi) a.ke[q] = max(v, carry);
+        carry = max(carry, wmax[31]);
+        __syncthreads();
     }
 }
 
@@ -1101,7 +1120,6 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
         return cuda_status(cudaGetLastError());
     }
     const uint32_t n = (uint32_t)n64;
-    const uint32_t nb = (n + VB - 1) / VB;
     const int sms = device_sm_count();
     int st = ODP_OK;
 
@@ -1118,8 +1136,6 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     const size_t N4 = 4ull * (n + 2);
     const size_t o_h = carve(sizeof(Hdr));
     const size_t o_cls = carve(N4);
-    const size_t o_bcnt = carve(4ull * (5 * nb + 2));
-    const size_t o_bscan = carve(4ull * (5 * nb + 2));
     const uint32_t nch = (n + 31) / 32;
     const size_t o_wcnt = carve(4ull * (5ull * nch + 2));
     const size_t o_wscan = carve(4ull * (5ull * nch + 2));
@@ -1151,10 +1167,8 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     A a;
     a.ev.p = (const uint8_t*)events;
     a.n = n;
-    a.nb = nb;
     a.h = (Hdr*)(b + o_h);
     a.cls = (uint32_t*)(b + o_cls);
-    a.bcnt = (uint32_t*)(b + o_bcnt);
     a.X = (uint32_t*)(b + o_X);
     a.P = (uint32_t*)(b + o_P);
     a.K = (uint32_t*)(b + o_K);
@@ -1277,7 +1291,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     k_dev_keys<<<gX, TPB, 0, s>>>(a, a.K, nK);
     prim::radix_sort(a.sk, a.sv, nK, n, 8, srt, s);
     k_k_bounds<<<gX, TPB, 0, s>>>(a);
-    k_k_pmax<<<1, 160, 0, s>>>(a);
+    k_k_pmax<<<NDEV, PMAX_THREADS, 0, s>>>(a);
 
     // ---- Alg. 4
     k_ua<<<gX, TPB, 0, s>>>(a);

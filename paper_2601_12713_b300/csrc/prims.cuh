@@ -138,19 +138,22 @@ sort_upsweep(const uint32_t* keys, const uint32_t* n_dev, uint32_t n_max, int sh
     }
 }
 
-// Stable scatter: items of a tile are ranked in index order (round-major,
-// then warp, then lane) with warp match_any and per-warp digit counts, placed
-// in shared memory in digit order, and written out so that each digit's run
-// of the tile lands contiguously in the output.  Blocks loop over tiles.
-__global__ void __launch_bounds__(SORT_THREADS)
+// Stable scatter.  Warp w of a block owns items [512 w, 512 w + 512) of the
+// tile and ranks them in 16 rounds of 32 (index order) against its own digit
+// counters: rank = items of the digit in the warp's earlier rounds + lower
+// lanes of this round (match_any); no block barrier inside the rounds.  Then
+// the counters are scanned across warps and digits, items are placed in
+// shared memory in digit order and written out so that each digit's run of
+// the tile lands contiguously at its global start.  Blocks loop over tiles.
+__global__ void __launch_bounds__(SORT_THREADS, 4)
 sort_downsweep(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
                uint32_t* vals_out, const uint32_t* n_dev, uint32_t n_max, int shift, int bits,
                const uint32_t* hist_scanned) {
     constexpr int W = SORT_THREADS / 32;
+    constexpr int PER_WARP = SORT_TILE / W;  // 512 items, SORT_ROUNDS rounds of 32
     __shared__ uint32_t base_d[256];   // global start of each digit for this tile
     __shared__ uint32_t loc_d[256];    // local start of each digit in the tile
-    __shared__ uint32_t run_d[256];    // items of each digit placed so far
-    __shared__ uint32_t wcnt[W][256];
+    __shared__ uint32_t wcnt[W][256];  // per-warp digit counts, then per-warp offsets
     __shared__ uint32_t ks[SORT_TILE];
     __shared__ uint32_t vs[SORT_TILE];
     __shared__ uint32_t scan_tmp[40];
@@ -164,57 +167,56 @@ sort_downsweep(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
         const uint32_t tile_n = min(SORT_TILE, n - tile0);
         for (uint32_t d = threadIdx.x; d < 256; d += SORT_THREADS) {
             base_d[d] = d < radix ? hist_scanned[d * ntd + t] : 0;
-            run_d[d] = 0;
             for (int w = 0; w < W; ++w) wcnt[w][d] = 0;
         }
         __syncthreads();
-        // the tile's own digit histogram and its exclusive scan
-        uint32_t k_r[SORT_ROUNDS], v_r[SORT_ROUNDS];
+        uint32_t k_r[SORT_ROUNDS], r_r[SORT_ROUNDS / 2];  // ranks < 4096: two per word
+        const uint32_t w0 = tile0 + warp * PER_WARP;
 #pragma unroll
         for (int r = 0; r < SORT_ROUNDS; ++r) {
-            const uint32_t i = tile0 + r * SORT_THREADS + threadIdx.x;
+            const uint32_t i = w0 + r * 32 + lane;
             k_r[r] = i < n ? keys[i] : 0;
-            v_r[r] = i < n ? vals[i] : 0;
-            if (i < n) atomicAdd(&run_d[(k_r[r] >> shift) & (radix - 1)], 1u);
         }
-        __syncthreads();
-        {
-            uint32_t tot;
-            const uint32_t c = threadIdx.x < 256 ? run_d[threadIdx.x] : 0;
-            const uint32_t e = block_exclusive_scan_u32(c, &tot, scan_tmp);
-            if (threadIdx.x < 256) {
-                loc_d[threadIdx.x] = e;
-                run_d[threadIdx.x] = 0;
-            }
-        }
-        __syncthreads();
 #pragma unroll
         for (int r = 0; r < SORT_ROUNDS; ++r) {
-            const uint32_t i = tile0 + r * SORT_THREADS + threadIdx.x;
+            const uint32_t i = w0 + r * 32 + lane;
             const bool valid = i < n;
             const uint32_t d = valid ? (k_r[r] >> shift) & (radix - 1) : radix;
             const uint32_t peers = __match_any_sync(ODP_FULL_MASK, d);
-            const uint32_t rank_w = __popc(peers & lt_mask);
-            const int leader = __ffs(peers) - 1;
-            if (valid && lane == leader) wcnt[warp][d] = __popc(peers);
-            __syncthreads();
-            if (valid) {
-                uint32_t pos = loc_d[d] + run_d[d] + rank_w;
-                for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
-                ks[pos] = k_r[r];
-                vs[pos] = v_r[r];
-            }
-            __syncthreads();
-            for (uint32_t dd = threadIdx.x; dd < radix; dd += SORT_THREADS) {
-                uint32_t sum = 0;
-                for (int w = 0; w < W; ++w) {
-                    sum += wcnt[w][dd];
-                    wcnt[w][dd] = 0;
-                }
-                run_d[dd] += sum;
-            }
-            __syncthreads();
+            const uint32_t before = valid ? wcnt[warp][d] : 0;
+            const uint32_t rank = before + __popc(peers & lt_mask);
+            if (r & 1) r_r[r / 2] |= rank << 16; else r_r[r / 2] = rank;
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
+            __syncwarp();
         }
+        __syncthreads();
+        // per digit: exclusive scan over warps, then over digits
+        uint32_t tot_d = 0;
+        if (threadIdx.x < 256) {
+            for (int w = 0; w < W; ++w) {
+                const uint32_t c = wcnt[w][threadIdx.x];
+                wcnt[w][threadIdx.x] = tot_d;
+                tot_d += c;
+            }
+        }
+        {
+            uint32_t tot;
+            const uint32_t e = block_exclusive_scan_u32(threadIdx.x < 256 ? tot_d : 0, &tot, scan_tmp);
+            if (threadIdx.x < 256) loc_d[threadIdx.x] = e;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < SORT_ROUNDS; ++r) {
+            const uint32_t i = w0 + r * 32 + lane;
+            if (i < n) {
+                const uint32_t d = (k_r[r] >> shift) & (radix - 1);
+                const uint32_t pos = loc_d[d] + wcnt[warp][d] + ((r_r[r / 2] >> (16 * (r & 1))) & 0xFFFFu);
+                ks[pos] = k_r[r];
+                vs[pos] = vals[i];
+            }
+        }
+        __syncthreads();
         for (uint32_t j = threadIdx.x; j < tile_n; j += SORT_THREADS) {
             const uint32_t k = ks[j];
             const uint32_t d = (k >> shift) & (radix - 1);

@@ -140,6 +140,43 @@ def test_multi_endpoint_one_long_group(cuda_ok, orc, odp):
         check(odp, orc, with_fp(b))
 
 
+def test_graph_capture_and_concurrent_streams(cuda_ok, orc, odp):
+    """odp_analyze captured in a CUDA graph and replayed, and two calls in
+    flight on two streams at once, give the oracle's results."""
+    b1 = traces.random_small(4242, n_ops=20_000, n_contents=50, n_hosts=40, n_devices=3, d2d=True)
+    b2 = traces.multi_endpoint(4243, 30_000, n_contents=300, n_devices=4)
+    e1, e2 = with_fp(b1), with_fp(b2)
+    o1, o2 = orc.analyze(e1), orc.analyze(e2)
+
+    def dev(e):
+        return torch.from_numpy(e.view(np.uint8).reshape(-1).copy()).cuda()
+
+    d1, d2 = dev(e1), dev(e2)
+    s = torch.cuda.Stream()
+    out = odp.Findings(6 * e1.size)
+    with torch.cuda.stream(s):
+        odp.analyze(d1, e1.size, out, s)  # first call on the stream allocates its scratch
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        odp.analyze(d1, e1.size, out, s)
+    out.items.zero_()
+    out.small.zero_()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    assert_same(out.to_host(), o1)
+
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    oa, ob = odp.Findings(6 * e1.size), odp.Findings(6 * e2.size)
+    for _ in range(3):
+        odp.analyze(d1, e1.size, oa, sa)
+        odp.analyze(d2, e2.size, ob, sb)
+    torch.cuda.synchronize()
+    assert_same(oa.to_host(), o1)
+    assert_same(ob.to_host(), o2)
+
+
 def test_plain_small_with_payload_fingerprints(cuda_ok, orc, odp):
     """Plain small workload: every transfer fingerprinted on the GPU, one
     buffer per launch, then the whole log analysed; fingerprints and findings
