@@ -233,34 +233,76 @@ __device__ __forceinline__ uint32_t slot_key(const A& a, uint32_t s, uint32_t e)
 // Content groups are keyed by their first transfer (the slot's minimum event
 // index), not by slot: groups then sort in time order, and the passes that
 // follow the sorted order touch the event-indexed arrays nearly sequentially.
+// Four list entries per thread per step (spaced a grid apart, so the list
+// loads and slot stores stay coalesced), their table probes in flight
+// together.
+constexpr int INS_B = 4;
+
+#define BATCH_STRIDE(j0, n)                                                        \
+    for (uint32_t j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < (n);            \
+         j0 += INS_B * gridDim.x * blockDim.x)
+
 __global__ void k_x_insert_fp(A a) {
     if (failed(a)) return;
     const uint32_t cap = *a.tab.cap_dev;
-    GRID_STRIDE(j, a.h->nX) {
-        const uint32_t e = a.X[j];
-        Key128 key{a.ev.fplo(e), a.ev.fphi(e)};
-        a.slot[j] = slot_key(a, prim::table_insert_min(a.tab, cap, key, e), e);
+    const uint32_t n = a.h->nX, str = gridDim.x * blockDim.x;
+    BATCH_STRIDE(j0, n) {
+        uint32_t e[INS_B], out[INS_B];
+        bool use[INS_B];
+        Key128 key[INS_B];
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const uint32_t j = j0 + b * str;
+            use[b] = j < n;
+            e[b] = use[b] ? a.X[j] : 0;
+        }
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const uint4 f = use[b] ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * e[b] + 2)
+                                   : make_uint4(0, 0, 0, 0);
+            const uint4 g = use[b] ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * e[b] + 3)
+                                   : make_uint4(0, 0, 0, 0);
+            key[b] = Key128{((uint64_t)f.w << 32) | f.z, ((uint64_t)g.y << 32) | g.x};
+        }
+        prim::table_insert_batch<INS_B, true>(a.tab, cap, key, e, use, out);
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b)
+            if (use[b]) a.slot[j0 + b * str] = slot_key(a, out[b], e[b]);
     }
 }
 
 __global__ void k_x_cid(A a) {
     if (failed(a)) return;
-    GRID_STRIDE(j, a.h->nX) {
-        a.sk[j] = a.tab.slots[a.slot[j]].v;
-        a.sv[j] = a.X[j];
+    const uint32_t n = a.h->nX, str = gridDim.x * blockDim.x;
+    BATCH_STRIDE(j0, n) {
+        uint32_t sl[INS_B], v[INS_B];
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) sl[b] = j0 + b * str < n ? a.slot[j0 + b * str] : NONE32;
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) v[b] = sl[b] != NONE32 ? a.tab.slots[sl[b]].v : 0;
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const uint32_t j = j0 + b * str;
+            if (j >= n) continue;
+            a.sk[j] = v[b];
+            a.sv[j] = a.X[j];
+        }
     }
 }
 
 // ------------------------------------------------------------- Alg. 2
 
+// Group and run heads; the class word of each sorted transfer is gathered
+// once into a.k2 (in sorted order) for the passes that follow.
 __global__ void k_rt_flags(A a) {
     if (failed(a)) return;
     GRID_STRIDE(q, a.h->nX) {
         const bool head = q == 0 || a.sk[q] != a.sk[q - 1];
-        const uint32_t dst = c_dst(a.cls[a.sv[q]]);
-        const bool run = head || dst != c_dst(a.cls[a.sv[q - 1]]);
+        const uint32_t c = a.cls[a.sv[q]];
+        const bool run = head || c_dst(c) != c_dst(a.cls[a.sv[q - 1]]);
         a.f1[q] = head;
         a.f2[q] = run;
+        a.k2[q] = c;
     }
 }
 
@@ -288,7 +330,7 @@ __global__ void k_rt_check(A a) {
     GRID_STRIDE(q, a.h->nX) {
         const uint32_t s = a.id1[q] + a.f1[q] - 1;
         const uint32_t h = a.H[s];
-        if (!same_endpoints(a.cls[a.sv[q]], a.cls[a.sv[h]])) a.bad[s] = 1;
+        if (!same_endpoints(a.k2[q], a.k2[h])) a.bad[s] = 1;
     }
 }
 
@@ -311,7 +353,7 @@ __global__ void k_rt_partner(A a) {
         }
         const uint32_t h = a.H[s];
         uint32_t first;
-        if (c_dst(a.cls[e]) == c_dst(a.cls[a.sv[h]])) first = a.sv[h];
+        if (c_dst(a.k2[q]) == c_dst(a.k2[h])) first = a.sv[h];
         else first = a.sv[a.R[a.id2[h] + 1]];
         if (first != e) a.dd[e] = first;
     }
@@ -527,17 +569,38 @@ __global__ void k_mx_partner(A a) {
 __global__ void k_p_insert(A a) {
     if (failed(a)) return;
     const uint32_t cap = *a.tab.cap_dev;
-    GRID_STRIDE(j, a.h->nP) {
-        const uint32_t e = a.P[j];
-        Key128 key{a.ev.daddr(e), (uint64_t)c_dst(a.cls[e])};
-        a.sk[j] = slot_key(a, prim::table_insert(a.tab, cap, key), e);
-        a.sv[j] = e;
+    const uint32_t n = a.h->nP, str = gridDim.x * blockDim.x;
+    BATCH_STRIDE(j0, n) {
+        uint32_t e[INS_B], out[INS_B];
+        bool use[INS_B];
+        Key128 key[INS_B];
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const uint32_t j = j0 + b * str;
+            use[b] = j < n;
+            e[b] = use[b] ? a.P[j] : 0;
+        }
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b)
+            key[b] = use[b] ? Key128{a.ev.daddr(e[b]), (uint64_t)c_dst(a.cls[e[b]])} : Key128{0, 0};
+        prim::table_insert_batch<INS_B, false>(a.tab, cap, key, e, use, out);
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            if (!use[b]) continue;
+            a.sk[j0 + b * str] = slot_key(a, out[b], e[b]);
+            a.sv[j0 + b * str] = e[b];
+        }
     }
 }
 
+// Group heads of the sorted alloc/delete list; whether each entry is an
+// ALLOC is gathered once into a.k2 (in sorted order).
 __global__ void k_seg_heads(A a, const uint32_t* count) {
     if (failed(a)) return;
-    GRID_STRIDE(q, *count) a.f1[q] = q == 0 || a.sk[q] != a.sk[q - 1];
+    GRID_STRIDE(q, *count) {
+        a.f1[q] = q == 0 || a.sk[q] != a.sk[q - 1];
+        a.k2[q] = c_kind(a.cls[a.sv[q]]) == ODP_ALLOC;
+    }
 }
 
 __global__ void k_seg_starts(A a, const uint32_t* count, const uint32_t* nseg) {
@@ -559,10 +622,10 @@ __global__ void k_p_check(A a) {
     GRID_STRIDE(q, a.h->nP) {
         const uint32_t s = a.id1[q] + a.f1[q] - 1;
         const uint32_t lo = a.H[s], hi = a.H[s + 1];
-        const bool al = is_alloc(a, a.sv[q]);
+        const bool al = a.k2[q];
         bool bad;
-        if (!al) bad = q == lo || !is_alloc(a, a.sv[q - 1]);
-        else bad = q + 1 < hi && is_alloc(a, a.sv[q + 1]);
+        if (!al) bad = q == lo || !a.k2[q - 1];
+        else bad = q + 1 < hi && a.k2[q + 1];
         if (bad) a.bad[s] = 1;
     }
 }
@@ -573,8 +636,7 @@ __global__ void k_p_match(A a) {
         const uint32_t s = a.id1[q] + a.f1[q] - 1;
         if (a.bad[s]) continue;
         const uint32_t hi = a.H[s + 1];
-        const uint32_t e = a.sv[q];
-        if (is_alloc(a, e) && q + 1 < hi) a.del_of[e] = a.sv[q + 1];
+        if (a.k2[q] && q + 1 < hi) a.del_of[a.sv[q]] = a.sv[q + 1];
     }
 }
 
@@ -605,25 +667,45 @@ __global__ void k_p_literal(A a) {
 __global__ void k_ra_insert(A a) {
     if (failed(a)) return;
     const uint32_t cap = *a.tab.cap_dev;
-    GRID_STRIDE(j, a.h->nP) {
-        const uint32_t e = a.P[j];
-        uint32_t s = NONE32;
-        if (is_alloc(a, e) && a.del_of[e] != NONE32) {
-            Key128 key{a.ev.host(e), a.ev.bytes(e) | ((uint64_t)c_dst(a.cls[e]) << 56)};
-            s = prim::table_insert_min(a.tab, cap, key, e);
+    const uint32_t n = a.h->nP, str = gridDim.x * blockDim.x;
+    BATCH_STRIDE(j0, n) {
+        uint32_t e[INS_B], out[INS_B];
+        bool use[INS_B], in[INS_B];
+        Key128 key[INS_B];
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const uint32_t j = j0 + b * str;
+            in[b] = j < n;
+            e[b] = in[b] ? a.P[j] : 0;
         }
-        a.slot[j] = s;
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            use[b] = in[b] && is_alloc(a, e[b]) && a.del_of[e[b]] != NONE32;
+            key[b] = use[b] ? Key128{a.ev.host(e[b]), a.ev.bytes(e[b]) | ((uint64_t)c_dst(a.cls[e[b]]) << 56)}
+                            : Key128{0, 0};
+        }
+        prim::table_insert_batch<INS_B, true>(a.tab, cap, key, e, use, out);
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b)
+            if (in[b]) a.slot[j0 + b * str] = out[b];
     }
 }
 
 __global__ void k_ra_flag(A a) {
     if (failed(a)) return;
-    GRID_STRIDE(j, a.h->nP) {
-        const uint32_t s = a.slot[j];
-        if (s == NONE32) continue;
-        const uint32_t e = a.P[j];
-        const uint32_t first = a.tab.slots[s].v;
-        if (first != e) a.ra[e] = first;
+    const uint32_t n = a.h->nP, str = gridDim.x * blockDim.x;
+    BATCH_STRIDE(j0, n) {
+        uint32_t sl[INS_B], first[INS_B];
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) sl[b] = j0 + b * str < n ? a.slot[j0 + b * str] : NONE32;
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) first[b] = sl[b] != NONE32 ? a.tab.slots[sl[b]].v : NONE32;
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            if (sl[b] == NONE32) continue;
+            const uint32_t e = a.P[j0 + b * str];
+            if (first[b] != e) a.ra[e] = first[b];
+        }
     }
 }
 
@@ -701,14 +783,30 @@ __device__ __forceinline__ uint32_t first_kernel(const A& a, uint32_t d, uint64_
 __global__ void k_ua(A a) {
     if (failed(a)) return;
     const uint64_t trace_end = a.h->t_end_max;
-    GRID_STRIDE(j, a.h->nP) {
-        const uint32_t e = a.P[j];
-        if (!is_alloc(a, e)) continue;
-        const uint32_t d = c_dst(a.cls[e]);  // device number + 1
-        const uint32_t del = a.del_of[e];
-        const uint64_t end = del != NONE32 ? a.ev.t1(del) : trace_end;
-        const uint32_t p = first_kernel(a, d, a.ev.t0(e));
-        if (p == a.dend[d] || a.ks[p] > end) a.ua[e] = del != NONE32 ? del : NOPART;
+    const uint32_t n = a.h->nP, str = gridDim.x * blockDim.x;
+    BATCH_STRIDE(j0, n) {
+        uint32_t e[INS_B], c[INS_B], del[INS_B];
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) e[b] = j0 + b * str < n ? a.P[j0 + b * str] : NONE32;
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            c[b] = e[b] != NONE32 ? a.cls[e[b]] : 0;
+            del[b] = e[b] != NONE32 ? a.del_of[e[b]] : NONE32;
+        }
+        uint64_t t0[INS_B], end[INS_B];
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const bool al = c_kind(c[b]) == ODP_ALLOC;
+            t0[b] = al ? a.ev.t0(e[b]) : 0;
+            end[b] = !al ? 0 : del[b] != NONE32 ? a.ev.t1(del[b]) : trace_end;
+        }
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            if (c_kind(c[b]) != ODP_ALLOC) continue;
+            const uint32_t d = c_dst(c[b]);  // device number + 1
+            const uint32_t p = first_kernel(a, d, t0[b]);
+            if (p == a.dend[d] || a.ks[p] > end[b]) a.ua[e[b]] = del[b] != NONE32 ? del[b] : NOPART;
+        }
     }
 }
 
@@ -748,14 +846,26 @@ __global__ void k_ut_heads(A a) {
 __global__ void k_ut_insert(A a) {
     if (failed(a)) return;
     const uint32_t cap = *a.tab.cap_dev;
-    GRID_STRIDE(q, a.h->nU) {
-        uint32_t k = a.tab.cap_max + 1;
-        if (a.uc[q] == 0) {
-            Key128 key{a.ev.host(a.sv[q]), 1};
-            k = slot_key(a, prim::table_insert(a.tab, cap, key), a.sv[q]);
+    const uint32_t n = a.h->nU, str = gridDim.x * blockDim.x;
+    BATCH_STRIDE(q0, n) {
+        uint32_t e[INS_B], out[INS_B];
+        bool use[INS_B];
+        Key128 key[INS_B];
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const uint32_t q = q0 + b * str;
+            use[b] = q < n && a.uc[q] == 0;
+            e[b] = use[b] ? a.sv[q] : 0;
+            key[b] = use[b] ? Key128{a.ev.host(e[b]), 1} : Key128{0, 0};
         }
-        a.k2[q] = k;
-        a.v2[q] = q;
+        prim::table_insert_batch<INS_B, false>(a.tab, cap, key, e, use, out);
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const uint32_t q = q0 + b * str;
+            if (q >= n) continue;
+            a.k2[q] = use[b] ? slot_key(a, out[b], e[b]) : a.tab.cap_max + 1;
+            a.v2[q] = q;
+        }
     }
 }
 

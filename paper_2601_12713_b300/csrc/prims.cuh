@@ -381,6 +381,53 @@ __device__ __forceinline__ uint32_t table_insert(const Table& t, uint32_t cap, K
     return NONE32;
 }
 
+// Inserts up to B keys per thread with their compare-and-swaps in flight
+// together (the probes of different keys are independent).  use[b] false:
+// out[b] = NONE32.  MIN: also lower the slot's value to v[b].
+template <int B, bool MIN>
+__device__ __forceinline__ void table_insert_batch(const Table& t, uint32_t cap, const Key128* k,
+                                                   const uint32_t* v, const bool* use,
+                                                   uint32_t* out) {
+    const uint32_t mask = cap - 1;
+    const Key128 empty{EMPTY_KEY, EMPTY_KEY};
+    uint32_t slot[B];
+    bool done[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        out[b] = NONE32;
+        done[b] = !use[b];
+        slot[b] = 0;
+        if (!use[b]) continue;
+        if (k[b].lo == EMPTY_KEY && k[b].hi == EMPTY_KEY) {
+            if (MIN) atomicMin(&t.slots[t.cap_max].v, v[b]);
+            out[b] = t.cap_max;
+            done[b] = true;
+        } else {
+            slot[b] = (uint32_t)mix64(k[b].lo ^ mix64(k[b].hi)) & mask;
+        }
+    }
+    for (uint32_t probe = 0; probe < cap; ++probe) {
+        Key128 cur[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (!done[b]) cur[b] = atomicCAS(&t.slots[slot[b]].k, empty, k[b]);
+        bool again = false;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (done[b]) continue;
+            if (key_eq(cur[b], empty) || key_eq(cur[b], k[b])) {
+                if (MIN) atomicMin(&t.slots[slot[b]].v, v[b]);
+                out[b] = slot[b];
+                done[b] = true;
+            } else {
+                slot[b] = (slot[b] + 1) & mask;
+                again = true;
+            }
+        }
+        if (!again) break;
+    }
+}
+
 }  // namespace
 }  // namespace prim
 }  // namespace odp
