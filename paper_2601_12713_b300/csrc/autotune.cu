@@ -104,7 +104,11 @@ FpLaunch fp_schedule_for(uint64_t n) {
     std::lock_guard<std::mutex> lk(g_mu);
     ensure_loaded_locked();
     auto it = g_cache.find(size_class(n));
-    return it == g_cache.end() ? FpLaunch() : it->second;
+    if (it != g_cache.end()) return it->second;
+    FpLaunch L;
+    // one buffer: about one tile per warp (static first tiles, least climbing)
+    if (n == 1) L.tmin_scale = 1;
+    return L;
 }
 
 }  // namespace odp

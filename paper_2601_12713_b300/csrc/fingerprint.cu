@@ -378,8 +378,6 @@ struct WarpStack {
     uint64_t count[40];
 };
 
-// Hash chunks [c0, c0 + cnt) of a buffer (`cnt` <= 2^m); returns the subtree
-// root in every lane.
 // ---------------------------------------------------------------- bulk ring
 // Optional load path: whole 4 KiB chunks of 16-byte-aligned buffers are
 // copied into a per-warp ring of shared-memory slots with 1D bulk copies
@@ -438,6 +436,9 @@ __device__ __forceinline__ void ring_wait(Ring& r, int s) {
     r.parity ^= 1u << s;
 }
 
+// Hash chunks [c0, c0 + cnt) of a buffer (`cnt` <= 2^m); returns the subtree
+// root in every lane.  With STAGES > 0, whole chunks of a 16-byte-aligned
+// buffer (all but a partial last one) stream through the warp's bulk ring.
 template <bool ALIGNED, int STAGES>
 __device__ __forceinline__ U128 hash_tile(const uint8_t* base, uint64_t size, uint64_t c0,
                                           uint64_t cnt, int lane, uint64_t a0, uint64_t b0,
@@ -445,7 +446,6 @@ __device__ __forceinline__ U128 hash_tile(const uint8_t* base, uint64_t size, ui
     int depth = 0;
     U128 root{0, 0};
     uint64_t root_c = 0;
-    // chunks of this tile that go through the bulk ring: all but a partial last
     uint64_t nbulk = 0;
     if constexpr (STAGES > 0) {
         if (ALIGNED) nbulk = (size - (c0 + cnt - 1) * CHUNK) >= CHUNK ? cnt : cnt - 1;
@@ -532,8 +532,91 @@ __device__ __forceinline__ U128 hash_tile(const uint8_t* base, uint64_t size, ui
     return root;
 }
 
+// Where tile t lies: its buffer, the buffer's size and base, and its chunk range.
+struct TileInfo {
+    const uint8_t* base;
+    uint64_t size, nchunk, c0, cnt;
+    uint32_t b, tb;
+    int m;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const FpArgs& a, uint32_t t, uint32_t m_floor) {
+    TileInfo ti;
+    ti.b = a.n == 1 ? 0u : a.tile_buf[t];
+    ti.tb = a.single ? t : t - a.tile_off[ti.b];
+    ti.size = a.sizes[ti.b];
+    ti.base = (const uint8_t*)a.ptrs[ti.b];
+    ti.nchunk = n_chunks(ti.size);
+    ti.m = tile_log2(ti.nchunk, a.tmin, m_floor);
+    ti.c0 = (uint64_t)ti.tb << ti.m;
+    ti.cnt = umin64(1ull << ti.m, ti.nchunk - ti.c0);
+    return ti;
+}
+
+// Finishes a buffer of one tile, or climbs the 32-ary groups of tile roots:
+// the last warp to arrive at a group combines it (level L holds nodes
+// covering 2^m * 32^L chunks) and the last one at the top finishes the hash.
+__device__ __forceinline__ void climb(const FpArgs& a, const TileInfo& ti, U128 root, int lane) {
+    const uint64_t ntile = n_tiles(ti.nchunk, ti.m);
+    if (ntile == 1) {
+        if (lane == 0) {
+            U128 o = fp::finish(root, ti.size, ti.nchunk);
+            a.out[ti.b].lo = o.x;
+            a.out[ti.b].hi = o.y;
+        }
+        return;
+    }
+    uint64_t nl = ntile, idx = ti.tb, off = a.single ? 0 : a.node_off[ti.b];
+    uint64_t span = 1ull << ti.m;
+    U128 node = root;
+    while (true) {
+        if (nl == 1) {
+            if (lane == 0) {
+                U128 o = fp::finish(node, ti.size, ti.nchunk);
+                a.out[ti.b].lo = o.x;
+                a.out[ti.b].hi = o.y;
+            }
+            return;
+        }
+        const uint64_t nup = (nl + 31) / 32;
+        const uint64_t g = idx / 32;
+        const uint32_t gsize = (uint32_t)umin64(32, nl - 32 * g);
+        uint32_t old = 0;
+        if (lane == 0) {
+            a.nodes[off + idx] = node;
+            __threadfence();
+            old = atomicAdd(&a.counters[off + nl + g], 1u);
+        }
+        old = __shfl_sync(ODP_FULL_MASK, old, 0);
+        if (old != gsize - 1) return;  // another warp finishes this group
+        __threadfence();
+        U128 v{0, 0};
+        uint64_t c = 0;
+        if ((uint32_t)lane < gsize) {
+            const U128* src = &a.nodes[off + 32 * g + lane];
+            v.x = __ldcg((const unsigned long long*)&src->x);
+            v.y = __ldcg((const unsigned long long*)&src->y);
+            const uint64_t first = (32 * g + lane) * span;
+            c = umin64(span, ti.nchunk - first);
+        }
+        if (lane == 0) a.counters[off + nl + g] = 0;  // ready for the next call
+        node = warp_tree(v, c, gsize, lane);
+        off += nl;
+        nl = nup;
+        idx = g;
+        span *= 32;
+    }
+}
+
+// Resident warps per SM the register budget is set for: the register-load
+// path (STAGES = 0) needs more warps in flight than the bulk-copy ring.
 template <int WARPS, int STAGES>
-__global__ void __launch_bounds__(WARPS * 32) fp_tiles(FpArgs a) {
+constexpr int fp_min_ctas() {
+    return (STAGES == 0 ? 24 : 16) / WARPS > 0 ? (STAGES == 0 ? 24 : 16) / WARPS : 1;
+}
+
+template <int WARPS, int STAGES>
+__global__ void __launch_bounds__(WARPS * 32, fp_min_ctas<WARPS, STAGES>()) fp_tiles(FpArgs a) {
     __shared__ WarpStack stacks[WARPS];
     extern __shared__ __align__(128) uint8_t ring_smem[];
     const int lane = lane_id();
@@ -570,87 +653,43 @@ __global__ void __launch_bounds__(WARPS * 32) fp_tiles(FpArgs a) {
         m_floor = a.hdr->m_floor;
     }
 
-    uint32_t t = 0;
-    if (lane == 0) t = atomicAdd(&a.hdr->tile_counter, 1u);
-    t = __shfl_sync(ODP_FULL_MASK, t, 0);
-    while (t < T) {
-        // fetch the next tile index early to hide the atomic's latency
-        uint32_t t_next = 0;
-        if (lane == 0) t_next = atomicAdd(&a.hdr->tile_counter, 1u);
-
-        const uint32_t b = a.n == 1 ? 0u : a.tile_buf[t];
-        const uint32_t tb = a.single ? t : t - a.tile_off[b];
-        const uint64_t size = a.sizes[b];
-        const uint8_t* base = (const uint8_t*)a.ptrs[b];
-        const uint64_t nchunk = n_chunks(size);
-        const int m = tile_log2(nchunk, a.tmin, m_floor);
-        const uint64_t c0 = (uint64_t)tb << m;
-        const uint64_t cnt = umin64(1ull << m, nchunk - c0);
-
-        U128 root;
-        if (((uintptr_t)base & 15) == 0)
-            root = hash_tile<true, STAGES>(base, size, c0, cnt, lane, a0, b0, st, ring);
-        else
-            root = hash_tile<false, STAGES>(base, size, c0, cnt, lane, a0, b0, st, ring);
-
-        const uint64_t ntile = n_tiles(nchunk, m);
-        if (ntile == 1) {
-            if (lane == 0) {
-                U128 o = fp::finish(root, size, nchunk);
-                a.out[b].lo = o.x;
-                a.out[b].hi = o.y;
-            }
-        } else {
-            // climb: level L holds nodes covering span = 2^m * 32^L chunks
-            uint64_t nl = ntile, idx = tb, off = a.single ? 0 : a.node_off[b];
-            uint64_t span = 1ull << m;
-            U128 node = root;
-            while (true) {
-                if (nl == 1) {
-                    if (lane == 0) {
-                        U128 o = fp::finish(node, size, nchunk);
-                        a.out[b].lo = o.x;
-                        a.out[b].hi = o.y;
-                    }
-                    break;
-                }
-                const uint64_t nup = (nl + 31) / 32;
-                const uint64_t g = idx / 32;
-                const uint32_t gsize = (uint32_t)umin64(32, nl - 32 * g);
-                uint32_t old = 0;
-                if (lane == 0) {
-                    a.nodes[off + idx] = node;
-                    __threadfence();
-                    old = atomicAdd(&a.counters[off + nl + g], 1u);
-                }
-                old = __shfl_sync(ODP_FULL_MASK, old, 0);
-                if (old != gsize - 1) break;  // another warp finishes this group
-                __threadfence();
-                U128 v{0, 0};
-                uint64_t c = 0;
-                if ((uint32_t)lane < gsize) {
-                    const U128* src = &a.nodes[off + 32 * g + lane];
-                    v.x = __ldcg((const unsigned long long*)&src->x);
-                    v.y = __ldcg((const unsigned long long*)&src->y);
-                    const uint64_t first = (32 * g + lane) * span;
-                    c = umin64(span, nchunk - first);
-                }
-                if (lane == 0) a.counters[off + nl + g] = 0;  // ready for the next call
-                node = warp_tree(v, c, gsize, lane);
-                off += nl;
-                nl = nup;
-                idx = g;
-                span *= 32;
-            }
+    // A warp's first tile is its global warp index and its second that plus
+    // the warp count; later tiles come from the shared counter, requested
+    // when the previous tile starts so the atomic (contended by every warp)
+    // completes while a tile is hashed.  Warps without a first tile exit at
+    // once and never touch the counter, so a small buffer costs a few
+    // atomics, not one per warp of the grid.
+    const uint32_t total = gridDim.x * WARPS;
+    uint32_t t = blockIdx.x * WARPS + warp;
+    if (t >= T) {
+        // no tiles at all (empty or null buffers only): publish the plan's error here
+        if (T == 0 && t == 0 && lane == 0 && !a.single && a.status) {
+            const unsigned long long e = a.hdr->err;
+            if (e != ~0ull) atomicCAS((int*)a.status, 0, -(int)(e & 0xFF));
         }
+        return;
+    }
+    uint32_t t_next = t + total;
+    bool first = true;
+    while (t < T) {
+        if (!first && lane == 0) t_next = 2 * total + atomicAdd(&a.hdr->tile_counter, 1u);
+        first = false;
+        const TileInfo cur = tile_info(a, t, m_floor);
+        U128 root;
+        if (((uintptr_t)cur.base & 15) == 0)
+            root = hash_tile<true, STAGES>(cur.base, cur.size, cur.c0, cur.cnt, lane, a0, b0, st, ring);
+        else
+            root = hash_tile<false, STAGES>(cur.base, cur.size, cur.c0, cur.cnt, lane, a0, b0, st, ring);
+        climb(a, cur, root, lane);
         t = __shfl_sync(ODP_FULL_MASK, t_next, 0);
     }
-    // The last warp out resets the tile counter for the next call and
-    // publishes the plan's error code (the first error index is not kept).
+    // The last warp out (of the min(T, warps) that took tiles) resets the
+    // tile counter for the next call and publishes the plan's error code (the
+    // first error index is not kept).
     if (lane == 0) {
         __threadfence();
-        const uint32_t total = gridDim.x * WARPS;
-        if (atomicAdd(&a.hdr->warps_done, 1u) == total - 1) {
+        const uint32_t takers = T < total ? T : total;
+        if (atomicAdd(&a.hdr->warps_done, 1u) == takers - 1) {
             a.hdr->tile_counter = 0;
             a.hdr->warps_done = 0;
             if (!a.single && a.status) {

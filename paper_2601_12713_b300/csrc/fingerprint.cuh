@@ -21,7 +21,7 @@ int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128
            cudaStream_t stream, const FpLaunch& L);
 
 // Schedule for a batch of n buffers: the autotuned entry for n's size class
-// if one exists, else the defaults.
+// if one exists, else the defaults (tile target scale 1 for a single buffer).
 FpLaunch fp_schedule_for(uint64_t n);
 
 }  // namespace odp
