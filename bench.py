@@ -31,8 +31,8 @@ METRIC = "fingerprint GB/s vs HBM peak; M events/s analyzed; p99 event-to-findin
 BUF_BYTES = 4 << 30
 SEED = 0x0DB2
 # dram read+write bytes of one fp_tiles launch over 512 MiB from an ncu full
-# capture of the default (8 warps, 2 bulk slots) kernel: 536.98 MB read +
-# 4.18 MB written.
+# capture of the default (8 warps, 2 bulk slots) kernel: 536.97 MB read +
+# 3.75 MB written.
 # Traffic grows with the bytes hashed: a launch over B bytes moves about
 # B / 512 MiB times this.
 FP_TILES_TRAFFIC_512MIB = 540.73e6
