@@ -296,7 +296,7 @@ def run_ours(args):
                 "parallelism": f"replicas x{world}",
             },
             "clocks": clocks,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": args.steps,
             "roofline": {
                 "bound": "hbm",
                 "achieved": round(achieved, 2),
@@ -314,6 +314,8 @@ def run_ours(args):
             },
             "e2e": e2e,
         })
+        if rank == 0:
+            result["l2_resident"] = l2_resident(odp, buf, stream, peak, peak_kind)
         if rank == 0 and not args.skip_cpu:
             result["cpu_baseline"] = cpu_baseline_fp(buf)
         del buf
@@ -621,7 +623,29 @@ def sweep(odp, sgpu, content, stream):
     return rows
 
 
+def l2_resident(odp, buf, stream, peak, peak_kind):
+    """The hash kernel's ceiling away from HBM: one call over 128 aliases of
+    one 32 MiB slice (4 GiB hashed, the slice stays in the 126 MB L2).  A rate
+    well above the HBM peak shows that the ALU does not bind the HBM-sized
+    case."""
+    import torch
+
+    sl, k = 32 << 20, 128
+    ptrs = torch.full((k,), buf.data_ptr(), dtype=torch.int64, device="cuda")
+    sizes = torch.full((k,), sl, dtype=torch.int64, device="cuda")
+    out = torch.empty((k, 2), dtype=torch.int64, device="cuda")
+    total, _ = time_calls(lambda: odp.fingerprint(ptrs, sizes, out, stream), 10, 3, stream)
+    gbs = sl * k * 10 / (total / 1e3) / 1e9
+    o = out.cpu().numpy()
+    return {"gbs": round(gbs, 1), "vs_hbm_peak": round(gbs / peak, 3),
+            "peak_kind": f"{peak_kind} (copy read+write)",
+            "input": "128 aliases of one 32 MiB slice of the benchmark buffer in one call",
+            "identical_fingerprints": bool((o == o[0]).all())}
+
+
 def cpu_baseline_fp(buf):
+    import concurrent.futures
+
     import oracle
 
     sample = 1 << 30
@@ -630,8 +654,19 @@ def cpu_baseline_fp(buf):
     t0 = time.perf_counter()
     oracle.fp128(host)
     dt = time.perf_counter() - t0
+    # the same oracle function on every host core (one slice per thread; the
+    # oracle call releases the interpreter lock)
+    threads = os.cpu_count() or 1
+    step = sample // threads
+    with concurrent.futures.ThreadPoolExecutor(threads) as ex:
+        t1 = time.perf_counter()
+        list(ex.map(lambda i: oracle.fp128(host[i * step:(i + 1) * step]), range(threads)))
+        dt_all = time.perf_counter() - t1
     return {"value": round(sample / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "first 1 GiB of the 4 GiB random buffer, FP128 by the single-threaded oracle"}
+            "sample": "first 1 GiB of the 4 GiB random buffer, FP128 by the single-threaded oracle",
+            "all_cores": {"value": round(step * threads / dt_all / 1e9, 4), "unit": "GB/s",
+                          "threads": threads,
+                          "sample": "the same 1 GiB in one slice per host thread"}}
 
 
 # ---------------------------------------------------------------- reference
