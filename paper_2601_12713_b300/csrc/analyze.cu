@@ -68,11 +68,6 @@ struct Ev {
     __device__ __forceinline__ uint64_t host(uint32_t i) const { return u64(i, 16); }
     __device__ __forceinline__ uint64_t daddr(uint32_t i) const { return u64(i, 24); }
     __device__ __forceinline__ uint64_t bytes(uint32_t i) const { return u64(i, 32); }
-    __device__ __forceinline__ uint64_t fplo(uint32_t i) const { return u64(i, 40); }
-    __device__ __forceinline__ uint64_t fphi(uint32_t i) const { return u64(i, 48); }
-    __device__ __forceinline__ uint32_t site(uint32_t i) const {
-        return *(const uint32_t*)(p + 64ull * i + 56);
-    }
 };
 
 // cls word: kind | (src + 1) << 8 | (dst + 1) << 16
@@ -96,6 +91,7 @@ struct A {
     uint32_t *dstart, *dend;  // kernel ranges per device, indexed by device number + 1
     unsigned long long* sites;  // [5][65536][3]
     Table tab;
+    prim::KeyTable ktab;  // the same memory as tab, 16-byte slots
     odp_findings out;
 };
 
@@ -568,7 +564,7 @@ __global__ void k_mx_partner(A a) {
 
 __global__ void k_p_insert(A a) {
     if (failed(a)) return;
-    const uint32_t cap = *a.tab.cap_dev;
+    const uint32_t cap = *a.ktab.cap_dev;
     const uint32_t n = a.h->nP, str = gridDim.x * blockDim.x;
     BATCH_STRIDE(j0, n) {
         uint32_t e[INS_B], out[INS_B];
@@ -583,7 +579,7 @@ __global__ void k_p_insert(A a) {
 #pragma unroll
         for (int b = 0; b < INS_B; ++b)
             key[b] = use[b] ? Key128{a.ev.daddr(e[b]), (uint64_t)c_dst(a.cls[e[b]])} : Key128{0, 0};
-        prim::table_insert_batch<INS_B, false>(a.tab, cap, key, e, use, out);
+        prim::table_insert_batch<INS_B, false>(a.ktab, cap, key, e, use, out);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             if (!use[b]) continue;
@@ -845,7 +841,7 @@ __global__ void k_ut_heads(A a) {
 // cap_max + 1 (above every slot).
 __global__ void k_ut_insert(A a) {
     if (failed(a)) return;
-    const uint32_t cap = *a.tab.cap_dev;
+    const uint32_t cap = *a.ktab.cap_dev;
     const uint32_t n = a.h->nU, str = gridDim.x * blockDim.x;
     BATCH_STRIDE(q0, n) {
         uint32_t e[INS_B], out[INS_B];
@@ -858,12 +854,12 @@ __global__ void k_ut_insert(A a) {
             e[b] = use[b] ? a.sv[q] : 0;
             key[b] = use[b] ? Key128{a.ev.host(e[b]), 1} : Key128{0, 0};
         }
-        prim::table_insert_batch<INS_B, false>(a.tab, cap, key, e, use, out);
+        prim::table_insert_batch<INS_B, false>(a.ktab, cap, key, e, use, out);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             const uint32_t q = q0 + b * str;
             if (q >= n) continue;
-            a.k2[q] = use[b] ? slot_key(a, out[b], e[b]) : a.tab.cap_max + 1;
+            a.k2[q] = use[b] ? slot_key(a, out[b], e[b]) : a.ktab.cap_max + 1;
             a.v2[q] = q;
         }
     }
@@ -875,7 +871,7 @@ __global__ void k_ut_next(A a) {
     if (failed(a)) return;
     const uint32_t nU = a.h->nU;
     GRID_STRIDE(r, nU) {
-        if (a.k2[r] > a.tab.cap_max || r + 1 >= nU || a.k2[r + 1] != a.k2[r]) continue;
+        if (a.k2[r] > a.ktab.cap_max || r + 1 >= nU || a.k2[r + 1] != a.k2[r]) continue;
         const uint32_t q = a.v2[r], q2 = a.v2[r + 1];
         const uint32_t s1 = a.id1[q] + a.f1[q] - 1, s2 = a.id1[q2] + a.f1[q2] - 1;
         if (s1 == s2) a.ut[a.sv[q]] = a.sv[q2];
@@ -884,7 +880,6 @@ __global__ void k_ut_next(A a) {
 
 // ------------------------------------------------------------ emission
 
-__device__ __forceinline__ uint64_t dur(const A& a, uint32_t i) { return a.ev.t1(i) - a.ev.t0(i); }
 __device__ __forceinline__ uint64_t lohi(uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; }
 
 __device__ __forceinline__ uint32_t partner_of(const A& a, int kind, uint32_t i) {
@@ -1317,6 +1312,9 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     a.tab.slots = (prim::Slot*)(b + o_tslots);
     a.tab.cap_max = cap_max;
     a.tab.cap_dev = &a.h->tcap;
+    a.ktab.keys = (Key128*)(b + o_tslots);
+    a.ktab.cap_max = cap_max;
+    a.ktab.cap_dev = &a.h->tcap;
     a.out = out;
     prim::SortTmp srt;
     srt.keys_alt = (uint32_t*)(b + o_keys_alt);
@@ -1382,7 +1380,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     k_mx_partner<<<gX, TPB, 0, s>>>(a);
 
     // ---- pairs
-    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nP, n);
+    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.ktab, nP, n);
     k_p_insert<<<gX, TPB, 0, s>>>(a);
     prim::radix_sort(a.sk, a.sv, nP, n, bits_slot, srt, s);
     k_seg_heads<<<gX, TPB, 0, s>>>(a, nP);
@@ -1412,7 +1410,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     k_ut_class<<<gX, TPB, 0, s>>>(a);
     k_ut_heads<<<gX, TPB, 0, s>>>(a);
     prim::exclusive_scan(a.f1, a.id1, nU, n, &a.h->nsegU, scan_tmp, s);
-    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nU, n);
+    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.ktab, nU, n);
     k_ut_insert<<<gX, TPB, 0, s>>>(a);
     prim::radix_sort(a.k2, a.v2, nU, n, bits_slot, srt, s);
     k_ut_next<<<gX, TPB, 0, s>>>(a);

@@ -312,6 +312,18 @@ struct Table {
     Slot* slots;        // capacity + 1 slots (the last one holds the all-ones key)
     uint32_t cap_max;   // power of two
     uint32_t* cap_dev;  // capacity in use (power of two, set on the device)
+    __device__ __forceinline__ Key128* key_at(uint32_t s) const { return &slots[s].k; }
+    __device__ __forceinline__ uint32_t* val_at(uint32_t s) const { return &slots[s].v; }
+};
+
+// Keys only, 16 bytes a slot: for grouping, where the slot index is the
+// group key and no value is kept.
+struct KeyTable {
+    Key128* keys;       // capacity + 1 slots (the last one holds the all-ones key)
+    uint32_t cap_max;
+    uint32_t* cap_dev;
+    __device__ __forceinline__ Key128* key_at(uint32_t s) const { return &keys[s]; }
+    __device__ __forceinline__ uint32_t* val_at(uint32_t) const { return nullptr; }
 };
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -323,13 +335,17 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     return x;
 }
 
+__device__ __forceinline__ uint32_t table_cap(uint32_t cnt, uint32_t cap_max) {
+    uint32_t cap = 1024;
+    while (cap < (uint64_t)cnt + cnt / 4 && cap < cap_max) cap <<= 1;
+    return cap;
+}
+
 // Set the capacity in use to the smallest power of two >= 1.25 * count (at
 // least 1024, at most cap_max; load stays <= 0.8) and clear it with whole
 // 32-byte slot writes.
 __global__ void table_clear(Table t, const uint32_t* count_dev, uint32_t count_max) {
-    const uint32_t cnt = dev_len(count_dev, count_max);
-    uint32_t cap = 1024;
-    while (cap < (uint64_t)cnt + cnt / 4 && cap < t.cap_max) cap <<= 1;
+    const uint32_t cap = table_cap(dev_len(count_dev, count_max), t.cap_max);
     if (blockIdx.x == 0 && threadIdx.x == 0) *t.cap_dev = cap;
     const uint32_t stride = gridDim.x * blockDim.x;
     uint4* w = reinterpret_cast<uint4*>(t.slots);
@@ -340,6 +356,17 @@ __global__ void table_clear(Table t, const uint32_t* count_dev, uint32_t count_m
         w[2 * (size_t)slot] = empty_key;
         w[2 * (size_t)slot + 1] = empty_val;
     }
+}
+
+// The same for a key-only table (one 16-byte write per slot).
+__global__ void table_clear(KeyTable t, const uint32_t* count_dev, uint32_t count_max) {
+    const uint32_t cap = table_cap(dev_len(count_dev, count_max), t.cap_max);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t.cap_dev = cap;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    uint4* w = reinterpret_cast<uint4*>(t.keys);
+    const uint4 empty_key = make_uint4(~0u, ~0u, ~0u, ~0u);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= cap; i += stride)
+        w[i == cap ? t.cap_max : i] = empty_key;
 }
 
 // Inserts `k` and lowers the slot's value to v; returns the slot index, or
@@ -384,8 +411,8 @@ __device__ __forceinline__ uint32_t table_insert(const Table& t, uint32_t cap, K
 // Inserts up to B keys per thread with their compare-and-swaps in flight
 // together (the probes of different keys are independent).  use[b] false:
 // out[b] = NONE32.  MIN: also lower the slot's value to v[b].
-template <int B, bool MIN>
-__device__ __forceinline__ void table_insert_batch(const Table& t, uint32_t cap, const Key128* k,
+template <int B, bool MIN, class TableT>
+__device__ __forceinline__ void table_insert_batch(const TableT& t, uint32_t cap, const Key128* k,
                                                    const uint32_t* v, const bool* use,
                                                    uint32_t* out) {
     const uint32_t mask = cap - 1;
@@ -399,7 +426,7 @@ __device__ __forceinline__ void table_insert_batch(const Table& t, uint32_t cap,
         slot[b] = 0;
         if (!use[b]) continue;
         if (k[b].lo == EMPTY_KEY && k[b].hi == EMPTY_KEY) {
-            if (MIN) atomicMin(&t.slots[t.cap_max].v, v[b]);
+            if (MIN) atomicMin(t.val_at(t.cap_max), v[b]);
             out[b] = t.cap_max;
             done[b] = true;
         } else {
@@ -410,13 +437,13 @@ __device__ __forceinline__ void table_insert_batch(const Table& t, uint32_t cap,
         Key128 cur[B];
 #pragma unroll
         for (int b = 0; b < B; ++b)
-            if (!done[b]) cur[b] = atomicCAS(&t.slots[slot[b]].k, empty, k[b]);
+            if (!done[b]) cur[b] = atomicCAS(t.key_at(slot[b]), empty, k[b]);
         bool again = false;
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             if (done[b]) continue;
             if (key_eq(cur[b], empty) || key_eq(cur[b], k[b])) {
-                if (MIN) atomicMin(&t.slots[slot[b]].v, v[b]);
+                if (MIN) atomicMin(t.val_at(slot[b]), v[b]);
                 out[b] = slot[b];
                 done[b] = true;
             } else {
