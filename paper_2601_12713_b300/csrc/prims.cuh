@@ -249,6 +249,106 @@ inline size_t sort_hist_words(uint32_t n_max) {
     return 256ull * ((n_max + SORT_TILE - 1) / SORT_TILE + 1);
 }
 
+// ------------------------------------------------------ one-block sort
+
+constexpr int SMALL_SORT_THREADS = 1024;
+constexpr uint32_t SMALL_SORT_MAX = 8192;  // 8 items per thread
+constexpr size_t SMALL_SORT_SMEM = 4ull * SMALL_SORT_MAX * 4 + 32ull * 256 * 4;
+
+// Up to 8192 (key, value) pairs sorted stably by the low key_bits bits of
+// the keys by one block, in shared memory: per 8-bit digit, warp w ranks its
+// 256 items (index order: round-major, then lane) against its own digit
+// counters, the counters are scanned across warps and digits, and the items
+// move to the other buffer.  One launch instead of five per pass.
+__global__ void __launch_bounds__(SMALL_SORT_THREADS)
+sort_small(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, uint32_t n_max, int key_bits) {
+    constexpr int W = SMALL_SORT_THREADS / 32;
+    constexpr int ROUNDS = SMALL_SORT_MAX / SMALL_SORT_THREADS;
+    extern __shared__ __align__(16) uint32_t small_sm[];
+    uint32_t* k0 = small_sm;
+    uint32_t* v0 = k0 + SMALL_SORT_MAX;
+    uint32_t* k1 = v0 + SMALL_SORT_MAX;
+    uint32_t* v1 = k1 + SMALL_SORT_MAX;
+    uint32_t(*cnt)[256] = reinterpret_cast<uint32_t(*)[256]>(v1 + SMALL_SORT_MAX);
+    __shared__ uint32_t scan_tmp[40];
+    __shared__ uint32_t dstart[256];
+    const uint32_t n = min(dev_len(n_dev, n_max), SMALL_SORT_MAX);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1;
+    for (uint32_t i = threadIdx.x; i < n; i += SMALL_SORT_THREADS) {
+        k0[i] = keys[i];
+        v0[i] = vals[i];
+    }
+    for (int shift = 0; shift < key_bits; shift += 8) {
+        const int bits = min(8, key_bits - shift);
+        const uint32_t radix = 1u << bits;
+        for (int d = lane; d < 256; d += 32) cnt[warp][d] = 0;
+        __syncthreads();
+        uint32_t rank[ROUNDS];
+#pragma unroll
+        for (int r = 0; r < ROUNDS; ++r) {
+            const uint32_t i = warp * (32 * ROUNDS) + r * 32 + lane;
+            const bool valid = i < n;
+            const uint32_t d = valid ? (k0[i] >> shift) & (radix - 1) : 256u;
+            const uint32_t peers = __match_any_sync(ODP_FULL_MASK, d);
+            const uint32_t before = valid ? cnt[warp][d] : 0;
+            rank[r] = before + __popc(peers & lt);
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) cnt[warp][d] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        uint32_t tot = 0;
+        if (threadIdx.x < 256) {
+            for (int w = 0; w < W; ++w) {
+                const uint32_t c = cnt[w][threadIdx.x];
+                cnt[w][threadIdx.x] = tot;
+                tot += c;
+            }
+        }
+        uint32_t all;
+        const uint32_t e = block_exclusive_scan_u32(threadIdx.x < 256 ? tot : 0, &all, scan_tmp);
+        if (threadIdx.x < 256) dstart[threadIdx.x] = e;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < ROUNDS; ++r) {
+            const uint32_t i = warp * (32 * ROUNDS) + r * 32 + lane;
+            if (i < n) {
+                const uint32_t d = (k0[i] >> shift) & (radix - 1);
+                const uint32_t pos = dstart[d] + cnt[warp][d] + rank[r];
+                k1[pos] = k0[i];
+                v1[pos] = v0[i];
+            }
+        }
+        __syncthreads();
+        uint32_t* t = k0;
+        k0 = k1;
+        k1 = t;
+        t = v0;
+        v0 = v1;
+        v1 = t;
+    }
+    for (uint32_t i = threadIdx.x; i < n; i += SMALL_SORT_THREADS) {
+        keys[i] = k0[i];
+        vals[i] = v0[i];
+    }
+}
+
+inline bool sort_small_ready() {
+    static bool done[256] = {};
+    const int dev = current_device();
+    if (dev < 0 || dev >= 256) return false;
+    if (!done[dev]) {
+        if (cudaFuncSetAttribute(sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SMALL_SORT_SMEM) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        done[dev] = true;
+    }
+    return true;
+}
+
 // Resident sort_downsweep blocks per SM (queried once per device).
 inline int downsweep_per_sm() {
     static int cache[256] = {};
@@ -269,6 +369,10 @@ inline int downsweep_per_sm() {
 inline void radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, uint32_t n_max,
                        int key_bits, const SortTmp& t, cudaStream_t s) {
     if (n_max == 0 || key_bits <= 0) return;
+    if (n_max <= SMALL_SORT_MAX && sort_small_ready()) {
+        sort_small<<<1, SMALL_SORT_THREADS, SMALL_SORT_SMEM, s>>>(keys, vals, n_dev, n_max, key_bits);
+        return;
+    }
     const uint32_t ntiles = (n_max + SORT_TILE - 1) / SORT_TILE;
     const int passes = (key_bits + 7) / 8;
     // an even number of passes leaves the data in place

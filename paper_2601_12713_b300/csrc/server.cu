@@ -20,6 +20,22 @@
 // list, which the first reception at that endpoint in a later batch closes.
 // Groups that ever show a third endpoint stop streaming round trips; their
 // exact result comes from odp_analyze over the log.
+// Streaming pairs and Alg. 3: a table <device address, device> holds the top
+// of each address's stack of open allocations (links per log index); a
+// DELETE closes the nearest open ALLOC, in batch order per address.  A
+// completed pair inserts <host address, device, bytes> with its alloc into a
+// second table; a pair whose alloc is not that key's first is a repeated
+// allocation.  (Equal to the offline result when pairs of one key complete
+// in alloc order, i.e. unless allocations of one key nest.)
+// Streaming Alg. 4: an allocation is used iff some kernel on its device
+// overlaps [alloc start, delete end].  Kernels of earlier batches are summed
+// up by their largest end per device; kernels of the pair's batch are checked
+// one by one; a pair still undecided waits in a list until a batch starts
+// after its delete ends (no later kernel can overlap it) or a kernel of a
+// later batch overlaps it.  Flush ends the trace: waiting pairs are unused,
+// and allocations never deleted are checked against every kernel seen.
+// Alg. 5 (unused transfers) is not streamed: it needs the next kernel of each
+// transfer's device and the end of the trace; odp_analyze over the log gives it.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -48,12 +64,19 @@ uint64_t now_ns() {
 }
 
 constexpr uint32_t EP_MORE = 1u << 16;  // endpoint set: more than two endpoints
+constexpr int SRV_NDEV = 129;            // host + devices 0..127
 
 struct SrvDev {
     odp_event* log;
     uint32_t* cid;     // per log index (transfers)
-    uint32_t* next;    // pending-list links, per log index
+    uint32_t* next;    // per log index: pending-list links (transfers), open-alloc stack links
     Table t_fp, t_dd, t_pend, t_ep, t_b;
+    Table t_pair;      // <device address, device> -> top of the open-alloc stack
+    Table t_rid;       // <host address, device, bytes> -> first completed pair's alloc
+    unsigned long long* kmax;  // per device: 1 + largest kernel end seen (0: none)
+    uint2* pend[2];    // pairs waiting for the Alg. 4 decision (alloc, delete), ping-pong
+    uint32_t* npend;   // [2] counts, [2] overflow count
+    uint32_t pend_cap;
 };
 
 struct SlotDev {
@@ -72,6 +95,11 @@ struct SlotDev {
     odp_finding* find;     // streamed findings of the batch
     uint64_t* complete;    // log index of the event that completed each finding
     uint32_t* nfind;
+    uint32_t* pa;          // pairs completed in the batch: alloc, delete
+    uint32_t* pd;
+    uint32_t* rslot;       // their slot in t_rid
+    uint32_t* bk;          // kernels of the batch (log indices)
+    uint32_t* cnt;         // [0] pairs, [1] kernels
 };
 
 __device__ __forceinline__ uint32_t ep_of(int8_t dev) { return (uint32_t)(dev + 1) & 0xFF; }
@@ -87,6 +115,20 @@ __device__ __forceinline__ void emit(const SlotDev& s, uint32_t cap, const odp_e
     if (j >= cap) return;
     store_finding(s.find, j, kind, log[e].site_id, log[p].site_id, e, p, log[wasted_of].bytes,
                   log[wasted_of].t_end_ns - log[wasted_of].t_start_ns);
+    s.complete[j] = completing;
+}
+
+__device__ __forceinline__ uint64_t dur_of(const odp_event& e) { return e.t_end_ns - e.t_start_ns; }
+
+// A finding with explicit wasted bytes and time; partner NONE32 = none.
+__device__ __forceinline__ void emit_w(const SlotDev& s, uint32_t cap, const odp_event* log,
+                                       uint8_t kind, uint64_t e, uint32_t p, uint64_t wb,
+                                       uint64_t wn, uint64_t completing) {
+    const uint32_t j = atomicAdd(s.nfind, 1u);
+    if (j >= cap) return;
+    const bool np = p == NONE32;
+    store_finding(s.find, j, kind, log[e].site_id, np ? 0xFFFFFFFFu : log[p].site_id, e,
+                  np ? ODP_NO_EVENT : (uint64_t)p, wb, wn);
     s.complete[j] = completing;
 }
 
@@ -215,6 +257,144 @@ __global__ void srv_rt_batch(SrvDev d, SlotDev s, uint64_t g0, uint32_t cap) {
     }
 }
 
+// Alloc/delete events of the batch keyed by their <device address, device>
+// slot (other events sort last); value = batch position.
+__global__ void srv_pair_keys(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
+    const uint32_t cap = *d.t_pair.cap_dev, none_key = d.t_pair.cap_max + 1;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+        const odp_event& e = d.log[g0 + q];
+        uint32_t k = none_key;
+        if (e.kind == ODP_ALLOC || e.kind == ODP_DELETE) {
+            const uint32_t sl = prim::table_insert(d.t_pair, cap, Key128{e.dev_addr, ep_of(e.dst_dev)});
+            if (sl != NONE32) k = sl;
+        }
+        s.skeys[q] = k;
+        s.svals[q] = q;
+    }
+}
+
+// One thread per address group of the batch (sorted, batch order inside)
+// walks it: ALLOC pushes on the address's open-alloc stack, DELETE pops the
+// nearest open ALLOC and records the pair.  Kernels of the batch are listed.
+__global__ void srv_pair_walk(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
+    const uint32_t none_key = d.t_pair.cap_max + 1;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+        if (d.log[g0 + r].kind == ODP_KERNEL) s.bk[atomicAdd(&s.cnt[1], 1u)] = (uint32_t)(g0 + r);
+        const uint32_t k = s.skeys[r];
+        if (k == none_key || (r > 0 && s.skeys[r - 1] == k)) continue;
+        uint32_t top = d.t_pair.slots[k].v;
+        for (uint32_t t = r; t < m && s.skeys[t] == k; ++t) {
+            const uint32_t g = (uint32_t)(g0 + s.svals[t]);
+            if (d.log[g].kind == ODP_ALLOC) {
+                d.next[g] = top;
+                top = g;
+            } else if (top != NONE32) {
+                const uint32_t i = atomicAdd(&s.cnt[0], 1u);
+                s.pa[i] = top;
+                s.pd[i] = g;
+                top = d.next[top];
+            }
+        }
+        d.t_pair.slots[k].v = top;
+    }
+}
+
+__device__ __forceinline__ Key128 rid_key(const odp_event& e) {
+    return Key128{e.host_addr, e.bytes | ((uint64_t)ep_of(e.dst_dev) << 56)};
+}
+
+__global__ void srv_ra_insert(SrvDev d, SlotDev s) {
+    const uint32_t cap = *d.t_rid.cap_dev, n = s.cnt[0];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        s.rslot[i] = prim::table_insert_min(d.t_rid, cap, rid_key(d.log[s.pa[i]]), s.pa[i]);
+}
+
+__global__ void srv_ra_emit(SrvDev d, SlotDev s, uint32_t cap) {
+    const uint32_t n = s.cnt[0];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (s.rslot[i] == NONE32) continue;
+        const uint32_t a = s.pa[i], first = d.t_rid.slots[s.rslot[i]].v;
+        if (first == a) continue;
+        const odp_event& ea = d.log[a];
+        emit_w(s, cap, d.log, ODP_RA, a, first, ea.bytes, dur_of(ea) + dur_of(d.log[s.pd[i]]),
+               s.pd[i]);
+    }
+}
+
+// Some kernel of the batch on `dev` overlaps [lo, hi].
+__device__ __forceinline__ bool batch_kernel_overlaps(const SrvDev& d, const SlotDev& s,
+                                                      uint32_t dev, uint64_t lo, uint64_t hi) {
+    const uint32_t nk = s.cnt[1];
+    for (uint32_t i = 0; i < nk; ++i) {
+        const odp_event& k = d.log[s.bk[i]];
+        if (ep_of(k.dst_dev) == dev && k.t_start_ns <= hi && k.t_end_ns >= lo) return true;
+    }
+    return false;
+}
+
+// Alg. 4 for the batch's pairs (against earlier kernels, then the batch's)
+// and for the waiting pairs (against the batch's kernels); undecided pairs
+// whose delete ends before t_next (the start of every later event) are
+// unused, the rest wait in list `nxt`.
+__global__ void srv_ua(SrvDev d, SlotDev s, uint32_t cap, uint64_t t_next, int cur) {
+    const int nxt = cur ^ 1;
+    const uint32_t n_new = s.cnt[0], n_old = min(d.npend[cur], d.pend_cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_new + n_old;
+         i += gridDim.x * blockDim.x) {
+        const bool fresh = i < n_new;
+        const uint32_t a = fresh ? s.pa[i] : d.pend[cur][i - n_new].x;
+        const uint32_t g = fresh ? s.pd[i] : d.pend[cur][i - n_new].y;
+        const odp_event& ea = d.log[a];
+        const odp_event& eg = d.log[g];
+        const uint32_t dev = ep_of(ea.dst_dev);
+        bool used = false;
+        if (fresh) {
+            const unsigned long long km = d.kmax[dev];
+            used = km != 0 && km - 1 >= ea.t_start_ns;
+        }
+        if (!used) used = batch_kernel_overlaps(d, s, dev, ea.t_start_ns, eg.t_end_ns);
+        if (used) continue;
+        if (eg.t_end_ns < t_next) {
+            emit_w(s, cap, d.log, ODP_UA, a, g, ea.bytes, dur_of(ea) + dur_of(eg), g);
+        } else {
+            const uint32_t j = atomicAdd(&d.npend[nxt], 1u);
+            if (j < d.pend_cap) d.pend[nxt][j] = make_uint2(a, g);
+            else atomicAdd(&d.npend[2], 1u);
+        }
+    }
+}
+
+__global__ void srv_kmax(SrvDev d, SlotDev s) {
+    const uint32_t nk = s.cnt[1];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += gridDim.x * blockDim.x) {
+        const odp_event& k = d.log[s.bk[i]];
+        atomicMax(&d.kmax[ep_of(k.dst_dev)], (unsigned long long)k.t_end_ns + 1ull);
+    }
+}
+
+// Flush: every waiting pair is unused (no kernel follows the end of the
+// trace); every allocation still open is checked against all kernels seen,
+// with the end of the trace as its delete end.
+__global__ void srv_flush_ua(SrvDev d, SlotDev s, uint32_t cap, int cur, uint64_t max_events) {
+    const uint32_t n_old = min(d.npend[cur], d.pend_cap);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_old; i += stride) {
+        const uint32_t a = d.pend[cur][i].x, g = d.pend[cur][i].y;
+        emit_w(s, cap, d.log, ODP_UA, a, g, d.log[a].bytes, dur_of(d.log[a]) + dur_of(d.log[g]),
+               ~0ull);
+    }
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= d.t_pair.cap_max; k += stride) {
+        uint32_t a = d.t_pair.slots[k].v;
+        for (uint64_t guard = 0; a != NONE32 && guard < max_events; ++guard) {
+            const odp_event& ea = d.log[a];
+            const unsigned long long km = d.kmax[ep_of(ea.dst_dev)];
+            if (!(km != 0 && km - 1 >= ea.t_start_ns))
+                emit_w(s, cap, d.log, ODP_UA, a, NONE32, ea.bytes, dur_of(ea), ~0ull);
+            a = d.next[a];
+        }
+    }
+}
+
 __global__ void srv_zero(uint32_t* p) { *p = 0; }
 
 struct Pending {
@@ -279,6 +459,12 @@ struct odp_server {
     std::deque<odp_finding> outq;
     std::vector<uint64_t> latencies;
     uint64_t batches = 0, streamed = 0, late = 0, first_submit = 0, last_done = 0;
+    std::mutex an_mu;             // orders work enqueued on the analysis stream
+    int pend_cur = 0;             // which waiting-pair list is current (an_mu)
+    uint64_t t_released_max = 0;  // largest start time launched so far (an_mu)
+    odp::SlotDev fl;              // flush-time finding buffers (find, complete, nfind)
+    odp_finding* h_fl_find = nullptr;
+    uint32_t* h_fl_n = nullptr;
     int error = ODP_OK;
 };
 
@@ -335,6 +521,7 @@ void launch_batch(odp_server* S, Slot& sl) {
     cudaEventRecord(sl.fp_done, fs);
 
     // analysis, in batch order on one stream
+    std::lock_guard<std::mutex> an_lk(S->an_mu);
     cudaStreamWaitEvent(as, sl.fp_done, 0);
     const uint64_t g0 = sl.g0;
     cudaMemcpyAsync(S->d.log + g0, sl.d.ev, sizeof(odp_event) * m, cudaMemcpyDeviceToDevice, as);
@@ -348,6 +535,22 @@ void launch_batch(odp_server* S, Slot& sl) {
     prim::radix_sort(sl.d.skeys, sl.d.svals, sl.d.nx, S->cfg.max_batch_events,
                      prim::bit_length(S->cfg.max_events), sl.d.sort, as);
     srv_rt_batch<<<grid, 256, 0, as>>>(S->d, sl.d, g0, S->find_cap);
+    // pairs, Alg. 3, Alg. 4
+    uint64_t t_next = S->t_released_max;
+    for (uint32_t q = 0; q < m; ++q) t_next = std::max(t_next, sl.h_ev[q].t_start_ns);
+    S->t_released_max = t_next;
+    cudaMemsetAsync(sl.d.cnt, 0, 8, as);
+    srv_pair_keys<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
+    prim::radix_sort(sl.d.skeys, sl.d.svals, nullptr, m, prim::bit_length(S->d.t_pair.cap_max + 1),
+                     sl.d.sort, as);
+    srv_pair_walk<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
+    srv_ra_insert<<<grid, 256, 0, as>>>(S->d, sl.d);
+    srv_ra_emit<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap);
+    const int cur = S->pend_cur;
+    srv_zero<<<1, 1, 0, as>>>(S->d.npend + (cur ^ 1));
+    srv_ua<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap, t_next, cur);
+    srv_kmax<<<grid, 256, 0, as>>>(S->d, sl.d);
+    S->pend_cur = cur ^ 1;
     cudaMemcpyAsync(sl.h_nfind, sl.d.nfind, 4, cudaMemcpyDeviceToHost, as);
     cudaMemcpyAsync(sl.h_find, sl.d.find, sizeof(odp_finding) * S->find_cap,
                     cudaMemcpyDeviceToHost, as);
@@ -472,13 +675,14 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     if (cudaSetDevice(cfg->device) != cudaSuccess) return ODP_ERR_CUDA;
     const uint64_t E = cfg->max_events, B = cfg->max_batch_events;
     const uint32_t cap_p = pow2_at_least(2 * E), cap_b = pow2_at_least(2 * B);
-    const uint64_t find_cap = 2 * B + 64;
+    const uint32_t pend_cap = (uint32_t)std::min<uint64_t>(E, 16 * B);
+    const uint64_t find_cap = 3 * B + pend_cap + 64;
     // device bytes: log + per-event arrays + four persistent tables + slots
     const uint64_t per_table = 32 * ((uint64_t)cap_p + 1);
     const uint64_t slot_bytes = B * (64 + 8 + 8 + 16 + 4 + 12 + 16 + 16) + 256ull * (B / 4096 + 2) * 4 +
                                 find_cap * (48 + 8) + (20ull << 20) + (46ull << 20);
-    const uint64_t need = E * (64 + 8) + 4 * per_table + 32 * ((uint64_t)cap_b + 1) +
-                          (uint64_t)cfg->n_slots * slot_bytes;
+    const uint64_t need = E * (64 + 8) + 6 * per_table + 32 * ((uint64_t)cap_b + 1) +
+                          16ull * pend_cap + ((uint64_t)cfg->n_slots + 1) * slot_bytes;
     if (cfg->device_budget_bytes && need > cfg->device_budget_bytes) return ODP_ERR_OOM;
 
     odp_server* S = new odp_server();
@@ -500,7 +704,22 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     if (!rc) rc = make_table(S, S->d.t_pend, cap_p, caps + 2, S->an_stream);
     if (!rc) rc = make_table(S, S->d.t_ep, cap_p, caps + 3, S->an_stream);
     if (!rc) rc = make_table(S, S->d.t_b, cap_b, caps + 4, S->an_stream);
+    if (!rc) rc = make_table(S, S->d.t_pair, cap_p, caps + 5, S->an_stream);
+    if (!rc) rc = make_table(S, S->d.t_rid, cap_p, caps + 6, S->an_stream);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.kmax, 8 * SRV_NDEV);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.pend[0], 8ull * pend_cap);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.pend[1], 8ull * pend_cap);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.npend, 16);
+    S->d.pend_cap = pend_cap;
+    if (!rc) rc = alloc_dev(S, (void**)&S->fl.find, sizeof(odp_finding) * find_cap);
+    if (!rc) rc = alloc_dev(S, (void**)&S->fl.complete, 8 * find_cap);
+    if (!rc) rc = alloc_dev(S, (void**)&S->fl.nfind, 16);
     if (rc) return fail(rc);
+    cudaMemsetAsync(S->d.kmax, 0, 8 * SRV_NDEV, S->an_stream);
+    cudaMemsetAsync(S->d.npend, 0, 16, S->an_stream);
+    if (cudaHostAlloc((void**)&S->h_fl_find, sizeof(odp_finding) * find_cap, 0) != cudaSuccess ||
+        cudaHostAlloc((void**)&S->h_fl_n, 16, 0) != cudaSuccess)
+        return fail(ODP_ERR_OOM);
     S->slots.resize(cfg->n_slots);
     for (auto& sl : S->slots) {
         SlotDev& d = sl.d;
@@ -525,6 +744,11 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
         if (!rc) rc = alloc_dev(S, (void**)&d.find, sizeof(odp_finding) * find_cap);
         if (!rc) rc = alloc_dev(S, (void**)&d.complete, 8 * find_cap);
         if (!rc) rc = alloc_dev(S, (void**)&d.nfind, 16);
+        if (!rc) rc = alloc_dev(S, (void**)&d.pa, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.pd, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.rslot, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.bk, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.cnt, 16);
         if (rc) return fail(rc);
         if (cudaHostAlloc((void**)&sl.h_ev, sizeof(odp_event) * B, 0) != cudaSuccess ||
             cudaHostAlloc((void**)&sl.h_ptrs, 8 * B, 0) != cudaSuccess ||
@@ -619,13 +843,34 @@ int odp_server_poll(odp_server* S, odp_finding* out, uint64_t cap, uint64_t* n_o
 int odp_server_flush(odp_server* S) {
     if (!S) return ODP_ERR_INVALID_ARG;
     S->flushing = true;
-    std::unique_lock<std::mutex> lk(S->mu);
-    const auto deadline = std::chrono::steady_clock::now() + std::chrono::minutes(10);
-    while (S->n_done < S->submitted) {
-        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
-            S->flushing = false;
-            return ODP_ERR_TIMEOUT;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        const auto deadline = std::chrono::steady_clock::now() + std::chrono::minutes(10);
+        while (S->n_done < S->submitted) {
+            if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+                S->flushing = false;
+                return ODP_ERR_TIMEOUT;
+            }
         }
+    }
+    // end of the trace: Alg. 4 for the pairs still waiting and the allocations
+    // still open (their findings carry no latency)
+    {
+        std::lock_guard<std::mutex> an_lk(S->an_mu);
+        cudaSetDevice(S->cfg.device);
+        cudaStream_t as = S->an_stream;
+        odp::srv_zero<<<1, 1, 0, as>>>(S->fl.nfind);
+        odp::srv_flush_ua<<<256, 256, 0, as>>>(S->d, S->fl, S->find_cap, S->pend_cur,
+                                               S->cfg.max_events);
+        odp::srv_zero<<<1, 1, 0, as>>>(S->d.npend + S->pend_cur);
+        cudaMemcpyAsync(S->h_fl_n, S->fl.nfind, 4, cudaMemcpyDeviceToHost, as);
+        cudaMemcpyAsync(S->h_fl_find, S->fl.find, sizeof(odp_finding) * S->find_cap,
+                        cudaMemcpyDeviceToHost, as);
+        if (cudaStreamSynchronize(as) != cudaSuccess) S->error = ODP_ERR_CUDA;
+        const uint32_t n = std::min(*S->h_fl_n, S->find_cap);
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (uint32_t j = 0; j < n; ++j) S->outq.push_back(S->h_fl_find[j]);
+        S->streamed += n;
     }
     S->flushing = false;
     return S->error;
@@ -709,6 +954,8 @@ int odp_server_destroy(odp_server* S) {
                         (void*)sl.h_nx, (void*)sl.h_find, (void*)sl.h_complete, (void*)sl.h_nfind})
             if (h) cudaFreeHost(h);
     }
+    if (S->h_fl_find) cudaFreeHost(S->h_fl_find);
+    if (S->h_fl_n) cudaFreeHost(S->h_fl_n);
     for (void* p : S->dev_blocks) cudaFree(p);
     if (S->an_stream) cudaStreamDestroy(S->an_stream);
     delete S;

@@ -38,6 +38,10 @@ def payload_views(srv, lg, ev):
     return views, is_x
 
 
+def sorted_findings(st):
+    return st[np.lexsort((st["partner"], st["event"], st["kind"]))]
+
+
 @pytest.mark.parametrize("n_slots,max_batch", [(1, 512), (4, 2048)])
 def test_streamed_findings_equal_offline(cuda_ok, orc, n_slots, max_batch):
     import paper_2601_12713_b300 as odp
@@ -56,13 +60,12 @@ def test_streamed_findings_equal_offline(cuda_ok, orc, n_slots, max_batch):
         o = orc.analyze(ev)
         assert g["status"] == o.status == 0 and g["count"] == o.count
         assert np.array_equal(g["findings"].view(np.uint8), o.findings.view(np.uint8))
-        # streamed DD and RT findings are exactly the offline ones
-        st = srv.poll()
-        key = np.lexsort((st["partner"], st["event"], st["kind"]))
-        st = st[key]
-        off = g["findings"][np.isin(g["findings"]["kind"], [1, 2])]
+        # streamed DD, RT, RA and UA findings are exactly the offline ones
+        st = sorted_findings(srv.poll())
+        off = g["findings"][np.isin(g["findings"]["kind"], [1, 2, 3, 4])]
         assert st.size == off.size and st.size > 0
         assert np.array_equal(st.view(np.uint8), off.view(np.uint8))
+        assert (st["kind"] == 3).sum() > 0
         # every transfer's fingerprint, alone, equals the one computed in the mix
         views, is_x = payload_views(srv, lg, ev)
         idx = np.flatnonzero(is_x)
@@ -96,5 +99,80 @@ def test_submit_argument_errors(cuda_ok):
             srv.submit(ev, np.zeros(20, dtype=np.uint64))   # beyond the log capacity
         srv.flush()
         assert srv.log()[1] == 0
+    finally:
+        srv.close()
+
+
+def pairs_trace():
+    """One producer's events with explicit times (ns): allocations used by a
+    kernel in the same or a later batch, unused ones (no kernel, or a kernel
+    on another device), a repeated allocation, a kernel that starts while a
+    delete runs, allocations never deleted (one covered by a later kernel),
+    an unmatched delete, and transfers."""
+    from synth import traces
+
+    T, rows = traces, []
+
+    def ev(t0, t1, kind, dev=0, host=0, daddr=0, nbytes=0, site=0):
+        src, dst = (-1, dev) if kind != T.FROM_DEV else (dev, -1)
+        rows.append((t0, t1, host, daddr, nbytes, 0, 0, site, kind, src, dst, 0))
+
+    t = 1000
+    for i in range(6):                       # used: ALLOC, TO_DEV, KERNEL, FROM_DEV, DELETE
+        ev(t, t + 5, T.ALLOC, 0, 0x1000, 0x100, 4096, 1)
+        ev(t + 10, t + 20, T.TO_DEV, 0, 0x1000, 0x100, 4096, 2)
+        ev(t + 30, t + 80, T.KERNEL, 0, site=3)
+        ev(t + 90, t + 99, T.FROM_DEV, 0, 0x1000, 0x100, 4096, 4)
+        ev(t + 100, t + 105, T.DELETE, 0, 0x1000, 0x100, 4096, 5)
+        t += 200
+    for i in range(4):                       # unused, repeated <host, dev, bytes>
+        ev(t, t + 5, T.ALLOC, 0, 0x2000, 0x200, 8192, 6)
+        ev(t + 10, t + 15, T.DELETE, 0, 0x2000, 0x200, 8192, 7)
+        t += 50
+    ev(t, t + 5, T.ALLOC, 1, 0x3000, 0x300, 64, 8)   # a kernel on device 0 only: unused
+    ev(t + 10, t + 40, T.KERNEL, 0, site=9)
+    ev(t + 50, t + 55, T.DELETE, 1, 0x3000, 0x300, 64, 10)
+    t += 100
+    ev(t, t + 5, T.ALLOC, 0, 0x4000, 0x400, 64, 11)   # a kernel starts while the delete runs
+    ev(t + 10, t + 500, T.DELETE, 0, 0x4000, 0x400, 64, 12)
+    ev(t + 20, t + 30, T.KERNEL, 0, site=13)
+    t += 600
+    ev(t, t + 5, T.DELETE, 0, 0x9000, 0x900, 64, 14)  # unmatched
+    ev(t + 10, t + 15, T.ALLOC, 0, 0x5000, 0x500, 64, 15)  # never deleted, later kernel
+    ev(t + 20, t + 25, T.ALLOC, 1, 0x6000, 0x600, 64, 16)  # never deleted, no kernel on 1
+    ev(t + 30, t + 90, T.KERNEL, 0, site=17)
+    t += 100
+    for i in range(5):                       # more unused allocations, same key
+        ev(t, t + 5, T.ALLOC, 1, 0x7000, 0x700, 128, 18)
+        ev(t + 10, t + 15, T.DELETE, 1, 0x7000, 0x700, 128, 19)
+        t += 30
+    return np.array(rows, dtype=T.EVENT_DTYPE)
+
+
+@pytest.mark.parametrize("max_batch", [1, 3, 8, 4096])
+def test_streamed_pairs_equal_offline(cuda_ok, orc, max_batch):
+    """Streamed repeated and unused allocations on a hand-made trace, in
+    batches of 1 to 4096 events (pairs decided in their own batch, waiting
+    across batches, and at the flush), equal the oracle's over the log."""
+    import paper_2601_12713_b300 as odp
+
+    ev = pairs_trace()
+    pool = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    is_x = np.isin(ev["kind"], [2, 3, 4])
+    ptrs = np.where(is_x, pool.data_ptr(), 0).astype(np.uint64)
+    srv = odp.Server(n_slots=2, max_events=1 << 12, max_batch_events=max_batch,
+                     device_budget_bytes=2 << 30)
+    try:
+        srv.attach(0)
+        srv.submit(ev, ptrs)
+        srv.flush()
+        log = odp.log_tensor(srv, ev.size)
+        merged = log.cpu().numpy().view(odp.EVENT_DTYPE).copy()
+        o = orc.analyze(merged)
+        off = o.findings[np.isin(o.findings["kind"], [3, 4])]
+        st = sorted_findings(srv.poll())
+        st = st[np.isin(st["kind"], [3, 4])]
+        assert (off["kind"] == 3).sum() >= 6 and (off["kind"] == 4).sum() >= 8
+        assert np.array_equal(st.view(np.uint8), off.view(np.uint8))
     finally:
         srv.close()
