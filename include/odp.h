@@ -320,15 +320,15 @@ int odp_analyze(const odp_event* events, uint64_t n, const odp_findings* out,
  * GPU, appends the events to a log resident in device memory and updates
  * state kept on the device for Algorithm 1 (duplicate transfers), Algorithm
  * 2 (round trips, content groups with at most two endpoints), the
- * alloc/delete pairing, Algorithm 3 (repeated allocations) and Algorithm 4
+ * alloc/delete pairing, Algorithm 3 (repeated allocations), Algorithm 4
  * (unused allocations: a pair is decided once a kernel on its device
- * overlaps it or the merged stream has passed its delete's end), so those
- * findings are reported while the program runs.  The streamed findings equal
- * odp_analyze's over the same log when round-trip groups have at most two
- * endpoints and allocations of one <host address, device, bytes> key do not
- * nest.  Algorithm 5 (unused transfers) is not streamed; the complete
- * Algorithms 1-5 run over the resident log with odp_analyze after
- * odp_server_flush (odp_server_log gives the log).
+ * overlaps it or the merged stream has passed its delete's end) and
+ * Algorithm 5 (unused transfers: decided when the next kernel of the
+ * transfer's device arrives), so those findings are reported while the
+ * program runs.  The streamed findings equal odp_analyze's over the same log
+ * when round-trip groups have at most two endpoints and allocations of one
+ * <host address, device, bytes> key do not nest; odp_analyze over the
+ * resident log (odp_server_log) after odp_server_flush is exact always.
  */
 typedef struct odp_server odp_server;
 
@@ -380,14 +380,15 @@ int odp_server_attach(odp_server* s, uint64_t start_t_ns);
 int odp_server_submit(odp_server* s, const odp_event* host_events,
                       const void* const* dev_payloads, uint64_t n);
 
-/* Moves up to cap streamed findings (DD, RT, RA and UA; event indices in the
+/* Moves up to cap streamed findings (all five kinds; event indices in the
  * merged log order) to host_out; *n_out receives the number moved. */
 int odp_server_poll(odp_server* s, odp_finding* host_out, uint64_t cap, uint64_t* n_out);
 
 /* Releases every submitted event (the watermark no longer waits), blocks
- * until all batches are done, and ends the trace for Algorithm 4: pairs
- * still waiting for a kernel are unused, and allocations never deleted are
- * unused unless a kernel seen on their device ends at or after their start
+ * until all batches are done, and ends the trace for Algorithms 4 and 5:
+ * pairs still waiting for a kernel are unused, allocations never deleted are
+ * unused unless a kernel seen on their device ends at or after their start,
+ * and to-device transfers still waiting for a kernel come after the last one
  * (these findings carry no latency).  Events submitted after a flush extend
  * the log; findings already reported are not revisited. */
 int odp_server_flush(odp_server* s);

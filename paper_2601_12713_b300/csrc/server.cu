@@ -34,8 +34,15 @@
 // after its delete ends (no later kernel can overlap it) or a kernel of a
 // later batch overlaps it.  Flush ends the trace: waiting pairs are unused,
 // and allocations never deleted are checked against every kernel seen.
-// Alg. 5 (unused transfers) is not streamed: it needs the next kernel of each
-// transfer's device and the end of the trace; odp_analyze over the log gives it.
+// Streaming Alg. 5: a to-device transfer that starts while a kernel of its
+// device runs (largest kernel end seen >= its start) is a barrier; any other
+// waits for its device's next kernel, so the transfers of one device between
+// two kernel arrivals form a segment (numbered by the kernels seen).  Per
+// <host address, device> the latest waiting transfer is kept; a transfer that
+// follows one of the same segment overwrites it, which is reported when the
+// next kernel closes the segment (unless that kernel starts exactly when the
+// later transfer does, which makes it a barrier).  Transfers still waiting at
+// the flush come after the last kernel.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -77,6 +84,12 @@ struct SrvDev {
     uint2* pend[2];    // pairs waiting for the Alg. 4 decision (alloc, delete), ping-pong
     uint32_t* npend;   // [2] counts, [2] overflow count
     uint32_t pend_cap;
+    Table t_ut;        // <host address, device> -> latest waiting to-device transfer
+    uint32_t* kcnt;    // per device: kernels seen (the current segment number)
+    uint32_t* useg;    // per log index: segment of a waiting to-device transfer
+    uint2* utf[2];     // overwrites waiting for their segment to close (earlier, later), ping-pong
+    uint32_t* utopen[2];  // to-device transfers still waiting for a kernel, ping-pong
+    uint32_t* nut;     // [0..1] overwrite counts, [2..3] waiting counts, [4] overflow
 };
 
 struct SlotDev {
@@ -101,6 +114,32 @@ struct SlotDev {
     uint32_t* bk;          // kernels of the batch (log indices)
     uint32_t* cnt;         // [0] pairs, [1] kernels
 };
+
+// The batch's kernels on `dev`: how many come before log index g and the
+// largest end among those (0: none), the total on dev, and the first one
+// after g (NONE32: none).
+struct BatchKernels {
+    uint32_t before, total, first_after;
+    unsigned long long max_end1;  // 1 + largest end of those before g
+};
+
+__device__ __forceinline__ BatchKernels batch_kernels_on(const odp_event* log, const uint32_t* bk,
+                                                         uint32_t nk, uint32_t dev, uint32_t g) {
+    BatchKernels r{0, 0, NONE32, 0};
+    for (uint32_t i = 0; i < nk; ++i) {
+        const uint32_t k = bk[i];
+        const odp_event& e = log[k];
+        if (((uint32_t)(e.dst_dev + 1) & 0xFF) != dev) continue;
+        ++r.total;
+        if (k < g) {
+            ++r.before;
+            r.max_end1 = max(r.max_end1, (unsigned long long)e.t_end_ns + 1ull);
+        } else if (r.first_after == NONE32 || k < r.first_after) {
+            r.first_after = k;
+        }
+    }
+    return r;
+}
 
 __device__ __forceinline__ uint32_t ep_of(int8_t dev) { return (uint32_t)(dev + 1) & 0xFF; }
 
@@ -369,19 +408,112 @@ __global__ void srv_kmax(SrvDev d, SlotDev s) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += gridDim.x * blockDim.x) {
         const odp_event& k = d.log[s.bk[i]];
         atomicMax(&d.kmax[ep_of(k.dst_dev)], (unsigned long long)k.t_end_ns + 1ull);
+        atomicAdd(&d.kcnt[ep_of(k.dst_dev)], 1u);
+    }
+}
+
+// To-device transfers of the batch: barriers drop out; a waiting transfer
+// gets its segment and is keyed by its <host address, device> slot (others
+// sort last).
+__global__ void srv_ut_keys(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
+    const uint32_t cap = *d.t_ut.cap_dev, none_key = d.t_ut.cap_max + 1, nk = s.cnt[1];
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+        const uint32_t g = (uint32_t)(g0 + q);
+        const odp_event& e = d.log[g];
+        uint32_t k = none_key;
+        if (e.kind == ODP_TO_DEV) {
+            const uint32_t dev = ep_of(e.dst_dev);
+            const BatchKernels bk = batch_kernels_on(d.log, s.bk, nk, dev, g);
+            const unsigned long long km = max(d.kmax[dev], bk.max_end1);
+            if (!(km != 0 && km - 1 >= e.t_start_ns)) {
+                d.useg[g] = d.kcnt[dev] + bk.before;
+                const uint32_t sl = prim::table_insert(d.t_ut, cap, Key128{e.host_addr, dev});
+                if (sl != NONE32) k = sl;
+            }
+        }
+        s.skeys[q] = k;
+        s.svals[q] = q;
+    }
+}
+
+// One thread per <host address, device> group of the batch, in order: a
+// transfer that follows the key's latest waiting transfer in the same
+// segment records an overwrite (into s.pa/s.pd, count s.cnt[2]); every
+// waiting transfer is listed (s.rslot, count s.cnt[3]).
+__global__ void srv_ut_walk(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
+    const uint32_t none_key = d.t_ut.cap_max + 1;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+        const uint32_t k = s.skeys[r];
+        if (k == none_key || (r > 0 && s.skeys[r - 1] == k)) continue;
+        uint32_t last = d.t_ut.slots[k].v;
+        for (uint32_t t = r; t < m && s.skeys[t] == k; ++t) {
+            const uint32_t g = (uint32_t)(g0 + s.svals[t]);
+            if (last != NONE32 && d.useg[last] == d.useg[g]) {
+                const uint32_t j = atomicAdd(&s.cnt[2], 1u);
+                s.pa[j] = last;
+                s.pd[j] = g;
+            }
+            s.rslot[atomicAdd(&s.cnt[3], 1u)] = g;
+            last = g;
+        }
+        d.t_ut.slots[k].v = last;
+    }
+}
+
+// Overwrites and waiting transfers, carried from earlier batches (list cur)
+// and new in this one: an overwrite whose segment a kernel of this batch
+// closes is reported if the later transfer starts before that kernel (else
+// it is a barrier); transfers whose segment stays open carry over to list
+// cur ^ 1.
+__global__ void srv_ut_resolve(SrvDev d, SlotDev s, uint32_t cap, int cur) {
+    const int nxt = cur ^ 1;
+    const uint32_t nk = s.cnt[1];
+    const uint32_t n_f = min(d.nut[cur], d.pend_cap), n_fb = s.cnt[2];
+    const uint32_t n_o = min(d.nut[2 + cur], d.pend_cap), n_ob = s.cnt[3];
+    const uint32_t n_all = n_f + n_fb + n_o + n_ob;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_all; i += gridDim.x * blockDim.x) {
+        if (i < n_f + n_fb) {
+            const uint32_t c = i < n_f ? d.utf[cur][i].x : s.pa[i - n_f];
+            const uint32_t t = i < n_f ? d.utf[cur][i].y : s.pd[i - n_f];
+            const uint32_t dev = ep_of(d.log[t].dst_dev);
+            const BatchKernels bk = batch_kernels_on(d.log, s.bk, nk, dev, t);
+            if (bk.first_after == NONE32) {  // segment still open
+                const uint32_t j = atomicAdd(&d.nut[nxt], 1u);
+                if (j < d.pend_cap) d.utf[nxt][j] = make_uint2(c, t);
+                else atomicAdd(&d.nut[4], 1u);
+            } else if (d.log[t].t_start_ns < d.log[bk.first_after].t_start_ns) {
+                emit_w(s, cap, d.log, ODP_UT, c, t, d.log[c].bytes, dur_of(d.log[c]),
+                       bk.first_after);
+            }
+        } else {
+            const uint32_t o = i - n_f - n_fb;
+            const uint32_t g = o < n_o ? d.utopen[cur][o] : s.rslot[o - n_o];
+            const uint32_t dev = ep_of(d.log[g].dst_dev);
+            if (batch_kernels_on(d.log, s.bk, nk, dev, g).first_after == NONE32) {
+                const uint32_t j = atomicAdd(&d.nut[2 + nxt], 1u);
+                if (j < d.pend_cap) d.utopen[nxt][j] = g;
+                else atomicAdd(&d.nut[4], 1u);
+            }
+        }
     }
 }
 
 // Flush: every waiting pair is unused (no kernel follows the end of the
 // trace); every allocation still open is checked against all kernels seen,
-// with the end of the trace as its delete end.
-__global__ void srv_flush_ua(SrvDev d, SlotDev s, uint32_t cap, int cur, uint64_t max_events) {
-    const uint32_t n_old = min(d.npend[cur], d.pend_cap);
+// with the end of the trace as its delete end; every to-device transfer still
+// waiting for a kernel comes after the last one.
+__global__ void srv_flush(SrvDev d, SlotDev s, uint32_t cap, int cur, uint64_t max_events) {
     const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t n_old = min(d.npend[cur], d.pend_cap);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_old; i += stride) {
         const uint32_t a = d.pend[cur][i].x, g = d.pend[cur][i].y;
         emit_w(s, cap, d.log, ODP_UA, a, g, d.log[a].bytes, dur_of(d.log[a]) + dur_of(d.log[g]),
                ~0ull);
+    }
+    const uint32_t n_open = min(d.nut[2 + cur], d.pend_cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_open; i += stride) {
+        const uint32_t g = d.utopen[cur][i];
+        emit_w(s, cap, d.log, ODP_UT, g, NONE32, d.log[g].bytes, dur_of(d.log[g]), ~0ull);
     }
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= d.t_pair.cap_max; k += stride) {
         uint32_t a = d.t_pair.slots[k].v;
@@ -539,7 +671,7 @@ void launch_batch(odp_server* S, Slot& sl) {
     uint64_t t_next = S->t_released_max;
     for (uint32_t q = 0; q < m; ++q) t_next = std::max(t_next, sl.h_ev[q].t_start_ns);
     S->t_released_max = t_next;
-    cudaMemsetAsync(sl.d.cnt, 0, 8, as);
+    cudaMemsetAsync(sl.d.cnt, 0, 16, as);
     srv_pair_keys<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
     prim::radix_sort(sl.d.skeys, sl.d.svals, nullptr, m, prim::bit_length(S->d.t_pair.cap_max + 1),
                      sl.d.sort, as);
@@ -549,6 +681,14 @@ void launch_batch(odp_server* S, Slot& sl) {
     const int cur = S->pend_cur;
     srv_zero<<<1, 1, 0, as>>>(S->d.npend + (cur ^ 1));
     srv_ua<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap, t_next, cur);
+    // Alg. 5
+    srv_ut_keys<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
+    prim::radix_sort(sl.d.skeys, sl.d.svals, nullptr, m, prim::bit_length(S->d.t_ut.cap_max + 1),
+                     sl.d.sort, as);
+    srv_ut_walk<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
+    cudaMemsetAsync(S->d.nut + (cur ^ 1), 0, 4, as);
+    cudaMemsetAsync(S->d.nut + 2 + (cur ^ 1), 0, 4, as);
+    srv_ut_resolve<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap, cur);
     srv_kmax<<<grid, 256, 0, as>>>(S->d, sl.d);
     S->pend_cur = cur ^ 1;
     cudaMemcpyAsync(sl.h_nfind, sl.d.nfind, 4, cudaMemcpyDeviceToHost, as);
@@ -681,8 +821,8 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     const uint64_t per_table = 32 * ((uint64_t)cap_p + 1);
     const uint64_t slot_bytes = B * (64 + 8 + 8 + 16 + 4 + 12 + 16 + 16) + 256ull * (B / 4096 + 2) * 4 +
                                 find_cap * (48 + 8) + (20ull << 20) + (46ull << 20);
-    const uint64_t need = E * (64 + 8) + 6 * per_table + 32 * ((uint64_t)cap_b + 1) +
-                          16ull * pend_cap + ((uint64_t)cfg->n_slots + 1) * slot_bytes;
+    const uint64_t need = E * (64 + 12) + 7 * per_table + 32 * ((uint64_t)cap_b + 1) +
+                          40ull * pend_cap + ((uint64_t)cfg->n_slots + 1) * slot_bytes;
     if (cfg->device_budget_bytes && need > cfg->device_budget_bytes) return ODP_ERR_OOM;
 
     odp_server* S = new odp_server();
@@ -711,12 +851,22 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     if (!rc) rc = alloc_dev(S, (void**)&S->d.pend[1], 8ull * pend_cap);
     if (!rc) rc = alloc_dev(S, (void**)&S->d.npend, 16);
     S->d.pend_cap = pend_cap;
+    if (!rc) rc = make_table(S, S->d.t_ut, cap_p, caps + 7, S->an_stream);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.kcnt, 4 * SRV_NDEV);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.useg, 4 * E);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.utf[0], 8ull * pend_cap);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.utf[1], 8ull * pend_cap);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.utopen[0], 4ull * pend_cap);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.utopen[1], 4ull * pend_cap);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.nut, 32);
     if (!rc) rc = alloc_dev(S, (void**)&S->fl.find, sizeof(odp_finding) * find_cap);
     if (!rc) rc = alloc_dev(S, (void**)&S->fl.complete, 8 * find_cap);
     if (!rc) rc = alloc_dev(S, (void**)&S->fl.nfind, 16);
     if (rc) return fail(rc);
     cudaMemsetAsync(S->d.kmax, 0, 8 * SRV_NDEV, S->an_stream);
     cudaMemsetAsync(S->d.npend, 0, 16, S->an_stream);
+    cudaMemsetAsync(S->d.kcnt, 0, 4 * SRV_NDEV, S->an_stream);
+    cudaMemsetAsync(S->d.nut, 0, 32, S->an_stream);
     if (cudaHostAlloc((void**)&S->h_fl_find, sizeof(odp_finding) * find_cap, 0) != cudaSuccess ||
         cudaHostAlloc((void**)&S->h_fl_n, 16, 0) != cudaSuccess)
         return fail(ODP_ERR_OOM);
@@ -860,9 +1010,11 @@ int odp_server_flush(odp_server* S) {
         cudaSetDevice(S->cfg.device);
         cudaStream_t as = S->an_stream;
         odp::srv_zero<<<1, 1, 0, as>>>(S->fl.nfind);
-        odp::srv_flush_ua<<<256, 256, 0, as>>>(S->d, S->fl, S->find_cap, S->pend_cur,
-                                               S->cfg.max_events);
+        odp::srv_flush<<<256, 256, 0, as>>>(S->d, S->fl, S->find_cap, S->pend_cur,
+                                            S->cfg.max_events);
         odp::srv_zero<<<1, 1, 0, as>>>(S->d.npend + S->pend_cur);
+        odp::srv_zero<<<1, 1, 0, as>>>(S->d.nut + S->pend_cur);
+        odp::srv_zero<<<1, 1, 0, as>>>(S->d.nut + 2 + S->pend_cur);
         cudaMemcpyAsync(S->h_fl_n, S->fl.nfind, 4, cudaMemcpyDeviceToHost, as);
         cudaMemcpyAsync(S->h_fl_find, S->fl.find, sizeof(odp_finding) * S->find_cap,
                         cudaMemcpyDeviceToHost, as);

@@ -60,9 +60,9 @@ def test_streamed_findings_equal_offline(cuda_ok, orc, n_slots, max_batch):
         o = orc.analyze(ev)
         assert g["status"] == o.status == 0 and g["count"] == o.count
         assert np.array_equal(g["findings"].view(np.uint8), o.findings.view(np.uint8))
-        # streamed DD, RT, RA and UA findings are exactly the offline ones
+        # the streamed findings (all five kinds) are exactly the offline ones
         st = sorted_findings(srv.poll())
-        off = g["findings"][np.isin(g["findings"]["kind"], [1, 2, 3, 4])]
+        off = g["findings"]
         assert st.size == off.size and st.size > 0
         assert np.array_equal(st.view(np.uint8), off.view(np.uint8))
         assert (st["kind"] == 3).sum() > 0
@@ -108,7 +108,8 @@ def pairs_trace():
     kernel in the same or a later batch, unused ones (no kernel, or a kernel
     on another device), a repeated allocation, a kernel that starts while a
     delete runs, allocations never deleted (one covered by a later kernel),
-    an unmatched delete, and transfers."""
+    an unmatched delete, and to-device transfers between, during and after
+    kernels on two devices."""
     from synth import traces
 
     T, rows = traces, []
@@ -146,14 +147,34 @@ def pairs_trace():
         ev(t, t + 5, T.ALLOC, 1, 0x7000, 0x700, 128, 18)
         ev(t + 10, t + 15, T.DELETE, 1, 0x7000, 0x700, 128, 19)
         t += 30
+    # unused transfers: overwritten before the next kernel, a transfer during
+    # a kernel (barrier), one that starts with the next kernel (barrier), and
+    # transfers after the last kernel of their device
+    for i in range(3):
+        ev(t, t + 50, T.KERNEL, 0, site=20)
+        ev(t + 60, t + 65, T.TO_DEV, 0, 0xA000, 0xA00, 256, 21)
+        ev(t + 70, t + 75, T.TO_DEV, 0, 0xA000, 0xA00, 256, 22)
+        ev(t + 80, t + 85, T.TO_DEV, 0, 0xB000, 0xB00, 256, 23)
+        ev(t + 90, t + 95, T.TO_DEV, 1, 0xA000, 0xA00, 256, 24)
+        ev(t + 100, t + 150, T.KERNEL, 0, site=25)
+        ev(t + 120, t + 125, T.TO_DEV, 0, 0xA000, 0xA00, 256, 26)
+        ev(t + 200, t + 205, T.TO_DEV, 0, 0xA000, 0xA00, 256, 27)
+        ev(t + 300, t + 305, T.TO_DEV, 0, 0xA000, 0xA00, 256, 28)
+        ev(t + 300, t + 350, T.KERNEL, 0, site=29)
+        t += 400
+    for i in range(3):
+        ev(t, t + 5, T.TO_DEV, 0, 0xC000, 0xC00, 512, 30)
+        ev(t + 10, t + 15, T.TO_DEV, 1, 0xC000, 0xC00, 512, 31)
+        t += 20
     return np.array(rows, dtype=T.EVENT_DTYPE)
 
 
 @pytest.mark.parametrize("max_batch", [1, 3, 8, 4096])
 def test_streamed_pairs_equal_offline(cuda_ok, orc, max_batch):
-    """Streamed repeated and unused allocations on a hand-made trace, in
-    batches of 1 to 4096 events (pairs decided in their own batch, waiting
-    across batches, and at the flush), equal the oracle's over the log."""
+    """Streamed repeated allocations, unused allocations and unused transfers
+    on a hand-made trace, in batches of 1 to 4096 events (decided in their
+    own batch, waiting across batches, and at the flush), equal the oracle's
+    over the log."""
     import paper_2601_12713_b300 as odp
 
     ev = pairs_trace()
@@ -169,10 +190,11 @@ def test_streamed_pairs_equal_offline(cuda_ok, orc, max_batch):
         log = odp.log_tensor(srv, ev.size)
         merged = log.cpu().numpy().view(odp.EVENT_DTYPE).copy()
         o = orc.analyze(merged)
-        off = o.findings[np.isin(o.findings["kind"], [3, 4])]
+        off = o.findings[np.isin(o.findings["kind"], [3, 4, 5])]
         st = sorted_findings(srv.poll())
-        st = st[np.isin(st["kind"], [3, 4])]
+        st = st[np.isin(st["kind"], [3, 4, 5])]
         assert (off["kind"] == 3).sum() >= 6 and (off["kind"] == 4).sum() >= 8
+        assert (off["kind"] == 5).sum() >= 9
         assert np.array_equal(st.view(np.uint8), off.view(np.uint8))
     finally:
         srv.close()
