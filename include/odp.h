@@ -192,6 +192,10 @@ enum {
 #define ODP_MAX_SITES 65536u
 #define ODP_MAX_BYTES (1ull << 56)
 #define ODP_NO_EVENT (~0ull)
+/* odp_event.flags bit for odp_server_submit: fp_lo/fp_hi already hold the
+ * transfer's fingerprint (taken when the bytes were known to be in place);
+ * the server uses it and ignores the payload pointer. */
+#define ODP_EVENT_FP_GIVEN 0x1u
 
 /*
  * One mapping event, 64 bytes, packed little-endian (the paper's log entry
@@ -205,6 +209,7 @@ enum {
  *   - src_dev/dst_dev: device numbers, host = -1.  ALLOC, DELETE and KERNEL
  *     use dst_dev for their device.
  *   - site_id: caller-assigned code-location id (< ODP_MAX_SITES).
+ *   - flags: ODP_EVENT_FP_GIVEN (serving only); odp_analyze ignores them.
  */
 #pragma pack(push, 1)
 typedef struct odp_event {
@@ -372,7 +377,9 @@ int odp_server_attach(odp_server* s, uint64_t start_t_ns);
 /*
  * Thread-safe.  Submits n events (host memory, 64-byte records).  For
  * transfers, dev_payloads[i] is the device address of the transferred bytes
- * (event.bytes of them); the server computes fp_lo/fp_hi.  Events of one
+ * (event.bytes of them); the server computes fp_lo/fp_hi, unless the event's
+ * flags carry ODP_EVENT_FP_GIVEN (then the record's fingerprint is used and
+ * dev_payloads[i] is ignored; it may be null).  Events of one
  * calling thread must have nondecreasing t_start_ns.  Returns
  * ODP_ERR_INVALID_ARG for null arrays, ODP_ERR_UNSUPPORTED when the log
  * capacity or the producer limit would be exceeded.

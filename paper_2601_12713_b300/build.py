@@ -1,5 +1,6 @@
-"""Builds libodp.so (and the synthetic-input fill library) in-tree with nvcc
-for sm_103a.  Run ``python -m paper_2601_12713_b300.build``."""
+"""Builds libodp.so, the OMPT tool libodp_ompt.so (and the synthetic-input
+libraries) in-tree with nvcc for sm_103a.  Run
+``python -m paper_2601_12713_b300.build``."""
 
 from __future__ import annotations
 
@@ -13,6 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libodp.so")
+OMPT_SRC = os.path.join(PKG, "ompt", "ompt_tool.cpp")
+OMPT_LIB = os.path.join(PKG, "libodp_ompt.so")
 SYNTH_SRC = os.path.join(ROOT, "synth", "gen.cu")
 SYNTH_LIB = os.path.join(ROOT, "synth", "libsynth.so")
 LOADGEN_SRC = os.path.join(ROOT, "synth", "loadgen.cpp")
@@ -59,6 +62,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
               log=os.path.join(PKG, "build.log"))
         if verbose:
             print(open(os.path.join(PKG, "build.log")).read())
+    if force or _stale(OMPT_LIB, [OMPT_SRC, LIB, os.path.join(INCLUDE, "odp.h"),
+                                  os.path.join(INCLUDE, "odp_ompt.h")]):
+        # host code only; links libodp.so from the same directory
+        tmp = OMPT_LIB + f".tmp{os.getpid()}"
+        cmd = [NVCC, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-I", INCLUDE,
+               "-o", tmp, OMPT_SRC, "-L", PKG, "-lodp", "-Xlinker", "-rpath=$ORIGIN"]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            sys.stderr.write(res.stdout + res.stderr)
+            raise RuntimeError("nvcc failed for the OMPT tool")
+        os.replace(tmp, OMPT_LIB)
     if force or _stale(SYNTH_LIB, [SYNTH_SRC]):
         _nvcc(SYNTH_LIB, [SYNTH_SRC])
     if force or _stale(LOADGEN_LIB, [LOADGEN_SRC]):

@@ -98,7 +98,8 @@ struct SlotDev {
     uint64_t* sizes;
     odp_fp128* fp;
     uint32_t* xpos;        // batch position of each transfer
-    uint32_t* nx;          // number of transfers (device copy)
+    uint32_t* fpos;        // batch position of each transfer the server fingerprints
+    uint32_t* nx;          // [0] transfers, [1] of them fingerprinted here (device copy)
     uint32_t* sfp;         // per batch position: slot in t_fp / t_dd / t_b
     uint32_t* sdd;
     uint32_t* sb;
@@ -173,9 +174,9 @@ __device__ __forceinline__ void emit_w(const SlotDev& s, uint32_t cap, const odp
 
 // Fingerprints into the batch's transfer records.
 __global__ void srv_scatter_fp(SlotDev s) {
-    const uint32_t nx = *s.nx;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nx; j += gridDim.x * blockDim.x) {
-        odp_event& e = s.ev[s.xpos[j]];
+    const uint32_t nf = s.nx[1];
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x) {
+        odp_event& e = s.ev[s.fpos[j]];
         e.fp_lo = s.fp[j].lo;
         e.fp_hi = s.fp[j].hi;
     }
@@ -549,6 +550,7 @@ struct Slot {
     const void** h_ptrs = nullptr;
     uint64_t* h_sizes = nullptr;
     uint32_t* h_xpos = nullptr;
+    uint32_t* h_fpos = nullptr;
     uint32_t* h_nx = nullptr;
     odp_finding* h_find = nullptr;
     uint64_t* h_complete = nullptr;
@@ -630,23 +632,27 @@ int make_table(odp_server* s, Table& t, uint32_t cap, uint32_t* cap_dev, cudaStr
 void launch_batch(odp_server* S, Slot& sl) {
     const uint32_t m = sl.m;
     cudaStream_t fs = sl.fp_stream, as = S->an_stream;
-    uint32_t nx = 0;
+    uint32_t nx = 0, nf = 0;  // transfers; those whose payload the server fingerprints
     for (uint32_t q = 0; q < m; ++q) {
         const uint8_t k = sl.h_ev[q].kind;
-        if (k == ODP_TO_DEV || k == ODP_FROM_DEV || k == ODP_DEV_TO_DEV) sl.h_xpos[nx++] = q;
+        if (k != ODP_TO_DEV && k != ODP_FROM_DEV && k != ODP_DEV_TO_DEV) continue;
+        sl.h_xpos[nx++] = q;
+        if (!(sl.h_ev[q].flags & ODP_EVENT_FP_GIVEN)) {
+            sl.h_sizes[nf] = sl.h_ev[q].bytes;
+            sl.h_fpos[nf++] = q;
+        }
     }
-    for (uint32_t j = 0; j < nx; ++j) {
-        sl.h_sizes[j] = sl.h_ev[sl.h_xpos[j]].bytes;
-    }
-    *sl.h_nx = nx;
+    sl.h_nx[0] = nx;
+    sl.h_nx[1] = nf;
     cudaMemcpyAsync(sl.d.ev, sl.h_ev, sizeof(odp_event) * m, cudaMemcpyHostToDevice, fs);
-    cudaMemcpyAsync(sl.d.ptrs, sl.h_ptrs, sizeof(void*) * nx, cudaMemcpyHostToDevice, fs);
-    cudaMemcpyAsync(sl.d.sizes, sl.h_sizes, 8ull * nx, cudaMemcpyHostToDevice, fs);
+    cudaMemcpyAsync(sl.d.ptrs, sl.h_ptrs, sizeof(void*) * nf, cudaMemcpyHostToDevice, fs);
+    cudaMemcpyAsync(sl.d.sizes, sl.h_sizes, 8ull * nf, cudaMemcpyHostToDevice, fs);
     cudaMemcpyAsync(sl.d.xpos, sl.h_xpos, 4ull * nx, cudaMemcpyHostToDevice, fs);
-    cudaMemcpyAsync(sl.d.nx, sl.h_nx, 4, cudaMemcpyHostToDevice, fs);
-    if (nx) {
-        FpLaunch L = fp_schedule_for(nx);
-        if (fp_run((const void* const*)sl.d.ptrs, sl.d.sizes, nx, sl.d.fp, fs, L) != ODP_OK)
+    cudaMemcpyAsync(sl.d.fpos, sl.h_fpos, 4ull * nf, cudaMemcpyHostToDevice, fs);
+    cudaMemcpyAsync(sl.d.nx, sl.h_nx, 8, cudaMemcpyHostToDevice, fs);
+    if (nf) {
+        FpLaunch L = fp_schedule_for(nf);
+        if (fp_run((const void* const*)sl.d.ptrs, sl.d.sizes, nf, sl.d.fp, fs, L) != ODP_OK)
             S->error = ODP_ERR_CUDA;
         srv_scatter_fp<<<64, 256, 0, fs>>>(sl.d);
     }
@@ -774,7 +780,8 @@ void batcher_main(odp_server* S) {
                     const Pending& p = S->ready.front();
                     sl.h_ev[q] = p.ev;
                     const uint8_t k = p.ev.kind;
-                    if (k == ODP_TO_DEV || k == ODP_FROM_DEV || k == ODP_DEV_TO_DEV)
+                    if ((k == ODP_TO_DEV || k == ODP_FROM_DEV || k == ODP_DEV_TO_DEV) &&
+                        !(p.ev.flags & ODP_EVENT_FP_GIVEN))
                         sl.h_ptrs[nx++] = p.payload;
                     S->submit_ns[S->n_log] = p.submit_ns;
                     S->origin_prod[S->n_log] = S->ready_prod.front();
@@ -878,6 +885,7 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
         if (!rc) rc = alloc_dev(S, (void**)&d.sizes, 8 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.fp, 16 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.xpos, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.fpos, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.nx, 16);
         if (!rc) d.sort.hlen = d.nx + 2;  // words 2-3 of the 16-byte count block
         if (!rc) rc = alloc_dev(S, (void**)&d.sfp, 4 * B);
@@ -904,6 +912,7 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
             cudaHostAlloc((void**)&sl.h_ptrs, 8 * B, 0) != cudaSuccess ||
             cudaHostAlloc((void**)&sl.h_sizes, 8 * B, 0) != cudaSuccess ||
             cudaHostAlloc((void**)&sl.h_xpos, 4 * B, 0) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.h_fpos, 4 * B, 0) != cudaSuccess ||
             cudaHostAlloc((void**)&sl.h_nx, 16, 0) != cudaSuccess ||
             cudaHostAlloc((void**)&sl.h_find, sizeof(odp_finding) * find_cap, 0) != cudaSuccess ||
             cudaHostAlloc((void**)&sl.h_complete, 8 * find_cap, 0) != cudaSuccess ||
@@ -1103,7 +1112,8 @@ int odp_server_destroy(odp_server* S) {
         if (sl.fp_done) cudaEventDestroy(sl.fp_done);
         if (sl.an_done) cudaEventDestroy(sl.an_done);
         for (void* h : {(void*)sl.h_ev, (void*)sl.h_ptrs, (void*)sl.h_sizes, (void*)sl.h_xpos,
-                        (void*)sl.h_nx, (void*)sl.h_find, (void*)sl.h_complete, (void*)sl.h_nfind})
+                        (void*)sl.h_fpos, (void*)sl.h_nx, (void*)sl.h_find, (void*)sl.h_complete,
+                        (void*)sl.h_nfind})
             if (h) cudaFreeHost(h);
     }
     if (S->h_fl_find) cudaFreeHost(S->h_fl_find);

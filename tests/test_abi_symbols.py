@@ -10,9 +10,9 @@ import subprocess
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
+def declared_functions(header="odp.h"):
     names = set()
-    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+    for h in [os.path.join(ROOT, "include", header)]:
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
@@ -32,6 +32,28 @@ def test_library_builds_and_exports_all_declared_symbols():
     missing = declared_functions() - exported
     assert not missing, missing
     assert "odp_fingerprint" in exported and "odp_analyze" in exported
+
+
+def test_ompt_tool_exports_its_symbols():
+    from paper_2601_12713_b300 import build
+
+    build.build()
+    assert sorted(os.path.basename(h) for h in glob.glob(os.path.join(ROOT, "include", "*.h"))) == [
+        "odp.h", "odp_ompt.h"]
+    out = subprocess.run(["nm", "-D", "--defined-only", build.OMPT_LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = (declared_functions("odp_ompt.h") | {"ompt_start_tool"}) - exported
+    assert not missing, missing
+    # the tool is found by the runtime through ompt_start_tool; it loads
+    # without a GPU and declines when disabled
+    os.environ["ODP_OMPT_DISABLE"] = "1"
+    try:
+        lib = ctypes.CDLL(build.OMPT_LIB)
+        lib.ompt_start_tool.restype = ctypes.c_void_p
+        assert lib.ompt_start_tool(51, b"x") is None
+    finally:
+        del os.environ["ODP_OMPT_DISABLE"]
 
 
 def test_library_loads_without_gpu():
