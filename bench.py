@@ -617,8 +617,32 @@ def sweep(odp, sgpu, content, stream):
             reps = 20 if size <= (64 << 20) else 5
             _, per = time_calls(lambda: odp.fingerprint(ptrs, sizes, out, stream), reps, 3, stream)
             med = statistics.median(per)
-            rows.append({"variant": variant_name, "bytes": size,
-                         "gbs": round(size / (med / 1e3) / 1e9, 2), "ms": round(med, 4)})
+            # the same buffer through odp_fingerprint_one (host-side pointer and
+            # size, launch sized to the buffer)
+            _, per1 = time_calls(lambda: odp.fingerprint_one(buf.data_ptr(), size, out, stream),
+                                 reps, 3, stream)
+            med1 = statistics.median(per1)
+            row = {"variant": variant_name, "bytes": size,
+                   "gbs": round(size / (med / 1e3) / 1e9, 2), "ms": round(med, 4),
+                   "one_gbs": round(size / (med1 / 1e3) / 1e9, 2), "one_ms": round(med1, 4)}
+            if size <= (16 << 20):
+                # small calls are bound by the host's launch rate: also the
+                # device time per call, 20 calls replayed from a CUDA graph
+                for key, fn in (("graph_ms", lambda s_: odp.fingerprint(ptrs, sizes, out, s_)),
+                                ("one_graph_ms",
+                                 lambda s_: odp.fingerprint_one(buf.data_ptr(), size, out, s_))):
+                    cap = torch.cuda.Stream()
+                    cap.wait_stream(stream)
+                    with torch.cuda.stream(cap):
+                        fn(cap)
+                    torch.cuda.synchronize()
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g, stream=cap):
+                        for _ in range(20):
+                            fn(cap)
+                    tot, _ = time_calls(g.replay, 5, 2, stream)
+                    row[key] = round(tot / 5 / 20, 5)
+            rows.append(row)
             del buf
     return rows
 

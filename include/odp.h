@@ -148,6 +148,18 @@ typedef struct odp_fp_schedule {
     int32_t load_stages;
 } odp_fp_schedule;
 
+/*
+ * odp_fingerprint_one -- FP128 of one device buffer given by a host-side
+ * pointer and size (no device argument arrays to copy first); the launch is
+ * sized to the buffer, which saves the idle warps of a full grid on small
+ * buffers.  out128 is device memory (16 bytes).  Asynchronous like
+ * odp_fingerprint; size 0 gives the empty-input hash; a null ptr with
+ * size > 0 writes zero and records ODP_ERR_INVALID_ARG in the status word
+ * (odp_fingerprint_status).  No paper counterpart: a host-side convenience
+ * for tools that fingerprint one transfer at a time.
+ */
+int odp_fingerprint_one(const void* ptr, uint64_t size, odp_fp128* out128, cudaStream_t stream);
+
 /* odp_fingerprint with an explicit schedule (ODP_ERR_INVALID_ARG for values
  * outside the ranges above). */
 int odp_fingerprint_with(const odp_fp_schedule* sched, const void* const* ptrs,

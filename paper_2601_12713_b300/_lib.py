@@ -24,6 +24,8 @@ _lib.odp_status_string.argtypes = [ctypes.c_int]
 _lib.odp_status_string.restype = ctypes.c_char_p
 _lib.odp_fingerprint.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, _vp]
 _lib.odp_fingerprint.restype = ctypes.c_int
+_lib.odp_fingerprint_one.argtypes = [_vp, ctypes.c_uint64, _vp, _vp]
+_lib.odp_fingerprint_one.restype = ctypes.c_int
 _lib.odp_fingerprint_noalloc.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, _vp]
 _lib.odp_fingerprint_noalloc.restype = ctypes.c_int
 class FpSchedule(ctypes.Structure):
@@ -93,6 +95,14 @@ def fingerprint(ptrs: torch.Tensor, sizes: torch.Tensor, out: torch.Tensor, stre
     _check(_lib.odp_fingerprint(ptrs.data_ptr() if n else None, sizes.data_ptr() if n else None,
                                 n, out.data_ptr() if n else None, _stream(stream)),
            "odp_fingerprint")
+
+
+def fingerprint_one(ptr: int, size: int, out: torch.Tensor, stream=None) -> None:
+    """FP128 of one device buffer given by its address and size (host ints);
+    ``out`` a CUDA tensor of at least 16 bytes receiving (lo, hi)."""
+    assert out.is_cuda and out.is_contiguous() and out.numel() * out.element_size() >= 16
+    _check(_lib.odp_fingerprint_one(ptr or None, size, out.data_ptr(), _stream(stream)),
+           "odp_fingerprint_one")
 
 
 def _fp_args(ptrs, sizes, out):

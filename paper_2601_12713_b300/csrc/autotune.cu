@@ -119,6 +119,7 @@ int odp_fingerprint_with(const odp_fp_schedule* sched, const void* const* ptrs,
                          const uint64_t* sizes, uint64_t n, odp_fp128* out128,
                          cudaStream_t stream) {
     if (!sched) return ODP_ERR_INVALID_ARG;
+    if (n > 0 && (!ptrs || !sizes)) return ODP_ERR_INVALID_ARG;
     if (sched->warps_per_cta != 4 && sched->warps_per_cta != 8 && sched->warps_per_cta != 16)
         return ODP_ERR_INVALID_ARG;
     if (sched->ctas_per_sm < 0 || sched->tmin_scale < 1) return ODP_ERR_INVALID_ARG;

@@ -59,26 +59,35 @@ struct FpArgs {
     U128* nodes;          // 2 * cap_tiles
     int32_t* status;      // per-device status word (null: not published)
     uint32_t single;      // 1: one buffer, planned inside fp_tiles
+    uint32_t host_one;    // 1: that buffer is one_ptr / one_size (given by value)
+    const void* one_ptr;
+    uint64_t one_size;
 };
 
-__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
-__device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
-__device__ __forceinline__ uint64_t n_chunks(uint64_t size) { return (size + CHUNK - 1) / CHUNK; }
+__host__ __device__ __forceinline__ uint64_t n_chunks(uint64_t size) {
+    return (size + CHUNK - 1) / CHUNK;
+}
 
-__device__ __forceinline__ int ceil_log2(uint64_t v) {
+__host__ __device__ __forceinline__ int ceil_log2(uint64_t v) {
+#ifdef __CUDA_ARCH__
     return v <= 1 ? 0 : 64 - __clzll((long long)(v - 1));
+#else
+    return v <= 1 ? 0 : 64 - __builtin_clzll(v - 1);
+#endif
 }
 
 // Tile size exponent of a buffer: aim for `tmin` tiles, at most 32 chunks per
 // tile unless the scratch capacity forces larger tiles (m_floor).
-__device__ __forceinline__ int tile_log2(uint64_t nchunk, uint32_t tmin, uint32_t m_floor) {
+__host__ __device__ __forceinline__ int tile_log2(uint64_t nchunk, uint32_t tmin, uint32_t m_floor) {
     uint64_t want = (nchunk + tmin - 1) / tmin;
-    int m = min(ceil_log2(want), 5);
-    return max(m, (int)m_floor);
+    int m = ceil_log2(want) < 5 ? ceil_log2(want) : 5;
+    return m > (int)m_floor ? m : (int)m_floor;
 }
 
-__device__ __forceinline__ uint64_t n_tiles(uint64_t nchunk, int m) {
+__host__ __device__ __forceinline__ uint64_t n_tiles(uint64_t nchunk, int m) {
     return (nchunk + (1ull << m) - 1) >> m;
 }
 
@@ -115,7 +124,8 @@ __device__ __forceinline__ uint64_t plan_chunks(const FpArgs& a, uint32_t i) {
     return n_chunks(size);
 }
 
-__device__ __forceinline__ uint32_t floor_for(unsigned long long total_chunks, uint32_t budget) {
+__host__ __device__ __forceinline__ uint32_t floor_for(unsigned long long total_chunks,
+                                                       uint32_t budget) {
     uint32_t m = 0;
     while ((total_chunks >> m) > budget) ++m;
     return m;
@@ -378,6 +388,75 @@ struct WarpStack {
     uint64_t count[40];
 };
 
+// ---------------------------------------------------- one small buffer
+// A buffer of at most ONE_SMALL_CHUNKS chunks whose address and size the
+// host knows, hashed by a single block: each warp hashes whole chunks into
+// leaves in shared memory, warp g reduces the aligned 32-leaf group g (a
+// complete subtree), and warp 0 combines the group roots -- the same
+// left-balanced tree as the tiled kernel, with no global counters or fences.
+constexpr uint32_t ONE_SMALL_CHUNKS = 64;
+
+__global__ void __launch_bounds__(1024) fp_one_small(const uint8_t* base, uint64_t size,
+                                                     odp_fp128* out, int32_t* status) {
+    __shared__ U128 leaves[ONE_SMALL_CHUNKS];
+    __shared__ U128 groups[ONE_SMALL_CHUNKS / 32];
+    __shared__ uint64_t gcount[ONE_SMALL_CHUNKS / 32];
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    if (size == 0 || base == nullptr) {
+        if (threadIdx.x == 0) {
+            const U128 e = size == 0 ? fp::empty_input() : U128{0, 0};
+            out->lo = e.x;
+            out->hi = e.y;
+            if (size != 0 && status) atomicCAS((int*)status, 0, ODP_ERR_INVALID_ARG);
+        }
+        return;
+    }
+    const uint64_t nc = n_chunks(size);
+    uint64_t a0, b0;
+    fp::lane_init(lane, a0, b0);
+    const bool aligned = ((uintptr_t)base & 15) == 0;
+    for (uint64_t c = warp; c < nc; c += blockDim.x / 32) {
+        const uint8_t* cp = base + c * CHUNK;
+        const uint32_t r = (uint32_t)umin64(CHUNK, size - c * CHUNK);
+        uint4 w[8];
+        if (aligned && r == CHUNK) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) w[j] = ld_stream(cp + 16 * (lane + 32 * j));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) w[j] = load_word_general(cp, lane + 32 * j, r);
+        }
+        uint64_t rx, ry;
+        absorb_and_combine(w, a0, b0, rx, ry);
+        rx = shfl64(rx, 0);
+        ry = shfl64(ry, 0);
+        if (lane == 0) leaves[c] = fp::leaf(rx, ry, r);
+    }
+    __syncthreads();
+    const uint32_t ng = (uint32_t)((nc + 31) / 32);
+    if ((uint32_t)warp < ng) {
+        const uint32_t gc = (uint32_t)umin64(32, nc - 32ull * warp);
+        U128 v = (uint32_t)lane < gc ? leaves[32 * warp + lane] : U128{0, 0};
+        uint64_t cc = 1;
+        const U128 gr = warp_tree(v, cc, gc, lane);
+        if (lane == 0) {
+            groups[warp] = gr;
+            gcount[warp] = cc;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        U128 v = (uint32_t)lane < ng ? groups[lane] : U128{0, 0};
+        uint64_t cc = (uint32_t)lane < ng ? gcount[lane] : 0;
+        const U128 root = warp_tree(v, cc, ng, lane);
+        if (lane == 0) {
+            const U128 o = fp::finish(root, size, nc);
+            out->lo = o.x;
+            out->hi = o.y;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- bulk ring
 // Optional load path: whole 4 KiB chunks of 16-byte-aligned buffers are
 // copied into a per-warp ring of shared-memory slots with 1D bulk copies
@@ -544,8 +623,8 @@ __device__ __forceinline__ TileInfo tile_info(const FpArgs& a, uint32_t t, uint3
     TileInfo ti;
     ti.b = a.n == 1 ? 0u : a.tile_buf[t];
     ti.tb = a.single ? t : t - a.tile_off[ti.b];
-    ti.size = a.sizes[ti.b];
-    ti.base = (const uint8_t*)a.ptrs[ti.b];
+    ti.size = a.host_one ? a.one_size : a.sizes[ti.b];
+    ti.base = (const uint8_t*)(a.host_one ? a.one_ptr : a.ptrs[ti.b]);
     ti.nchunk = n_chunks(ti.size);
     ti.m = tile_log2(ti.nchunk, a.tmin, m_floor);
     ti.c0 = (uint64_t)ti.tb << ti.m;
@@ -632,8 +711,8 @@ __global__ void __launch_bounds__(WARPS * 32, fp_min_ctas<WARPS, STAGES>()) fp_t
     uint32_t T, m_floor;
     if (a.single) {
         // one buffer: the plan is a few integer operations, done by every warp
-        const uint64_t size = a.sizes[0];
-        const bool null_ptr = a.ptrs[0] == nullptr;
+        const uint64_t size = a.host_one ? a.one_size : a.sizes[0];
+        const bool null_ptr = (a.host_one ? a.one_ptr : a.ptrs[0]) == nullptr;
         if (size == 0 || null_ptr) {
             T = 0;
             m_floor = 0;
@@ -726,8 +805,8 @@ static int fp_prepare() {
 }
 
 template <int W, int S>
-static void fp_tiles_launch(const FpArgs& a, int ctas_per_sm, int sms, cudaStream_t stream) {
-    fp_tiles<W, S><<<sms * ctas_per_sm, W * 32, fp_dyn_smem<W, S>(), stream>>>(a);
+static void fp_tiles_launch(const FpArgs& a, int grid, cudaStream_t stream) {
+    fp_tiles<W, S><<<grid, W * 32, fp_dyn_smem<W, S>(), stream>>>(a);
 }
 
 // The (warps per CTA, stages) pairs that are instantiated.
@@ -748,16 +827,16 @@ static int fp_occupancy(int W, int S) {
     }
 }
 
-static void fp_launch(const FpArgs& a, int W, int S, int ctas, int sms, cudaStream_t stream) {
+static void fp_launch(const FpArgs& a, int W, int S, int grid, cudaStream_t stream) {
     switch (W * 16 + S) {
-        case 4 * 16 + 0: fp_tiles_launch<4, 0>(a, ctas, sms, stream); break;
-        case 4 * 16 + 2: fp_tiles_launch<4, 2>(a, ctas, sms, stream); break;
-        case 4 * 16 + 4: fp_tiles_launch<4, 4>(a, ctas, sms, stream); break;
-        case 8 * 16 + 2: fp_tiles_launch<8, 2>(a, ctas, sms, stream); break;
-        case 8 * 16 + 4: fp_tiles_launch<8, 4>(a, ctas, sms, stream); break;
-        case 16 * 16 + 0: fp_tiles_launch<16, 0>(a, ctas, sms, stream); break;
-        case 16 * 16 + 2: fp_tiles_launch<16, 2>(a, ctas, sms, stream); break;
-        default: fp_tiles_launch<8, 0>(a, ctas, sms, stream); break;
+        case 4 * 16 + 0: fp_tiles_launch<4, 0>(a, grid, stream); break;
+        case 4 * 16 + 2: fp_tiles_launch<4, 2>(a, grid, stream); break;
+        case 4 * 16 + 4: fp_tiles_launch<4, 4>(a, grid, stream); break;
+        case 8 * 16 + 2: fp_tiles_launch<8, 2>(a, grid, stream); break;
+        case 8 * 16 + 4: fp_tiles_launch<8, 4>(a, grid, stream); break;
+        case 16 * 16 + 0: fp_tiles_launch<16, 0>(a, grid, stream); break;
+        case 16 * 16 + 2: fp_tiles_launch<16, 2>(a, grid, stream); break;
+        default: fp_tiles_launch<8, 0>(a, grid, stream); break;
     }
 }
 
@@ -767,9 +846,17 @@ static std::mutex g_zero_mu;
 static std::map<void*, size_t> g_zeroed;
 
 int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128* out,
-           cudaStream_t stream, const FpLaunch& L) {
+           cudaStream_t stream, const FpLaunch& L, const void* one_ptr, uint64_t one_size) {
+    const bool host_one = ptrs == nullptr && sizes == nullptr && n == 1;
     if (n == 0) return ODP_OK;
-    if (!ptrs || !sizes || !out) return ODP_ERR_INVALID_ARG;
+    if ((!host_one && (!ptrs || !sizes)) || !out) return ODP_ERR_INVALID_ARG;
+    if (host_one && n_chunks(one_size) <= ONE_SMALL_CHUNKS) {
+        int st = ODP_OK;
+        int32_t* status = device_status_word(&st);
+        if (!status) return st;
+        fp_one_small<<<1, 1024, 0, stream>>>((const uint8_t*)one_ptr, one_size, out, status);
+        return cuda_status(cudaGetLastError());
+    }
     if (n > (1ull << 28)) return ODP_ERR_UNSUPPORTED;
     int st = ODP_OK;
     int32_t* status = device_status_word(&st);
@@ -825,6 +912,9 @@ int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128
     a.nodes = (U128*)(s + o_nodes);
     a.status = status;
     a.single = nn == 1;
+    a.host_one = host_one;
+    a.one_ptr = one_ptr;
+    a.one_size = one_size;
 
     const bool ok = fp_variant_ok(L.warps_per_cta, L.stages);
     const int W = ok ? L.warps_per_cta : TILE_WARPS;
@@ -848,7 +938,14 @@ int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128
         }
         fp_plan_tiles<<<sms * 4, 256, 0, stream>>>(a);
     }
-    fp_launch(a, W, S, ctas, sms, stream);
+    int grid = sms * ctas;
+    if (host_one) {
+        // the buffer is known here: launch only the warps that get a tile
+        const uint64_t nc = n_chunks(one_size);
+        const uint64_t T = nc ? n_tiles(nc, tile_log2(nc, a.tmin, floor_for(nc, cap_tiles - 1))) : 0;
+        grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(grid, (T + W - 1) / W));
+    }
+    fp_launch(a, W, S, grid, stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         {
@@ -865,8 +962,16 @@ int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128
 
 extern "C" int odp_fingerprint(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
                                odp_fp128* out128, cudaStream_t stream) {
+    if (!ptrs || !sizes) return n == 0 ? ODP_OK : ODP_ERR_INVALID_ARG;
     odp::FpLaunch L = odp::fp_schedule_for(n);
     return odp::fp_run(ptrs, sizes, n, out128, stream, L);
+}
+
+extern "C" int odp_fingerprint_one(const void* ptr, uint64_t size, odp_fp128* out128,
+                                   cudaStream_t stream) {
+    if (!out128) return ODP_ERR_INVALID_ARG;
+    odp::FpLaunch L = odp::fp_schedule_for(1);
+    return odp::fp_run(nullptr, nullptr, 1, out128, stream, L, ptr, size);
 }
 
 // ---------------------------------------------------------------------------
@@ -946,6 +1051,9 @@ static int fp_run_noalloc(const void* const* ptrs, const uint64_t* sizes, uint64
     a.nodes = (U128*)(s + NA_O_NODES);
     a.status = nullptr;
     a.single = 0;
+    a.host_one = 0;
+    a.one_ptr = nullptr;
+    a.one_size = 0;
 
     const int sms = device_sm_count();
     int occ = 0;

@@ -17,8 +17,11 @@ struct FpLaunch {
     int stages = 2;                  // 0: register loads; 2 or 4: bulk-copy ring slots per warp
 };
 
+// ptrs == sizes == null with n == 1: the one buffer is (one_ptr, one_size),
+// given by value from the host.
 int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128* out,
-           cudaStream_t stream, const FpLaunch& L);
+           cudaStream_t stream, const FpLaunch& L, const void* one_ptr = nullptr,
+           uint64_t one_size = 0);
 
 // Schedule for a batch of n buffers: the autotuned entry for n's size class
 // if one exists, else the defaults (tile target scale 1 for a single buffer).

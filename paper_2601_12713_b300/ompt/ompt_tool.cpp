@@ -102,13 +102,13 @@ int8_t dev_num(int d) { return d == g_tool.host_device || d < 0 ? (int8_t)-1 : (
 struct ThreadState {
     std::unordered_map<uint64_t, uint64_t> begin_ns;  // host_op_id -> start
     cudaStream_t stream = nullptr;
-    uint64_t* h_args = nullptr;   // pinned: ptr, size, out lo, out hi
-    uint64_t* d_args = nullptr;   // device: ptr, size, out lo, out hi
+    uint64_t* h_out = nullptr;   // pinned: lo, hi
+    uint64_t* d_out = nullptr;   // device: lo, hi
     bool ready = false;
     ~ThreadState() {
         if (stream) cudaStreamDestroy(stream);
-        if (h_args) cudaFreeHost(h_args);
-        if (d_args) cudaFree(d_args);
+        if (h_out) cudaFreeHost(h_out);
+        if (d_out) cudaFree(d_out);
     }
 };
 thread_local ThreadState t_state;
@@ -118,26 +118,19 @@ bool fingerprint_device(const void* p, uint64_t bytes, uint64_t* lo, uint64_t* h
     ThreadState& t = t_state;
     if (!t.ready) {
         if (cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaHostAlloc((void**)&t.h_args, 32, 0) != cudaSuccess ||
-            cudaMalloc((void**)&t.d_args, 32) != cudaSuccess) {
+            cudaHostAlloc((void**)&t.h_out, 16, 0) != cudaSuccess ||
+            cudaMalloc((void**)&t.d_out, 16) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
         t.ready = true;
     }
-    t.h_args[0] = (uint64_t)(uintptr_t)p;
-    t.h_args[1] = bytes;
-    if (cudaMemcpyAsync(t.d_args, t.h_args, 16, cudaMemcpyHostToDevice, t.stream) != cudaSuccess)
-        return false;
-    if (odp_fingerprint((const void* const*)t.d_args, t.d_args + 1, 1, (odp_fp128*)(t.d_args + 2),
-                        t.stream) != ODP_OK)
-        return false;
-    if (cudaMemcpyAsync(t.h_args + 2, t.d_args + 2, 16, cudaMemcpyDeviceToHost, t.stream) !=
-            cudaSuccess ||
+    if (odp_fingerprint_one(p, bytes, (odp_fp128*)t.d_out, t.stream) != ODP_OK) return false;
+    if (cudaMemcpyAsync(t.h_out, t.d_out, 16, cudaMemcpyDeviceToHost, t.stream) != cudaSuccess ||
         cudaStreamSynchronize(t.stream) != cudaSuccess)
         return false;
-    *lo = t.h_args[2];
-    *hi = t.h_args[3];
+    *lo = t.h_out[0];
+    *hi = t.h_out[1];
     return true;
 }
 

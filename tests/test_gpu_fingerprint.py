@@ -159,3 +159,31 @@ def test_full_scale_batched_ragged(cuda_ok, orc, odp):
     assert np.array_equal(fps[d], fps[dup_of[d]])
     orig = fps[dup_of < 0]
     assert np.unique(orig, axis=0).shape[0] == orig.shape[0]
+
+
+def test_fingerprint_one_equals_batched_call(cuda_ok, orc, odp):
+    """odp_fingerprint_one (host-side pointer and size, launch sized to the
+    buffer) gives the same fingerprints as odp_fingerprint, for sizes from 0
+    to 256 MiB and start offsets that break 16-byte alignment."""
+    big = dev_buffer((256 << 20) + 64, seed=0x0DB7, pad=0)
+    out1 = torch.empty(2, dtype=torch.int64, device="cuda")
+    for size in (0, 1, 15, 16, 17, 4095, 4096, 4097, 65536, (1 << 20) + 7, (64 << 20) + 13,
+                 256 << 20):
+        for off in (0, 1, 16, 4099):
+            if off + size > big.numel():
+                continue
+            ptr = big.data_ptr() + off
+            odp.fingerprint_one(ptr, size, out1)
+            ptrs = torch.tensor([ptr], dtype=torch.int64, device="cuda")
+            sizes = torch.tensor([size], dtype=torch.int64, device="cuda")
+            out = torch.empty((1, 2), dtype=torch.int64, device="cuda")
+            odp.fingerprint(ptrs, sizes, out)
+            assert out1.tolist() == out[0].tolist(), (size, off)
+            if size <= (1 << 20) + 7 and off in (0, 1):
+                host = big[off:off + size].cpu().numpy()
+                got = tuple(int(x) for x in out1.cpu().numpy().view(np.uint64))
+                assert got == orc.fp128(host), (size, off)
+    assert odp.fingerprint_status() == 0
+    odp.fingerprint_one(0, 10, out1)  # null pointer with bytes: zero and a status
+    assert odp.fingerprint_status() == -1
+    assert out1.tolist() == [0, 0]
