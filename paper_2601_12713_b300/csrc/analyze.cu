@@ -1420,12 +1420,12 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     uint32_t* wscan = (uint32_t*)(b + o_wscan);
     k_em_count<<<sms * 8, 256, 0, s>>>(a, wcnt, nch);
     prim::exclusive_scan(wcnt, wscan, nullptr, 5 * nch, misc + 0, scan_tmp, s);
-    static bool em_attr[256] = {};
+    static std::atomic<bool> em_attr[256] = {};
     const int dev = current_device();
-    if (dev < 256 && !em_attr[dev]) {
+    if (dev < 256 && !em_attr[dev].load(std::memory_order_acquire)) {
         ODP_CHECK_CUDA(cudaFuncSetAttribute(k_em_write, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)sizeof(SiteSmem)));
-        em_attr[dev] = true;
+        em_attr[dev].store(true, std::memory_order_release);
     }
     k_em_write<<<sms * 2, EMW_THREADS, sizeof(SiteSmem), s>>>(a, wscan, nch);
     k_site_flags<<<grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s>>>(a, sflag);

@@ -17,6 +17,7 @@
 // 2^m chunks and 32-aligned groups of tile roots give the same root as the
 // plain recursive split.
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 
@@ -789,15 +790,15 @@ static size_t fp_dyn_smem() {
 template <int W, int S>
 static int fp_prepare() {
     // opt in to more than 48 KiB of dynamic shared memory, once per device
-    static bool done[256] = {};
+    static std::atomic<bool> done[256] = {};
     const int dev = current_device();
-    if (S > 0 && dev < 256 && !done[dev]) {
+    if (S > 0 && dev < 256 && !done[dev].load(std::memory_order_acquire)) {
         if (cudaFuncSetAttribute(fp_tiles<W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)fp_dyn_smem<W, S>()) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
-        done[dev] = true;
+        done[dev].store(true, std::memory_order_release);
     }
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp_tiles<W, S>, W * 32, fp_dyn_smem<W, S>());

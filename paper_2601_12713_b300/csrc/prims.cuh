@@ -8,6 +8,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 
@@ -335,33 +336,33 @@ sort_small(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, uint32_t n_max
 }
 
 inline bool sort_small_ready() {
-    static bool done[256] = {};
+    static std::atomic<bool> done[256] = {};
     const int dev = current_device();
     if (dev < 0 || dev >= 256) return false;
-    if (!done[dev]) {
+    if (!done[dev].load(std::memory_order_acquire)) {
         if (cudaFuncSetAttribute(sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)SMALL_SORT_SMEM) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
-        done[dev] = true;
+        done[dev].store(true, std::memory_order_release);
     }
     return true;
 }
 
 // Resident sort_downsweep blocks per SM (queried once per device).
 inline int downsweep_per_sm() {
-    static int cache[256] = {};
+    static std::atomic<int> cache[256] = {};
     const int dev = current_device();
     if (dev < 0 || dev >= 256) return 4;
-    if (!cache[dev]) {
+    if (!cache[dev].load(std::memory_order_acquire)) {
         int b = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sort_downsweep, SORT_THREADS, 0) !=
                 cudaSuccess || b < 1)
             b = 4;
-        cache[dev] = b;
+        cache[dev].store(b, std::memory_order_release);
     }
-    return cache[dev];
+    return cache[dev].load(std::memory_order_acquire);
 }
 
 // Stable sort of (keys, vals) by the low `key_bits` bits of the keys; the
