@@ -53,6 +53,7 @@ struct Hdr {
     uint32_t nX, nP, nK, nU;
     uint32_t nseg, nrun, nseg2, nsegU;
     uint32_t nB, nsegB;  // transfers / endpoint segments of groups with > 2 endpoints
+    uint32_t nA;         // allocations (at most this many pairs go into the Alg. 3 table)
     uint32_t total_findings, n_site_rows;
     uint32_t tcap;
 };
@@ -191,6 +192,7 @@ __global__ void k_list_lengths(A a, const uint32_t* scanned, const uint32_t* tot
     a.h->nP = scanned[2 * nch] - scanned[1 * nch];
     a.h->nK = scanned[3 * nch] - scanned[2 * nch];
     a.h->nU = *total - scanned[3 * nch];
+    a.h->nA = (uint32_t)a.h->n_allocs;
 }
 
 // Stable compaction of event indices into the four lists, a warp per chunk.
@@ -1391,7 +1393,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     k_p_literal<<<gX, TPB, 0, s>>>(a);
 
     // ---- Alg. 3
-    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nP, n);
+    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, &a.h->nA, n);
     k_ra_insert<<<gX, TPB, 0, s>>>(a);
     k_ra_flag<<<gX, TPB, 0, s>>>(a);
 
