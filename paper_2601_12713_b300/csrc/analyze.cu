@@ -54,6 +54,7 @@ struct Hdr {
     uint32_t nseg, nrun, nseg2, nsegU;
     uint32_t nB, nsegB;  // transfers / endpoint segments of groups with > 2 endpoints
     uint32_t nA;         // allocations (at most this many pairs go into the Alg. 3 table)
+    uint32_t scan_fault; // a scan's bounded wait gave up (reported as ODP_ERR_TIMEOUT)
     uint32_t total_findings, n_site_rows;
     uint32_t tcap;
 };
@@ -1159,12 +1160,12 @@ __global__ void k_finalize(A a, const uint32_t* n_findings, const uint32_t* n_ro
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     odp_summary* S = a.out.summary;
     const Hdr* h = a.h;
-    if (h->err != NO_ERR) {
+    if (h->err != NO_ERR || h->scan_fault) {
         uint64_t* z = (uint64_t*)S;
         for (size_t k = 0; k < sizeof(odp_summary) / 8; ++k) z[k] = 0;
         *a.out.count = 0;
         *a.out.sites_count = 0;
-        *a.out.status = -(int32_t)(h->err & 0xFF);
+        *a.out.status = h->err != NO_ERR ? -(int32_t)(h->err & 0xFF) : ODP_ERR_TIMEOUT;
         return;
     }
     S->n_events = a.n;
@@ -1324,6 +1325,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     srt.hist = (uint32_t*)(b + o_hist);
     srt.scan_tmp = (uint32_t*)(b + o_scan);
     srt.hlen = misc + 3;
+    srt.fault = &a.h->scan_fault;
     uint32_t* scan_tmp = srt.scan_tmp;
 
     const int bits_n = prim::bit_length(n);              // keys < n + 1
@@ -1338,12 +1340,13 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     ODP_CHECK_CUDA(cudaMemsetAsync(a.wbits, 0, 4ull * ((n + 31) / 32) + 16, s));
     ODP_CHECK_CUDA(cudaMemsetAsync(a.dstart, 0, 2 * 4 * NDEV, s));
     ODP_CHECK_CUDA(cudaMemsetAsync(a.sites, 0, 8ull * 3 * 5 * ODP_MAX_SITES, s));
+    ODP_CHECK_CUDA(cudaMemsetAsync(scan_tmp, 0, 4 * (scan_words + 16), s));
 
     // ---- validate, lists
     uint32_t* ccnt = (uint32_t*)(b + o_wcnt);
     uint32_t* cscan = (uint32_t*)(b + o_wscan);
     k_validate<<<sms * 16, TPB, 0, s>>>(a, ccnt, nch);
-    prim::exclusive_scan(ccnt, cscan, nullptr, 4 * nch, misc + 2, scan_tmp, s);
+    prim::exclusive_scan(ccnt, cscan, nullptr, 4 * nch, misc + 2, scan_tmp, s, srt.fault);
     k_list_lengths<<<1, 32, 0, s>>>(a, cscan, misc + 2, nch);
     k_compact<<<sms * 16, TPB, 0, s>>>(a, cscan, nch);
     uint32_t* nX = &a.h->nX;
@@ -1359,26 +1362,26 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     // ---- Alg. 2
     prim::radix_sort(a.sk, a.sv, nX, n, bits_n, srt, s);
     k_rt_flags<<<gX, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.f1, a.id1, nX, n, &a.h->nseg, scan_tmp, s);
-    prim::exclusive_scan(a.f2, a.id2, nX, n, &a.h->nrun, scan_tmp, s);
+    prim::exclusive_scan(a.f1, a.id1, nX, n, &a.h->nseg, scan_tmp, s, srt.fault);
+    prim::exclusive_scan(a.f2, a.id2, nX, n, &a.h->nrun, scan_tmp, s, srt.fault);
     k_rt_starts<<<gX, TPB, 0, s>>>(a);
     k_rt_check<<<gX, TPB, 0, s>>>(a);
     k_rt_partner<<<gX, TPB, 0, s>>>(a);
     // groups with more than two endpoints
     uint32_t* nB = &a.h->nB;
     k_mx_flag<<<gX, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.f2, a.id2, nX, n, nB, scan_tmp, s);
+    prim::exclusive_scan(a.f2, a.id2, nX, n, nB, scan_tmp, s, srt.fault);
     k_mx_scatter<<<gX, TPB, 0, s>>>(a);
     prim::radix_sort(a.k2, a.v2, nB, n, 8, srt, s);
     k_mx_gkey<<<gX, TPB, 0, s>>>(a);
     prim::radix_sort(a.k2, a.v2, nB, n, bits_n, srt, s);
     k_mx_heads<<<gX, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.f2, a.id2, nB, n, &a.h->nsegB, scan_tmp, s);
+    prim::exclusive_scan(a.f2, a.id2, nB, n, &a.h->nsegB, scan_tmp, s, srt.fault);
     k_mx_starts<<<gX, TPB, 0, s>>>(a);
     k_mx_late<<<gX, TPB, 0, s>>>(a);
     k_mx_ok<<<gX, TPB, 0, s>>>(a);
     k_mx_succ<<<gX, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.k2, a.sk, nB, n, nullptr, scan_tmp, s);
+    prim::exclusive_scan(a.k2, a.sk, nB, n, nullptr, scan_tmp, s, srt.fault);
     k_mx_partner<<<gX, TPB, 0, s>>>(a);
 
     // ---- pairs
@@ -1386,7 +1389,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     k_p_insert<<<gX, TPB, 0, s>>>(a);
     prim::radix_sort(a.sk, a.sv, nP, n, bits_slot, srt, s);
     k_seg_heads<<<gX, TPB, 0, s>>>(a, nP);
-    prim::exclusive_scan(a.f1, a.id1, nP, n, &a.h->nseg2, scan_tmp, s);
+    prim::exclusive_scan(a.f1, a.id1, nP, n, &a.h->nseg2, scan_tmp, s, srt.fault);
     k_seg_starts<<<gX, TPB, 0, s>>>(a, nP, &a.h->nseg2);
     k_p_check<<<gX, TPB, 0, s>>>(a);
     k_p_match<<<gX, TPB, 0, s>>>(a);
@@ -1411,7 +1414,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     prim::radix_sort(a.sk, a.sv, nU, n, 8, srt, s);
     k_ut_class<<<gX, TPB, 0, s>>>(a);
     k_ut_heads<<<gX, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.f1, a.id1, nU, n, &a.h->nsegU, scan_tmp, s);
+    prim::exclusive_scan(a.f1, a.id1, nU, n, &a.h->nsegU, scan_tmp, s, srt.fault);
     prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.ktab, nU, n);
     k_ut_insert<<<gX, TPB, 0, s>>>(a);
     prim::radix_sort(a.k2, a.v2, nU, n, bits_slot, srt, s);
@@ -1421,7 +1424,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     uint32_t* wcnt = (uint32_t*)(b + o_wcnt);
     uint32_t* wscan = (uint32_t*)(b + o_wscan);
     k_em_count<<<sms * 8, 256, 0, s>>>(a, wcnt, nch);
-    prim::exclusive_scan(wcnt, wscan, nullptr, 5 * nch, misc + 0, scan_tmp, s);
+    prim::exclusive_scan(wcnt, wscan, nullptr, 5 * nch, misc + 0, scan_tmp, s, srt.fault);
     static std::atomic<bool> em_attr[256] = {};
     const int dev = current_device();
     if (dev < 256 && !em_attr[dev].load(std::memory_order_acquire)) {
@@ -1431,7 +1434,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     }
     k_em_write<<<sms * 2, EMW_THREADS, sizeof(SiteSmem), s>>>(a, wscan, nch);
     k_site_flags<<<grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s>>>(a, sflag);
-    prim::exclusive_scan(sflag, spos, nullptr, 5u * ODP_MAX_SITES, misc + 1, scan_tmp, s);
+    prim::exclusive_scan(sflag, spos, nullptr, 5u * ODP_MAX_SITES, misc + 1, scan_tmp, s, srt.fault);
     k_site_write<<<grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s>>>(a, sflag, spos);
     k_finalize<<<1, 32, 0, s>>>(a, misc + 0, misc + 1);
     return cuda_status(cudaGetLastError());

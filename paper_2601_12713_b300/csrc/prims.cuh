@@ -30,62 +30,119 @@ constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr uint32_t SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
-// Tile-local exclusive scan; tile sums to `sums`.  Blocks loop over tiles,
-// so the grid can be capped and a short device length costs little.
+// Single-pass exclusive scan with decoupled look-back: blocks take tiles from
+// a counter in order, publish each tile's sum ("aggregate"), then walk back
+// over their predecessors' published words, 32 at a time (one per lane),
+// adding aggregates until a predecessor that already published its
+// inclusive prefix; then publish their own inclusive prefix.  A block only
+// waits on tiles handed out before its own, which are held by running
+// blocks, so every wait ends; each wait is also bounded (SCAN_WAIT_LIMIT
+// polls, then *fault is set and the scan goes on with a wrong prefix, never a
+// hang).
+//
+// tmp (u32 words, zero before its first use; every scan leaves it ready for
+// the next): [0] tile counter, [1] finished blocks, [2] epoch, [3] unused,
+// then one u64 per tile: epoch (30 bits) | flag (2 bits: 1 aggregate,
+// 2 inclusive) | value (32 bits).  The last block out resets the counters and
+// advances the epoch, so words of earlier scans never look current (also
+// when a captured graph replays the same launch).
+constexpr uint32_t SCAN_WAIT_LIMIT = 1u << 20;
+
 __global__ void __launch_bounds__(SCAN_THREADS)
-scan_local(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t n_max,
-           uint32_t* sums) {
+scan_chained(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t n_max,
+             uint32_t* total, uint32_t* tmp, uint32_t* fault) {
     __shared__ uint32_t sm[40];
+    __shared__ uint32_t s_tile, s_prefix;
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(tmp + 4);
     const uint32_t n = dev_len(n_dev, n_max);
-    for (uint32_t base = blockIdx.x * SCAN_TILE; base < n; base += gridDim.x * SCAN_TILE) {
-        uint32_t v[SCAN_ITEMS], s = 0;
+    const uint32_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    const uint32_t epoch = *(volatile uint32_t*)(tmp + 2) & 0x3FFFFFFFu;
+    const unsigned long long tag = (unsigned long long)epoch << 34;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0 && total) *total = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(tmp, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= ntiles) break;
+        const uint32_t base = t * SCAN_TILE;
+        uint32_t v[SCAN_ITEMS], sum = 0;
 #pragma unroll
         for (int k = 0; k < SCAN_ITEMS; ++k) {
-            uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
+            const uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
             v[k] = i < n ? in[i] : 0;
-            s += v[k];
+            sum += v[k];
         }
         uint32_t tot;
-        uint32_t e = block_exclusive_scan_u32(s, &tot, sm);
+        uint32_t e = block_exclusive_scan_u32(sum, &tot, sm);
+        if (warp == 0) {
+            uint32_t prefix = 0;
+            if (t == 0) {
+                if (lane == 0) atomicExch(&status[0], tag | (2ull << 32) | tot);
+            } else {
+                if (lane == 0) atomicExch(&status[t], tag | (1ull << 32) | tot);
+                bool ok = true;
+                for (long long back = (long long)t - 1; back >= 0; back -= 32) {
+                    const long long j = back - lane;
+                    unsigned long long w = 0;
+                    bool ready = j < 0;
+                    if (!ready) {
+                        w = __ldcv(&status[j]);
+                        ready = (w >> 34) == epoch && ((w >> 32) & 3ull) != 0;
+                    }
+                    uint32_t polls = 0;
+                    while (!__all_sync(ODP_FULL_MASK, ready)) {
+                        if (++polls > SCAN_WAIT_LIMIT) {
+                            ok = false;
+                            break;
+                        }
+                        if (!ready) {
+                            w = __ldcv(&status[j]);
+                            ready = (w >> 34) == epoch && ((w >> 32) & 3ull) != 0;
+                        }
+                    }
+                    if (!ok) break;
+                    const bool incl = j < 0 || ((w >> 32) & 3ull) == 2ull;
+                    const uint32_t val = j < 0 ? 0u : (uint32_t)w;
+                    const uint32_t im = __ballot_sync(ODP_FULL_MASK, incl);
+                    if (im) {
+                        const int k = __ffs(im) - 1;
+                        prefix += __reduce_add_sync(ODP_FULL_MASK, lane <= k ? val : 0u);
+                        break;
+                    }
+                    prefix += __reduce_add_sync(ODP_FULL_MASK, val);
+                }
+                if (!ok && lane == 0 && fault) atomicOr(fault, 1u);
+                if (lane == 0) atomicExch(&status[t], tag | (2ull << 32) | (uint32_t)(prefix + tot));
+            }
+            if (lane == 0) s_prefix = prefix;
+        }
+        __syncthreads();
+        e += s_prefix;
 #pragma unroll
         for (int k = 0; k < SCAN_ITEMS; ++k) {
-            uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
+            const uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
             if (i < n) out[i] = e;
             e += v[k];
         }
-        if (threadIdx.x == 0) sums[base / SCAN_TILE] = tot;
-        __syncthreads();  // sm is reused by the next tile
+        if (t == ntiles - 1 && threadIdx.x == 0 && total) *total = s_prefix + tot;
+        __syncthreads();  // s_tile, s_prefix and sm are reused by the next tile
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(tmp + 1, 1u) == gridDim.x - 1) {  // last block out
+            tmp[0] = 0;
+            tmp[1] = 0;
+            tmp[2] = (epoch + 1) & 0x3FFFFFFFu;
+            __threadfence();
+        }
     }
 }
 
-// One block: exclusive scan of the tile sums; total to *total.
-__global__ void __launch_bounds__(SCAN_THREADS)
-scan_blocks(uint32_t* sums, const uint32_t* n_dev, uint32_t n_max, uint32_t* total) {
-    __shared__ uint32_t sm[40];
-    const uint32_t n = dev_len(n_dev, n_max);
-    const uint32_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    uint32_t run = 0;
-    for (uint32_t b0 = 0; b0 < nb; b0 += SCAN_THREADS) {
-        uint32_t b = b0 + threadIdx.x;
-        uint32_t v = b < nb ? sums[b] : 0, t;
-        uint32_t e = block_exclusive_scan_u32(v, &t, sm);
-        if (b < nb) sums[b] = run + e;
-        run += t;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && total) *total = run;
+// u32 words of scan scratch for up to n_max elements.
+inline size_t scan_tmp_words(uint32_t n_max) {
+    return 4 + 2 * ((size_t)(n_max + SCAN_TILE - 1) / SCAN_TILE + 1);
 }
-
-__global__ void __launch_bounds__(256)
-scan_add(uint32_t* out, const uint32_t* n_dev, uint32_t n_max, const uint32_t* sums) {
-    const uint32_t n = dev_len(n_dev, n_max);
-    for (uint32_t base = blockIdx.x * SCAN_TILE; base < n; base += gridDim.x * SCAN_TILE) {
-        const uint32_t add = sums[base / SCAN_TILE];
-        for (uint32_t i = base + threadIdx.x; i < min(base + SCAN_TILE, n); i += 256) out[i] += add;
-    }
-}
-
-inline size_t scan_tmp_words(uint32_t n_max) { return (n_max + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
 // Grid for a loop over `tiles` tiles: at most `per_sm` blocks per SM.
 inline uint32_t tile_grid(uint32_t tiles, int per_sm) {
@@ -94,17 +151,18 @@ inline uint32_t tile_grid(uint32_t tiles, int per_sm) {
 }
 
 // out[i] = sum of in[0..i) for i < n; *total = sum of all (may be null).
-// In place (in == out) is allowed.
+// In place (in == out) is allowed.  tmp: scan_tmp_words(n_max) words, zero
+// before its first scan; fault (may be null) is set if a wait gave up.
 inline void exclusive_scan(const uint32_t* in, uint32_t* out, const uint32_t* n_dev,
-                           uint32_t n_max, uint32_t* total, uint32_t* tmp, cudaStream_t s) {
+                           uint32_t n_max, uint32_t* total, uint32_t* tmp, cudaStream_t s,
+                           uint32_t* fault = nullptr) {
     if (n_max == 0) {
         if (total) cudaMemsetAsync(total, 0, 4, s);
         return;
     }
     const uint32_t nb = (n_max + SCAN_TILE - 1) / SCAN_TILE;
-    scan_local<<<tile_grid(nb, 2), SCAN_THREADS, 0, s>>>(in, out, n_dev, n_max, tmp);
-    scan_blocks<<<1, SCAN_THREADS, 0, s>>>(tmp, n_dev, n_max, total);
-    scan_add<<<tile_grid(nb, 8), 256, 0, s>>>(out, n_dev, n_max, tmp);
+    scan_chained<<<tile_grid(nb, 2), SCAN_THREADS, 0, s>>>(in, out, n_dev, n_max, total, tmp,
+                                                           fault);
 }
 
 // ------------------------------------------------------------ radix sort
@@ -242,8 +300,9 @@ struct SortTmp {
     uint32_t* keys_alt;
     uint32_t* vals_alt;
     uint32_t* hist;      // 256 * ntiles_max
-    uint32_t* scan_tmp;  // scan_tmp_words(256 * ntiles_max)
+    uint32_t* scan_tmp;  // scan_tmp_words(256 * ntiles_max), zero before first use
     uint32_t* hlen;      // one device word: histogram length of the current pass
+    uint32_t* fault = nullptr;  // set if a scan's wait gave up (may be null)
 };
 
 inline size_t sort_hist_words(uint32_t n_max) {
@@ -386,7 +445,7 @@ inline void radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, ui
         const uint32_t hn = (1u << bits) * ntiles;
         sort_upsweep<<<tile_grid(ntiles, 8), SORT_THREADS, 0, s>>>(k_in, n_dev, n_max, shift, bits,
                                                                    t.hist, t.hlen);
-        exclusive_scan(t.hist, t.hist, t.hlen, hn, nullptr, t.scan_tmp, s);
+        exclusive_scan(t.hist, t.hist, t.hlen, hn, nullptr, t.scan_tmp, s, t.fault);
         sort_downsweep<<<tile_grid(ntiles, downsweep_per_sm()), SORT_THREADS, 0, s>>>(k_in, v_in, k_out, v_out, n_dev,
                                                                      n_max, shift, bits, t.hist);
         shift += bits;

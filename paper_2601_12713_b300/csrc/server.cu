@@ -896,9 +896,11 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
         if (!rc) rc = alloc_dev(S, (void**)&d.sort.keys_alt, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.sort.vals_alt, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.sort.hist, 4 * prim::sort_hist_words((uint32_t)B));
-        if (!rc)
-            rc = alloc_dev(S, (void**)&d.sort.scan_tmp,
-                           4 * (prim::scan_tmp_words(256u * ((uint32_t)B / prim::SORT_TILE + 2)) + 16));
+        if (!rc) {
+            const size_t words = prim::scan_tmp_words(256u * ((uint32_t)B / prim::SORT_TILE + 2)) + 16;
+            rc = alloc_dev(S, (void**)&d.sort.scan_tmp, 4 * words);
+            if (!rc) cudaMemsetAsync(d.sort.scan_tmp, 0, 4 * words, S->an_stream);  // scans need it zero once
+        }
         if (!rc) rc = alloc_dev(S, (void**)&d.find, sizeof(odp_finding) * find_cap);
         if (!rc) rc = alloc_dev(S, (void**)&d.complete, 8 * find_cap);
         if (!rc) rc = alloc_dev(S, (void**)&d.nfind, 16);
