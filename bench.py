@@ -465,7 +465,7 @@ def bench_serving(args, odp, dist, rank, stream):
     srv = odp.Server(n_slots=4, device_budget_bytes=8 << 30, max_events=max_events,
                      max_batch_events=8192, max_producers=128, watermark_timeout_us=50_000)
     lg = load.Load(64, rate, secs, 0x0DB5 + rank, pool.data_ptr(), pool_bytes, 256, 64 << 20)
-    n = lg.run(srv)
+    n = lg.run(srv, announce=args.serve_stamp == "begin")
     srv.flush()
     st = srv.stats()
     streamed = srv.poll(1 << 24)
@@ -505,12 +505,17 @@ def bench_serving(args, odp, dist, rank, stream):
         "higher_is_better": False,
         "p50_ms": round(st["latency_p50_ns"] / 1e6, 3),
         "max_ms": round(st["latency_max_ns"] / 1e6, 3),
+        "before_launch_p50_ms": round(st["queue_p50_ns"] / 1e6, 3),
+        "before_launch_p99_ms": round(st["queue_p99_ns"] / 1e6, 3),
         "sustained_events_per_s": round(sustained, 1),
         "offline_batched_events_per_s": round(offline_rate, 1),
         "config": {"workload": f"64 producer threads, Poisson arrivals, {rate:.0f} events/s "
                                f"aggregate for {secs} s, payloads log-uniform 256 B..64 MiB "
                                "(views of a 1 GiB device pool), 4 slots, 8192-event batches, "
                                "8 GiB device budget", "events": n, "batches": st["batches"],
+                   "start_stamps": ("odp_server_begin (the merge waits only for open events)"
+                                    if args.serve_stamp == "begin" else
+                                    "by each producer (the merge waits for each one's next event)"),
                    "transfers": int(idx.size), "payload_bytes": int(views[:, 1].sum())},
         "findings_streamed": int(streamed.size),
         "streamed_equal_offline": same_findings,
@@ -758,6 +763,10 @@ def main():
     ap.add_argument("--per-buffer-sample", type=int, default=20_000)
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-rate", type=float, default=200_000.0)
+    ap.add_argument("--serve-stamp", default="begin", choices=["begin", "self"],
+                    help="producers open each event with odp_server_begin (the merge waits only "
+                         "for open events) or stamp it themselves (the merge waits for every "
+                         "producer's next event)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if captured")
     args = ap.parse_args()

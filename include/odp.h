@@ -371,6 +371,17 @@ typedef struct odp_server_stats {
     uint64_t latency_p50_ns, latency_p99_ns, latency_max_ns;
     uint64_t first_submit_ns, last_done_ns;  /* steady-clock stamps */
     uint64_t rt_groups_unstreamed;  /* content groups with > 2 endpoints */
+    uint64_t stream_overflow;       /* findings, and decisions waiting for a
+                                       later event, that did not fit the
+                                       server's capacities (3 * max_batch_events
+                                       + min(max_events, 16 * max_batch_events)
+                                       + 64 findings per batch; that minimum of
+                                       waiting pairs and transfers): the streamed
+                                       findings then miss them; odp_analyze over
+                                       the log stays exact */
+    uint64_t queue_p50_ns, queue_p99_ns;  /* the part of the latency before the
+                                       reporting batch was launched (merge
+                                       watermark and batch formation) */
 } odp_server_stats;
 
 /* Creates a server and allocates all of its device memory up front
@@ -385,6 +396,25 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out);
  * first submit (and may then see its first events counted as late).
  */
 int odp_server_attach(odp_server* s, uint64_t start_t_ns);
+
+/*
+ * Opens an event on the calling thread (registering the thread if needed):
+ * *t_start_ns receives its start time on the server's clock (steady clock,
+ * ns), to be used as the event's t_start_ns.  A thread that has called begin
+ * once announces its events: the merge watermark waits for it only while it
+ * has events open (at the start of the earliest), and otherwise passes it at
+ * the server's current time instead of waiting for its next submit.  Such a
+ * thread must begin every event it submits.  Submitting an event closes the
+ * latest open event that starts no later than it; odp_server_cancel closes
+ * one without submitting it; an event open longer than watermark_timeout_us
+ * stops holding the watermark.  Returns ODP_ERR_INVALID_ARG for a null
+ * argument, ODP_ERR_UNSUPPORTED past the producer limit.
+ */
+int odp_server_begin(odp_server* s, uint64_t* t_start_ns);
+
+/* Closes the calling thread's open event that started at t_start_ns without
+ * submitting it (ODP_ERR_INVALID_ARG if no such event is open). */
+int odp_server_cancel(odp_server* s, uint64_t t_start_ns);
 
 /*
  * Thread-safe.  Submits n events (host memory, 64-byte records).  For

@@ -267,7 +267,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in (
         "events_submitted", "events_processed", "batches", "findings_streamed", "late_events",
         "latency_p50_ns", "latency_p99_ns", "latency_max_ns", "first_submit_ns", "last_done_ns",
-        "rt_groups_unstreamed")]
+        "rt_groups_unstreamed", "stream_overflow", "queue_p50_ns", "queue_p99_ns")]
 
 
 _lib.odp_server_create.argtypes = [ctypes.POINTER(ServerCfg), ctypes.POINTER(_vp)]
@@ -276,6 +276,10 @@ _lib.odp_server_submit.argtypes = [_vp, _vp, _vp, ctypes.c_uint64]
 _lib.odp_server_submit.restype = ctypes.c_int
 _lib.odp_server_attach.argtypes = [_vp, ctypes.c_uint64]
 _lib.odp_server_attach.restype = ctypes.c_int
+_lib.odp_server_begin.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64)]
+_lib.odp_server_begin.restype = ctypes.c_int
+_lib.odp_server_cancel.argtypes = [_vp, ctypes.c_uint64]
+_lib.odp_server_cancel.restype = ctypes.c_int
 _lib.odp_server_poll.argtypes = [_vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
 _lib.odp_server_poll.restype = ctypes.c_int
 _lib.odp_server_flush.argtypes = [_vp]
@@ -303,9 +307,20 @@ class Server:
         self.h = h
         self.submit_fn = ctypes.cast(_lib.odp_server_submit, _vp).value
         self.attach_fn = ctypes.cast(_lib.odp_server_attach, _vp).value
+        self.begin_fn = ctypes.cast(_lib.odp_server_begin, _vp).value
 
     def attach(self, start_t_ns: int = 0) -> None:
         _check(_lib.odp_server_attach(self.h, start_t_ns), "odp_server_attach")
+
+    def begin(self) -> int:
+        """Opens an event on the calling thread; returns its start time (ns)."""
+        t = ctypes.c_uint64(0)
+        _check(_lib.odp_server_begin(self.h, ctypes.byref(t)), "odp_server_begin")
+        return int(t.value)
+
+    def cancel(self, t_start_ns: int) -> None:
+        """Closes an event opened by begin() without submitting it."""
+        _check(_lib.odp_server_cancel(self.h, t_start_ns), "odp_server_cancel")
 
     def submit(self, events: np.ndarray, payload_ptrs) -> None:
         ev = np.ascontiguousarray(events)

@@ -1,8 +1,10 @@
 // server.cu -- continuous-batching serving loop over mapping events.
 //
 // Producers (any host threads) submit events as they happen.  A batcher
-// thread merges them in start-time order behind a watermark (the smallest
-// last start time among producers that submitted recently), cuts batches and
+// thread merges them in start-time order behind a watermark (the smallest,
+// over producers that submitted recently, of the last start time; for a
+// producer that opens its events with odp_server_begin, the start of its
+// earliest open event, or the current time if none is open), cuts batches and
 // runs each through a slot: the payloads of its transfers are fingerprinted
 // on the slot's own stream (slots overlap), then, in order on the analysis
 // stream, the batch is appended to the log resident in device memory and the
@@ -48,8 +50,11 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <iterator>
 #include <map>
+#include <memory>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -90,6 +95,18 @@ struct SrvDev {
     uint2* utf[2];     // overwrites waiting for their segment to close (earlier, later), ping-pong
     uint32_t* utopen[2];  // to-device transfers still waiting for a kernel, ping-pong
     uint32_t* nut;     // [0..1] overwrite counts, [2..3] waiting counts, [4] overflow
+    uint32_t* cur;     // which of the ping-pong lists is current (flipped per batch)
+};
+
+// Per-batch parameters, staged from the host with the batch, so that the
+// analysis launch sequence is one CUDA graph replayed for every batch.
+struct BatchPar {
+    uint32_t nx;      // transfers in the batch
+    uint32_t nf;      // of them, fingerprinted by the server
+    uint32_t m;       // events in the batch
+    uint32_t hlen;    // sort scratch: histogram length of the current pass
+    uint64_t g0;      // log index of the batch's first event
+    uint64_t t_next;  // largest start released so far: every later event starts at or after it
 };
 
 struct SlotDev {
@@ -99,7 +116,8 @@ struct SlotDev {
     odp_fp128* fp;
     uint32_t* xpos;        // batch position of each transfer
     uint32_t* fpos;        // batch position of each transfer the server fingerprints
-    uint32_t* nx;          // [0] transfers, [1] of them fingerprinted here (device copy)
+    BatchPar* par;         // the batch's parameters (device copy)
+    uint32_t* nx;          // = &par->nx: [0] transfers, [1] of them fingerprinted here
     uint32_t* sfp;         // per batch position: slot in t_fp / t_dd / t_b
     uint32_t* sdd;
     uint32_t* sb;
@@ -183,8 +201,9 @@ __global__ void srv_scatter_fp(SlotDev s) {
 }
 
 // Content ids: insert <fingerprint> with the log index.
-__global__ void srv_insert_fp(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
-    const uint32_t cap = *d.t_fp.cap_dev;
+__global__ void srv_insert_fp(SrvDev d, SlotDev s) {
+    const uint64_t g0 = s.par->g0;
+    const uint32_t m = s.par->m, cap = *d.t_fp.cap_dev;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
         const odp_event& e = d.log[g0 + q];
         s.sfp[q] = is_xfer(e.kind) ? prim::table_insert_min(d.t_fp, cap, Key128{e.fp_lo, e.fp_hi},
@@ -194,7 +213,9 @@ __global__ void srv_insert_fp(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
 }
 
 // cid; first-receiver and batch-first-receiver tables; endpoint sets.
-__global__ void srv_insert_dd(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
+__global__ void srv_insert_dd(SrvDev d, SlotDev s) {
+    const uint64_t g0 = s.par->g0;
+    const uint32_t m = s.par->m;
     const uint32_t cap_dd = *d.t_dd.cap_dev, cap_b = *d.t_b.cap_dev, cap_ep = *d.t_ep.cap_dev;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
         const uint64_t g = g0 + q;
@@ -239,9 +260,9 @@ __device__ __forceinline__ bool complex_group(const SrvDev& d, uint32_t cid) {
 
 // Duplicate transfers, and the first reception of each group at each
 // endpoint in this batch closes the round trips waiting for it.
-__global__ void srv_dd_resolve(SrvDev d, SlotDev s, uint64_t g0, uint32_t m, uint32_t cap,
-                               uint64_t max_events) {
-    const uint32_t cap_pend = *d.t_pend.cap_dev;
+__global__ void srv_dd_resolve(SrvDev d, SlotDev s, uint32_t cap, uint64_t max_events) {
+    const uint64_t g0 = s.par->g0;
+    const uint32_t m = s.par->m, cap_pend = *d.t_pend.cap_dev;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
         if (s.sdd[q] == NONE32) continue;
         const uint64_t g = g0 + q;
@@ -262,7 +283,8 @@ __global__ void srv_dd_resolve(SrvDev d, SlotDev s, uint64_t g0, uint32_t m, uin
 }
 
 // Sort keys: content id of each transfer, value = batch position.
-__global__ void srv_sort_keys(SrvDev d, SlotDev s, uint64_t g0) {
+__global__ void srv_sort_keys(SrvDev d, SlotDev s) {
+    const uint64_t g0 = s.par->g0;
     const uint32_t nx = *s.nx;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nx; j += gridDim.x * blockDim.x) {
         const uint32_t q = s.xpos[j];
@@ -274,7 +296,8 @@ __global__ void srv_sort_keys(SrvDev d, SlotDev s, uint64_t g0) {
 // In-batch round trips on the content-sorted transfers: the partner of a
 // transfer is the first event of the next destination run of its group;
 // transfers without one wait in the group's list for their source.
-__global__ void srv_rt_batch(SrvDev d, SlotDev s, uint64_t g0, uint32_t cap) {
+__global__ void srv_rt_batch(SrvDev d, SlotDev s, uint32_t cap) {
+    const uint64_t g0 = s.par->g0;
     const uint32_t nx = *s.nx;
     const uint32_t cap_pend = *d.t_pend.cap_dev;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nx; r += gridDim.x * blockDim.x) {
@@ -299,7 +322,9 @@ __global__ void srv_rt_batch(SrvDev d, SlotDev s, uint64_t g0, uint32_t cap) {
 
 // Alloc/delete events of the batch keyed by their <device address, device>
 // slot (other events sort last); value = batch position.
-__global__ void srv_pair_keys(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
+__global__ void srv_pair_keys(SrvDev d, SlotDev s) {
+    const uint64_t g0 = s.par->g0;
+    const uint32_t m = s.par->m;
     const uint32_t cap = *d.t_pair.cap_dev, none_key = d.t_pair.cap_max + 1;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
         const odp_event& e = d.log[g0 + q];
@@ -316,7 +341,9 @@ __global__ void srv_pair_keys(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
 // One thread per address group of the batch (sorted, batch order inside)
 // walks it: ALLOC pushes on the address's open-alloc stack, DELETE pops the
 // nearest open ALLOC and records the pair.  Kernels of the batch are listed.
-__global__ void srv_pair_walk(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
+__global__ void srv_pair_walk(SrvDev d, SlotDev s) {
+    const uint64_t g0 = s.par->g0;
+    const uint32_t m = s.par->m;
     const uint32_t none_key = d.t_pair.cap_max + 1;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
         if (d.log[g0 + r].kind == ODP_KERNEL) s.bk[atomicAdd(&s.cnt[1], 1u)] = (uint32_t)(g0 + r);
@@ -376,8 +403,9 @@ __device__ __forceinline__ bool batch_kernel_overlaps(const SrvDev& d, const Slo
 // and for the waiting pairs (against the batch's kernels); undecided pairs
 // whose delete ends before t_next (the start of every later event) are
 // unused, the rest wait in list `nxt`.
-__global__ void srv_ua(SrvDev d, SlotDev s, uint32_t cap, uint64_t t_next, int cur) {
-    const int nxt = cur ^ 1;
+__global__ void srv_ua(SrvDev d, SlotDev s, uint32_t cap) {
+    const uint64_t t_next = s.par->t_next;
+    const uint32_t cur = *d.cur, nxt = cur ^ 1;
     const uint32_t n_new = s.cnt[0], n_old = min(d.npend[cur], d.pend_cap);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_new + n_old;
          i += gridDim.x * blockDim.x) {
@@ -404,7 +432,9 @@ __global__ void srv_ua(SrvDev d, SlotDev s, uint32_t cap, uint64_t t_next, int c
     }
 }
 
+// Also flips the current waiting lists: the last kernel of a batch to read them.
 __global__ void srv_kmax(SrvDev d, SlotDev s) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d.cur ^= 1u;
     const uint32_t nk = s.cnt[1];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += gridDim.x * blockDim.x) {
         const odp_event& k = d.log[s.bk[i]];
@@ -416,7 +446,9 @@ __global__ void srv_kmax(SrvDev d, SlotDev s) {
 // To-device transfers of the batch: barriers drop out; a waiting transfer
 // gets its segment and is keyed by its <host address, device> slot (others
 // sort last).
-__global__ void srv_ut_keys(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
+__global__ void srv_ut_keys(SrvDev d, SlotDev s) {
+    const uint64_t g0 = s.par->g0;
+    const uint32_t m = s.par->m;
     const uint32_t cap = *d.t_ut.cap_dev, none_key = d.t_ut.cap_max + 1, nk = s.cnt[1];
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
         const uint32_t g = (uint32_t)(g0 + q);
@@ -441,7 +473,9 @@ __global__ void srv_ut_keys(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
 // transfer that follows the key's latest waiting transfer in the same
 // segment records an overwrite (into s.pa/s.pd, count s.cnt[2]); every
 // waiting transfer is listed (s.rslot, count s.cnt[3]).
-__global__ void srv_ut_walk(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
+__global__ void srv_ut_walk(SrvDev d, SlotDev s) {
+    const uint64_t g0 = s.par->g0;
+    const uint32_t m = s.par->m;
     const uint32_t none_key = d.t_ut.cap_max + 1;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
         const uint32_t k = s.skeys[r];
@@ -466,8 +500,8 @@ __global__ void srv_ut_walk(SrvDev d, SlotDev s, uint64_t g0, uint32_t m) {
 // closes is reported if the later transfer starts before that kernel (else
 // it is a barrier); transfers whose segment stays open carry over to list
 // cur ^ 1.
-__global__ void srv_ut_resolve(SrvDev d, SlotDev s, uint32_t cap, int cur) {
-    const int nxt = cur ^ 1;
+__global__ void srv_ut_resolve(SrvDev d, SlotDev s, uint32_t cap) {
+    const uint32_t cur = *d.cur, nxt = cur ^ 1;
     const uint32_t nk = s.cnt[1];
     const uint32_t n_f = min(d.nut[cur], d.pend_cap), n_fb = s.cnt[2];
     const uint32_t n_o = min(d.nut[2 + cur], d.pend_cap), n_ob = s.cnt[3];
@@ -503,7 +537,8 @@ __global__ void srv_ut_resolve(SrvDev d, SlotDev s, uint32_t cap, int cur) {
 // trace); every allocation still open is checked against all kernels seen,
 // with the end of the trace as its delete end; every to-device transfer still
 // waiting for a kernel comes after the last one.
-__global__ void srv_flush(SrvDev d, SlotDev s, uint32_t cap, int cur, uint64_t max_events) {
+__global__ void srv_flush(SrvDev d, SlotDev s, uint32_t cap, uint64_t max_events) {
+    const uint32_t cur = *d.cur;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t n_old = min(d.npend[cur], d.pend_cap);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_old; i += stride) {
@@ -530,6 +565,32 @@ __global__ void srv_flush(SrvDev d, SlotDev s, uint32_t cap, int cur, uint64_t m
 
 __global__ void srv_zero(uint32_t* p) { *p = 0; }
 
+// First step of a batch: append its events to the log; reset the batch's
+// counters and the counts of the next waiting lists.
+__global__ void srv_append(SrvDev d, SlotDev s) {
+    const uint32_t m = s.par->m;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *s.nfind = 0;
+        s.cnt[0] = s.cnt[1] = s.cnt[2] = s.cnt[3] = 0;
+        const uint32_t nxt = *d.cur ^ 1u;
+        d.npend[nxt] = 0;
+        d.nut[nxt] = 0;
+        d.nut[2 + nxt] = 0;
+    }
+    const uint4* src = reinterpret_cast<const uint4*>(s.ev);
+    uint4* dst = reinterpret_cast<uint4*>(d.log + s.par->g0);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * m; i += gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// After the flush: the current waiting lists are empty.
+__global__ void srv_flush_reset(SrvDev d) {
+    const uint32_t cur = *d.cur;
+    d.npend[cur] = 0;
+    d.nut[cur] = 0;
+    d.nut[2 + cur] = 0;
+}
+
 struct Pending {
     odp_event ev;
     const void* payload;
@@ -537,11 +598,18 @@ struct Pending {
     uint64_t seq;
 };
 
+// One submitting thread.  Its own mutex guards its state, so threads do not
+// contend with each other; the batcher takes each producer's lock briefly.
 struct Producer {
+    std::mutex mu;
     std::deque<Pending> q;
     uint64_t last_t = 0;
     uint64_t last_seen = 0;
     uint64_t seq = 0;
+    // Threads that open their events with odp_server_begin hold the merge
+    // back only while events are open (at the earliest open start time).
+    bool announces = false;
+    std::multiset<uint64_t> open;  // start times of events begun, not yet submitted
 };
 
 struct Slot {
@@ -551,15 +619,18 @@ struct Slot {
     uint64_t* h_sizes = nullptr;
     uint32_t* h_xpos = nullptr;
     uint32_t* h_fpos = nullptr;
-    uint32_t* h_nx = nullptr;
+    BatchPar* h_par = nullptr;
     odp_finding* h_find = nullptr;
     uint64_t* h_complete = nullptr;
     uint32_t* h_nfind = nullptr;
+    uint32_t eager = 0;  // findings copied back with the batch
     cudaStream_t fp_stream = nullptr;
     cudaEvent_t fp_done = nullptr, an_done = nullptr;
+    cudaGraphExec_t an_graph = nullptr;  // the batch analysis (enqueue_analysis)
     bool busy = false;
     uint64_t g0 = 0;
     uint32_t m = 0;
+    uint64_t t_launch = 0;  // when the batch was formed and launched
 };
 
 }  // namespace
@@ -568,14 +639,19 @@ struct Slot {
 struct odp_server {
     odp_server_cfg cfg;
     std::mutex mu;
-    std::map<std::thread::id, uint32_t> producer_of;
-    std::vector<odp::Producer> producers;
+    uint64_t serial = 0;                        // unique per server (thread-local caches)
+    std::map<uint64_t, uint32_t> producer_of;  // thread serial -> producer (mu)
+    std::unique_ptr<odp::Producer[]> producers;  // max_producers of them
+    std::atomic<uint32_t> n_producers{0};
+    std::vector<std::deque<odp::Pending>> staged;  // batcher: released, not yet merged
     std::thread batcher;
     std::atomic<bool> stop{false};
     std::atomic<bool> flushing{false};
     std::condition_variable cv_done;
-    uint64_t submitted = 0;
-    uint64_t released_t = 0;
+    std::atomic<uint64_t> submitted{0};
+    std::atomic<uint64_t> first_submit{0};
+    std::atomic<uint64_t> late{0};  // events behind the released watermark
+    uint64_t released_t = 0;        // batcher thread
     // device
     odp::SrvDev d;
     std::vector<void*> dev_blocks;
@@ -592,10 +668,11 @@ struct odp_server {
     std::deque<uint32_t> ready_prod;
     std::deque<odp_finding> outq;
     std::vector<uint64_t> latencies;
-    uint64_t batches = 0, streamed = 0, late = 0, first_submit = 0, last_done = 0;
+    std::vector<uint64_t> queue_lat;  // submit -> launch of the reporting batch
+    uint64_t batches = 0, streamed = 0, last_done = 0;
+    uint64_t find_overflow = 0;  // findings past a batch's (or the flush's) capacity
     std::mutex an_mu;             // orders work enqueued on the analysis stream
-    int pend_cur = 0;             // which waiting-pair list is current (an_mu)
-    uint64_t t_released_max = 0;  // largest start time launched so far (an_mu)
+    uint64_t t_released_max = 0;  // largest start time launched so far (batcher thread)
     odp::SlotDev fl;              // flush-time finding buffers (find, complete, nfind)
     odp_finding* h_fl_find = nullptr;
     uint32_t* h_fl_n = nullptr;
@@ -629,11 +706,65 @@ int make_table(odp_server* s, Table& t, uint32_t cap, uint32_t* cap_dev, cudaStr
     return ODP_OK;
 }
 
+// The analysis of one batch on stream `as`, in batch order: Alg. 1 and 2,
+// pairs, Alg. 3 and 4, Alg. 5.  Captured once per slot into a CUDA graph;
+// every value that changes between batches is read from the slot's
+// parameter block, so one graph launch replays the whole sequence.
+void enqueue_analysis(odp_server* S, Slot& sl, cudaStream_t as) {
+    const uint32_t B = S->cfg.max_batch_events;
+    const int grid = (int)std::min<uint32_t>(1024, (B + 255) / 256);
+    const uint32_t* m_dev = &sl.d.par->m;
+    srv_append<<<grid, 256, 0, as>>>(S->d, sl.d);
+    prim::table_clear<<<64, 256, 0, as>>>(S->d.t_b, m_dev, B);
+    srv_insert_fp<<<grid, 256, 0, as>>>(S->d, sl.d);
+    srv_insert_dd<<<grid, 256, 0, as>>>(S->d, sl.d);
+    srv_dd_resolve<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap, S->cfg.max_events);
+    srv_sort_keys<<<grid, 256, 0, as>>>(S->d, sl.d);
+    prim::radix_sort(sl.d.skeys, sl.d.svals, sl.d.nx, B, prim::bit_length(S->cfg.max_events),
+                     sl.d.sort, as);
+    srv_rt_batch<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap);
+    srv_pair_keys<<<grid, 256, 0, as>>>(S->d, sl.d);
+    prim::radix_sort(sl.d.skeys, sl.d.svals, m_dev, B, prim::bit_length(S->d.t_pair.cap_max + 1),
+                     sl.d.sort, as);
+    srv_pair_walk<<<grid, 256, 0, as>>>(S->d, sl.d);
+    srv_ra_insert<<<grid, 256, 0, as>>>(S->d, sl.d);
+    srv_ra_emit<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap);
+    srv_ua<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap);
+    srv_ut_keys<<<grid, 256, 0, as>>>(S->d, sl.d);
+    prim::radix_sort(sl.d.skeys, sl.d.svals, m_dev, B, prim::bit_length(S->d.t_ut.cap_max + 1),
+                     sl.d.sort, as);
+    srv_ut_walk<<<grid, 256, 0, as>>>(S->d, sl.d);
+    srv_ut_resolve<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap);
+    srv_kmax<<<grid, 256, 0, as>>>(S->d, sl.d);
+}
+
+int capture_analysis(odp_server* S, Slot& sl) {
+    prim::sort_small_ready();  // sets a kernel attribute: outside the capture
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return ODP_ERR_CUDA;
+    int rc = ODP_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        rc = ODP_ERR_CUDA;
+    } else {
+        enqueue_analysis(S, sl, cs);
+        if (cudaStreamEndCapture(cs, &g) != cudaSuccess ||
+            cudaGraphInstantiate(&sl.an_graph, g, 0) != cudaSuccess)
+            rc = ODP_ERR_CUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (rc) cudaGetLastError();
+    return rc;
+}
+
 void launch_batch(odp_server* S, Slot& sl) {
     const uint32_t m = sl.m;
     cudaStream_t fs = sl.fp_stream, as = S->an_stream;
     uint32_t nx = 0, nf = 0;  // transfers; those whose payload the server fingerprints
+    uint64_t t_next = S->t_released_max;
     for (uint32_t q = 0; q < m; ++q) {
+        t_next = std::max(t_next, sl.h_ev[q].t_start_ns);
         const uint8_t k = sl.h_ev[q].kind;
         if (k != ODP_TO_DEV && k != ODP_FROM_DEV && k != ODP_DEV_TO_DEV) continue;
         sl.h_xpos[nx++] = q;
@@ -642,14 +773,14 @@ void launch_batch(odp_server* S, Slot& sl) {
             sl.h_fpos[nf++] = q;
         }
     }
-    sl.h_nx[0] = nx;
-    sl.h_nx[1] = nf;
+    S->t_released_max = t_next;
+    *sl.h_par = BatchPar{nx, nf, m, 0, sl.g0, t_next};
     cudaMemcpyAsync(sl.d.ev, sl.h_ev, sizeof(odp_event) * m, cudaMemcpyHostToDevice, fs);
     cudaMemcpyAsync(sl.d.ptrs, sl.h_ptrs, sizeof(void*) * nf, cudaMemcpyHostToDevice, fs);
     cudaMemcpyAsync(sl.d.sizes, sl.h_sizes, 8ull * nf, cudaMemcpyHostToDevice, fs);
     cudaMemcpyAsync(sl.d.xpos, sl.h_xpos, 4ull * nx, cudaMemcpyHostToDevice, fs);
     cudaMemcpyAsync(sl.d.fpos, sl.h_fpos, 4ull * nf, cudaMemcpyHostToDevice, fs);
-    cudaMemcpyAsync(sl.d.nx, sl.h_nx, 8, cudaMemcpyHostToDevice, fs);
+    cudaMemcpyAsync(sl.d.par, sl.h_par, sizeof(BatchPar), cudaMemcpyHostToDevice, fs);
     if (nf) {
         FpLaunch L = fp_schedule_for(nf);
         if (fp_run((const void* const*)sl.d.ptrs, sl.d.sizes, nf, sl.d.fp, fs, L) != ODP_OK)
@@ -661,91 +792,95 @@ void launch_batch(odp_server* S, Slot& sl) {
     // analysis, in batch order on one stream
     std::lock_guard<std::mutex> an_lk(S->an_mu);
     cudaStreamWaitEvent(as, sl.fp_done, 0);
-    const uint64_t g0 = sl.g0;
-    cudaMemcpyAsync(S->d.log + g0, sl.d.ev, sizeof(odp_event) * m, cudaMemcpyDeviceToDevice, as);
-    srv_zero<<<1, 1, 0, as>>>(sl.d.nfind);
-    const int grid = (int)std::min<uint32_t>(1024, (m + 255) / 256);
-    prim::table_clear<<<64, 256, 0, as>>>(S->d.t_b, nullptr, m);
-    srv_insert_fp<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
-    srv_insert_dd<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
-    srv_dd_resolve<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m, S->find_cap, S->cfg.max_events);
-    srv_sort_keys<<<grid, 256, 0, as>>>(S->d, sl.d, g0);
-    prim::radix_sort(sl.d.skeys, sl.d.svals, sl.d.nx, S->cfg.max_batch_events,
-                     prim::bit_length(S->cfg.max_events), sl.d.sort, as);
-    srv_rt_batch<<<grid, 256, 0, as>>>(S->d, sl.d, g0, S->find_cap);
-    // pairs, Alg. 3, Alg. 4
-    uint64_t t_next = S->t_released_max;
-    for (uint32_t q = 0; q < m; ++q) t_next = std::max(t_next, sl.h_ev[q].t_start_ns);
-    S->t_released_max = t_next;
-    cudaMemsetAsync(sl.d.cnt, 0, 16, as);
-    srv_pair_keys<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
-    prim::radix_sort(sl.d.skeys, sl.d.svals, nullptr, m, prim::bit_length(S->d.t_pair.cap_max + 1),
-                     sl.d.sort, as);
-    srv_pair_walk<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
-    srv_ra_insert<<<grid, 256, 0, as>>>(S->d, sl.d);
-    srv_ra_emit<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap);
-    const int cur = S->pend_cur;
-    srv_zero<<<1, 1, 0, as>>>(S->d.npend + (cur ^ 1));
-    srv_ua<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap, t_next, cur);
-    // Alg. 5
-    srv_ut_keys<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
-    prim::radix_sort(sl.d.skeys, sl.d.svals, nullptr, m, prim::bit_length(S->d.t_ut.cap_max + 1),
-                     sl.d.sort, as);
-    srv_ut_walk<<<grid, 256, 0, as>>>(S->d, sl.d, g0, m);
-    cudaMemsetAsync(S->d.nut + (cur ^ 1), 0, 4, as);
-    cudaMemsetAsync(S->d.nut + 2 + (cur ^ 1), 0, 4, as);
-    srv_ut_resolve<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap, cur);
-    srv_kmax<<<grid, 256, 0, as>>>(S->d, sl.d);
-    S->pend_cur = cur ^ 1;
+    if (cudaGraphLaunch(sl.an_graph, as) != cudaSuccess) S->error = ODP_ERR_CUDA;
+    // copy back the count and the findings a batch of m events usually has
+    // at most; harvest fetches the rest when there are more
+    sl.eager = (uint32_t)std::min<uint64_t>(S->find_cap, 2ull * m + 256);
     cudaMemcpyAsync(sl.h_nfind, sl.d.nfind, 4, cudaMemcpyDeviceToHost, as);
-    cudaMemcpyAsync(sl.h_find, sl.d.find, sizeof(odp_finding) * S->find_cap,
-                    cudaMemcpyDeviceToHost, as);
-    cudaMemcpyAsync(sl.h_complete, sl.d.complete, 8ull * S->find_cap, cudaMemcpyDeviceToHost, as);
+    cudaMemcpyAsync(sl.h_find, sl.d.find, sizeof(odp_finding) * sl.eager, cudaMemcpyDeviceToHost, as);
+    cudaMemcpyAsync(sl.h_complete, sl.d.complete, 8ull * sl.eager, cudaMemcpyDeviceToHost, as);
     cudaEventRecord(sl.an_done, as);
     if (cudaGetLastError() != cudaSuccess) S->error = ODP_ERR_CUDA;
 }
 
-// Moves releasable events into the ready queue in merged order (mu held).
-void release_locked(odp_server* S, uint64_t now) {
-    uint64_t wm = ~0ull;
+// Moves releasable events into the ready queue in merged order (batcher
+// thread).  The watermark is the smallest bound any producer puts on its
+// future events; each bound is read under that producer's lock.  `now` is
+// read before any of those locks, so an announcing producer with nothing
+// open begins its next event (under its lock) at or after it.
+void release(odp_server* S) {
+    const uint64_t now = now_ns();
     const bool all = S->flushing.load();
     const uint64_t timeout = (uint64_t)S->cfg.watermark_timeout_us * 1000ull;
+    const uint32_t np = S->n_producers.load(std::memory_order_acquire);
+    uint64_t wm = ~0ull;
     if (!all) {
-        for (auto& p : S->producers) {
-            if (now - p.last_seen > timeout && p.q.empty()) continue;  // silent producer
-            wm = std::min(wm, p.last_t);
+        for (uint32_t i = 0; i < np; ++i) {
+            Producer& p = S->producers[i];
+            std::lock_guard<std::mutex> lk(p.mu);
+            if (now > p.last_seen + timeout && p.q.empty()) continue;  // silent producer
+            if (!p.announces) {
+                wm = std::min(wm, p.last_t);
+                continue;
+            }
+            // an event open longer than the timeout was abandoned
+            while (!p.open.empty() && *p.open.begin() + timeout < now) p.open.erase(p.open.begin());
+            wm = std::min(wm, p.open.empty() ? now : *p.open.begin());
         }
     }
-    // k-way merge of the queue prefixes with t_start <= wm
-    while (true) {
+    // take the queue prefixes with t_start <= wm, then merge them
+    bool any = false;
+    for (uint32_t i = 0; i < np; ++i) {
+        Producer& p = S->producers[i];
+        std::lock_guard<std::mutex> lk(p.mu);
+        while (!p.q.empty() && p.q.front().ev.t_start_ns <= wm) {
+            S->staged[i].push_back(p.q.front());
+            p.q.pop_front();
+            any = true;
+        }
+    }
+    while (any) {
         int best = -1;
         uint64_t bt = 0;
-        for (size_t i = 0; i < S->producers.size(); ++i) {
-            auto& q = S->producers[i].q;
-            if (q.empty() || q.front().ev.t_start_ns > wm) continue;
+        for (uint32_t i = 0; i < np; ++i) {
+            const auto& q = S->staged[i];
+            if (q.empty()) continue;
             if (best < 0 || q.front().ev.t_start_ns < bt) {
                 best = (int)i;
                 bt = q.front().ev.t_start_ns;
             }
         }
         if (best < 0) break;
-        Pending p = S->producers[best].q.front();
-        S->producers[best].q.pop_front();
-        if (p.ev.t_start_ns < S->released_t) ++S->late;
+        const Pending& p = S->staged[best].front();
+        if (p.ev.t_start_ns < S->released_t) S->late.fetch_add(1, std::memory_order_relaxed);
         S->released_t = std::max(S->released_t, p.ev.t_start_ns);
         S->ready.push_back(p);
         S->ready_prod.push_back((uint32_t)best);
+        S->staged[best].pop_front();
     }
 }
 
 void harvest(odp_server* S, Slot& sl) {
-    const uint64_t t = now_ns();
     const uint32_t n = std::min(*sl.h_nfind, S->find_cap);
+    if (n > sl.eager) {  // the slot's streams are idle until it is released
+        const uint32_t e = sl.eager;
+        cudaMemcpyAsync(sl.h_find + e, sl.d.find + e, sizeof(odp_finding) * (n - e),
+                        cudaMemcpyDeviceToHost, sl.fp_stream);
+        cudaMemcpyAsync(sl.h_complete + e, sl.d.complete + e, 8ull * (n - e),
+                        cudaMemcpyDeviceToHost, sl.fp_stream);
+        if (cudaStreamSynchronize(sl.fp_stream) != cudaSuccess) S->error = ODP_ERR_CUDA;
+    }
+    const uint64_t t = now_ns();
     std::lock_guard<std::mutex> lk(S->mu);
+    S->find_overflow += *sl.h_nfind - n;
     for (uint32_t j = 0; j < n; ++j) {
         S->outq.push_back(sl.h_find[j]);
         const uint64_t c = sl.h_complete[j];
-        if (c < S->submit_ns.size()) S->latencies.push_back(t - S->submit_ns[c]);
+        if (c < S->submit_ns.size()) {
+            const uint64_t t0 = S->submit_ns[c];
+            S->latencies.push_back(t - t0);
+            S->queue_lat.push_back(sl.t_launch > t0 ? sl.t_launch - t0 : 0);
+        }
     }
     S->streamed += n;
     S->n_done += sl.m;
@@ -766,9 +901,9 @@ void batcher_main(odp_server* S) {
                 idle = false;
             }
         }
+        release(S);
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            release_locked(S, now_ns());
             for (auto& sl : S->slots) {
                 if (S->ready.empty()) break;
                 if (sl.busy) continue;
@@ -791,6 +926,7 @@ void batcher_main(odp_server* S) {
                     S->ready_prod.pop_front();
                 }
                 sl.busy = true;
+                sl.t_launch = now_ns();
                 lk.unlock();
                 launch_batch(S, sl);
                 lk.lock();
@@ -800,7 +936,11 @@ void batcher_main(odp_server* S) {
                 bool any = false;
                 for (auto& sl : S->slots) any |= sl.busy;
                 bool queued = false;
-                for (auto& p : S->producers) queued |= !p.q.empty();
+                const uint32_t np = S->n_producers.load(std::memory_order_acquire);
+                for (uint32_t i = 0; i < np; ++i) {
+                    std::lock_guard<std::mutex> plk(S->producers[i].mu);
+                    queued |= !S->producers[i].q.empty();
+                }
                 if (!any && !queued) break;
             }
         }
@@ -832,8 +972,12 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
                           40ull * pend_cap + ((uint64_t)cfg->n_slots + 1) * slot_bytes;
     if (cfg->device_budget_bytes && need > cfg->device_budget_bytes) return ODP_ERR_OOM;
 
+    static std::atomic<uint64_t> next_server{1};
     odp_server* S = new odp_server();
     S->cfg = *cfg;
+    S->serial = next_server.fetch_add(1);
+    S->producers.reset(new odp::Producer[cfg->max_producers]);
+    S->staged.resize(cfg->max_producers);
     S->find_cap = (uint32_t)find_cap;
     auto fail = [&](int rc) {
         odp_server_destroy(S);
@@ -866,6 +1010,7 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     if (!rc) rc = alloc_dev(S, (void**)&S->d.utopen[0], 4ull * pend_cap);
     if (!rc) rc = alloc_dev(S, (void**)&S->d.utopen[1], 4ull * pend_cap);
     if (!rc) rc = alloc_dev(S, (void**)&S->d.nut, 32);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.cur, 16);
     if (!rc) rc = alloc_dev(S, (void**)&S->fl.find, sizeof(odp_finding) * find_cap);
     if (!rc) rc = alloc_dev(S, (void**)&S->fl.complete, 8 * find_cap);
     if (!rc) rc = alloc_dev(S, (void**)&S->fl.nfind, 16);
@@ -874,6 +1019,7 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     cudaMemsetAsync(S->d.npend, 0, 16, S->an_stream);
     cudaMemsetAsync(S->d.kcnt, 0, 4 * SRV_NDEV, S->an_stream);
     cudaMemsetAsync(S->d.nut, 0, 32, S->an_stream);
+    cudaMemsetAsync(S->d.cur, 0, 16, S->an_stream);
     if (cudaHostAlloc((void**)&S->h_fl_find, sizeof(odp_finding) * find_cap, 0) != cudaSuccess ||
         cudaHostAlloc((void**)&S->h_fl_n, 16, 0) != cudaSuccess)
         return fail(ODP_ERR_OOM);
@@ -886,8 +1032,11 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
         if (!rc) rc = alloc_dev(S, (void**)&d.fp, 16 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.xpos, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.fpos, 4 * B);
-        if (!rc) rc = alloc_dev(S, (void**)&d.nx, 16);
-        if (!rc) d.sort.hlen = d.nx + 2;  // words 2-3 of the 16-byte count block
+        if (!rc) rc = alloc_dev(S, (void**)&d.par, sizeof(BatchPar));
+        if (!rc) {
+            d.nx = &d.par->nx;
+            d.sort.hlen = &d.par->hlen;
+        }
         if (!rc) rc = alloc_dev(S, (void**)&d.sfp, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.sdd, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.sb, 4 * B);
@@ -915,7 +1064,7 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
             cudaHostAlloc((void**)&sl.h_sizes, 8 * B, 0) != cudaSuccess ||
             cudaHostAlloc((void**)&sl.h_xpos, 4 * B, 0) != cudaSuccess ||
             cudaHostAlloc((void**)&sl.h_fpos, 4 * B, 0) != cudaSuccess ||
-            cudaHostAlloc((void**)&sl.h_nx, 16, 0) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.h_par, sizeof(BatchPar), 0) != cudaSuccess ||
             cudaHostAlloc((void**)&sl.h_find, sizeof(odp_finding) * find_cap, 0) != cudaSuccess ||
             cudaHostAlloc((void**)&sl.h_complete, 8 * find_cap, 0) != cudaSuccess ||
             cudaHostAlloc((void**)&sl.h_nfind, 16, 0) != cudaSuccess)
@@ -924,9 +1073,12 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
             cudaEventCreateWithFlags(&sl.fp_done, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.an_done, cudaEventDisableTiming) != cudaSuccess)
             return fail(ODP_ERR_CUDA);
+        if ((rc = capture_analysis(S, sl)) != ODP_OK) return fail(rc);
     }
     if (cudaStreamSynchronize(S->an_stream) != cudaSuccess) return fail(ODP_ERR_CUDA);
     S->submit_ns.assign(E, 0);
+    S->latencies.reserve(E);  // no reallocation (under mu) while serving
+    S->queue_lat.reserve(E);
     S->origin_prod.assign(E, 0);
     S->origin_seq.assign(E, 0);
     S->batcher = std::thread(odp::batcher_main, S);
@@ -935,31 +1087,73 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
 }
 
 namespace {
-// Index of the calling thread's producer, registering it if needed (mu held).
-int producer_index_locked(odp_server* S, uint32_t* p) {
-    auto id = std::this_thread::get_id();
-    auto it = S->producer_of.find(id);
-    if (it != S->producer_of.end()) {
-        *p = it->second;
+// The calling thread's producer, registering it if needed.  A thread's id
+// can be reused by a later thread once it has exited; the serial in its
+// thread-local storage cannot, so a new thread never inherits an old
+// producer's state.  The last server seen is cached per thread.
+int producer_of_thread(odp_server* S, odp::Producer** out) {
+    static std::atomic<uint64_t> next_serial{1};
+    thread_local const uint64_t id = next_serial.fetch_add(1);
+    thread_local uint64_t cached_server = 0;
+    thread_local odp::Producer* cached = nullptr;
+    if (cached_server == S->serial) {
+        *out = cached;
         return ODP_OK;
     }
-    if (S->producers.size() >= S->cfg.max_producers) return ODP_ERR_UNSUPPORTED;
-    *p = (uint32_t)S->producers.size();
-    S->producer_of[id] = *p;
-    S->producers.emplace_back();
+    std::lock_guard<std::mutex> lk(S->mu);
+    uint32_t p;
+    auto it = S->producer_of.find(id);
+    if (it != S->producer_of.end()) {
+        p = it->second;
+    } else {
+        p = S->n_producers.load(std::memory_order_relaxed);
+        if (p >= S->cfg.max_producers) return ODP_ERR_UNSUPPORTED;
+        S->producer_of[id] = p;
+        S->n_producers.store(p + 1, std::memory_order_release);
+    }
+    cached_server = S->serial;
+    cached = &S->producers[p];
+    *out = cached;
     return ODP_OK;
 }
 }  // namespace
 
 int odp_server_attach(odp_server* S, uint64_t start_t_ns) {
     if (!S) return ODP_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(S->mu);
-    uint32_t p;
-    int rc = producer_index_locked(S, &p);
+    odp::Producer* pr;
+    int rc = producer_of_thread(S, &pr);
     if (rc) return rc;
-    odp::Producer& pr = S->producers[p];
-    pr.last_t = std::max(pr.last_t, start_t_ns);
-    pr.last_seen = odp::now_ns();
+    std::lock_guard<std::mutex> lk(pr->mu);
+    pr->last_t = std::max(pr->last_t, start_t_ns);
+    pr->last_seen = odp::now_ns();
+    return ODP_OK;
+}
+
+int odp_server_begin(odp_server* S, uint64_t* t_start_ns) {
+    if (!S || !t_start_ns) return ODP_ERR_INVALID_ARG;
+    odp::Producer* pr;
+    int rc = producer_of_thread(S, &pr);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(pr->mu);
+    const uint64_t now = odp::now_ns();
+    const uint64_t t = std::max(now, pr->last_t);
+    pr->open.insert(t);
+    pr->announces = true;
+    pr->last_seen = now;
+    *t_start_ns = t;
+    return ODP_OK;
+}
+
+int odp_server_cancel(odp_server* S, uint64_t t_start_ns) {
+    if (!S) return ODP_ERR_INVALID_ARG;
+    odp::Producer* pr;
+    int rc = producer_of_thread(S, &pr);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(pr->mu);
+    auto it = pr->open.find(t_start_ns);
+    if (it == pr->open.end()) return ODP_ERR_INVALID_ARG;
+    pr->open.erase(it);
+    pr->last_seen = odp::now_ns();
     return ODP_OK;
 }
 
@@ -968,24 +1162,30 @@ int odp_server_submit(odp_server* S, const odp_event* ev, const void* const* pay
     if (!S || (n && (!ev || !payloads))) return ODP_ERR_INVALID_ARG;
     if (n == 0) return ODP_OK;
     const uint64_t t = odp::now_ns();
-    std::lock_guard<std::mutex> lk(S->mu);
-    if (S->submitted + n > S->cfg.max_events) return ODP_ERR_UNSUPPORTED;
-    uint32_t p;
-    int rc = producer_index_locked(S, &p);
+    odp::Producer* pr;
+    int rc = producer_of_thread(S, &pr);
     if (rc) return rc;
-    odp::Producer& pr = S->producers[p];
-    if (!S->first_submit) S->first_submit = t;
+    // reserve log capacity
+    uint64_t cur = S->submitted.load();
+    do {
+        if (cur + n > S->cfg.max_events) return ODP_ERR_UNSUPPORTED;
+    } while (!S->submitted.compare_exchange_weak(cur, cur + n));
+    uint64_t zero = 0;
+    S->first_submit.compare_exchange_strong(zero, t);
+    std::lock_guard<std::mutex> lk(pr->mu);
     for (uint64_t i = 0; i < n; ++i) {
         odp::Pending q;
         q.ev = ev[i];
         q.payload = payloads[i];
         q.submit_ns = t;
-        q.seq = pr.seq++;
-        pr.last_t = std::max(pr.last_t, ev[i].t_start_ns);
-        pr.q.push_back(q);
+        q.seq = pr->seq++;
+        pr->last_t = std::max(pr->last_t, ev[i].t_start_ns);
+        pr->q.push_back(q);
+        // closes the latest open event that starts no later than this one
+        auto it = pr->open.upper_bound(ev[i].t_start_ns);
+        if (it != pr->open.begin()) pr->open.erase(std::prev(it));
     }
-    pr.last_seen = t;
-    S->submitted += n;
+    pr->last_seen = t;
     return ODP_OK;
 }
 
@@ -1021,19 +1221,18 @@ int odp_server_flush(odp_server* S) {
         cudaSetDevice(S->cfg.device);
         cudaStream_t as = S->an_stream;
         odp::srv_zero<<<1, 1, 0, as>>>(S->fl.nfind);
-        odp::srv_flush<<<256, 256, 0, as>>>(S->d, S->fl, S->find_cap, S->pend_cur,
-                                            S->cfg.max_events);
-        odp::srv_zero<<<1, 1, 0, as>>>(S->d.npend + S->pend_cur);
-        odp::srv_zero<<<1, 1, 0, as>>>(S->d.nut + S->pend_cur);
-        odp::srv_zero<<<1, 1, 0, as>>>(S->d.nut + 2 + S->pend_cur);
+        odp::srv_flush<<<256, 256, 0, as>>>(S->d, S->fl, S->find_cap, S->cfg.max_events);
+        odp::srv_flush_reset<<<1, 1, 0, as>>>(S->d);
         cudaMemcpyAsync(S->h_fl_n, S->fl.nfind, 4, cudaMemcpyDeviceToHost, as);
-        cudaMemcpyAsync(S->h_fl_find, S->fl.find, sizeof(odp_finding) * S->find_cap,
-                        cudaMemcpyDeviceToHost, as);
         if (cudaStreamSynchronize(as) != cudaSuccess) S->error = ODP_ERR_CUDA;
         const uint32_t n = std::min(*S->h_fl_n, S->find_cap);
+        cudaMemcpyAsync(S->h_fl_find, S->fl.find, sizeof(odp_finding) * n, cudaMemcpyDeviceToHost,
+                        as);
+        if (cudaStreamSynchronize(as) != cudaSuccess) S->error = ODP_ERR_CUDA;
         std::lock_guard<std::mutex> lk(S->mu);
         for (uint32_t j = 0; j < n; ++j) S->outq.push_back(S->h_fl_find[j]);
         S->streamed += n;
+        S->find_overflow += *S->h_fl_n - n;
     }
     S->flushing = false;
     return S->error;
@@ -1060,31 +1259,42 @@ int odp_server_origin(odp_server* S, uint32_t* producer, uint64_t* seq, uint64_t
 
 int odp_server_stats_get(odp_server* S, odp_server_stats* st) {
     if (!S || !st) return ODP_ERR_INVALID_ARG;
-    std::vector<uint64_t> lat;
+    std::vector<uint64_t> lat, qlat;
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        st->events_submitted = S->submitted;
+        st->events_submitted = S->submitted.load();
         st->events_processed = S->n_done;
         st->batches = S->batches;
         st->findings_streamed = S->streamed;
-        st->late_events = S->late;
-        st->first_submit_ns = S->first_submit;
+        st->late_events = S->late.load();
+        st->first_submit_ns = S->first_submit.load();
         st->last_done_ns = S->last_done;
         lat = S->latencies;
+        qlat = S->queue_lat;
     }
     std::sort(lat.begin(), lat.end());
-    auto pct = [&](double q) -> uint64_t {
-        if (lat.empty()) return 0;
-        size_t i = (size_t)(q * (double)(lat.size() - 1) + 0.5);
-        return lat[std::min(i, lat.size() - 1)];
+    std::sort(qlat.begin(), qlat.end());
+    auto pct = [](const std::vector<uint64_t>& v, double q) -> uint64_t {
+        if (v.empty()) return 0;
+        size_t i = (size_t)(q * (double)(v.size() - 1) + 0.5);
+        return v[std::min(i, v.size() - 1)];
     };
-    st->latency_p50_ns = pct(0.50);
-    st->latency_p99_ns = pct(0.99);
+    st->latency_p50_ns = pct(lat, 0.50);
+    st->latency_p99_ns = pct(lat, 0.99);
     st->latency_max_ns = lat.empty() ? 0 : lat.back();
-    // groups with more than two endpoints (counted on the device table)
+    st->queue_p50_ns = pct(qlat, 0.50);
+    st->queue_p99_ns = pct(qlat, 0.99);
+    // groups with more than two endpoints (counted on the device table), and
+    // findings or waiting decisions that did not fit
     st->rt_groups_unstreamed = 0;
     {
         std::lock_guard<std::mutex> lk(S->mu);
+        cudaSetDevice(S->cfg.device);
+        uint32_t lost[2] = {0, 0};
+        if (cudaMemcpy(&lost[0], S->d.npend + 2, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(&lost[1], S->d.nut + 4, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return ODP_ERR_CUDA;
+        st->stream_overflow = S->find_overflow + lost[0] + lost[1];
         if (S->n_done > 0 && S->d.t_ep.slots) {
             const uint32_t cap = S->d.t_ep.cap_max;
             std::vector<odp::prim::Slot> v((size_t)cap + 1);
@@ -1113,8 +1323,9 @@ int odp_server_destroy(odp_server* S) {
         }
         if (sl.fp_done) cudaEventDestroy(sl.fp_done);
         if (sl.an_done) cudaEventDestroy(sl.an_done);
+        if (sl.an_graph) cudaGraphExecDestroy(sl.an_graph);
         for (void* h : {(void*)sl.h_ev, (void*)sl.h_ptrs, (void*)sl.h_sizes, (void*)sl.h_xpos,
-                        (void*)sl.h_fpos, (void*)sl.h_nx, (void*)sl.h_find, (void*)sl.h_complete,
+                        (void*)sl.h_fpos, (void*)sl.h_par, (void*)sl.h_find, (void*)sl.h_complete,
                         (void*)sl.h_nfind})
             if (h) cudaFreeHost(h);
     }

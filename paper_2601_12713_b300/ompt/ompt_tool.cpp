@@ -6,7 +6,11 @@
 // fingerprinted on the GPU when its bytes are in device memory (at the end
 // of a transfer to the device, at the end of a transfer from or between
 // devices), synchronously, so later kernels cannot change them first; the
-// event then goes to odp_server_submit with ODP_EVENT_FP_GIVEN.  At the end
+// event then goes to odp_server_submit with ODP_EVENT_FP_GIVEN.  Each event
+// is opened with odp_server_begin at its begin callback (which stamps its
+// start), so the server's merge waits only for threads inside an operation
+// and passes idle ones at once; an event that is not logged after all is
+// cancelled.  At the end
 // of the program the tool flushes the server, runs odp_analyze over the
 // resident log and prints the counts; with ODP_OMPT_OUT=<prefix> it also
 // writes <prefix>.events (the merged 64-byte records) and <prefix>.sites (one
@@ -134,27 +138,60 @@ bool fingerprint_device(const void* p, uint64_t bytes, uint64_t* lo, uint64_t* h
     return true;
 }
 
+// Start time of a new event, opened on the server so that the merge waits
+// for it; every opened event is later submitted or cancelled.
+uint64_t open_event() {
+    uint64_t t = 0;
+    if (g_tool.server && odp_server_begin(g_tool.server, &t) == ODP_OK) return t;
+    return now_ns();
+}
+
+void drop(const odp_event& e) {
+    if (g_tool.server) odp_server_cancel(g_tool.server, e.t_start_ns);
+    g_tool.dropped.fetch_add(1);
+}
+
 void submit(const odp_event& e) {
     const void* payload = nullptr;
-    if (!g_tool.server || odp_server_submit(g_tool.server, &e, &payload, 1) != ODP_OK)
-        g_tool.dropped.fetch_add(1);
+    if (!g_tool.server || odp_server_submit(g_tool.server, &e, &payload, 1) != ODP_OK) drop(e);
 }
 
 uint64_t begin_of(ompt_id_t* host_op_id, int endpoint) {
-    const uint64_t t = now_ns();
-    if (endpoint == OMPT_SCOPE_BEGINEND || !host_op_id) return t;
-    auto& m = t_state.begin_ns;
-    auto it = m.find(*host_op_id);
-    if (it == m.end()) return t;
-    const uint64_t b = it->second;
-    m.erase(it);
-    return b;
+    if (endpoint != OMPT_SCOPE_BEGINEND && host_op_id) {
+        auto& m = t_state.begin_ns;
+        auto it = m.find(*host_op_id);
+        if (it != m.end()) {
+            const uint64_t b = it->second;
+            m.erase(it);
+            return b;
+        }
+    }
+    return open_event();
 }
 
 void on_begin(ompt_id_t* host_op_id) {
     if (!host_op_id) return;
     *host_op_id = g_tool.next_op.fetch_add(1);
-    t_state.begin_ns[*host_op_id] = now_ns();
+    t_state.begin_ns[*host_op_id] = open_event();
+}
+
+// Data operations that become events: allocations, deletes and transfers of
+// a non-empty range with a device on at least one side.
+bool logged_op(int optype, int src_device_num, int dest_device_num, size_t bytes) {
+    switch (optype) {
+        case OP_ALLOC:
+        case OP_ALLOC_ASYNC:
+        case OP_DELETE:
+        case OP_DELETE_ASYNC:
+            return true;
+        case OP_TO_DEVICE:
+        case OP_TO_DEVICE_ASYNC:
+        case OP_FROM_DEVICE:
+        case OP_FROM_DEVICE_ASYNC:
+            return bytes != 0 && (dev_num(src_device_num) >= 0 || dev_num(dest_device_num) >= 0);
+        default:
+            return false;  // associate / disassociate: no data moves
+    }
 }
 
 // target region: the device number rides in target_data for its kernels
@@ -168,6 +205,7 @@ void cb_target_data_op_emi(int endpoint, ompt_data_t* /*target_task_data*/,
                            ompt_data_t* /*target_data*/, ompt_id_t* host_op_id, int optype,
                            void* src_address, int src_device_num, void* dest_address,
                            int dest_device_num, size_t bytes, const void* codeptr_ra) {
+    if (!logged_op(optype, src_device_num, dest_device_num, bytes)) return;
     if (endpoint == OMPT_SCOPE_BEGIN) {
         on_begin(host_op_id);
         return;
@@ -201,23 +239,21 @@ void cb_target_data_op_emi(int endpoint, ompt_data_t* /*target_task_data*/,
             const bool to_dev = optype == OP_TO_DEVICE || optype == OP_TO_DEVICE_ASYNC;
             e.src_dev = dev_num(src_device_num);
             e.dst_dev = dev_num(dest_device_num);
-            if (bytes == 0) return;
             // the bytes in device memory: the destination of a transfer to a
             // device, else the source
             const void* dev_bytes = to_dev || e.src_dev < 0 ? dest_address : src_address;
-            if (e.src_dev < 0 && e.dst_dev < 0) return;  // host to host: not a mapping
             e.kind = e.src_dev < 0 ? ODP_TO_DEV : e.dst_dev < 0 ? ODP_FROM_DEV : ODP_DEV_TO_DEV;
             e.host_addr = (uint64_t)(uintptr_t)(e.kind == ODP_TO_DEV ? src_address : dest_address);
             e.dev_addr = (uint64_t)(uintptr_t)(e.kind == ODP_FROM_DEV ? src_address : dest_address);
             if (!fingerprint_device(dev_bytes, bytes, &e.fp_lo, &e.fp_hi)) {
-                g_tool.dropped.fetch_add(1);
+                drop(e);
                 return;
             }
             e.flags = ODP_EVENT_FP_GIVEN;
             break;
         }
         default:
-            return;  // associate / disassociate: no data moves
+            return;  // not reached: logged_op filtered the other kinds
     }
     submit(e);
 }

@@ -21,7 +21,7 @@ def lib():
                                          ctypes.c_uint64, ctypes.c_uint64]
         so.synth_load_create.restype = ctypes.c_void_p
         so.synth_load_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                      ctypes.c_void_p]
+                                      ctypes.c_void_p, ctypes.c_void_p]
         so.synth_load_run.restype = ctypes.c_int64
         so.synth_load_payload.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
                                           ctypes.POINTER(ctypes.c_uint64),
@@ -44,8 +44,12 @@ class Load:
         self.h = lib().synth_load_create(n_threads, events_per_s, seconds, seed, pool_ptr,
                                          pool_bytes, min_payload, max_payload)
 
-    def run(self, server) -> int:
-        return int(lib().synth_load_run(self.h, server.h, server.submit_fn, server.attach_fn))
+    def run(self, server, announce: bool = True) -> int:
+        """Runs the producers into ``server``.  With ``announce`` each event
+        is opened with the server's begin call, which stamps its start time."""
+        begin = server.begin_fn if announce else None
+        return int(lib().synth_load_run(self.h, server.h, server.submit_fn, server.attach_fn,
+                                        begin))
 
     def payload(self, thread, seq):
         off, size = ctypes.c_uint64(), ctypes.c_uint64()

@@ -30,6 +30,7 @@ enum { ALLOC = 1, TO_DEV = 2, FROM_DEV = 3, DELETE = 5, KERNEL = 6 };
 
 typedef int (*submit_fn)(void* server, const void* events, const void* const* payloads, uint64_t n);
 typedef int (*attach_fn)(void* server, uint64_t start_t_ns);
+typedef int (*begin_fn)(void* server, uint64_t* t_start_ns);
 
 struct Rng {
     uint64_t s, i = 0;
@@ -75,7 +76,7 @@ struct Gen {
 };
 
 void producer(Gen* g, uint32_t k, void* server, submit_fn submit, attach_fn attach,
-              std::atomic<bool>* go, std::atomic<uint32_t>* ready) {
+              begin_fn begin, std::atomic<bool>* go, std::atomic<uint32_t>* ready) {
     const Cfg& c = g->cfg;
     Thread& T = g->th[k];
     Rng r(c.seed ^ (0x5EED0000ull + k) * 0xD1342543DE82EF95ull);
@@ -110,6 +111,15 @@ void producer(Gen* g, uint32_t k, void* server, submit_fn submit, attach_fn atta
             now = now_ns();
         }
         if (now >= t_stop) return false;
+        // with a begin call the server stamps the start (its clock is the
+        // same steady clock)
+        if (begin) {
+            int rc = begin(server, &now);
+            if (rc < 0) {
+                T.rc = rc;
+                return false;
+            }
+        }
         const uint64_t dur = e.t_end_ns;  // duration stashed by the caller
         e.t_start_ns = now;
         e.t_end_ns = now + dur;
@@ -190,14 +200,16 @@ void* synth_load_create(uint32_t n_threads, double events_per_s, double seconds,
 }
 
 // Runs all producer threads to completion; returns the number of events
-// submitted, or a negative submit status.
-int64_t synth_load_run(void* h, void* server, void* submit, void* attach) {
+// submitted, or a negative submit status.  `begin` may be null (events are
+// then stamped with the thread's own clock at submit time).
+int64_t synth_load_run(void* h, void* server, void* submit, void* attach, void* begin) {
     Gen* g = (Gen*)h;
     std::atomic<bool> go{false};
     std::atomic<uint32_t> ready{0};
     std::vector<std::thread> ts;
     for (uint32_t k = 0; k < g->cfg.n_threads; ++k)
-        ts.emplace_back(producer, g, k, server, (submit_fn)submit, (attach_fn)attach, &go, &ready);
+        ts.emplace_back(producer, g, k, server, (submit_fn)submit, (attach_fn)attach,
+                        (begin_fn)begin, &go, &ready);
     while (ready.load() < g->cfg.n_threads) std::this_thread::yield();
     go = true;
     for (auto& t : ts) t.join();

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 HOST = 1  # the runtime's number for the host (one device: device 0)
 BEGIN, END = 1, 2
-ALLOC, TO_DEVICE, FROM_DEVICE, DELETE = 1, 2, 3, 4
+ALLOC, TO_DEVICE, FROM_DEVICE, DELETE, ASSOCIATE = 1, 2, 3, 4, 5
 
 
 class OmptData(ctypes.Union):
@@ -119,6 +119,8 @@ def test_ompt_tool_with_stand_in_runtime(cuda_ok, orc, tmp_path):
         rt.op(FROM_DEVICE, dp, 0, hp, HOST, nbytes, 0x401020,
               fill=lambda: host_t.copy_(dev.cpu()))
         rt.op(DELETE, dp, 0, hp, HOST, nbytes, 0x401030)
+        rt.op(ASSOCIATE, hp, HOST, dp, 0, nbytes, 0x401040)   # no data moves: not logged
+        rt.op(TO_DEVICE, hp, HOST, dp, 0, 0, 0x401050)        # empty: not logged
         rt.region(False)
 
     cycle(False)  # round trip: the content goes back unchanged
@@ -152,4 +154,9 @@ def test_ompt_tool_with_stand_in_runtime(cuda_ok, orc, tmp_path):
     st = out[: k.value]
     st = st[np.lexsort((st["partner"], st["event"], st["kind"]))]
     assert np.array_equal(st.view(np.uint8), o.findings.view(np.uint8))
+    from paper_2601_12713_b300._lib import ServerStats
+
+    stats = ServerStats()
+    assert odp.lib().odp_server_stats_get(srv, ctypes.byref(stats)) == 0
+    assert stats.late_events == 0 and stats.events_processed == ev.size
     lib.odp_ompt_shutdown()

@@ -11,7 +11,8 @@ from synth import content
 pytestmark = pytest.mark.gpu
 
 
-def run_server(odp, n_threads, rate, seconds, n_slots, max_batch, seed, max_payload=1 << 20):
+def run_server(odp, n_threads, rate, seconds, n_slots, max_batch, seed, max_payload=1 << 20,
+               announce=True):
     from synth import gpu, load
 
     pool_bytes = 64 << 20
@@ -21,7 +22,7 @@ def run_server(odp, n_threads, rate, seconds, n_slots, max_batch, seed, max_payl
     srv = odp.Server(n_slots=n_slots, max_events=1 << 20, max_batch_events=max_batch,
                      device_budget_bytes=4 << 30, watermark_timeout_us=200_000)
     lg = load.Load(n_threads, rate, seconds, seed, pool.data_ptr(), pool_bytes, 256, max_payload)
-    n = lg.run(srv)
+    n = lg.run(srv, announce=announce)
     assert n > 0
     srv.flush()
     return srv, lg, pool, n
@@ -42,11 +43,15 @@ def sorted_findings(st):
     return st[np.lexsort((st["partner"], st["event"], st["kind"]))]
 
 
-@pytest.mark.parametrize("n_slots,max_batch", [(1, 512), (4, 2048)])
-def test_streamed_findings_equal_offline(cuda_ok, orc, n_slots, max_batch):
+@pytest.mark.parametrize("n_slots,max_batch,announce", [(1, 512, False), (4, 2048, True),
+                                                         (2, 256, True)])
+def test_streamed_findings_equal_offline(cuda_ok, orc, n_slots, max_batch, announce):
+    """Producers that stamp events themselves (the merge waits for each
+    one's next event) or open them with begin (it waits only for open ones)."""
     import paper_2601_12713_b300 as odp
 
-    srv, lg, pool, n = run_server(odp, 8, 20_000, 1.5, n_slots, max_batch, 5 + n_slots)
+    srv, lg, pool, n = run_server(odp, 8, 20_000, 1.5, n_slots, max_batch, 5 + n_slots,
+                                  announce=announce)
     try:
         ptr, m = srv.log()
         assert m == n
@@ -87,6 +92,162 @@ def test_streamed_findings_equal_offline(cuda_ok, orc, n_slots, max_batch):
     finally:
         srv.close()
         lg.close()
+
+
+def kernel_event(odp, t):
+    e = np.zeros(1, dtype=odp.EVENT_DTYPE)
+    e["t_start_ns"], e["t_end_ns"], e["kind"], e["src_dev"], e["dst_dev"] = t, t + 10, 6, -1, 0
+    return e
+
+
+def test_begin_holds_the_merge_only_while_open(cuda_ok):
+    """An open event holds back every later event of other threads until
+    it is submitted; a thread with nothing open does not hold the merge; an
+    event closed by cancel stops holding it; a thread that stamps its own
+    events holds the merge at its last one."""
+    import threading
+    import time
+
+    import paper_2601_12713_b300 as odp
+
+    srv = odp.Server(n_slots=1, max_events=1 << 10, max_batch_events=64,
+                     device_budget_bytes=1 << 30, watermark_timeout_us=30_000_000)
+    none = np.zeros(1, dtype=np.uint64)
+
+    def processed():
+        return srv.stats()["events_processed"]
+
+    def wait_processed(k, secs=10.0):
+        t_end = time.time() + secs
+        while processed() < k and time.time() < t_end:
+            time.sleep(0.01)
+        return processed()
+
+    opened, go, done_a = threading.Event(), threading.Event(), threading.Event()
+    t_a = {}
+
+    def thread_a():
+        t_a["t"] = srv.begin()
+        opened.set()
+        go.wait(30)
+        srv.submit(kernel_event(odp, t_a["t"]), none)
+        done_a.set()
+
+    def thread_b(k):
+        for _ in range(k):
+            srv.submit(kernel_event(odp, srv.begin()), none)
+
+    try:
+        a = threading.Thread(target=thread_a)
+        a.start()
+        assert opened.wait(30)
+        b = threading.Thread(target=thread_b, args=(8,))
+        b.start()
+        b.join()
+        time.sleep(0.3)
+        assert processed() == 0          # all of B's events start after A's open one
+        go.set()
+        a.join()
+        assert wait_processed(9) == 9    # no flush: nothing is open any more
+        # a cancelled event stops holding the merge
+        c_open, c_go = threading.Event(), threading.Event()
+
+        def thread_c():
+            t = srv.begin()
+            c_open.set()
+            c_go.wait(30)
+            srv.cancel(t)
+            with pytest.raises(odp.OdpError):
+                srv.cancel(t)            # no longer open
+
+        c = threading.Thread(target=thread_c)
+        c.start()
+        assert c_open.wait(30)
+        thread_b(4)
+        time.sleep(0.3)
+        assert processed() == 9
+        c_go.set()
+        c.join()
+        assert wait_processed(13) == 13
+        # a self-stamping thread holds the merge at its last start time (the
+        # server's clock is the monotonic clock)
+        t_d = time.monotonic_ns()
+        d = threading.Thread(target=lambda: srv.submit(kernel_event(odp, t_d), none))
+        d.start()
+        d.join()
+        assert wait_processed(14) == 14
+        b2 = threading.Thread(target=thread_b, args=(3,))
+        b2.start()
+        b2.join()
+        time.sleep(0.3)
+        assert processed() == 14         # held at D's last start time
+        srv.flush()
+        assert processed() == 17
+        st = srv.stats()
+        assert st["late_events"] == 0
+        log = odp.log_tensor(srv, 17).cpu().numpy().view(odp.EVENT_DTYPE)
+        assert np.all(np.diff(log["t_start_ns"].astype(np.int64)) >= 0)
+        assert int(log["t_start_ns"][0]) == t_a["t"]
+    finally:
+        srv.close()
+
+
+def xfer_events(odp, n, t0, host0, host_step, nbytes=256):
+    e = np.zeros(n, dtype=odp.EVENT_DTYPE)
+    e["t_start_ns"] = t0 + 10 * np.arange(n)
+    e["t_end_ns"] = e["t_start_ns"] + 5
+    e["host_addr"] = host0 + host_step * np.arange(n)
+    e["dev_addr"] = 0xA00
+    e["bytes"] = nbytes
+    e["kind"], e["src_dev"], e["dst_dev"] = 2, -1, 0
+    return e
+
+
+def test_batch_with_many_findings_and_overflow_report(cuda_ok, orc):
+    """A one-event batch (a kernel) that decides 599 waiting unused
+    transfers: its findings exceed the copy made with the batch and are
+    fetched in full.  A server whose waiting lists are too small reports the
+    decisions it could not keep."""
+    import time
+
+    import paper_2601_12713_b300 as odp
+
+    pool = torch.zeros(1 << 12, dtype=torch.uint8, device="cuda")
+    srv = odp.Server(n_slots=1, max_events=4096, max_batch_events=4096,
+                     device_budget_bytes=2 << 30)
+    try:
+        srv.attach(0)
+        x = xfer_events(odp, 600, 1000, 0xA000, 0)      # one host range, overwritten 599 times
+        srv.submit(x, np.full(600, pool.data_ptr(), dtype=np.uint64))
+        t_end = time.time() + 30
+        while srv.stats()["events_processed"] < 600 and time.time() < t_end:
+            time.sleep(0.01)
+        assert srv.stats()["events_processed"] == 600
+        srv.submit(kernel_event(odp, 1000 + 10 * 600 + 100), np.zeros(1, dtype=np.uint64))
+        srv.flush()
+        st = srv.stats()
+        assert st["events_processed"] == 601 and st["batches"] >= 2
+        assert st["stream_overflow"] == 0
+        log = odp.log_tensor(srv, 601).cpu().numpy().view(odp.EVENT_DTYPE).copy()
+        o = orc.analyze(log)
+        assert (o.findings["kind"] == 5).sum() == 599
+        got = sorted_findings(srv.poll())
+        assert np.array_equal(got.view(np.uint8), o.findings.view(np.uint8))
+    finally:
+        srv.close()
+    # 40 transfers to distinct ranges wait for a kernel; one-event batches
+    # keep 16 waiting at most
+    srv = odp.Server(n_slots=1, max_events=256, max_batch_events=1, device_budget_bytes=1 << 30)
+    try:
+        srv.attach(0)
+        x = xfer_events(odp, 40, 1000, 0xB000, 0x1000)
+        srv.submit(x, np.full(40, pool.data_ptr(), dtype=np.uint64))
+        srv.flush()
+        st = srv.stats()
+        assert st["events_processed"] == 40
+        assert st["stream_overflow"] == 40 - 16
+    finally:
+        srv.close()
 
 
 def test_submit_argument_errors(cuda_ok):
