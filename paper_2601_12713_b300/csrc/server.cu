@@ -130,8 +130,12 @@ struct SlotDev {
     uint32_t* pa;          // pairs completed in the batch: alloc, delete
     uint32_t* pd;
     uint32_t* rslot;       // their slot in t_rid
-    uint32_t* bk;          // kernels of the batch (log indices)
-    uint32_t* cnt;         // [0] pairs, [1] kernels
+    uint32_t* bk;          // kernels of the batch (log indices), by device, in log order
+    uint32_t* bktmp;       // the same in log order
+    unsigned long long* end1;  // per bk entry: 1 + largest end among its device's kernels up to it
+    uint32_t* kst;         // [256] per device: first bk entry
+    uint32_t* kcn;         // [256] per device: number of bk entries
+    uint32_t* cnt;         // [0] pairs, [1] kernels, [2] overwrites, [3] waiting transfers
 };
 
 // The batch's kernels on `dev`: how many come before log index g and the
@@ -142,21 +146,20 @@ struct BatchKernels {
     unsigned long long max_end1;  // 1 + largest end of those before g
 };
 
-__device__ __forceinline__ BatchKernels batch_kernels_on(const odp_event* log, const uint32_t* bk,
-                                                         uint32_t nk, uint32_t dev, uint32_t g) {
-    BatchKernels r{0, 0, NONE32, 0};
-    for (uint32_t i = 0; i < nk; ++i) {
-        const uint32_t k = bk[i];
-        const odp_event& e = log[k];
-        if (((uint32_t)(e.dst_dev + 1) & 0xFF) != dev) continue;
-        ++r.total;
-        if (k < g) {
-            ++r.before;
-            r.max_end1 = max(r.max_end1, (unsigned long long)e.t_end_ns + 1ull);
-        } else if (r.first_after == NONE32 || k < r.first_after) {
-            r.first_after = k;
-        }
+__device__ __forceinline__ BatchKernels batch_kernels_on(const SlotDev& s, uint32_t dev,
+                                                         uint32_t g) {
+    const uint32_t st = s.kst[dev], c = s.kcn[dev];
+    uint32_t lo = 0, hi = c;  // first entry of the device's run with log index >= g
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s.bk[st + mid] < g) lo = mid + 1;
+        else hi = mid;
     }
+    BatchKernels r;
+    r.before = lo;
+    r.total = c;
+    r.first_after = lo < c ? s.bk[st + lo] : NONE32;
+    r.max_end1 = lo ? s.end1[st + lo - 1] : 0ull;
     return r;
 }
 
@@ -346,7 +349,6 @@ __global__ void srv_pair_walk(SrvDev d, SlotDev s) {
     const uint32_t m = s.par->m;
     const uint32_t none_key = d.t_pair.cap_max + 1;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
-        if (d.log[g0 + r].kind == ODP_KERNEL) s.bk[atomicAdd(&s.cnt[1], 1u)] = (uint32_t)(g0 + r);
         const uint32_t k = s.skeys[r];
         if (k == none_key || (r > 0 && s.skeys[r - 1] == k)) continue;
         uint32_t top = d.t_pair.slots[k].v;
@@ -388,15 +390,19 @@ __global__ void srv_ra_emit(SrvDev d, SlotDev s, uint32_t cap) {
     }
 }
 
-// Some kernel of the batch on `dev` overlaps [lo, hi].
+// Some kernel of the batch on `dev` overlaps [lo, hi]: of the device's
+// kernels that start by hi (a prefix: the log is in start order), the
+// latest end reaches lo.
 __device__ __forceinline__ bool batch_kernel_overlaps(const SrvDev& d, const SlotDev& s,
                                                       uint32_t dev, uint64_t lo, uint64_t hi) {
-    const uint32_t nk = s.cnt[1];
-    for (uint32_t i = 0; i < nk; ++i) {
-        const odp_event& k = d.log[s.bk[i]];
-        if (ep_of(k.dst_dev) == dev && k.t_start_ns <= hi && k.t_end_ns >= lo) return true;
+    const uint32_t st = s.kst[dev], c = s.kcn[dev];
+    uint32_t a = 0, b = c;  // kernels with t_start <= hi
+    while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        if (d.log[s.bk[st + mid]].t_start_ns <= hi) a = mid + 1;
+        else b = mid;
     }
-    return false;
+    return a > 0 && s.end1[st + a - 1] > lo;
 }
 
 // Alg. 4 for the batch's pairs (against earlier kernels, then the batch's)
@@ -449,14 +455,14 @@ __global__ void srv_kmax(SrvDev d, SlotDev s) {
 __global__ void srv_ut_keys(SrvDev d, SlotDev s) {
     const uint64_t g0 = s.par->g0;
     const uint32_t m = s.par->m;
-    const uint32_t cap = *d.t_ut.cap_dev, none_key = d.t_ut.cap_max + 1, nk = s.cnt[1];
+    const uint32_t cap = *d.t_ut.cap_dev, none_key = d.t_ut.cap_max + 1;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
         const uint32_t g = (uint32_t)(g0 + q);
         const odp_event& e = d.log[g];
         uint32_t k = none_key;
         if (e.kind == ODP_TO_DEV) {
             const uint32_t dev = ep_of(e.dst_dev);
-            const BatchKernels bk = batch_kernels_on(d.log, s.bk, nk, dev, g);
+            const BatchKernels bk = batch_kernels_on(s, dev, g);
             const unsigned long long km = max(d.kmax[dev], bk.max_end1);
             if (!(km != 0 && km - 1 >= e.t_start_ns)) {
                 d.useg[g] = d.kcnt[dev] + bk.before;
@@ -502,7 +508,6 @@ __global__ void srv_ut_walk(SrvDev d, SlotDev s) {
 // cur ^ 1.
 __global__ void srv_ut_resolve(SrvDev d, SlotDev s, uint32_t cap) {
     const uint32_t cur = *d.cur, nxt = cur ^ 1;
-    const uint32_t nk = s.cnt[1];
     const uint32_t n_f = min(d.nut[cur], d.pend_cap), n_fb = s.cnt[2];
     const uint32_t n_o = min(d.nut[2 + cur], d.pend_cap), n_ob = s.cnt[3];
     const uint32_t n_all = n_f + n_fb + n_o + n_ob;
@@ -511,7 +516,7 @@ __global__ void srv_ut_resolve(SrvDev d, SlotDev s, uint32_t cap) {
             const uint32_t c = i < n_f ? d.utf[cur][i].x : s.pa[i - n_f];
             const uint32_t t = i < n_f ? d.utf[cur][i].y : s.pd[i - n_f];
             const uint32_t dev = ep_of(d.log[t].dst_dev);
-            const BatchKernels bk = batch_kernels_on(d.log, s.bk, nk, dev, t);
+            const BatchKernels bk = batch_kernels_on(s, dev, t);
             if (bk.first_after == NONE32) {  // segment still open
                 const uint32_t j = atomicAdd(&d.nut[nxt], 1u);
                 if (j < d.pend_cap) d.utf[nxt][j] = make_uint2(c, t);
@@ -524,7 +529,7 @@ __global__ void srv_ut_resolve(SrvDev d, SlotDev s, uint32_t cap) {
             const uint32_t o = i - n_f - n_fb;
             const uint32_t g = o < n_o ? d.utopen[cur][o] : s.rslot[o - n_o];
             const uint32_t dev = ep_of(d.log[g].dst_dev);
-            if (batch_kernels_on(d.log, s.bk, nk, dev, g).first_after == NONE32) {
+            if (batch_kernels_on(s, dev, g).first_after == NONE32) {
                 const uint32_t j = atomicAdd(&d.nut[2 + nxt], 1u);
                 if (j < d.pend_cap) d.utopen[nxt][j] = g;
                 else atomicAdd(&d.nut[4], 1u);
@@ -581,6 +586,110 @@ __global__ void srv_append(SrvDev d, SlotDev s) {
     uint4* dst = reinterpret_cast<uint4*>(d.log + s.par->g0);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * m; i += gridDim.x * blockDim.x)
         dst[i] = src[i];
+}
+
+// The batch's kernels grouped by device, in log (= start) order within each
+// device, with the running maximum of their ends (one block; three ordered
+// passes: compaction, stable scatter by device, per-device max scan).  The
+// questions Alg. 4 and 5 ask about the batch's kernels then become binary
+// searches; s.cnt[1] receives the count.
+constexpr int BKI_THREADS = 1024;
+
+__global__ void __launch_bounds__(BKI_THREADS) srv_bk_index(SrvDev d, SlotDev s) {
+    constexpr int W = BKI_THREADS / 32;
+    __shared__ uint32_t wofs[W + 1];
+    __shared__ uint32_t dbase[256];
+    __shared__ uint32_t wdev[W][256];
+    const uint64_t g0 = s.par->g0;
+    const uint32_t m = s.par->m;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1;
+    for (int i = threadIdx.x; i < 256; i += BKI_THREADS) dbase[i] = 0;
+    // 1. compaction of the batch's kernels in log order; counts per device
+    uint32_t nk = 0;
+    for (uint32_t c0 = 0; c0 < m; c0 += BKI_THREADS) {
+        const uint32_t q = c0 + threadIdx.x;
+        const bool isk = q < m && d.log[g0 + q].kind == ODP_KERNEL;
+        const uint32_t bal = __ballot_sync(ODP_FULL_MASK, isk);
+        if (lane == 0) wofs[warp] = __popc(bal);
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t v = wofs[lane];
+            uint32_t incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(ODP_FULL_MASK, incl, o);
+                if (lane >= o) incl += t;
+            }
+            wofs[lane] = incl - v;
+            if (lane == 31) wofs[W] = incl;
+        }
+        __syncthreads();
+        if (isk) {
+            s.bktmp[nk + wofs[warp] + __popc(bal & lt)] = (uint32_t)(g0 + q);
+            atomicAdd(&dbase[ep_of(d.log[g0 + q].dst_dev)], 1u);
+        }
+        nk += wofs[W];
+        __syncthreads();
+    }
+    // 2. device runs: exclusive scan of the 256 counts (thread t owns device t)
+    if (threadIdx.x < 256) {
+        const uint32_t c = dbase[threadIdx.x];
+        s.kcn[threadIdx.x] = c;
+        wdev[0][threadIdx.x] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int t = 0; t < 256; ++t) {
+            const uint32_t c = wdev[0][t];
+            dbase[t] = run;
+            s.kst[t] = run;
+            run += c;
+        }
+        s.cnt[1] = nk;
+    }
+    __syncthreads();
+    // 3. stable scatter by device, chunk by chunk in log order
+    for (uint32_t c0 = 0; c0 < nk; c0 += BKI_THREADS) {
+        const uint32_t i = c0 + threadIdx.x;
+        const bool valid = i < nk;
+        const uint32_t k = valid ? s.bktmp[i] : 0u;
+        const uint32_t dev = valid ? ep_of(d.log[k].dst_dev) : 256u;
+        for (int t = lane; t < 256; t += 32) wdev[warp][t] = 0;
+        __syncwarp();
+        const uint32_t peers = __match_any_sync(ODP_FULL_MASK, dev);
+        if (valid && lane == __ffs(peers) - 1) wdev[warp][dev] = __popc(peers);
+        __syncthreads();
+        uint32_t tot = 0;
+        if (threadIdx.x < 256) {
+            for (int w = 0; w < W; ++w) {
+                const uint32_t c = wdev[w][threadIdx.x];
+                wdev[w][threadIdx.x] = tot;
+                tot += c;
+            }
+        }
+        __syncthreads();
+        if (valid) s.bk[dbase[dev] + wdev[warp][dev] + __popc(peers & lt)] = k;
+        __syncthreads();
+        if (threadIdx.x < 256) dbase[threadIdx.x] += tot;
+        __syncthreads();
+    }
+    // 4. running maximum of end + 1 along each device's run (warp per device)
+    for (uint32_t dev = warp; dev < 256; dev += W) {
+        const uint32_t st = s.kst[dev], c = s.kcn[dev];
+        unsigned long long carry = 0;
+        for (uint32_t j0 = 0; j0 < c; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            unsigned long long v = j < c ? d.log[s.bk[st + j]].t_end_ns + 1ull : 0ull;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long t = __shfl_up_sync(ODP_FULL_MASK, v, o);
+                if (lane >= o) v = max(v, t);
+            }
+            v = max(v, carry);
+            if (j < c) s.end1[st + j] = v;
+            carry = __shfl_sync(ODP_FULL_MASK, v, 31);
+        }
+    }
 }
 
 // After the flush: the current waiting lists are empty.
@@ -715,6 +824,7 @@ void enqueue_analysis(odp_server* S, Slot& sl, cudaStream_t as) {
     const int grid = (int)std::min<uint32_t>(1024, (B + 255) / 256);
     const uint32_t* m_dev = &sl.d.par->m;
     srv_append<<<grid, 256, 0, as>>>(S->d, sl.d);
+    srv_bk_index<<<1, BKI_THREADS, 0, as>>>(S->d, sl.d);
     prim::table_clear<<<64, 256, 0, as>>>(S->d.t_b, m_dev, B);
     srv_insert_fp<<<grid, 256, 0, as>>>(S->d, sl.d);
     srv_insert_dd<<<grid, 256, 0, as>>>(S->d, sl.d);
@@ -1057,6 +1167,10 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
         if (!rc) rc = alloc_dev(S, (void**)&d.pd, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.rslot, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.bk, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.bktmp, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.end1, 8 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.kst, 4 * 256);
+        if (!rc) rc = alloc_dev(S, (void**)&d.kcn, 4 * 256);
         if (!rc) rc = alloc_dev(S, (void**)&d.cnt, 16);
         if (rc) return fail(rc);
         if (cudaHostAlloc((void**)&sl.h_ev, sizeof(odp_event) * B, 0) != cudaSuccess ||

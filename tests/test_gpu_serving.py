@@ -330,6 +330,66 @@ def pairs_trace():
     return np.array(rows, dtype=T.EVENT_DTYPE)
 
 
+def kernel_heavy_trace(seed, n_cycles=800):
+    """Allocation cycles on three devices (ALLOC, one or two TO_DEV of the
+    same host range, DELETE) among kernels of random length on random
+    devices, many of them overlapping several cycles; contents repeat, so
+    duplicates and overwritten transfers occur.  Cycles of one <host, device,
+    bytes> key never overlap, and content goes only from the host to one
+    device."""
+    from synth import traces as T
+
+    rng = np.random.default_rng(seed)
+    rows, t = [], 1000
+    for c in range(n_cycles):
+        dev, key = int(rng.integers(0, 3)), c % 40
+        host, daddr, nbytes = 0x10000 + key * 0x1000, 0x100 * (key + 1), 256 * (1 + key % 3)
+        site = int(rng.integers(0, 32))
+        d_end = t + int(rng.integers(60, 400))
+        rows.append((t, t + 5, host, daddr, nbytes, 0, 0, site, T.ALLOC, -1, dev, 0))
+        for j in range(int(rng.integers(1, 3))):
+            t1 = t + 10 + 20 * j
+            content = int(rng.integers(0, 6)) * 16 + dev
+            rows.append((t1, t1 + 5, host, daddr, nbytes, content + 1, 0, site, T.TO_DEV, -1, dev, 0))
+        if rng.random() < 0.6:
+            k0 = t + int(rng.integers(0, 300))
+            kd = int(rng.integers(0, 3))
+            rows.append((k0, k0 + int(rng.integers(1, 3000)), 0, 0, 0, 0, 0, site, T.KERNEL, -1, kd, 0))
+        rows.append((d_end, d_end + 5, host, daddr, nbytes, 0, 0, site, T.DELETE, -1, dev, 0))
+        t += int(rng.integers(20, 200))
+    ev = np.array(rows, dtype=T.EVENT_DTYPE)
+    ev = ev[np.argsort(ev["t_start_ns"], kind="stable")]
+    ev["flags"] = np.where(np.isin(ev["kind"], [2, 3, 4]), 1, 0)  # fingerprints given
+    return ev
+
+
+@pytest.mark.parametrize("max_batch", [64, 4096])
+def test_streamed_kernel_heavy_batches_equal_offline(cuda_ok, orc, max_batch):
+    """Batches holding hundreds of kernels on three devices (the per-device
+    kernel index of a batch) stream the same findings as the offline
+    analysis."""
+    import paper_2601_12713_b300 as odp
+
+    ev = kernel_heavy_trace(11)
+    srv = odp.Server(n_slots=2, max_events=1 << 13, max_batch_events=max_batch,
+                     device_budget_bytes=2 << 30)
+    try:
+        srv.attach(0)
+        srv.submit(ev, np.zeros(ev.size, dtype=np.uint64))
+        srv.flush()
+        st = srv.stats()
+        assert st["events_processed"] == ev.size
+        assert st["stream_overflow"] == 0 and st["rt_groups_unstreamed"] == 0
+        log = odp.log_tensor(srv, ev.size).cpu().numpy().view(odp.EVENT_DTYPE).copy()
+        o = orc.analyze(log)
+        counts = [int((o.findings["kind"] == k).sum()) for k in range(1, 6)]
+        assert counts[0] > 50 and counts[2] > 50 and counts[3] > 10 and counts[4] > 10
+        got = sorted_findings(srv.poll())
+        assert np.array_equal(got.view(np.uint8), o.findings.view(np.uint8))
+    finally:
+        srv.close()
+
+
 @pytest.mark.parametrize("max_batch", [1, 3, 8, 4096])
 def test_streamed_pairs_equal_offline(cuda_ok, orc, max_batch):
     """Streamed repeated allocations, unused allocations and unused transfers
