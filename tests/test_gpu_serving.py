@@ -363,15 +363,16 @@ def kernel_heavy_trace(seed, n_cycles=800):
     return ev
 
 
-@pytest.mark.parametrize("max_batch", [64, 4096])
+@pytest.mark.parametrize("max_batch", [64, 4096, 16384])
 def test_streamed_kernel_heavy_batches_equal_offline(cuda_ok, orc, max_batch):
     """Batches holding hundreds of kernels on three devices (the per-device
     kernel index of a batch) stream the same findings as the offline
     analysis."""
     import paper_2601_12713_b300 as odp
 
-    ev = kernel_heavy_trace(11)
-    srv = odp.Server(n_slots=2, max_events=1 << 13, max_batch_events=max_batch,
+    # 16384-event batches sort with the multi-pass radix sort inside the graph
+    ev = kernel_heavy_trace(11, n_cycles=800 if max_batch < 16384 else 3600)
+    srv = odp.Server(n_slots=2, max_events=1 << 15, max_batch_events=max_batch,
                      device_budget_bytes=2 << 30)
     try:
         srv.attach(0)
