@@ -1024,9 +1024,15 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
     for (uint32_t c = gw; c < nch; c += nw) {
         const uint32_t i = c * 32 + lane;
         const bool valid = i < a.n;
+        // Round 1: the partner arrays, and with them (before knowing whether
+        // the event has a finding) its own record and the delete that closes
+        // it, so a chunk waits for memory twice, not three times.
         uint32_t part[5];
         uint32_t bal[5];
         uint32_t any = 0;
+        const uint4* rec = reinterpret_cast<const uint4*>(a.ev.p) + 4ull * (valid ? i : 0u);
+        const uint4 o0 = __ldg(rec), o2 = __ldg(rec + 2), o3 = __ldg(rec + 3);
+        const uint32_t del = valid ? __ldg(a.del_of + i) : NONE32;
         for (int kind = 0; kind < 5; ++kind) {
             part[kind] = valid ? partner_of(a, kind + 1, i) : NONE32;
             bal[kind] = __ballot_sync(ODP_FULL_MASK, part[kind] != NONE32);
@@ -1037,74 +1043,71 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
         // Whoever sets an event's bit adds its duration to the saved time, so
         // the union is summed once.
         const uint32_t own = bal[ODP_DD - 1] | bal[ODP_RA - 1] | bal[ODP_UA - 1] | bal[ODP_UT - 1];
+        // (the old bits are read back only at the end of the chunk)
         uint32_t own_old = 0;
         if (lane == 0 && own) own_old = atomicOr(a.wbits + c, own);
-        own_old = __shfl_sync(ODP_FULL_MASK, own_old, 0);
-        if (!(any & (1u << lane))) continue;
-        // All global loads of the chunk are issued before any store, in two
-        // dependent rounds, so a warp waits for memory twice per chunk.
-        // Round 1: the event's own record, the delete closing an RA alloc.
-        const uint4* rec = reinterpret_cast<const uint4*>(a.ev.p) + 4ull * i;
-        const uint4 o0 = __ldg(rec), o2 = __ldg(rec + 2), o3 = __ldg(rec + 3);
-        const uint32_t d = part[ODP_RA - 1] != NONE32 ? __ldg(a.del_of + i) : NONE32;
-        // Round 2: partner sites, the RT partner's times and bytes, the UA
-        // partner's and the RA delete's times.
-        uint32_t psite[5];
-#pragma unroll
-        for (int kind = 0; kind < 5; ++kind) {
-            const uint32_t p = part[kind];
-            psite[kind] = (p != NONE32 && p != NOPART)
-                              ? __ldg(reinterpret_cast<const uint32_t*>(a.ev.p + 64ull * p + 56))
-                              : 0xFFFFFFFFu;
-        }
-        const uint32_t p_rt = part[ODP_RT - 1], p_ua = part[ODP_UA - 1];
-        const uint4* rrt = reinterpret_cast<const uint4*>(a.ev.p) + 4ull * p_rt;
-        const uint4 z4 = make_uint4(0, 0, 0, 0);
-        const uint4 rt0 = p_rt != NONE32 ? __ldg(rrt) : z4;
-        const uint4 rt2 = p_rt != NONE32 ? __ldg(rrt + 2) : z4;
-        const uint4 ua0 = (p_ua != NONE32 && p_ua != NOPART)
-                              ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * p_ua)
-                              : z4;
-        const uint4 d0 = d != NONE32 ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * d) : z4;
-        // Stores.
-        const uint64_t t0 = lohi(o0.x, o0.y), t1 = lohi(o0.z, o0.w), own_bytes = lohi(o2.x, o2.y);
-        const uint32_t site = o3.z;
-        if ((own >> lane) & 1 & ~(own_old >> lane)) saved += t1 - t0;
-#pragma unroll
-        for (int kind = 0; kind < 5; ++kind) {
-            const uint32_t p = part[kind];
-            if (p == NONE32) continue;
-            const bool np = p == NOPART;
-            uint64_t wb = own_bytes, wn = t1 - t0;
-            switch (kind + 1) {
-                case ODP_RT:
-                    wb = lohi(rt2.x, rt2.y);
-                    wn = lohi(rt0.z, rt0.w) - lohi(rt0.x, rt0.y);
-                    saved += mark_wasted(a, p, wn);
-                    break;
-                case ODP_RA:
-                    if (d != NONE32) {
-                        const uint64_t dd = lohi(d0.z, d0.w) - lohi(d0.x, d0.y);
-                        wn += dd;
-                        saved += mark_wasted(a, d, dd);
-                    }
-                    break;
-                case ODP_UA:
-                    if (!np) {
-                        const uint64_t dp = lohi(ua0.z, ua0.w) - lohi(ua0.x, ua0.y);
-                        wn += dp;
-                        saved += mark_wasted(a, p, dp);
-                    }
-                    break;
-                default:  // DD, UT: the event itself (marked above)
-                    break;
+        if (any & (1u << lane)) {
+            const uint32_t d = part[ODP_RA - 1] != NONE32 ? del : NONE32;
+            // Round 2: partner sites, the RT partner's times and bytes, the UA
+            // partner's and the RA delete's times.
+            uint32_t psite[5];
+    #pragma unroll
+            for (int kind = 0; kind < 5; ++kind) {
+                const uint32_t p = part[kind];
+                psite[kind] = (p != NONE32 && p != NOPART)
+                                  ? __ldg(reinterpret_cast<const uint32_t*>(a.ev.p + 64ull * p + 56))
+                                  : 0xFFFFFFFFu;
             }
-            site_add(st, a, kind, site, wb, wn);
-            const uint64_t pos = (uint64_t)wscan[kind * nch + c] + __popc(bal[kind] & lt);
-            if (pos < cap)
-                store_finding(items, pos, kind + 1, site, psite[kind], i,
-                              np ? ODP_NO_EVENT : (uint64_t)p, wb, wn);
+            const uint32_t p_rt = part[ODP_RT - 1], p_ua = part[ODP_UA - 1];
+            const uint4* rrt = reinterpret_cast<const uint4*>(a.ev.p) + 4ull * p_rt;
+            const uint4 z4 = make_uint4(0, 0, 0, 0);
+            const uint4 rt0 = p_rt != NONE32 ? __ldg(rrt) : z4;
+            const uint4 rt2 = p_rt != NONE32 ? __ldg(rrt + 2) : z4;
+            const uint4 ua0 = (p_ua != NONE32 && p_ua != NOPART)
+                                  ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * p_ua)
+                                  : z4;
+            const uint4 d0 = d != NONE32 ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * d) : z4;
+            // Stores.
+            const uint64_t t0 = lohi(o0.x, o0.y), t1 = lohi(o0.z, o0.w), own_bytes = lohi(o2.x, o2.y);
+            const uint32_t site = o3.z;
+    #pragma unroll
+            for (int kind = 0; kind < 5; ++kind) {
+                const uint32_t p = part[kind];
+                if (p == NONE32) continue;
+                const bool np = p == NOPART;
+                uint64_t wb = own_bytes, wn = t1 - t0;
+                switch (kind + 1) {
+                    case ODP_RT:
+                        wb = lohi(rt2.x, rt2.y);
+                        wn = lohi(rt0.z, rt0.w) - lohi(rt0.x, rt0.y);
+                        saved += mark_wasted(a, p, wn);
+                        break;
+                    case ODP_RA:
+                        if (d != NONE32) {
+                            const uint64_t dd = lohi(d0.z, d0.w) - lohi(d0.x, d0.y);
+                            wn += dd;
+                            saved += mark_wasted(a, d, dd);
+                        }
+                        break;
+                    case ODP_UA:
+                        if (!np) {
+                            const uint64_t dp = lohi(ua0.z, ua0.w) - lohi(ua0.x, ua0.y);
+                            wn += dp;
+                            saved += mark_wasted(a, p, dp);
+                        }
+                        break;
+                    default:  // DD, UT: the event itself (marked above)
+                        break;
+                }
+                site_add(st, a, kind, site, wb, wn);
+                const uint64_t pos = (uint64_t)wscan[kind * nch + c] + __popc(bal[kind] & lt);
+                if (pos < cap)
+                    store_finding(items, pos, kind + 1, site, psite[kind], i,
+                                  np ? ODP_NO_EVENT : (uint64_t)p, wb, wn);
+            }
         }
+        own_old = __shfl_sync(ODP_FULL_MASK, own_old, 0);
+        if ((own >> lane) & 1 & ~(own_old >> lane)) saved += lohi(o0.z, o0.w) - lohi(o0.x, o0.y);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < SITE_SLOTS; i += blockDim.x) {
