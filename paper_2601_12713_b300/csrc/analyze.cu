@@ -263,7 +263,7 @@ __global__ void k_x_insert_fp(A a) {
                                    : make_uint4(0, 0, 0, 0);
             key[b] = Key128{((uint64_t)f.w << 32) | f.z, ((uint64_t)g.y << 32) | g.x};
         }
-        prim::table_insert_batch<INS_B, true>(a.tab, cap, key, e, use, out);
+        prim::table_insert_batch<INS_B, true, false>(a.tab, cap, key, e, use, out);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b)
             if (use[b]) a.slot[j0 + b * str] = slot_key(a, out[b], e[b]);
@@ -582,7 +582,7 @@ __global__ void k_p_insert(A a) {
 #pragma unroll
         for (int b = 0; b < INS_B; ++b)
             key[b] = use[b] ? Key128{a.ev.daddr(e[b]), (uint64_t)c_dst(a.cls[e[b]])} : Key128{0, 0};
-        prim::table_insert_batch<INS_B, false>(a.ktab, cap, key, e, use, out);
+        prim::table_insert_batch<INS_B, false, true>(a.ktab, cap, key, e, use, out);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             if (!use[b]) continue;
@@ -683,7 +683,7 @@ __global__ void k_ra_insert(A a) {
             key[b] = use[b] ? Key128{a.ev.host(e[b]), a.ev.bytes(e[b]) | ((uint64_t)c_dst(a.cls[e[b]]) << 56)}
                             : Key128{0, 0};
         }
-        prim::table_insert_batch<INS_B, true>(a.tab, cap, key, e, use, out);
+        prim::table_insert_batch<INS_B, true, true>(a.tab, cap, key, e, use, out);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b)
             if (in[b]) a.slot[j0 + b * str] = out[b];
@@ -857,7 +857,7 @@ __global__ void k_ut_insert(A a) {
             e[b] = use[b] ? a.sv[q] : 0;
             key[b] = use[b] ? Key128{a.ev.host(e[b]), 1} : Key128{0, 0};
         }
-        prim::table_insert_batch<INS_B, false>(a.ktab, cap, key, e, use, out);
+        prim::table_insert_batch<INS_B, false, true>(a.ktab, cap, key, e, use, out);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             const uint32_t q = q0 + b * str;

@@ -536,6 +536,27 @@ __global__ void table_clear(KeyTable t, const uint32_t* count_dev, uint32_t coun
 // Inserts `k` and lowers the slot's value to v; returns the slot index, or
 // NONE32 if the probe sequence exhausted the table (cannot happen at <= 50%
 // load).
+// What a plain (non-atomic) read of a slot's key shows: PEEK_ASK (empty,
+// or possibly half-written: ask the compare-and-swap), PEEK_MINE (the slot
+// holds k), PEEK_OTHER (the slot holds another key for good).  Slots change
+// once per table lifetime, empty -> key; a 16-byte read may pair one
+// all-ones (empty) half with a half of the new key, so only a read with no
+// all-ones half is taken as a complete key.  Repeated keys then find their
+// slot without an atomic, and occupied slots are passed without one.
+enum { PEEK_ASK = 0, PEEK_MINE = 1, PEEK_OTHER = 2 };
+
+__device__ __forceinline__ int peek_slot(const Key128* p, Key128 k) {
+    const Key128 c = *p;
+    if (c.lo == EMPTY_KEY || c.hi == EMPTY_KEY) return PEEK_ASK;
+    return key_eq(c, k) ? PEEK_MINE : PEEK_OTHER;
+}
+
+// Lowers a slot's value to v; values only decrease, so a plain read at or
+// below v means the atomic would change nothing.
+__device__ __forceinline__ void lower_to(uint32_t* p, uint32_t v) {
+    if (*p > v) atomicMin(p, v);
+}
+
 __device__ __forceinline__ uint32_t table_insert_min(const Table& t, uint32_t cap, Key128 k,
                                                      uint32_t v) {
     if (k.lo == EMPTY_KEY && k.hi == EMPTY_KEY) {
@@ -547,10 +568,17 @@ __device__ __forceinline__ uint32_t table_insert_min(const Table& t, uint32_t ca
     const Key128 empty{EMPTY_KEY, EMPTY_KEY};
     for (uint32_t probe = 0; probe < cap; ++probe) {
         // slots change only once (empty -> key), always through the 16-byte CAS
-        const Key128 cur = atomicCAS(&t.slots[slot].k, empty, k);
-        if (key_eq(cur, empty) || key_eq(cur, k)) {
-            atomicMin(&t.slots[slot].v, v);
+        const int seen = peek_slot(&t.slots[slot].k, k);
+        if (seen == PEEK_MINE) {
+            lower_to(&t.slots[slot].v, v);
             return slot;
+        }
+        if (seen == PEEK_ASK) {
+            const Key128 cur = atomicCAS(&t.slots[slot].k, empty, k);
+            if (key_eq(cur, empty) || key_eq(cur, k)) {
+                lower_to(&t.slots[slot].v, v);
+                return slot;
+            }
         }
         slot = (slot + 1) & mask;
     }
@@ -565,8 +593,12 @@ __device__ __forceinline__ uint32_t table_insert(const Table& t, uint32_t cap, K
     uint32_t slot = (uint32_t)mix64(k.lo ^ mix64(k.hi)) & mask;
     const Key128 empty{EMPTY_KEY, EMPTY_KEY};
     for (uint32_t probe = 0; probe < cap; ++probe) {
-        const Key128 cur = atomicCAS(&t.slots[slot].k, empty, k);
-        if (key_eq(cur, empty) || key_eq(cur, k)) return slot;
+        const int seen = peek_slot(&t.slots[slot].k, k);
+        if (seen == PEEK_MINE) return slot;
+        if (seen == PEEK_ASK) {
+            const Key128 cur = atomicCAS(&t.slots[slot].k, empty, k);
+            if (key_eq(cur, empty) || key_eq(cur, k)) return slot;
+        }
         slot = (slot + 1) & mask;
     }
     return NONE32;
@@ -574,8 +606,12 @@ __device__ __forceinline__ uint32_t table_insert(const Table& t, uint32_t cap, K
 
 // Inserts up to B keys per thread with their compare-and-swaps in flight
 // together (the probes of different keys are independent).  use[b] false:
-// out[b] = NONE32.  MIN: also lower the slot's value to v[b].
-template <int B, bool MIN, class TableT>
+// out[b] = NONE32.  MIN: also lower the slot's value to v[b].  PEEK: read
+// each slot before the compare-and-swap (peek_slot), which pays where many
+// inserts repeat a few keys (the atomics would queue on them) and costs a
+// round trip where most keys are new or rarely repeated in a table far
+// larger than L2.
+template <int B, bool MIN, bool PEEK, class TableT>
 __device__ __forceinline__ void table_insert_batch(const TableT& t, uint32_t cap, const Key128* k,
                                                    const uint32_t* v, const bool* use,
                                                    uint32_t* out) {
@@ -598,16 +634,23 @@ __device__ __forceinline__ void table_insert_batch(const TableT& t, uint32_t cap
         }
     }
     for (uint32_t probe = 0; probe < cap; ++probe) {
-        Key128 cur[B];
+        int seen[B];
 #pragma unroll
         for (int b = 0; b < B; ++b)
-            if (!done[b]) cur[b] = atomicCAS(t.key_at(slot[b]), empty, k[b]);
+            seen[b] = done[b] || !PEEK ? PEEK_ASK : peek_slot(t.key_at(slot[b]), k[b]);
+        Key128 cur[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            cur[b] = k[b];
+            if (!done[b] && seen[b] == PEEK_ASK) cur[b] = atomicCAS(t.key_at(slot[b]), empty, k[b]);
+        }
         bool again = false;
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             if (done[b]) continue;
-            if (key_eq(cur[b], empty) || key_eq(cur[b], k[b])) {
-                if (MIN) atomicMin(t.val_at(slot[b]), v[b]);
+            if (seen[b] != PEEK_OTHER && (key_eq(cur[b], empty) || key_eq(cur[b], k[b]))) {
+                if (MIN && PEEK) lower_to(t.val_at(slot[b]), v[b]);
+                else if (MIN) atomicMin(t.val_at(slot[b]), v[b]);
                 out[b] = slot[b];
                 done[b] = true;
             } else {
