@@ -80,6 +80,7 @@ __device__ __forceinline__ uint32_t c_dst(uint32_t c) { return (c >> 16) & 0xFF;
 struct A {
     Ev ev;
     uint32_t n;
+    uint32_t pack_alloc;  // slot keys leave bit 31 free: it carries "is ALLOC" through the pairs sort
     Hdr* h;
     uint32_t* cls;
     uint32_t *X, *P, *K, *U;
@@ -579,26 +580,33 @@ __global__ void k_p_insert(A a) {
             use[b] = j < n;
             e[b] = use[b] ? a.P[j] : 0;
         }
+        uint32_t flag[INS_B];
 #pragma unroll
-        for (int b = 0; b < INS_B; ++b)
-            key[b] = use[b] ? Key128{a.ev.daddr(e[b]), (uint64_t)c_dst(a.cls[e[b]])} : Key128{0, 0};
+        for (int b = 0; b < INS_B; ++b) {
+            const uint32_t c = use[b] ? a.cls[e[b]] : 0;
+            key[b] = use[b] ? Key128{a.ev.daddr(e[b]), (uint64_t)c_dst(c)} : Key128{0, 0};
+            flag[b] = a.pack_alloc && c_kind(c) == ODP_ALLOC ? 0x80000000u : 0u;
+        }
         prim::table_insert_batch<INS_B, false, true>(a.ktab, cap, key, e, use, out);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             if (!use[b]) continue;
-            a.sk[j0 + b * str] = slot_key(a, out[b], e[b]);
+            a.sk[j0 + b * str] = slot_key(a, out[b], e[b]) | flag[b];
             a.sv[j0 + b * str] = e[b];
         }
     }
 }
 
-// Group heads of the sorted alloc/delete list; whether each entry is an
-// ALLOC is gathered once into a.k2 (in sorted order).
+// Group heads of the sorted alloc/delete list, and whether each entry is an
+// ALLOC into a.k2 (in sorted order): from bit 31 of the sort key where the
+// sort carried it there, else gathered from the class words.
 __global__ void k_seg_heads(A a, const uint32_t* count) {
     if (failed(a)) return;
+    const uint32_t m = a.pack_alloc ? 0x7FFFFFFFu : 0xFFFFFFFFu;
     GRID_STRIDE(q, *count) {
-        a.f1[q] = q == 0 || a.sk[q] != a.sk[q - 1];
-        a.k2[q] = c_kind(a.cls[a.sv[q]]) == ODP_ALLOC;
+        const uint32_t k = a.sk[q];
+        a.f1[q] = q == 0 || (k & m) != (a.sk[q - 1] & m);
+        a.k2[q] = a.pack_alloc ? k >> 31 : c_kind(a.cls[a.sv[q]]) == ODP_ALLOC;
     }
 }
 
@@ -1333,6 +1341,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
 
     const int bits_n = prim::bit_length(n);              // keys < n + 1
     const int bits_slot = prim::bit_length(cap_max + 1);  // slot keys <= cap_max + 1
+    a.pack_alloc = bits_slot <= 31;
     const int gX = grid_for(n, sms);
     const int clear_grid = sms * 8;
 
