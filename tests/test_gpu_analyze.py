@@ -88,6 +88,27 @@ def test_random_medium_traces(cuda_ok, orc, odp):
         check(odp, orc, with_fp(b))
 
 
+@pytest.mark.parametrize("where", ["near_2_64", "span_over_2_63"])
+def test_extreme_time_ranges(cuda_ok, orc, odp, where):
+    """Times near 2^64 ns and kernel spans over 2^63 ns (the widest buckets
+    of the per-device kernel index, whose bucket starts saturate): Alg. 4
+    and 5 still agree with the oracle."""
+    b = traces.random_small(77, n_ops=5000, n_contents=30, n_hosts=20, n_devices=3, d2d=True)
+    ev = with_fp(b).copy()
+    t0 = ev["t_start_ns"].astype(object)
+    t1 = ev["t_end_ns"].astype(object)
+    lo, hi = min(t0), max(t1)
+    if where == "near_2_64":
+        base, scale = (1 << 64) - 1 - (hi - lo) * 4, 4
+    else:
+        base, scale = 0, ((1 << 63) + (1 << 62)) // (hi - lo)
+    ev["t_start_ns"] = np.array([base + (t - lo) * scale for t in t0], dtype=np.uint64)
+    ev["t_end_ns"] = np.array([base + (t - lo) * scale for t in t1], dtype=np.uint64)
+    assert int(ev["t_end_ns"].max()) < (1 << 64)
+    g = check(odp, orc, ev)
+    assert g["summary"]["count4"] + g["summary"]["count5"] > 0
+
+
 def test_exhaustive_two_endpoint_rt(cuda_ok, orc, odp):
     # every direction pattern of length 6 over 2 contents, concatenated with
     # distinct content ids per pattern so the groups stay independent
