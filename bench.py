@@ -328,6 +328,8 @@ def run_ours(args):
         result["analysis"] = bench_analysis(args, odp, dist, rank, stream, peak, peak_kind)
     if "serving" in parts:
         result["serving"] = bench_serving(args, odp, dist, rank, stream)
+        if args.serve_sweep:
+            result["serving"]["rate_sweep"] = serving_rate_sweep(args, odp, rank)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist is not None:
@@ -446,6 +448,41 @@ def bench_batched(args, odp, dist, rank, stream, peak, peak_kind):
     del arena, out, out_s, graph
     torch.cuda.empty_cache()
     return res
+
+
+def serving_rate_sweep(args, odp, rank):
+    """Latency and sustained rate of the serving loop at higher offered
+    rates (same producers and payloads, shorter runs so the log fits)."""
+    import torch
+    from synth import content, gpu as sgpu, load
+
+    pool_bytes = 1 << 30
+    pool = torch.empty(pool_bytes, dtype=torch.uint8, device="cuda")
+    sgpu.fill(pool, content.RANDOM, 0x0DB6 + rank)
+    torch.cuda.synchronize()
+    rows = []
+    for rate in [float(x) for x in args.serve_sweep.split(",")]:
+        cap = 1 << 23
+        secs = min(args.serve_sweep_seconds, 0.9 * cap / rate)  # the log holds the run
+        srv = odp.Server(n_slots=4, device_budget_bytes=8 << 30, max_events=cap,
+                         max_batch_events=8192, max_producers=128, watermark_timeout_us=50_000)
+        lg = load.Load(64, rate, secs, 0x0DB6 + rank, pool.data_ptr(), pool_bytes, 256, 64 << 20)
+        n = lg.run(srv, announce=args.serve_stamp == "begin")
+        srv.flush()
+        st = srv.stats()
+        span_s = (st["last_done_ns"] - st["first_submit_ns"]) / 1e9
+        rows.append({"offered_events_per_s": rate, "seconds": round(secs, 2), "events": n,
+                     "sustained_events_per_s": round(st["events_processed"] / span_s, 1),
+                     "p50_ms": round(st["latency_p50_ns"] / 1e6, 3),
+                     "p99_ms": round(st["latency_p99_ns"] / 1e6, 3),
+                     "before_launch_p99_ms": round(st["queue_p99_ns"] / 1e6, 3),
+                     "batches": st["batches"], "late_events": st["late_events"],
+                     "stream_overflow": st["stream_overflow"]})
+        srv.close()
+        lg.close()
+    del pool
+    torch.cuda.empty_cache()
+    return rows
 
 
 def bench_serving(args, odp, dist, rank, stream):
@@ -763,6 +800,9 @@ def main():
     ap.add_argument("--per-buffer-sample", type=int, default=20_000)
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-rate", type=float, default=200_000.0)
+    ap.add_argument("--serve-sweep", default="",
+                    help="comma list of offered rates (events/s) for an extra latency sweep")
+    ap.add_argument("--serve-sweep-seconds", type=float, default=5.0)
     ap.add_argument("--serve-stamp", default="begin", choices=["begin", "self"],
                     help="producers open each event with odp_server_begin (the merge waits only "
                          "for open events) or stamp it themselves (the merge waits for every "
