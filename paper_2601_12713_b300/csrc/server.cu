@@ -767,14 +767,15 @@ struct odp_server {
     cudaStream_t an_stream = nullptr;
     std::vector<odp::Slot> slots;
     uint32_t find_cap = 0;
+    // merged events not yet in a batch (batcher thread)
+    std::deque<odp::Pending> ready;
+    std::deque<uint32_t> ready_prod;
     // host bookkeeping (guarded by mu)
     uint64_t n_log = 0;       // events released into the log
     uint64_t n_done = 0;      // events whose batch completed
     std::vector<uint64_t> submit_ns;
     std::vector<uint32_t> origin_prod;
     std::vector<uint64_t> origin_seq;
-    std::deque<odp::Pending> ready;
-    std::deque<uint32_t> ready_prod;
     std::deque<odp_finding> outq;
     std::vector<uint64_t> latencies;
     std::vector<uint64_t> queue_lat;  // submit -> launch of the reporting batch
@@ -785,7 +786,7 @@ struct odp_server {
     odp::SlotDev fl;              // flush-time finding buffers (find, complete, nfind)
     odp_finding* h_fl_find = nullptr;
     uint32_t* h_fl_n = nullptr;
-    int error = ODP_OK;
+    std::atomic<int> error{ODP_OK};
 };
 
 namespace odp {
@@ -1076,8 +1077,9 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     const uint64_t find_cap = 3 * B + pend_cap + 64;
     // device bytes: log + per-event arrays + four persistent tables + slots
     const uint64_t per_table = 32 * ((uint64_t)cap_p + 1);
-    const uint64_t slot_bytes = B * (64 + 8 + 8 + 16 + 4 + 12 + 16 + 16) + 256ull * (B / 4096 + 2) * 4 +
-                                find_cap * (48 + 8) + (20ull << 20) + (46ull << 20);
+    const uint64_t slot_bytes = B * (64 + 8 + 8 + 16 + 4 + 12 + 16 + 16 + 12) +
+                                256ull * (B / 4096 + 2) * 4 + 2048 + find_cap * (48 + 8) +
+                                (20ull << 20) + (46ull << 20);
     const uint64_t need = E * (64 + 12) + 7 * per_table + 32 * ((uint64_t)cap_b + 1) +
                           40ull * pend_cap + ((uint64_t)cfg->n_slots + 1) * slot_bytes;
     if (cfg->device_budget_bytes && need > cfg->device_budget_bytes) return ODP_ERR_OOM;
