@@ -36,7 +36,6 @@ namespace {
 
 using prim::Key128;
 using prim::NONE32;
-using prim::Table;
 
 constexpr uint32_t NOPART = 0xFFFFFFFEu;  // flagged without a partner
 constexpr unsigned long long NO_ERR = ~0ull;
@@ -93,8 +92,8 @@ struct A {
     uint64_t *ks, *ke;    // kernels sorted by device: start, running max of end
     uint32_t *dstart, *dend;  // kernel ranges per device, indexed by device number + 1
     unsigned long long* sites;  // [5][65536][3]
-    Table tab;
-    prim::KeyTable ktab;  // the same memory as tab, 16-byte slots
+    prim::SplitTable tab;  // keys, then values: content ids (Alg. 1/2), then Alg. 3
+    prim::KeyTable ktab;   // the same memory as tab, keys only
     odp_findings out;
 };
 
@@ -264,7 +263,7 @@ __global__ void k_x_insert_fp(A a) {
                                    : make_uint4(0, 0, 0, 0);
             key[b] = Key128{((uint64_t)f.w << 32) | f.z, ((uint64_t)g.y << 32) | g.x};
         }
-        prim::table_insert_batch<INS_B, true, false>(a.tab, cap, key, e, use, out);
+        prim::table_insert_batch<INS_B, true, false, true>(a.tab, cap, key, e, use, out);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b)
             if (use[b]) a.slot[j0 + b * str] = slot_key(a, out[b], e[b]);
@@ -279,7 +278,7 @@ __global__ void k_x_cid(A a) {
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) sl[b] = j0 + b * str < n ? a.slot[j0 + b * str] : NONE32;
 #pragma unroll
-        for (int b = 0; b < INS_B; ++b) v[b] = sl[b] != NONE32 ? a.tab.slots[sl[b]].v : 0;
+        for (int b = 0; b < INS_B; ++b) v[b] = sl[b] != NONE32 ? a.tab.vals[sl[b]] : 0;
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             const uint32_t j = j0 + b * str;
@@ -587,7 +586,7 @@ __global__ void k_p_insert(A a) {
             key[b] = use[b] ? Key128{a.ev.daddr(e[b]), (uint64_t)c_dst(c)} : Key128{0, 0};
             flag[b] = a.pack_alloc && c_kind(c) == ODP_ALLOC ? 0x80000000u : 0u;
         }
-        prim::table_insert_batch<INS_B, false, true>(a.ktab, cap, key, e, use, out);
+        prim::table_insert_batch<INS_B, false, true, false>(a.ktab, cap, key, e, use, out);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             if (!use[b]) continue;
@@ -691,7 +690,7 @@ __global__ void k_ra_insert(A a) {
             key[b] = use[b] ? Key128{a.ev.host(e[b]), a.ev.bytes(e[b]) | ((uint64_t)c_dst(a.cls[e[b]]) << 56)}
                             : Key128{0, 0};
         }
-        prim::table_insert_batch<INS_B, true, true>(a.tab, cap, key, e, use, out);
+        prim::table_insert_batch<INS_B, true, true, true>(a.tab, cap, key, e, use, out);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b)
             if (in[b]) a.slot[j0 + b * str] = out[b];
@@ -706,7 +705,7 @@ __global__ void k_ra_flag(A a) {
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) sl[b] = j0 + b * str < n ? a.slot[j0 + b * str] : NONE32;
 #pragma unroll
-        for (int b = 0; b < INS_B; ++b) first[b] = sl[b] != NONE32 ? a.tab.slots[sl[b]].v : NONE32;
+        for (int b = 0; b < INS_B; ++b) first[b] = sl[b] != NONE32 ? a.tab.vals[sl[b]] : NONE32;
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             if (sl[b] == NONE32) continue;
@@ -865,7 +864,7 @@ __global__ void k_ut_insert(A a) {
             e[b] = use[b] ? a.sv[q] : 0;
             key[b] = use[b] ? Key128{a.ev.host(e[b]), 1} : Key128{0, 0};
         }
-        prim::table_insert_batch<INS_B, false, true>(a.ktab, cap, key, e, use, out);
+        prim::table_insert_batch<INS_B, false, true, false>(a.ktab, cap, key, e, use, out);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             const uint32_t q = q0 + b * str;
@@ -1323,7 +1322,8 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     uint32_t* sflag = (uint32_t*)(b + o_sflag);
     uint32_t* spos = (uint32_t*)(b + o_spos);
     uint32_t* misc = (uint32_t*)(b + o_misc);  // [0] total findings, [1] site rows, [2] scan total, [3] sort histogram length
-    a.tab.slots = (prim::Slot*)(b + o_tslots);
+    a.tab.keys = (Key128*)(b + o_tslots);
+    a.tab.vals = (uint32_t*)(b + o_tslots + sizeof(Key128) * ((size_t)cap_max + 1));
     a.tab.cap_max = cap_max;
     a.tab.cap_dev = &a.h->tcap;
     a.ktab.keys = (Key128*)(b + o_tslots);

@@ -480,6 +480,18 @@ struct Table {
     __device__ __forceinline__ uint32_t* val_at(uint32_t s) const { return &slots[s].v; }
 };
 
+// Keys and values in two arrays (16 + 4 bytes a slot): a probe touches a
+// 16-byte key, and the values, read back by slot after the inserts, sit in
+// an array a quarter the size of the keys (mostly in L2 at the sizes used).
+struct SplitTable {
+    Key128* keys;       // capacity + 1 slots (the last one holds the all-ones key)
+    uint32_t* vals;     // capacity + 1 values
+    uint32_t cap_max;
+    uint32_t* cap_dev;
+    __device__ __forceinline__ Key128* key_at(uint32_t s) const { return &keys[s]; }
+    __device__ __forceinline__ uint32_t* val_at(uint32_t s) const { return &vals[s]; }
+};
+
 // Keys only, 16 bytes a slot: for grouping, where the slot index is the
 // group key and no value is kept.
 struct KeyTable {
@@ -520,6 +532,20 @@ __global__ void table_clear(Table t, const uint32_t* count_dev, uint32_t count_m
         w[2 * (size_t)slot] = empty_key;
         w[2 * (size_t)slot + 1] = empty_val;
     }
+}
+
+// The same for a split table: keys, then values (NONE32), 16 bytes a write.
+__global__ void table_clear(SplitTable t, const uint32_t* count_dev, uint32_t count_max) {
+    const uint32_t cap = table_cap(dev_len(count_dev, count_max), t.cap_max);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t.cap_dev = cap;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    uint4* wk = reinterpret_cast<uint4*>(t.keys);
+    uint4* wv = reinterpret_cast<uint4*>(t.vals);
+    const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= cap; i += stride)
+        wk[i == cap ? t.cap_max : i] = ones;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap / 4; i += stride) wv[i] = ones;
+    if (blockIdx.x == 0 && threadIdx.x == 0) t.vals[t.cap_max] = NONE32;
 }
 
 // The same for a key-only table (one 16-byte write per slot).
@@ -610,8 +636,9 @@ __device__ __forceinline__ uint32_t table_insert(const Table& t, uint32_t cap, K
 // each slot before the compare-and-swap (peek_slot), which pays where many
 // inserts repeat a few keys (the atomics would queue on them) and costs a
 // round trip where most keys are new or rarely repeated in a table far
-// larger than L2.
-template <int B, bool MIN, bool PEEK, class TableT>
+// larger than L2.  LOWER: read the value before lowering it (lower_to),
+// which spares the atomic when an earlier insert already set a smaller one.
+template <int B, bool MIN, bool PEEK, bool LOWER, class TableT>
 __device__ __forceinline__ void table_insert_batch(const TableT& t, uint32_t cap, const Key128* k,
                                                    const uint32_t* v, const bool* use,
                                                    uint32_t* out) {
@@ -649,7 +676,7 @@ __device__ __forceinline__ void table_insert_batch(const TableT& t, uint32_t cap
         for (int b = 0; b < B; ++b) {
             if (done[b]) continue;
             if (seen[b] != PEEK_OTHER && (key_eq(cur[b], empty) || key_eq(cur[b], k[b]))) {
-                if (MIN && PEEK) lower_to(t.val_at(slot[b]), v[b]);
+                if (MIN && LOWER) lower_to(t.val_at(slot[b]), v[b]);
                 else if (MIN) atomicMin(t.val_at(slot[b]), v[b]);
                 out[b] = slot[b];
                 done[b] = true;
