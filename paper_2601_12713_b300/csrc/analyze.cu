@@ -1058,7 +1058,7 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
             // Round 2: partner sites, the RT partner's times and bytes, the UA
             // partner's and the RA delete's times.
             uint32_t psite[5];
-    #pragma unroll
+#pragma unroll
             for (int kind = 0; kind < 5; ++kind) {
                 const uint32_t p = part[kind];
                 psite[kind] = (p != NONE32 && p != NOPART)
@@ -1077,7 +1077,7 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
             // Stores.
             const uint64_t t0 = lohi(o0.x, o0.y), t1 = lohi(o0.z, o0.w), own_bytes = lohi(o2.x, o2.y);
             const uint32_t site = o3.z;
-    #pragma unroll
+#pragma unroll
             for (int kind = 0; kind < 5; ++kind) {
                 const uint32_t p = part[kind];
                 if (p == NONE32) continue;
