@@ -26,8 +26,8 @@ __device__ __forceinline__ uint32_t dev_len(const uint32_t* n_dev, uint32_t n_ma
 
 // ------------------------------------------------------------------ scan
 
-constexpr int SCAN_THREADS = 1024;
-constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 16;  // consecutive items per thread, moved as four 16-byte words
 constexpr uint32_t SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 // Single-pass exclusive scan with decoupled look-back: blocks take tiles from
@@ -48,7 +48,7 @@ constexpr uint32_t SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 // when a captured graph replays the same launch).
 constexpr uint32_t SCAN_WAIT_LIMIT = 1u << 20;
 
-__global__ void __launch_bounds__(SCAN_THREADS)
+__global__ void __launch_bounds__(SCAN_THREADS, 3)
 scan_chained(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t n_max,
              uint32_t* total, uint32_t* tmp, uint32_t* fault) {
     __shared__ uint32_t sm[40];
@@ -59,6 +59,7 @@ scan_chained(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t 
     const uint32_t epoch = *(volatile uint32_t*)(tmp + 2) & 0x3FFFFFFFu;
     const unsigned long long tag = (unsigned long long)epoch << 34;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0 && total) *total = 0;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(tmp, 1u);
@@ -66,13 +67,25 @@ scan_chained(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t 
         const uint32_t t = s_tile;
         if (t >= ntiles) break;
         const uint32_t base = t * SCAN_TILE;
+        const uint32_t i0 = base + threadIdx.x * SCAN_ITEMS;
+        const bool whole = vec && i0 + SCAN_ITEMS <= n;
         uint32_t v[SCAN_ITEMS], sum = 0;
+        if (whole) {
+            const uint4* p = reinterpret_cast<const uint4*>(in + i0);
 #pragma unroll
-        for (int k = 0; k < SCAN_ITEMS; ++k) {
-            const uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
-            v[k] = i < n ? in[i] : 0;
-            sum += v[k];
+            for (int q = 0; q < SCAN_ITEMS / 4; ++q) {
+                const uint4 w = p[q];
+                v[4 * q] = w.x;
+                v[4 * q + 1] = w.y;
+                v[4 * q + 2] = w.z;
+                v[4 * q + 3] = w.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < SCAN_ITEMS; ++k) v[k] = i0 + k < n ? in[i0 + k] : 0;
         }
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) sum += v[k];
         uint32_t tot;
         uint32_t e = block_exclusive_scan_u32(sum, &tot, sm);
         if (warp == 0) {
@@ -121,9 +134,19 @@ scan_chained(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t 
         e += s_prefix;
 #pragma unroll
         for (int k = 0; k < SCAN_ITEMS; ++k) {
-            const uint32_t i = base + threadIdx.x * SCAN_ITEMS + k;
-            if (i < n) out[i] = e;
-            e += v[k];
+            const uint32_t x = v[k];
+            v[k] = e;
+            e += x;
+        }
+        if (whole) {
+            uint4* p = reinterpret_cast<uint4*>(out + i0);
+#pragma unroll
+            for (int q = 0; q < SCAN_ITEMS / 4; ++q)
+                p[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < SCAN_ITEMS; ++k)
+                if (i0 + k < n) out[i0 + k] = v[k];
         }
         if (t == ntiles - 1 && threadIdx.x == 0 && total) *total = s_prefix + tot;
         __syncthreads();  // s_tile, s_prefix and sm are reused by the next tile
@@ -161,7 +184,7 @@ inline void exclusive_scan(const uint32_t* in, uint32_t* out, const uint32_t* n_
         return;
     }
     const uint32_t nb = (n_max + SCAN_TILE - 1) / SCAN_TILE;
-    scan_chained<<<tile_grid(nb, 2), SCAN_THREADS, 0, s>>>(in, out, n_dev, n_max, total, tmp,
+    scan_chained<<<tile_grid(nb, 3), SCAN_THREADS, 0, s>>>(in, out, n_dev, n_max, total, tmp,
                                                            fault);
 }
 
