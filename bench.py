@@ -500,7 +500,8 @@ def bench_serving(args, odp, dist, rank, stream):
     secs = args.serve_seconds
     max_events = 1 << 23
     srv = odp.Server(n_slots=4, device_budget_bytes=8 << 30, max_events=max_events,
-                     max_batch_events=8192, max_producers=128, watermark_timeout_us=50_000)
+                     max_batch_events=8192, max_producers=128, watermark_timeout_us=50_000,
+                     batch_interval_us=args.serve_interval_us)
     lg = load.Load(64, rate, secs, 0x0DB5 + rank, pool.data_ptr(), pool_bytes, 256, 64 << 20)
     n = lg.run(srv, announce=args.serve_stamp == "begin")
     srv.flush()
@@ -800,6 +801,8 @@ def main():
     ap.add_argument("--per-buffer-sample", type=int, default=20_000)
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-rate", type=float, default=200_000.0)
+    ap.add_argument("--serve-interval-us", type=int, default=50,
+                    help="batcher polling period of the serving loop")
     ap.add_argument("--serve-sweep", default="",
                     help="comma list of offered rates (events/s) for an extra latency sweep")
     ap.add_argument("--serve-sweep-seconds", type=float, default=5.0)

@@ -343,8 +343,9 @@ constexpr size_t SMALL_SORT_SMEM = 4ull * SMALL_SORT_MAX * 4 + 32ull * 256 * 4;
 // 256 items (index order: round-major, then lane) against its own digit
 // counters, the counters are scanned across warps and digits, and the items
 // move to the other buffer.  One launch instead of five per pass.
-__global__ void __launch_bounds__(SMALL_SORT_THREADS)
-sort_small(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, uint32_t n_max, int key_bits) {
+__device__ __forceinline__ void sort_small_body(uint32_t* keys, uint32_t* vals,
+                                                const uint32_t* n_dev, uint32_t n_max,
+                                                int key_bits) {
     constexpr int W = SMALL_SORT_THREADS / 32;
     constexpr int ROUNDS = SMALL_SORT_MAX / SMALL_SORT_THREADS;
     extern __shared__ __align__(16) uint32_t small_sm[];
@@ -415,6 +416,12 @@ sort_small(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, uint32_t n_max
         keys[i] = k0[i];
         vals[i] = v0[i];
     }
+}
+
+__global__ void __launch_bounds__(SMALL_SORT_THREADS) sort_small(uint32_t* keys, uint32_t* vals,
+                                                                 const uint32_t* n_dev,
+                                                                 uint32_t n_max, int key_bits) {
+    sort_small_body(keys, vals, n_dev, n_max, key_bits);
 }
 
 inline bool sort_small_ready() {
@@ -543,7 +550,8 @@ __device__ __forceinline__ uint32_t table_cap(uint32_t cnt, uint32_t cap_max) {
 // Set the capacity in use to the smallest power of two >= 1.25 * count (at
 // least 1024, at most cap_max; load stays <= 0.8) and clear it with whole
 // 32-byte slot writes.
-__global__ void table_clear(Table t, const uint32_t* count_dev, uint32_t count_max) {
+__device__ __forceinline__ void table_clear_body(Table t, const uint32_t* count_dev,
+                                                 uint32_t count_max) {
     const uint32_t cap = table_cap(dev_len(count_dev, count_max), t.cap_max);
     if (blockIdx.x == 0 && threadIdx.x == 0) *t.cap_dev = cap;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -555,6 +563,10 @@ __global__ void table_clear(Table t, const uint32_t* count_dev, uint32_t count_m
         w[2 * (size_t)slot] = empty_key;
         w[2 * (size_t)slot + 1] = empty_val;
     }
+}
+
+__global__ void table_clear(Table t, const uint32_t* count_dev, uint32_t count_max) {
+    table_clear_body(t, count_dev, count_max);
 }
 
 // The same for a split table: keys, then values (NONE32), 16 bytes a write.

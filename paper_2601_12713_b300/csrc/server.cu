@@ -204,7 +204,7 @@ __global__ void srv_scatter_fp(SlotDev s) {
 }
 
 // Content ids: insert <fingerprint> with the log index.
-__global__ void srv_insert_fp(SrvDev d, SlotDev s) {
+__device__ __forceinline__ void srv_insert_fp_body(SrvDev d, SlotDev s) {
     const uint64_t g0 = s.par->g0;
     const uint32_t m = s.par->m, cap = *d.t_fp.cap_dev;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
@@ -215,8 +215,10 @@ __global__ void srv_insert_fp(SrvDev d, SlotDev s) {
     }
 }
 
+__global__ void srv_insert_fp(SrvDev d, SlotDev s) { srv_insert_fp_body(d, s); }
+
 // cid; first-receiver and batch-first-receiver tables; endpoint sets.
-__global__ void srv_insert_dd(SrvDev d, SlotDev s) {
+__device__ __forceinline__ void srv_insert_dd_body(SrvDev d, SlotDev s) {
     const uint64_t g0 = s.par->g0;
     const uint32_t m = s.par->m;
     const uint32_t cap_dd = *d.t_dd.cap_dev, cap_b = *d.t_b.cap_dev, cap_ep = *d.t_ep.cap_dev;
@@ -254,6 +256,8 @@ __global__ void srv_insert_dd(SrvDev d, SlotDev s) {
     }
 }
 
+__global__ void srv_insert_dd(SrvDev d, SlotDev s) { srv_insert_dd_body(d, s); }
+
 __device__ __forceinline__ bool complex_group(const SrvDev& d, uint32_t cid) {
     const uint32_t cap = *d.t_ep.cap_dev;
     const uint32_t es = prim::table_insert_min(d.t_ep, cap, Key128{cid, 1}, NONE32);
@@ -263,7 +267,8 @@ __device__ __forceinline__ bool complex_group(const SrvDev& d, uint32_t cid) {
 
 // Duplicate transfers, and the first reception of each group at each
 // endpoint in this batch closes the round trips waiting for it.
-__global__ void srv_dd_resolve(SrvDev d, SlotDev s, uint32_t cap, uint64_t max_events) {
+__device__ __forceinline__ void srv_dd_resolve_body(SrvDev d, SlotDev s, uint32_t cap,
+                                                    uint64_t max_events) {
     const uint64_t g0 = s.par->g0;
     const uint32_t m = s.par->m, cap_pend = *d.t_pend.cap_dev;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
@@ -285,8 +290,12 @@ __global__ void srv_dd_resolve(SrvDev d, SlotDev s, uint32_t cap, uint64_t max_e
     }
 }
 
+__global__ void srv_dd_resolve(SrvDev d, SlotDev s, uint32_t cap, uint64_t max_events) {
+    srv_dd_resolve_body(d, s, cap, max_events);
+}
+
 // Sort keys: content id of each transfer, value = batch position.
-__global__ void srv_sort_keys(SrvDev d, SlotDev s) {
+__device__ __forceinline__ void srv_sort_keys_body(SrvDev d, SlotDev s) {
     const uint64_t g0 = s.par->g0;
     const uint32_t nx = *s.nx;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nx; j += gridDim.x * blockDim.x) {
@@ -296,10 +305,12 @@ __global__ void srv_sort_keys(SrvDev d, SlotDev s) {
     }
 }
 
+__global__ void srv_sort_keys(SrvDev d, SlotDev s) { srv_sort_keys_body(d, s); }
+
 // In-batch round trips on the content-sorted transfers: the partner of a
 // transfer is the first event of the next destination run of its group;
 // transfers without one wait in the group's list for their source.
-__global__ void srv_rt_batch(SrvDev d, SlotDev s, uint32_t cap) {
+__device__ __forceinline__ void srv_rt_batch_body(SrvDev d, SlotDev s, uint32_t cap) {
     const uint64_t g0 = s.par->g0;
     const uint32_t nx = *s.nx;
     const uint32_t cap_pend = *d.t_pend.cap_dev;
@@ -323,9 +334,11 @@ __global__ void srv_rt_batch(SrvDev d, SlotDev s, uint32_t cap) {
     }
 }
 
+__global__ void srv_rt_batch(SrvDev d, SlotDev s, uint32_t cap) { srv_rt_batch_body(d, s, cap); }
+
 // Alloc/delete events of the batch keyed by their <device address, device>
 // slot (other events sort last); value = batch position.
-__global__ void srv_pair_keys(SrvDev d, SlotDev s) {
+__device__ __forceinline__ void srv_pair_keys_body(SrvDev d, SlotDev s) {
     const uint64_t g0 = s.par->g0;
     const uint32_t m = s.par->m;
     const uint32_t cap = *d.t_pair.cap_dev, none_key = d.t_pair.cap_max + 1;
@@ -341,10 +354,12 @@ __global__ void srv_pair_keys(SrvDev d, SlotDev s) {
     }
 }
 
+__global__ void srv_pair_keys(SrvDev d, SlotDev s) { srv_pair_keys_body(d, s); }
+
 // One thread per address group of the batch (sorted, batch order inside)
 // walks it: ALLOC pushes on the address's open-alloc stack, DELETE pops the
 // nearest open ALLOC and records the pair.  Kernels of the batch are listed.
-__global__ void srv_pair_walk(SrvDev d, SlotDev s) {
+__device__ __forceinline__ void srv_pair_walk_body(SrvDev d, SlotDev s) {
     const uint64_t g0 = s.par->g0;
     const uint32_t m = s.par->m;
     const uint32_t none_key = d.t_pair.cap_max + 1;
@@ -368,17 +383,21 @@ __global__ void srv_pair_walk(SrvDev d, SlotDev s) {
     }
 }
 
+__global__ void srv_pair_walk(SrvDev d, SlotDev s) { srv_pair_walk_body(d, s); }
+
 __device__ __forceinline__ Key128 rid_key(const odp_event& e) {
     return Key128{e.host_addr, e.bytes | ((uint64_t)ep_of(e.dst_dev) << 56)};
 }
 
-__global__ void srv_ra_insert(SrvDev d, SlotDev s) {
+__device__ __forceinline__ void srv_ra_insert_body(SrvDev d, SlotDev s) {
     const uint32_t cap = *d.t_rid.cap_dev, n = s.cnt[0];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         s.rslot[i] = prim::table_insert_min(d.t_rid, cap, rid_key(d.log[s.pa[i]]), s.pa[i]);
 }
 
-__global__ void srv_ra_emit(SrvDev d, SlotDev s, uint32_t cap) {
+__global__ void srv_ra_insert(SrvDev d, SlotDev s) { srv_ra_insert_body(d, s); }
+
+__device__ __forceinline__ void srv_ra_emit_body(SrvDev d, SlotDev s, uint32_t cap) {
     const uint32_t n = s.cnt[0];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (s.rslot[i] == NONE32) continue;
@@ -389,6 +408,8 @@ __global__ void srv_ra_emit(SrvDev d, SlotDev s, uint32_t cap) {
                s.pd[i]);
     }
 }
+
+__global__ void srv_ra_emit(SrvDev d, SlotDev s, uint32_t cap) { srv_ra_emit_body(d, s, cap); }
 
 // Some kernel of the batch on `dev` overlaps [lo, hi]: of the device's
 // kernels that start by hi (a prefix: the log is in start order), the
@@ -409,7 +430,7 @@ __device__ __forceinline__ bool batch_kernel_overlaps(const SrvDev& d, const Slo
 // and for the waiting pairs (against the batch's kernels); undecided pairs
 // whose delete ends before t_next (the start of every later event) are
 // unused, the rest wait in list `nxt`.
-__global__ void srv_ua(SrvDev d, SlotDev s, uint32_t cap) {
+__device__ __forceinline__ void srv_ua_body(SrvDev d, SlotDev s, uint32_t cap) {
     const uint64_t t_next = s.par->t_next;
     const uint32_t cur = *d.cur, nxt = cur ^ 1;
     const uint32_t n_new = s.cnt[0], n_old = min(d.npend[cur], d.pend_cap);
@@ -438,8 +459,10 @@ __global__ void srv_ua(SrvDev d, SlotDev s, uint32_t cap) {
     }
 }
 
+__global__ void srv_ua(SrvDev d, SlotDev s, uint32_t cap) { srv_ua_body(d, s, cap); }
+
 // Also flips the current waiting lists: the last kernel of a batch to read them.
-__global__ void srv_kmax(SrvDev d, SlotDev s) {
+__device__ __forceinline__ void srv_kmax_body(SrvDev d, SlotDev s) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *d.cur ^= 1u;
     const uint32_t nk = s.cnt[1];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += gridDim.x * blockDim.x) {
@@ -449,10 +472,12 @@ __global__ void srv_kmax(SrvDev d, SlotDev s) {
     }
 }
 
+__global__ void srv_kmax(SrvDev d, SlotDev s) { srv_kmax_body(d, s); }
+
 // To-device transfers of the batch: barriers drop out; a waiting transfer
 // gets its segment and is keyed by its <host address, device> slot (others
 // sort last).
-__global__ void srv_ut_keys(SrvDev d, SlotDev s) {
+__device__ __forceinline__ void srv_ut_keys_body(SrvDev d, SlotDev s) {
     const uint64_t g0 = s.par->g0;
     const uint32_t m = s.par->m;
     const uint32_t cap = *d.t_ut.cap_dev, none_key = d.t_ut.cap_max + 1;
@@ -475,11 +500,13 @@ __global__ void srv_ut_keys(SrvDev d, SlotDev s) {
     }
 }
 
+__global__ void srv_ut_keys(SrvDev d, SlotDev s) { srv_ut_keys_body(d, s); }
+
 // One thread per <host address, device> group of the batch, in order: a
 // transfer that follows the key's latest waiting transfer in the same
 // segment records an overwrite (into s.pa/s.pd, count s.cnt[2]); every
 // waiting transfer is listed (s.rslot, count s.cnt[3]).
-__global__ void srv_ut_walk(SrvDev d, SlotDev s) {
+__device__ __forceinline__ void srv_ut_walk_body(SrvDev d, SlotDev s) {
     const uint64_t g0 = s.par->g0;
     const uint32_t m = s.par->m;
     const uint32_t none_key = d.t_ut.cap_max + 1;
@@ -501,12 +528,14 @@ __global__ void srv_ut_walk(SrvDev d, SlotDev s) {
     }
 }
 
+__global__ void srv_ut_walk(SrvDev d, SlotDev s) { srv_ut_walk_body(d, s); }
+
 // Overwrites and waiting transfers, carried from earlier batches (list cur)
 // and new in this one: an overwrite whose segment a kernel of this batch
 // closes is reported if the later transfer starts before that kernel (else
 // it is a barrier); transfers whose segment stays open carry over to list
 // cur ^ 1.
-__global__ void srv_ut_resolve(SrvDev d, SlotDev s, uint32_t cap) {
+__device__ __forceinline__ void srv_ut_resolve_body(SrvDev d, SlotDev s, uint32_t cap) {
     const uint32_t cur = *d.cur, nxt = cur ^ 1;
     const uint32_t n_f = min(d.nut[cur], d.pend_cap), n_fb = s.cnt[2];
     const uint32_t n_o = min(d.nut[2 + cur], d.pend_cap), n_ob = s.cnt[3];
@@ -536,6 +565,10 @@ __global__ void srv_ut_resolve(SrvDev d, SlotDev s, uint32_t cap) {
             }
         }
     }
+}
+
+__global__ void srv_ut_resolve(SrvDev d, SlotDev s, uint32_t cap) {
+    srv_ut_resolve_body(d, s, cap);
 }
 
 // Flush: every waiting pair is unused (no kernel follows the end of the
@@ -572,7 +605,7 @@ __global__ void srv_zero(uint32_t* p) { *p = 0; }
 
 // First step of a batch: append its events to the log; reset the batch's
 // counters and the counts of the next waiting lists.
-__global__ void srv_append(SrvDev d, SlotDev s) {
+__device__ __forceinline__ void srv_append_body(SrvDev d, SlotDev s) {
     const uint32_t m = s.par->m;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *s.nfind = 0;
@@ -588,6 +621,8 @@ __global__ void srv_append(SrvDev d, SlotDev s) {
         dst[i] = src[i];
 }
 
+__global__ void srv_append(SrvDev d, SlotDev s) { srv_append_body(d, s); }
+
 // The batch's kernels grouped by device, in log (= start) order within each
 // device, with the running maximum of their ends (one block; three ordered
 // passes: compaction, stable scatter by device, per-device max scan).  The
@@ -595,7 +630,7 @@ __global__ void srv_append(SrvDev d, SlotDev s) {
 // searches; s.cnt[1] receives the count.
 constexpr int BKI_THREADS = 1024;
 
-__global__ void __launch_bounds__(BKI_THREADS) srv_bk_index(SrvDev d, SlotDev s) {
+__device__ __forceinline__ void srv_bk_index_body(SrvDev d, SlotDev s) {
     constexpr int W = BKI_THREADS / 32;
     __shared__ uint32_t wofs[W + 1];
     __shared__ uint32_t dbase[256];
@@ -690,6 +725,63 @@ __global__ void __launch_bounds__(BKI_THREADS) srv_bk_index(SrvDev d, SlotDev s)
             carry = __shfl_sync(ODP_FULL_MASK, v, 31);
         }
     }
+}
+
+__global__ void __launch_bounds__(BKI_THREADS) srv_bk_index(SrvDev d, SlotDev s) {
+    srv_bk_index_body(d, s);
+}
+
+// A batch of at most SRV_SMALL_BATCH events runs as one block: the steps of
+// the batch graph (enqueue_analysis) in the same order, with block barriers
+// instead of kernel boundaries (every step loops over the batch with all the
+// threads it is given) and the three sorts in shared memory.  A small batch
+// then costs one launch and no inter-kernel gaps.
+constexpr uint32_t SRV_SMALL_BATCH = 2048;
+constexpr int SRV_SMALL_THREADS = 1024;  // = BKI_THREADS = SMALL_SORT_THREADS
+
+__global__ void __launch_bounds__(SRV_SMALL_THREADS)
+srv_batch_small(SrvDev d, SlotDev s, uint32_t B, uint32_t cap, uint64_t max_events, int bits_cid,
+                int bits_pair, int bits_ut) {
+    const uint32_t* m_dev = &s.par->m;
+    srv_append_body(d, s);
+    __syncthreads();
+    srv_bk_index_body(d, s);
+    __syncthreads();
+    prim::table_clear_body(d.t_b, m_dev, B);
+    __syncthreads();
+    srv_insert_fp_body(d, s);
+    __syncthreads();
+    srv_insert_dd_body(d, s);
+    __syncthreads();
+    srv_dd_resolve_body(d, s, cap, max_events);
+    __syncthreads();
+    srv_sort_keys_body(d, s);
+    __syncthreads();
+    prim::sort_small_body(s.skeys, s.svals, s.nx, prim::SMALL_SORT_MAX, bits_cid);
+    __syncthreads();
+    srv_rt_batch_body(d, s, cap);
+    __syncthreads();
+    srv_pair_keys_body(d, s);
+    __syncthreads();
+    prim::sort_small_body(s.skeys, s.svals, m_dev, prim::SMALL_SORT_MAX, bits_pair);
+    __syncthreads();
+    srv_pair_walk_body(d, s);
+    __syncthreads();
+    srv_ra_insert_body(d, s);
+    __syncthreads();
+    srv_ra_emit_body(d, s, cap);
+    __syncthreads();
+    srv_ua_body(d, s, cap);
+    __syncthreads();
+    srv_ut_keys_body(d, s);
+    __syncthreads();
+    prim::sort_small_body(s.skeys, s.svals, m_dev, prim::SMALL_SORT_MAX, bits_ut);
+    __syncthreads();
+    srv_ut_walk_body(d, s);
+    __syncthreads();
+    srv_ut_resolve_body(d, s, cap);
+    __syncthreads();
+    srv_kmax_body(d, s);
 }
 
 // After the flush: the current waiting lists are empty.
@@ -787,6 +879,7 @@ struct odp_server {
     odp_finding* h_fl_find = nullptr;
     uint32_t* h_fl_n = nullptr;
     std::atomic<int> error{ODP_OK};
+    bool small_ok = false;  // srv_batch_small may take its shared memory
 };
 
 namespace odp {
@@ -903,7 +996,14 @@ void launch_batch(odp_server* S, Slot& sl) {
     // analysis, in batch order on one stream
     std::lock_guard<std::mutex> an_lk(S->an_mu);
     cudaStreamWaitEvent(as, sl.fp_done, 0);
-    if (cudaGraphLaunch(sl.an_graph, as) != cudaSuccess) S->error = ODP_ERR_CUDA;
+    if (m <= SRV_SMALL_BATCH && S->small_ok) {
+        const uint32_t B = S->cfg.max_batch_events;
+        srv_batch_small<<<1, SRV_SMALL_THREADS, prim::SMALL_SORT_SMEM, as>>>(
+            S->d, sl.d, B, S->find_cap, S->cfg.max_events, prim::bit_length(S->cfg.max_events),
+            prim::bit_length(S->d.t_pair.cap_max + 1), prim::bit_length(S->d.t_ut.cap_max + 1));
+    } else if (cudaGraphLaunch(sl.an_graph, as) != cudaSuccess) {
+        S->error = ODP_ERR_CUDA;
+    }
     // copy back the count and the findings a batch of m events usually has
     // at most; harvest fetches the rest when there are more
     sl.eager = (uint32_t)std::min<uint64_t>(S->find_cap, 2ull * m + 256);
@@ -1191,6 +1291,9 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
             return fail(ODP_ERR_CUDA);
         if ((rc = capture_analysis(S, sl)) != ODP_OK) return fail(rc);
     }
+    S->small_ok = cudaFuncSetAttribute(srv_batch_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)prim::SMALL_SORT_SMEM) == cudaSuccess;
+    if (!S->small_ok) cudaGetLastError();
     if (cudaStreamSynchronize(S->an_stream) != cudaSuccess) return fail(ODP_ERR_CUDA);
     S->submit_ns.assign(E, 0);
     S->latencies.reserve(E);  // no reallocation (under mu) while serving
