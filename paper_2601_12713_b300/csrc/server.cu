@@ -8,9 +8,11 @@
 // runs each through a slot: the payloads of its transfers are fingerprinted
 // on the slot's own stream (slots overlap), then, in order on the analysis
 // stream, the batch is appended to the log resident in device memory and the
-// duplicate-transfer (Alg. 1) and round-trip (Alg. 2) state kept in device
-// tables is updated.  Findings are copied to pinned host memory and handed to
-// the poll queue with their latency.
+// state of Algorithms 1-5 kept in device tables is updated: by one block
+// (srv_batch_small) for batches of up to 2,048 events, else by a CUDA graph
+// of the same steps captured per slot.  Each producer has its own lock;
+// findings are copied to pinned host memory and handed to the poll queue
+// with their latency.
 //
 // Streaming Alg. 1: table <fingerprint> -> first log index (content id) and
 // table <content id, destination> -> first receiver persist across batches;
@@ -31,8 +33,9 @@
 // in alloc order, i.e. unless allocations of one key nest.)
 // Streaming Alg. 4: an allocation is used iff some kernel on its device
 // overlaps [alloc start, delete end].  Kernels of earlier batches are summed
-// up by their largest end per device; kernels of the pair's batch are checked
-// one by one; a pair still undecided waits in a list until a batch starts
+// up by their largest end per device; the pair's batch's kernels are indexed
+// per device (start order, running maximum of ends) and searched by
+// bisection; a pair still undecided waits in a list until a batch starts
 // after its delete ends (no later kernel can overlap it) or a kernel of a
 // later batch overlaps it.  Flush ends the trace: waiting pairs are unused,
 // and allocations never deleted are checked against every kernel seen.
