@@ -83,7 +83,8 @@ struct A {
     Hdr* h;
     uint32_t* cls;
     uint32_t *X, *P, *K, *U;
-    uint32_t *dd, *rt, *ra, *ua, *ut, *del_of;
+    uint2* drt;  // per event: .x the Alg. 1 partner, .y the Alg. 2 partner (one 8-byte word)
+    uint32_t *ra, *ua, *ut, *del_of;
     uint32_t* wbits;      // wasted events, one bit per event
     uint8_t* bad;
     uint32_t *slot, *sk, *sv, *k2, *v2, *f1, *f2, *id1, *id2, *H, *R, *stk;
@@ -346,15 +347,17 @@ __global__ void k_rt_partner(A a) {
         if (a.bad[s]) continue;
         const uint32_t e = a.sv[q];
         const uint32_t r = a.id2[q] + a.f2[q] - 1;
+        uint32_t rt = NONE32;
         if (r + 1 < nrun) {
             const uint32_t q2 = a.R[r + 1];
-            if (!a.f1[q2]) a.rt[e] = a.sv[q2];
+            if (!a.f1[q2]) rt = a.sv[q2];
         }
         const uint32_t h = a.H[s];
         uint32_t first;
         if (c_dst(a.k2[q]) == c_dst(a.k2[h])) first = a.sv[h];
         else first = a.sv[a.R[a.id2[h] + 1]];
-        if (first != e) a.dd[e] = first;
+        // one write for both partners (the events scatter: one sector, not two)
+        if (rt != NONE32 || first != e) a.drt[e] = make_uint2(first != e ? first : NONE32, rt);
     }
 }
 
@@ -547,7 +550,7 @@ __global__ void k_mx_partner(A a) {
         const uint32_t q = a.v2[i];
         const uint32_t e = a.sv[q];
         const uint32_t head = a.R[a.id2[i] + a.f2[i] - 1];
-        if (head != i) a.dd[e] = a.sv[a.v2[head]];
+        if (head != i) a.drt[e].x = a.sv[a.v2[head]];
         const uint32_t xs = a.stk[i];
         if (xs == NONE32) continue;
         const uint32_t st = a.R[xs], en = a.R[xs + 1];
@@ -559,7 +562,7 @@ __global__ void k_mx_partner(A a) {
         }
         // successes among [st, lo): a.k2 = success flags, a.sk = their exclusive scan
         const uint32_t k = lo == st ? 0 : a.sk[lo - 1] + a.k2[lo - 1] - a.sk[st];
-        if (st + k < en) a.rt[e] = a.sv[a.v2[st + k]];
+        if (st + k < en) a.drt[e].y = a.sv[a.v2[st + k]];
     }
 }
 
@@ -894,8 +897,8 @@ __device__ __forceinline__ uint64_t lohi(uint32_t lo, uint32_t hi) { return ((ui
 
 __device__ __forceinline__ uint32_t partner_of(const A& a, int kind, uint32_t i) {
     switch (kind) {
-        case ODP_DD: return a.dd[i];
-        case ODP_RT: return a.rt[i];
+        case ODP_DD: return a.drt[i].x;
+        case ODP_RT: return a.drt[i].y;
         case ODP_RA: return a.ra[i];
         case ODP_UA: return a.ua[i];
         default: return a.ut[i];
@@ -904,8 +907,6 @@ __device__ __forceinline__ uint32_t partner_of(const A& a, int kind, uint32_t i)
 
 __device__ __forceinline__ const uint32_t* partner_array(const A& a, int kind) {
     switch (kind) {
-        case ODP_DD: return a.dd;
-        case ODP_RT: return a.rt;
         case ODP_RA: return a.ra;
         case ODP_UA: return a.ua;
         default: return a.ut;
@@ -936,9 +937,21 @@ __global__ void k_em_count(A a, uint32_t* wcnt, uint32_t nch) {
     for (uint32_t g = gw; g < nq; g += nw) {
         const uint32_t i0 = g * 128 + lane * 4;
         const uint32_t c = g * 4 + (lane >> 3);
+        // Alg. 1 and 2 partners of events i0..i0+3 (two 16-byte words of drt)
+        uint4 p0 = make_uint4(NONE32, NONE32, NONE32, NONE32), p1 = p0;
+        if (i0 + 4 <= a.n) {
+            p0 = __ldg(reinterpret_cast<const uint4*>(a.drt + i0));
+            p1 = __ldg(reinterpret_cast<const uint4*>(a.drt + i0 + 2));
+        } else {
+            if (i0 < a.n) p0.x = a.drt[i0].x, p0.y = a.drt[i0].y;
+            if (i0 + 1 < a.n) p0.z = a.drt[i0 + 1].x, p0.w = a.drt[i0 + 1].y;
+            if (i0 + 2 < a.n) p1.x = a.drt[i0 + 2].x, p1.y = a.drt[i0 + 2].y;
+        }
 #pragma unroll
         for (int kind = 1; kind <= 5; ++kind) {
-            const uint4 v = load4(partner_array(a, kind), i0, a.n, NONE32);
+            const uint4 v = kind == ODP_DD   ? make_uint4(p0.x, p0.z, p1.x, p1.z)
+                            : kind == ODP_RT ? make_uint4(p0.y, p0.w, p1.y, p1.w)
+                                             : load4(partner_array(a, kind), i0, a.n, NONE32);
             uint32_t k = (v.x != NONE32) + (v.y != NONE32) + (v.z != NONE32) + (v.w != NONE32);
             k += __shfl_xor_sync(ODP_FULL_MASK, k, 1);
             k += __shfl_xor_sync(ODP_FULL_MASK, k, 2);
@@ -1292,8 +1305,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     a.K = (uint32_t*)(b + o_K);
     a.U = (uint32_t*)(b + o_U);
     uint32_t* part = (uint32_t*)(b + o_part);
-    a.dd = part;
-    a.rt = part + PS;
+    a.drt = reinterpret_cast<uint2*>(part);  // two rows
     a.ra = part + 2 * PS;
     a.ua = part + 3 * PS;
     a.ut = part + 4 * PS;
