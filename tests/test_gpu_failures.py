@@ -86,3 +86,29 @@ def test_stalled_producer_does_not_block_serving(cuda_ok):
         th.join()
         srv.close()
         lg.close()
+
+
+def test_scan_lookback_wait_is_bounded(cuda_ok, tmp_path):
+    """The scan's look-back waits on status words of earlier tiles with a
+    bounded poll count.  A hook (tests/hooks/scan_timeout.cu) starts the tile
+    counter past tile 0, so the wait can only run out: the kernel ends, the
+    fault word is set (odp_analyze reports it as ODP_ERR_TIMEOUT), and a
+    normal scan right after is correct."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    so = str(tmp_path / "libscan_timeout.so")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-shared",
+                    "-Xcompiler", "-fPIC", "-I", os.path.join(root, "include"),
+                    "-I", os.path.join(root, "paper_2601_12713_b300", "csrc"),
+                    os.path.join(root, "tests", "hooks", "scan_timeout.cu"), "-o", so],
+                   check=True)
+    lib = ctypes.CDLL(so)
+    fault, correct = ctypes.c_uint32(0), ctypes.c_uint32(0)
+    assert lib.scan_timeout_case(ctypes.byref(fault), ctypes.byref(correct)) == 0
+    assert fault.value == 1
+    assert correct.value == 1
