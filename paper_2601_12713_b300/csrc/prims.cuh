@@ -336,27 +336,33 @@ inline size_t sort_hist_words(uint32_t n_max) {
 
 constexpr int SMALL_SORT_THREADS = 1024;
 constexpr uint32_t SMALL_SORT_MAX = 8192;  // 8 items per thread
-constexpr size_t SMALL_SORT_SMEM = 4ull * SMALL_SORT_MAX * 4 + 32ull * 256 * 4;
+// dynamic shared memory of a one-block sort of up to `max_items` items
+constexpr size_t small_sort_smem(uint32_t max_items) { return 4ull * max_items * 4 + 32ull * 256 * 4; }
+constexpr size_t SMALL_SORT_SMEM = small_sort_smem(SMALL_SORT_MAX);
 
 // Up to 8192 (key, value) pairs sorted stably by the low key_bits bits of
 // the keys by one block, in shared memory: per 8-bit digit, warp w ranks its
 // 256 items (index order: round-major, then lane) against its own digit
 // counters, the counters are scanned across warps and digits, and the items
 // move to the other buffer.  One launch instead of five per pass.
+// MAXN (a multiple of 1,024, at most SMALL_SORT_MAX) sizes the shared-memory
+// buffers: the caller launches with small_sort_smem(MAXN) bytes.
+template <uint32_t MAXN = SMALL_SORT_MAX>
 __device__ __forceinline__ void sort_small_body(uint32_t* keys, uint32_t* vals,
                                                 const uint32_t* n_dev, uint32_t n_max,
                                                 int key_bits) {
+    static_assert(MAXN % SMALL_SORT_THREADS == 0 && MAXN <= SMALL_SORT_MAX, "tile size");
     constexpr int W = SMALL_SORT_THREADS / 32;
-    constexpr int ROUNDS = SMALL_SORT_MAX / SMALL_SORT_THREADS;
+    constexpr int ROUNDS = MAXN / SMALL_SORT_THREADS;
     extern __shared__ __align__(16) uint32_t small_sm[];
     uint32_t* k0 = small_sm;
-    uint32_t* v0 = k0 + SMALL_SORT_MAX;
-    uint32_t* k1 = v0 + SMALL_SORT_MAX;
-    uint32_t* v1 = k1 + SMALL_SORT_MAX;
-    uint32_t(*cnt)[256] = reinterpret_cast<uint32_t(*)[256]>(v1 + SMALL_SORT_MAX);
+    uint32_t* v0 = k0 + MAXN;
+    uint32_t* k1 = v0 + MAXN;
+    uint32_t* v1 = k1 + MAXN;
+    uint32_t(*cnt)[256] = reinterpret_cast<uint32_t(*)[256]>(v1 + MAXN);
     __shared__ uint32_t scan_tmp[40];
     __shared__ uint32_t dstart[256];
-    const uint32_t n = min(dev_len(n_dev, n_max), SMALL_SORT_MAX);
+    const uint32_t n = min(dev_len(n_dev, n_max), MAXN);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1;
     for (uint32_t i = threadIdx.x; i < n; i += SMALL_SORT_THREADS) {

@@ -633,11 +633,12 @@ __global__ void srv_append(SrvDev d, SlotDev s) { srv_append_body(d, s); }
 // searches; s.cnt[1] receives the count.
 constexpr int BKI_THREADS = 1024;
 
-__device__ __forceinline__ void srv_bk_index_body(SrvDev d, SlotDev s) {
+// wdev_sm: W x 256 words of shared memory for the per-warp device counts.
+__device__ __forceinline__ void srv_bk_index_body(SrvDev d, SlotDev s, uint32_t* wdev_sm) {
     constexpr int W = BKI_THREADS / 32;
     __shared__ uint32_t wofs[W + 1];
     __shared__ uint32_t dbase[256];
-    __shared__ uint32_t wdev[W][256];
+    uint32_t(*wdev)[256] = reinterpret_cast<uint32_t(*)[256]>(wdev_sm);
     const uint64_t g0 = s.par->g0;
     const uint32_t m = s.par->m;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -731,14 +732,16 @@ __device__ __forceinline__ void srv_bk_index_body(SrvDev d, SlotDev s) {
 }
 
 __global__ void __launch_bounds__(BKI_THREADS) srv_bk_index(SrvDev d, SlotDev s) {
-    srv_bk_index_body(d, s);
+    __shared__ uint32_t wdev[BKI_THREADS / 32 * 256];
+    srv_bk_index_body(d, s, wdev);
 }
 
 // A batch of at most SRV_SMALL_BATCH events runs as one block: the steps of
 // the batch graph (enqueue_analysis) in the same order, with block barriers
 // instead of kernel boundaries (every step loops over the batch with all the
-// threads it is given) and the three sorts in shared memory.  A small batch
-// then costs one launch and no inter-kernel gaps.
+// threads it is given) and the three sorts in shared memory (sized for
+// SRV_SMALL_BATCH items, so the block fits beside fingerprint blocks on an
+// SM).  A small batch then costs one launch and no inter-kernel gaps.
 constexpr uint32_t SRV_SMALL_BATCH = 2048;
 constexpr int SRV_SMALL_THREADS = 1024;  // = BKI_THREADS = SMALL_SORT_THREADS
 
@@ -748,7 +751,8 @@ srv_batch_small(SrvDev d, SlotDev s, uint32_t B, uint32_t cap, uint64_t max_even
     const uint32_t* m_dev = &s.par->m;
     srv_append_body(d, s);
     __syncthreads();
-    srv_bk_index_body(d, s);
+    extern __shared__ __align__(16) uint32_t small_sm[];  // the sorts' buffers, free until then
+    srv_bk_index_body(d, s, small_sm);
     __syncthreads();
     prim::table_clear_body(d.t_b, m_dev, B);
     __syncthreads();
@@ -760,13 +764,13 @@ srv_batch_small(SrvDev d, SlotDev s, uint32_t B, uint32_t cap, uint64_t max_even
     __syncthreads();
     srv_sort_keys_body(d, s);
     __syncthreads();
-    prim::sort_small_body(s.skeys, s.svals, s.nx, prim::SMALL_SORT_MAX, bits_cid);
+    prim::sort_small_body<SRV_SMALL_BATCH>(s.skeys, s.svals, s.nx, SRV_SMALL_BATCH, bits_cid);
     __syncthreads();
     srv_rt_batch_body(d, s, cap);
     __syncthreads();
     srv_pair_keys_body(d, s);
     __syncthreads();
-    prim::sort_small_body(s.skeys, s.svals, m_dev, prim::SMALL_SORT_MAX, bits_pair);
+    prim::sort_small_body<SRV_SMALL_BATCH>(s.skeys, s.svals, m_dev, SRV_SMALL_BATCH, bits_pair);
     __syncthreads();
     srv_pair_walk_body(d, s);
     __syncthreads();
@@ -778,7 +782,7 @@ srv_batch_small(SrvDev d, SlotDev s, uint32_t B, uint32_t cap, uint64_t max_even
     __syncthreads();
     srv_ut_keys_body(d, s);
     __syncthreads();
-    prim::sort_small_body(s.skeys, s.svals, m_dev, prim::SMALL_SORT_MAX, bits_ut);
+    prim::sort_small_body<SRV_SMALL_BATCH>(s.skeys, s.svals, m_dev, SRV_SMALL_BATCH, bits_ut);
     __syncthreads();
     srv_ut_walk_body(d, s);
     __syncthreads();
@@ -1001,7 +1005,7 @@ void launch_batch(odp_server* S, Slot& sl) {
     cudaStreamWaitEvent(as, sl.fp_done, 0);
     if (m <= SRV_SMALL_BATCH && S->small_ok) {
         const uint32_t B = S->cfg.max_batch_events;
-        srv_batch_small<<<1, SRV_SMALL_THREADS, prim::SMALL_SORT_SMEM, as>>>(
+        srv_batch_small<<<1, SRV_SMALL_THREADS, prim::small_sort_smem(SRV_SMALL_BATCH), as>>>(
             S->d, sl.d, B, S->find_cap, S->cfg.max_events, prim::bit_length(S->cfg.max_events),
             prim::bit_length(S->d.t_pair.cap_max + 1), prim::bit_length(S->d.t_ut.cap_max + 1));
     } else if (cudaGraphLaunch(sl.an_graph, as) != cudaSuccess) {
@@ -1295,7 +1299,7 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
         if ((rc = capture_analysis(S, sl)) != ODP_OK) return fail(rc);
     }
     S->small_ok = cudaFuncSetAttribute(srv_batch_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)prim::SMALL_SORT_SMEM) == cudaSuccess;
+                                       (int)prim::small_sort_smem(SRV_SMALL_BATCH)) == cudaSuccess;
     if (!S->small_ok) cudaGetLastError();
     if (cudaStreamSynchronize(S->an_stream) != cudaSuccess) return fail(ODP_ERR_CUDA);
     S->submit_ns.assign(E, 0);
