@@ -499,7 +499,7 @@ def bench_serving(args, odp, dist, rank, stream):
     rate = args.serve_rate
     secs = args.serve_seconds
     max_events = 1 << 23
-    srv = odp.Server(n_slots=4, device_budget_bytes=8 << 30, max_events=max_events,
+    srv = odp.Server(n_slots=args.serve_slots, device_budget_bytes=8 << 30, max_events=max_events,
                      max_batch_events=8192, max_producers=128, watermark_timeout_us=50_000,
                      batch_interval_us=args.serve_interval_us)
     lg = load.Load(64, rate, secs, 0x0DB5 + rank, pool.data_ptr(), pool_bytes, 256, 64 << 20)
@@ -549,7 +549,7 @@ def bench_serving(args, odp, dist, rank, stream):
         "offline_batched_events_per_s": round(offline_rate, 1),
         "config": {"workload": f"64 producer threads, Poisson arrivals, {rate:.0f} events/s "
                                f"aggregate for {secs} s, payloads log-uniform 256 B..64 MiB "
-                               "(views of a 1 GiB device pool), 4 slots, 8192-event batches, "
+                               f"(views of a 1 GiB device pool), {args.serve_slots} slots, 8192-event batches, "
                                "8 GiB device budget", "events": n, "batches": st["batches"],
                    "start_stamps": ("odp_server_begin (the merge waits only for open events)"
                                     if args.serve_stamp == "begin" else
@@ -801,6 +801,7 @@ def main():
     ap.add_argument("--per-buffer-sample", type=int, default=20_000)
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-rate", type=float, default=200_000.0)
+    ap.add_argument("--serve-slots", type=int, default=4, help="batches in flight at most")
     ap.add_argument("--serve-interval-us", type=int, default=50,
                     help="batcher polling period of the serving loop")
     ap.add_argument("--serve-sweep", default="",
