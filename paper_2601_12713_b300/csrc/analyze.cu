@@ -198,23 +198,52 @@ __global__ void k_list_lengths(A a, const uint32_t* scanned, const uint32_t* tot
 }
 
 // Stable compaction of event indices into the four lists, a warp per chunk.
+// Four consecutive u32 from a 16-byte-aligned array (i0 % 4 == 0); entries at
+// or past n read as `fill`.
+__device__ __forceinline__ uint4 load4(const uint32_t* p, uint32_t i0, uint32_t n, uint32_t fill) {
+    if (i0 + 4 <= n) return __ldg(reinterpret_cast<const uint4*>(p + i0));
+    uint4 v = make_uint4(fill, fill, fill, fill);
+    if (i0 < n) v.x = p[i0];
+    if (i0 + 1 < n) v.y = p[i0 + 1];
+    if (i0 + 2 < n) v.z = p[i0 + 2];
+    return v;
+}
+
+// A warp takes 128 events (four chunks), four consecutive ones per lane;
+// each list's entries of the group are placed by a warp scan of the lanes'
+// counts after the group's scanned chunk offset.
 __global__ void __launch_bounds__(TPB) k_compact(A a, const uint32_t* scanned, uint32_t nch) {
     const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nq = (nch + 3) / 4;
     uint32_t* lists[4] = {a.X, a.P, a.K, a.U};
-    for (uint32_t c = gw; c < nch; c += nw) {
-        const uint32_t i = c * 32 + lane;
-        const uint32_t kd = i < a.n ? c_kind(a.cls[i]) : 0;
-        const bool pred[4] = {kd == ODP_TO_DEV || kd == ODP_FROM_DEV || kd == ODP_DEV_TO_DEV,
-                              kd == ODP_ALLOC || kd == ODP_DELETE, kd == ODP_KERNEL,
-                              kd == ODP_TO_DEV};
+    for (uint32_t g = gw; g < nq; g += nw) {
+        const uint32_t i0 = g * 128 + lane * 4;
+        const uint4 cl = load4(a.cls, i0, a.n, 0);
+        const uint32_t kd[4] = {c_kind(cl.x), c_kind(cl.y), c_kind(cl.z), c_kind(cl.w)};
 #pragma unroll
         for (int L = 0; L < 4; ++L) {
-            const uint32_t bal = __ballot_sync(ODP_FULL_MASK, pred[L]);
-            if (pred[L])
-                lists[L][scanned[L * nch + c] - scanned[L * nch] + __popc(bal & lt)] = i;
+            bool pred[4];
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t k = i0 + j < a.n ? kd[j] : 0u;
+                pred[j] = L == 0   ? k == ODP_TO_DEV || k == ODP_FROM_DEV || k == ODP_DEV_TO_DEV
+                          : L == 1 ? k == ODP_ALLOC || k == ODP_DELETE
+                          : L == 2 ? k == ODP_KERNEL
+                                   : k == ODP_TO_DEV;
+                cnt += pred[j];
+            }
+            uint32_t incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(ODP_FULL_MASK, incl, o);
+                if (lane >= o) incl += t;
+            }
+            uint32_t pos = scanned[L * nch + 4 * g] - scanned[L * nch] + incl - cnt;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (pred[j]) lists[L][pos++] = i0 + j;
         }
     }
 }
@@ -913,16 +942,6 @@ __device__ __forceinline__ const uint32_t* partner_array(const A& a, int kind) {
     }
 }
 
-// Four consecutive u32 from a 16-byte-aligned array (i0 % 4 == 0); entries at
-// or past n read as `fill`.
-__device__ __forceinline__ uint4 load4(const uint32_t* p, uint32_t i0, uint32_t n, uint32_t fill) {
-    if (i0 + 4 <= n) return __ldg(reinterpret_cast<const uint4*>(p + i0));
-    uint4 v = make_uint4(fill, fill, fill, fill);
-    if (i0 < n) v.x = p[i0];
-    if (i0 + 1 < n) v.y = p[i0 + 1];
-    if (i0 + 2 < n) v.z = p[i0 + 2];
-    return v;
-}
 
 // Findings per (kind, 32-event chunk) from the partner arrays alone, and
 // pair counts.  A warp takes 128 events (four chunks), four per lane with
