@@ -187,3 +187,24 @@ def test_fingerprint_one_equals_batched_call(cuda_ok, orc, odp):
     odp.fingerprint_one(0, 10, out1)  # null pointer with bytes: zero and a status
     assert odp.fingerprint_status() == -1
     assert out1.tolist() == [0, 0]
+
+
+def test_reference_vectors(cuda_ok, odp):
+    """The GPU reproduces the reference vectors of tests/golden (written by the
+    oracle), each buffer alone and all of them in one batched call."""
+    import sys
+
+    sys.path.insert(0, __import__("os").path.dirname(__file__))
+    from test_oracle_fp128 import load_vectors
+
+    vecs = load_vectors()
+    bufs = []
+    for _, data, _ in vecs:
+        t = torch.zeros(len(data) + 64, dtype=torch.uint8, device="cuda")
+        if data:
+            t[: len(data)] = torch.frombuffer(bytearray(data), dtype=torch.uint8).cuda()
+        bufs.append(t[: len(data)])
+    want = [w for _, _, w in vecs]
+    assert gpu_fp(odp, bufs) == want
+    for b, w in zip(bufs, want):
+        assert gpu_fp(odp, [b]) == [w]

@@ -307,3 +307,34 @@ def test_avalanche(orc):
         h1 = fp(orc, buf)
         flips.append(bin(h0[0] ^ h1[0]).count("1") + bin(h0[1] ^ h1[1]).count("1"))
     assert abs(np.mean(flips) - 64.0) < 2.0
+
+
+def load_vectors():
+    """(name, data, (lo, hi)) from tests/golden/fp128_vectors.txt with the
+    inputs of the script that wrote it."""
+    import importlib.util
+    import os
+
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_fp128_vectors",
+                                                  os.path.join(here, "make_fp128_vectors.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    data = dict(mod.inputs())
+    out = []
+    for line in open(os.path.join(here, "fp128_vectors.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, length, lo, hi = line.split()
+        assert len(data[name]) == int(length)
+        out.append((name, data[name], (int(lo, 16), int(hi, 16))))
+    return out
+
+
+def test_reference_vectors_reproduce():
+    import oracle
+
+    vecs = load_vectors()
+    assert len(vecs) == 8
+    for name, data, want in vecs:
+        assert oracle.fp128(data) == want, name
