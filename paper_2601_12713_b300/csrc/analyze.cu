@@ -52,6 +52,8 @@ struct Hdr {
     uint32_t nX, nP, nK, nU;
     uint32_t nseg, nrun, nseg2, nsegU;
     uint32_t nB, nsegB;  // transfers / endpoint segments of groups with > 2 endpoints
+    uint32_t any_bad;    // some content group has more than two endpoints
+    uint32_t mx_n;       // transfers the multi-endpoint path scans: nX if any_bad, else 0
     uint32_t nA;         // allocations (at most this many pairs go into the Alg. 3 table)
     uint32_t scan_fault; // a scan's bounded wait gave up (reported as ODP_ERR_TIMEOUT)
     uint32_t total_findings, n_site_rows;
@@ -356,11 +358,19 @@ __device__ __forceinline__ bool same_endpoints(uint32_t c, uint32_t d) {
 
 __global__ void k_rt_check(A a) {
     if (failed(a)) return;
+    __shared__ int blk_bad;
+    if (threadIdx.x == 0) blk_bad = 0;
+    __syncthreads();
     GRID_STRIDE(q, a.h->nX) {
         const uint32_t s = a.id1[q] + a.f1[q] - 1;
         const uint32_t h = a.H[s];
-        if (!same_endpoints(a.k2[q], a.k2[h])) a.bad[s] = 1;
+        if (!same_endpoints(a.k2[q], a.k2[h])) {
+            a.bad[s] = 1;
+            blk_bad = 1;
+        }
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && blk_bad) atomicOr(&a.h->any_bad, 1u);
 }
 
 // Two endpoints: a transfer pairs with the first event of the next run of
@@ -371,6 +381,8 @@ __global__ void k_rt_check(A a) {
 __global__ void k_rt_partner(A a) {
     if (failed(a)) return;
     const uint32_t nrun = a.h->nrun;
+    // the multi-endpoint passes that follow scan the transfers only if needed
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.h->mx_n = a.h->any_bad ? a.h->nX : 0u;
     GRID_STRIDE(q, a.h->nX) {
         const uint32_t s = a.id1[q] + a.f1[q] - 1;
         if (a.bad[s]) continue;
@@ -422,13 +434,13 @@ __device__ __forceinline__ uint32_t group_of(const A& a, uint32_t q) { return a.
 // flags of the transfers in groups with more than two endpoints
 __global__ void k_mx_flag(A a) {
     if (failed(a)) return;
-    GRID_STRIDE(q, a.h->nX) a.f2[q] = a.bad[group_of(a, q)];
+    GRID_STRIDE(q, a.h->mx_n) a.f2[q] = a.bad[group_of(a, q)];
 }
 
 // compacted list: key = destination, value = position in content order
 __global__ void k_mx_scatter(A a) {
     if (failed(a)) return;
-    GRID_STRIDE(q, a.h->nX) {
+    GRID_STRIDE(q, a.h->mx_n) {
         if (!a.f2[q]) continue;
         const uint32_t j = a.id2[q];
         a.k2[j] = c_dst(a.cls[a.sv[q]]);
@@ -1413,7 +1425,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     // groups with more than two endpoints
     uint32_t* nB = &a.h->nB;
     k_mx_flag<<<gX, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.f2, a.id2, nX, n, nB, scan_tmp, s, srt.fault);
+    prim::exclusive_scan(a.f2, a.id2, &a.h->mx_n, n, nB, scan_tmp, s, srt.fault);
     k_mx_scatter<<<gX, TPB, 0, s>>>(a);
     prim::radix_sort(a.k2, a.v2, nB, n, 8, srt, s);
     k_mx_gkey<<<gX, TPB, 0, s>>>(a);
