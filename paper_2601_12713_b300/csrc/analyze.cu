@@ -53,6 +53,8 @@ struct Hdr {
     uint32_t nseg, nrun, nseg2, nsegU;
     uint32_t nB, nsegB;  // transfers / endpoint segments of groups with > 2 endpoints
     uint32_t any_bad;    // some content group has more than two endpoints
+    uint32_t k_mixed, u_mixed;  // kernels / to-device transfers on more than one device
+    uint32_t k_sortn, u_sortn;  // entries their by-device sorts move (0: one device, in order)
     uint32_t mx_n;       // transfers the multi-endpoint path scans: nX if any_bad, else 0
     uint32_t nA;         // allocations (at most this many pairs go into the Alg. 3 table)
     uint32_t scan_fault; // a scan's bounded wait gave up (reported as ODP_ERR_TIMEOUT)
@@ -761,13 +763,29 @@ __global__ void k_ra_flag(A a) {
 
 // ------------------------------------------------------------ kernels
 
-__global__ void k_dev_keys(A a, const uint32_t* list, const uint32_t* count) {
+// Device keys of a list in time order; *mixed is set when they are not all
+// the device of the list's first entry.
+__global__ void k_dev_keys(A a, const uint32_t* list, const uint32_t* count, uint32_t* mixed) {
     if (failed(a)) return;
-    GRID_STRIDE(j, *count) {
+    __shared__ int blk_mixed;
+    if (threadIdx.x == 0) blk_mixed = 0;
+    __syncthreads();
+    const uint32_t n = *count;
+    const uint32_t d0 = n ? c_dst(a.cls[list[0]]) : 0u;
+    GRID_STRIDE(j, n) {
         const uint32_t e = list[j];
-        a.sk[j] = c_dst(a.cls[e]);
+        const uint32_t d = c_dst(a.cls[e]);
+        a.sk[j] = d;
         a.sv[j] = e;
+        if (d != d0) blk_mixed = 1;
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && blk_mixed) atomicOr(mixed, 1u);
+}
+
+// A list on one device is already sorted by device: its sort moves nothing.
+__global__ void k_sort_count(const uint32_t* count, const uint32_t* mixed, uint32_t* sort_n) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *sort_n = *mixed ? *count : 0u;
 }
 
 __global__ void k_k_bounds(A a) {
@@ -1456,8 +1474,9 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     k_ra_flag<<<gX, TPB, 0, s>>>(a);
 
     // ---- kernels per device
-    k_dev_keys<<<gX, TPB, 0, s>>>(a, a.K, nK);
-    prim::radix_sort(a.sk, a.sv, nK, n, 8, srt, s);
+    k_dev_keys<<<gX, TPB, 0, s>>>(a, a.K, nK, &a.h->k_mixed);
+    k_sort_count<<<1, 32, 0, s>>>(nK, &a.h->k_mixed, &a.h->k_sortn);
+    prim::radix_sort(a.sk, a.sv, &a.h->k_sortn, n, 8, srt, s);
     k_k_bounds<<<gX, TPB, 0, s>>>(a);
     k_k_pmax<<<NDEV, PMAX_THREADS, 0, s>>>(a);
 
@@ -1465,8 +1484,9 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     k_ua<<<gX, TPB, 0, s>>>(a);
 
     // ---- Alg. 5
-    k_dev_keys<<<gX, TPB, 0, s>>>(a, a.U, nU);
-    prim::radix_sort(a.sk, a.sv, nU, n, 8, srt, s);
+    k_dev_keys<<<gX, TPB, 0, s>>>(a, a.U, nU, &a.h->u_mixed);
+    k_sort_count<<<1, 32, 0, s>>>(nU, &a.h->u_mixed, &a.h->u_sortn);
+    prim::radix_sort(a.sk, a.sv, &a.h->u_sortn, n, 8, srt, s);
     k_ut_class<<<gX, TPB, 0, s>>>(a);
     k_ut_heads<<<gX, TPB, 0, s>>>(a);
     prim::exclusive_scan(a.f1, a.id1, nU, n, &a.h->nsegU, scan_tmp, s, srt.fault);
