@@ -1093,7 +1093,7 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
     for (uint32_t c = gw; c < nch; c += nw) {
         const uint32_t i = c * 32 + lane;
         const bool valid = i < a.n;
-        // Round 1: the partner arrays, and with them (before knowing whether
+        // First loads: the partner arrays, and with them (before knowing whether
         // the event has a finding) its own record and the delete that closes
         // it, so a chunk waits for memory twice, not three times.
         uint32_t part[5];
@@ -1117,7 +1117,7 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
         if (lane == 0 && own) own_old = atomicOr(a.wbits + c, own);
         if (any & (1u << lane)) {
             const uint32_t d = part[ODP_RA - 1] != NONE32 ? del : NONE32;
-            // Round 2: partner sites, the RT partner's times and bytes, the UA
+            // Second loads: partner sites, the RT partner's times and bytes, the UA
             // partner's and the RA delete's times.
             uint32_t psite[5];
 #pragma unroll
