@@ -107,6 +107,7 @@ __device__ __forceinline__ bool failed(const A& a) { return a.h->err != NO_ERR; 
 #define GRID_STRIDE(i, n) \
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
+
 // ------------------------------------------------------------ validate
 
 // Record checks on the fields of one event (loaded as three 16-byte words).
@@ -130,6 +131,7 @@ __device__ __forceinline__ bool record_ok(uint64_t t0, uint64_t t1, uint64_t by,
 // One warp per 32-event chunk: record checks, order check, class word,
 // per-(list, chunk) counts for the four lists.
 __global__ void __launch_bounds__(TPB) k_validate(A a, uint32_t* ccnt, uint32_t nch) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(TPB) k_validate(A a, uint32_t* ccnt, uint32_t 
 
 // list lengths from the scanned chunk counts (scan covers 4 * nch)
 __global__ void k_list_lengths(A a, const uint32_t* scanned, const uint32_t* total, uint32_t nch) {
+    pdl_entry();
     if (threadIdx.x != 0) return;
     a.h->nX = scanned[1 * nch] - scanned[0];
     a.h->nP = scanned[2 * nch] - scanned[1 * nch];
@@ -217,6 +220,7 @@ __device__ __forceinline__ uint4 load4(const uint32_t* p, uint32_t i0, uint32_t 
 // each list's entries of the group are placed by a warp scan of the lanes'
 // counts after the group's scanned chunk offset.
 __global__ void __launch_bounds__(TPB) k_compact(A a, const uint32_t* scanned, uint32_t nch) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -276,6 +280,7 @@ constexpr int INS_B = 4;
          j0 += INS_B * gridDim.x * blockDim.x)
 
 __global__ void k_x_insert_fp(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t cap = *a.tab.cap_dev;
     const uint32_t n = a.h->nX, str = gridDim.x * blockDim.x;
@@ -305,6 +310,7 @@ __global__ void k_x_insert_fp(A a) {
 }
 
 __global__ void k_x_cid(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t n = a.h->nX, str = gridDim.x * blockDim.x;
     BATCH_STRIDE(j0, n) {
@@ -328,6 +334,7 @@ __global__ void k_x_cid(A a) {
 // Group and run heads; the class word of each sorted transfer is gathered
 // once into a.k2 (in sorted order) for the passes that follow.
 __global__ void k_rt_flags(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(q, a.h->nX) {
         const bool head = q == 0 || a.sk[q] != a.sk[q - 1];
@@ -340,6 +347,7 @@ __global__ void k_rt_flags(A a) {
 }
 
 __global__ void k_rt_starts(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t n = a.h->nX;
     GRID_STRIDE(q, n) {
@@ -359,6 +367,7 @@ __device__ __forceinline__ bool same_endpoints(uint32_t c, uint32_t d) {
 }
 
 __global__ void k_rt_check(A a) {
+    pdl_entry();
     if (failed(a)) return;
     __shared__ int blk_bad;
     if (threadIdx.x == 0) blk_bad = 0;
@@ -381,6 +390,7 @@ __global__ void k_rt_check(A a) {
 // receiver of <content, destination> is the group head when the destination
 // matches the head's, else the start of the group's second run.
 __global__ void k_rt_partner(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t nrun = a.h->nrun;
     // the multi-endpoint passes that follow scan the transfers only if needed
@@ -435,12 +445,14 @@ __device__ __forceinline__ uint32_t group_of(const A& a, uint32_t q) { return a.
 
 // flags of the transfers in groups with more than two endpoints
 __global__ void k_mx_flag(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(q, a.h->mx_n) a.f2[q] = a.bad[group_of(a, q)];
 }
 
 // compacted list: key = destination, value = position in content order
 __global__ void k_mx_scatter(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(q, a.h->mx_n) {
         if (!a.f2[q]) continue;
@@ -451,12 +463,14 @@ __global__ void k_mx_scatter(A a) {
 }
 
 __global__ void k_mx_gkey(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(i, a.h->nB) a.k2[i] = group_of(a, a.v2[i]);
 }
 
 // Ld[i] = destination (in a.slot), segment heads (in a.f2), group starts.
 __global__ void k_mx_heads(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(i, a.h->nB) {
         const uint32_t s = a.k2[i];
@@ -473,6 +487,7 @@ __global__ void k_mx_heads(A a) {
 // segment bit 0 = late from code 128, bit 1 = allOK, bit 2 = late from an
 // endpoint that never receives.
 __global__ void k_mx_starts(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t nB = a.h->nB;
     uint4* mask = reinterpret_cast<uint4*>(a.ks);
@@ -503,6 +518,7 @@ __device__ __forceinline__ uint32_t mx_last(const A& a, uint32_t g) { return a.v
 // destination segment's set (one atomic per distinct (segment, source) of a
 // warp).
 __global__ void k_mx_late(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t nB = a.h->nB;
     const int lane = threadIdx.x & 31;
@@ -537,6 +553,7 @@ __global__ void k_mx_late(A a) {
 
 // Per group: allOK of its endpoints in increasing order of last reception.
 __global__ void k_mx_ok(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t nseg = a.h->nseg;
     const uint4* mask = reinterpret_cast<const uint4*>(a.ks);
@@ -577,6 +594,7 @@ __global__ void k_mx_ok(A a) {
 
 // Per reception: success (in a.k2, scanned into a.sk next).
 __global__ void k_mx_succ(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(i, a.h->nB) {
         const uint32_t xs = a.stk[i];
@@ -588,6 +606,7 @@ __global__ void k_mx_succ(A a) {
 
 // Per transfer: Alg. 1 inside its segment, Alg. 2 partner.
 __global__ void k_mx_partner(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(i, a.h->nB) {
         const uint32_t q = a.v2[i];
@@ -612,6 +631,7 @@ __global__ void k_mx_partner(A a) {
 // ------------------------------------------------------------- pairs
 
 __global__ void k_p_insert(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t cap = *a.ktab.cap_dev;
     const uint32_t n = a.h->nP, str = gridDim.x * blockDim.x;
@@ -646,6 +666,7 @@ __global__ void k_p_insert(A a) {
 // ALLOC into a.k2 (in sorted order): from bit 31 of the sort key where the
 // sort carried it there, else gathered from the class words.
 __global__ void k_seg_heads(A a, const uint32_t* count) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t m = a.pack_alloc ? 0x7FFFFFFFu : 0xFFFFFFFFu;
     GRID_STRIDE(q, *count) {
@@ -656,6 +677,7 @@ __global__ void k_seg_heads(A a, const uint32_t* count) {
 }
 
 __global__ void k_seg_starts(A a, const uint32_t* count, const uint32_t* nseg) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t n = *count;
     GRID_STRIDE(q, n) {
@@ -670,6 +692,7 @@ __device__ __forceinline__ bool is_alloc(const A& a, uint32_t e) {
 }
 
 __global__ void k_p_check(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(q, a.h->nP) {
         const uint32_t s = a.id1[q] + a.f1[q] - 1;
@@ -683,6 +706,7 @@ __global__ void k_p_check(A a) {
 }
 
 __global__ void k_p_match(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(q, a.h->nP) {
         const uint32_t s = a.id1[q] + a.f1[q] - 1;
@@ -694,6 +718,7 @@ __global__ void k_p_match(A a) {
 
 // Non-alternating groups: a DELETE closes the nearest earlier open ALLOC.
 __global__ void k_p_literal(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(s, a.h->nseg2) {
         if (!a.bad[s]) continue;
@@ -717,6 +742,7 @@ __global__ void k_p_literal(A a) {
 // ------------------------------------------------------------- Alg. 3
 
 __global__ void k_ra_insert(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t cap = *a.tab.cap_dev;
     const uint32_t n = a.h->nP, str = gridDim.x * blockDim.x;
@@ -744,6 +770,7 @@ __global__ void k_ra_insert(A a) {
 }
 
 __global__ void k_ra_flag(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t n = a.h->nP, str = gridDim.x * blockDim.x;
     BATCH_STRIDE(j0, n) {
@@ -766,6 +793,7 @@ __global__ void k_ra_flag(A a) {
 // Device keys of a list in time order; *mixed is set when they are not all
 // the device of the list's first entry.
 __global__ void k_dev_keys(A a, const uint32_t* list, const uint32_t* count, uint32_t* mixed) {
+    pdl_entry();
     if (failed(a)) return;
     __shared__ int blk_mixed;
     if (threadIdx.x == 0) blk_mixed = 0;
@@ -785,10 +813,12 @@ __global__ void k_dev_keys(A a, const uint32_t* list, const uint32_t* count, uin
 
 // A list on one device is already sorted by device: its sort moves nothing.
 __global__ void k_sort_count(const uint32_t* count, const uint32_t* mixed, uint32_t* sort_n) {
+    pdl_entry();
     if (blockIdx.x == 0 && threadIdx.x == 0) *sort_n = *mixed ? *count : 0u;
 }
 
 __global__ void k_k_bounds(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t n = a.h->nK;
     GRID_STRIDE(q, n) {
@@ -805,6 +835,7 @@ __global__ void k_k_bounds(A a) {
 constexpr int PMAX_THREADS = 1024;
 
 __global__ void __launch_bounds__(PMAX_THREADS) k_k_pmax(A a) {
+    pdl_entry();
     if (failed(a)) return;
     __shared__ unsigned long long wmax[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -849,6 +880,7 @@ __device__ __forceinline__ uint32_t first_kernel(const A& a, uint32_t d, uint64_
 // ------------------------------------------------------------- Alg. 4
 
 __global__ void k_ua(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint64_t trace_end = a.h->t_end_max;
     const uint32_t n = a.h->nP, str = gridDim.x * blockDim.x;
@@ -881,6 +913,7 @@ __global__ void k_ua(A a) {
 // ------------------------------------------------------------- Alg. 5
 
 __global__ void k_ut_class(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(q, a.h->nU) {
         const uint32_t e = a.sv[q];
@@ -902,6 +935,7 @@ __global__ void k_ut_class(A a) {
 }
 
 __global__ void k_ut_heads(A a) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(q, a.h->nU) {
         a.f1[q] = q == 0 || a.sk[q] != a.sk[q - 1] || a.pq[q] != a.pq[q - 1] || a.uc[q - 1] == 1;
@@ -912,6 +946,7 @@ __global__ void k_ut_heads(A a) {
 // stays in L2); the group key is the address's slot, non-candidates get
 // cap_max + 1 (above every slot).
 __global__ void k_ut_insert(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t cap = *a.ktab.cap_dev;
     const uint32_t n = a.h->nU, str = gridDim.x * blockDim.x;
@@ -940,6 +975,7 @@ __global__ void k_ut_insert(A a) {
 // After the stable sort by host group, a candidate is overwritten by the
 // next candidate of its group when both lie in the same segment.
 __global__ void k_ut_next(A a) {
+    pdl_entry();
     if (failed(a)) return;
     const uint32_t nU = a.h->nU;
     GRID_STRIDE(r, nU) {
@@ -977,6 +1013,7 @@ __device__ __forceinline__ const uint32_t* partner_array(const A& a, int kind) {
 // pair counts.  A warp takes 128 events (four chunks), four per lane with
 // 16-byte loads; lanes 8k..8k+7 sum chunk k.
 __global__ void k_em_count(A a, uint32_t* wcnt, uint32_t nch) {
+    pdl_entry();
     if (failed(a)) return;
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1073,6 +1110,7 @@ __device__ __forceinline__ uint64_t mark_wasted(const A& a, uint32_t e, uint64_t
 }
 
 __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* wscan, uint32_t nch) {
+    pdl_entry();
     if (failed(a)) return;
     extern __shared__ __align__(16) unsigned char em_dyn[];
     SiteSmem& st = *reinterpret_cast<SiteSmem*>(em_dyn);
@@ -1194,6 +1232,7 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
 // the per-kind totals of the summary as sums of the rows (every finding was
 // added to exactly one row).  A warp's 32 rows share one kind.
 __global__ void k_site_flags(A a, uint32_t* flags) {
+    pdl_entry();
     const bool bad = failed(a);
     GRID_STRIDE(r, 5u * ODP_MAX_SITES) {
         const unsigned long long* row = a.sites + 3ull * r;
@@ -1214,6 +1253,7 @@ __global__ void k_site_flags(A a, uint32_t* flags) {
 }
 
 __global__ void k_site_write(A a, const uint32_t* flags, const uint32_t* pos) {
+    pdl_entry();
     if (failed(a)) return;
     GRID_STRIDE(r, 5u * ODP_MAX_SITES) {
         if (!flags[r] || pos[r] >= a.out.sites_capacity) continue;
@@ -1229,6 +1269,7 @@ __global__ void k_site_write(A a, const uint32_t* flags, const uint32_t* pos) {
 }
 
 __global__ void k_finalize(A a, const uint32_t* n_findings, const uint32_t* n_rows) {
+    pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     odp_summary* S = a.out.summary;
     const Hdr* h = a.h;
@@ -1268,6 +1309,7 @@ __global__ void k_finalize(A a, const uint32_t* n_findings, const uint32_t* n_ro
 }
 
 __global__ void k_empty_outputs(odp_findings out) {
+    pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     uint64_t* z = (uint64_t*)out.summary;
     for (size_t k = 0; k < sizeof(odp_summary) / 8; ++k) z[k] = 0;
@@ -1277,6 +1319,14 @@ __global__ void k_empty_outputs(odp_findings out) {
 }
 
 }  // namespace
+
+// prim::table_clear for table type T (the overload picked by type).
+template <class T>
+void clear_table(bool P, const T& t, const uint32_t* count, uint32_t count_max, int grid,
+                 cudaStream_t s) {
+    void (*kernel)(T, const uint32_t*, uint32_t) = prim::table_clear;
+    pdl_if(P, kernel, grid, TPB, 0, s, t, count, count_max);
+}
 
 static int grid_for(uint64_t n, int sms) {
     uint64_t g = (n + TPB - 1) / TPB;
@@ -1296,7 +1346,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     if (((uintptr_t)events & 15) != 0) return ODP_ERR_INVALID_ARG;  // records are read as 16-byte words
     if (n64 >= 0xFFFFFFF0ull) return ODP_ERR_UNSUPPORTED;
     if (n64 == 0) {
-        k_empty_outputs<<<1, 1, 0, s>>>(out);
+        pdl(k_empty_outputs, 1, 1, 0, s, out);
         return cuda_status(cudaGetLastError());
     }
     const uint32_t n = (uint32_t)n64;
@@ -1398,6 +1448,9 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     srt.scan_tmp = (uint32_t*)(b + o_scan);
     srt.hlen = misc + 3;
     srt.fault = &a.h->scan_fault;
+    // programmatic dependent launch for the whole chain of a small call
+    const bool P = n <= prim::PDL_MAX_ITEMS;
+    srt.pdl = P;
     uint32_t* scan_tmp = srt.scan_tmp;
 
     const int bits_n = prim::bit_length(n);              // keys < n + 1
@@ -1418,88 +1471,88 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     // ---- validate, lists
     uint32_t* ccnt = (uint32_t*)(b + o_wcnt);
     uint32_t* cscan = (uint32_t*)(b + o_wscan);
-    k_validate<<<sms * 16, TPB, 0, s>>>(a, ccnt, nch);
-    prim::exclusive_scan(ccnt, cscan, nullptr, 4 * nch, misc + 2, scan_tmp, s, srt.fault);
-    k_list_lengths<<<1, 32, 0, s>>>(a, cscan, misc + 2, nch);
-    k_compact<<<sms * 16, TPB, 0, s>>>(a, cscan, nch);
+    pdl_if(P, k_validate, sms * 16, TPB, 0, s, a, ccnt, nch);
+    prim::exclusive_scan(ccnt, cscan, nullptr, 4 * nch, misc + 2, scan_tmp, s, srt.fault, P);
+    pdl_if(P, k_list_lengths, 1, 32, 0, s, a, cscan, misc + 2, nch);
+    pdl_if(P, k_compact, sms * 16, TPB, 0, s, a, cscan, nch);
     uint32_t* nX = &a.h->nX;
     uint32_t* nP = &a.h->nP;
     uint32_t* nK = &a.h->nK;
     uint32_t* nU = &a.h->nU;
 
     // ---- Alg. 1: content ids, first receivers
-    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, nX, n);
-    k_x_insert_fp<<<gX, TPB, 0, s>>>(a);
-    k_x_cid<<<gX, TPB, 0, s>>>(a);
+    clear_table(P, a.tab, nX, n, clear_grid, s);
+    pdl_if(P, k_x_insert_fp, gX, TPB, 0, s, a);
+    pdl_if(P, k_x_cid, gX, TPB, 0, s, a);
 
     // ---- Alg. 2
     prim::radix_sort(a.sk, a.sv, nX, n, bits_n, srt, s);
-    k_rt_flags<<<gX, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.f1, a.id1, nX, n, &a.h->nseg, scan_tmp, s, srt.fault);
-    prim::exclusive_scan(a.f2, a.id2, nX, n, &a.h->nrun, scan_tmp, s, srt.fault);
-    k_rt_starts<<<gX, TPB, 0, s>>>(a);
-    k_rt_check<<<gX, TPB, 0, s>>>(a);
-    k_rt_partner<<<gX, TPB, 0, s>>>(a);
+    pdl_if(P, k_rt_flags, gX, TPB, 0, s, a);
+    prim::exclusive_scan(a.f1, a.id1, nX, n, &a.h->nseg, scan_tmp, s, srt.fault, P);
+    prim::exclusive_scan(a.f2, a.id2, nX, n, &a.h->nrun, scan_tmp, s, srt.fault, P);
+    pdl_if(P, k_rt_starts, gX, TPB, 0, s, a);
+    pdl_if(P, k_rt_check, gX, TPB, 0, s, a);
+    pdl_if(P, k_rt_partner, gX, TPB, 0, s, a);
     // groups with more than two endpoints
     uint32_t* nB = &a.h->nB;
-    k_mx_flag<<<gX, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.f2, a.id2, &a.h->mx_n, n, nB, scan_tmp, s, srt.fault);
-    k_mx_scatter<<<gX, TPB, 0, s>>>(a);
+    pdl_if(P, k_mx_flag, gX, TPB, 0, s, a);
+    prim::exclusive_scan(a.f2, a.id2, &a.h->mx_n, n, nB, scan_tmp, s, srt.fault, P);
+    pdl_if(P, k_mx_scatter, gX, TPB, 0, s, a);
     prim::radix_sort(a.k2, a.v2, nB, n, 8, srt, s);
-    k_mx_gkey<<<gX, TPB, 0, s>>>(a);
+    pdl_if(P, k_mx_gkey, gX, TPB, 0, s, a);
     prim::radix_sort(a.k2, a.v2, nB, n, bits_n, srt, s);
-    k_mx_heads<<<gX, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.f2, a.id2, nB, n, &a.h->nsegB, scan_tmp, s, srt.fault);
-    k_mx_starts<<<gX, TPB, 0, s>>>(a);
-    k_mx_late<<<gX, TPB, 0, s>>>(a);
-    k_mx_ok<<<gX, TPB, 0, s>>>(a);
-    k_mx_succ<<<gX, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.k2, a.sk, nB, n, nullptr, scan_tmp, s, srt.fault);
-    k_mx_partner<<<gX, TPB, 0, s>>>(a);
+    pdl_if(P, k_mx_heads, gX, TPB, 0, s, a);
+    prim::exclusive_scan(a.f2, a.id2, nB, n, &a.h->nsegB, scan_tmp, s, srt.fault, P);
+    pdl_if(P, k_mx_starts, gX, TPB, 0, s, a);
+    pdl_if(P, k_mx_late, gX, TPB, 0, s, a);
+    pdl_if(P, k_mx_ok, gX, TPB, 0, s, a);
+    pdl_if(P, k_mx_succ, gX, TPB, 0, s, a);
+    prim::exclusive_scan(a.k2, a.sk, nB, n, nullptr, scan_tmp, s, srt.fault, P);
+    pdl_if(P, k_mx_partner, gX, TPB, 0, s, a);
 
     // ---- pairs
-    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.ktab, nP, n);
-    k_p_insert<<<gX, TPB, 0, s>>>(a);
+    clear_table(P, a.ktab, nP, n, clear_grid, s);
+    pdl_if(P, k_p_insert, gX, TPB, 0, s, a);
     prim::radix_sort(a.sk, a.sv, nP, n, bits_slot, srt, s);
-    k_seg_heads<<<gX, TPB, 0, s>>>(a, nP);
-    prim::exclusive_scan(a.f1, a.id1, nP, n, &a.h->nseg2, scan_tmp, s, srt.fault);
-    k_seg_starts<<<gX, TPB, 0, s>>>(a, nP, &a.h->nseg2);
-    k_p_check<<<gX, TPB, 0, s>>>(a);
-    k_p_match<<<gX, TPB, 0, s>>>(a);
-    k_p_literal<<<gX, TPB, 0, s>>>(a);
+    pdl_if(P, k_seg_heads, gX, TPB, 0, s, a, nP);
+    prim::exclusive_scan(a.f1, a.id1, nP, n, &a.h->nseg2, scan_tmp, s, srt.fault, P);
+    pdl_if(P, k_seg_starts, gX, TPB, 0, s, a, nP, &a.h->nseg2);
+    pdl_if(P, k_p_check, gX, TPB, 0, s, a);
+    pdl_if(P, k_p_match, gX, TPB, 0, s, a);
+    pdl_if(P, k_p_literal, gX, TPB, 0, s, a);
 
     // ---- Alg. 3
-    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.tab, &a.h->nA, n);
-    k_ra_insert<<<gX, TPB, 0, s>>>(a);
-    k_ra_flag<<<gX, TPB, 0, s>>>(a);
+    clear_table(P, a.tab, &a.h->nA, n, clear_grid, s);
+    pdl_if(P, k_ra_insert, gX, TPB, 0, s, a);
+    pdl_if(P, k_ra_flag, gX, TPB, 0, s, a);
 
     // ---- kernels per device
-    k_dev_keys<<<gX, TPB, 0, s>>>(a, a.K, nK, &a.h->k_mixed);
-    k_sort_count<<<1, 32, 0, s>>>(nK, &a.h->k_mixed, &a.h->k_sortn);
+    pdl_if(P, k_dev_keys, gX, TPB, 0, s, a, a.K, nK, &a.h->k_mixed);
+    pdl_if(P, k_sort_count, 1, 32, 0, s, nK, &a.h->k_mixed, &a.h->k_sortn);
     prim::radix_sort(a.sk, a.sv, &a.h->k_sortn, n, 8, srt, s);
-    k_k_bounds<<<gX, TPB, 0, s>>>(a);
-    k_k_pmax<<<NDEV, PMAX_THREADS, 0, s>>>(a);
+    pdl_if(P, k_k_bounds, gX, TPB, 0, s, a);
+    pdl_if(P, k_k_pmax, NDEV, PMAX_THREADS, 0, s, a);
 
     // ---- Alg. 4
-    k_ua<<<gX, TPB, 0, s>>>(a);
+    pdl_if(P, k_ua, gX, TPB, 0, s, a);
 
     // ---- Alg. 5
-    k_dev_keys<<<gX, TPB, 0, s>>>(a, a.U, nU, &a.h->u_mixed);
-    k_sort_count<<<1, 32, 0, s>>>(nU, &a.h->u_mixed, &a.h->u_sortn);
+    pdl_if(P, k_dev_keys, gX, TPB, 0, s, a, a.U, nU, &a.h->u_mixed);
+    pdl_if(P, k_sort_count, 1, 32, 0, s, nU, &a.h->u_mixed, &a.h->u_sortn);
     prim::radix_sort(a.sk, a.sv, &a.h->u_sortn, n, 8, srt, s);
-    k_ut_class<<<gX, TPB, 0, s>>>(a);
-    k_ut_heads<<<gX, TPB, 0, s>>>(a);
-    prim::exclusive_scan(a.f1, a.id1, nU, n, &a.h->nsegU, scan_tmp, s, srt.fault);
-    prim::table_clear<<<clear_grid, TPB, 0, s>>>(a.ktab, nU, n);
-    k_ut_insert<<<gX, TPB, 0, s>>>(a);
+    pdl_if(P, k_ut_class, gX, TPB, 0, s, a);
+    pdl_if(P, k_ut_heads, gX, TPB, 0, s, a);
+    prim::exclusive_scan(a.f1, a.id1, nU, n, &a.h->nsegU, scan_tmp, s, srt.fault, P);
+    clear_table(P, a.ktab, nU, n, clear_grid, s);
+    pdl_if(P, k_ut_insert, gX, TPB, 0, s, a);
     prim::radix_sort(a.k2, a.v2, nU, n, bits_slot, srt, s);
-    k_ut_next<<<gX, TPB, 0, s>>>(a);
+    pdl_if(P, k_ut_next, gX, TPB, 0, s, a);
 
     // ---- emission
     uint32_t* wcnt = (uint32_t*)(b + o_wcnt);
     uint32_t* wscan = (uint32_t*)(b + o_wscan);
-    k_em_count<<<sms * 8, 256, 0, s>>>(a, wcnt, nch);
-    prim::exclusive_scan(wcnt, wscan, nullptr, 5 * nch, misc + 0, scan_tmp, s, srt.fault);
+    pdl_if(P, k_em_count, sms * 8, 256, 0, s, a, wcnt, nch);
+    prim::exclusive_scan(wcnt, wscan, nullptr, 5 * nch, misc + 0, scan_tmp, s, srt.fault, P);
     static std::atomic<bool> em_attr[256] = {};
     const int dev = current_device();
     if (dev < 256 && !em_attr[dev].load(std::memory_order_acquire)) {
@@ -1507,11 +1560,12 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
                                             (int)sizeof(SiteSmem)));
         em_attr[dev].store(true, std::memory_order_release);
     }
-    k_em_write<<<sms * 2, EMW_THREADS, sizeof(SiteSmem), s>>>(a, wscan, nch);
-    k_site_flags<<<grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s>>>(a, sflag);
-    prim::exclusive_scan(sflag, spos, nullptr, 5u * ODP_MAX_SITES, misc + 1, scan_tmp, s, srt.fault);
-    k_site_write<<<grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s>>>(a, sflag, spos);
-    k_finalize<<<1, 32, 0, s>>>(a, misc + 0, misc + 1);
+    pdl_if(P, k_em_write, sms * 2, EMW_THREADS, sizeof(SiteSmem), s, a, wscan, nch);
+    pdl_if(P, k_site_flags, grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s, a, sflag);
+    prim::exclusive_scan(sflag, spos, nullptr, 5u * ODP_MAX_SITES, misc + 1, scan_tmp, s, srt.fault,
+                         P);
+    pdl_if(P, k_site_write, grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s, a, sflag, spos);
+    pdl_if(P, k_finalize, 1, 32, 0, s, a, misc + 0, misc + 1);
     return cuda_status(cudaGetLastError());
 }
 

@@ -26,6 +26,13 @@ __device__ __forceinline__ uint32_t dev_len(const uint32_t* n_dev, uint32_t n_ma
 
 // ------------------------------------------------------------------ scan
 
+// Launch chains over at most this many items use programmatic dependent
+// launch (each kernel may be placed while its predecessor drains).  Measured
+// on an analysis of 5e6 events it saved 12 %; on 5e7 events, whose kernels run
+// many waves, the early-resident successors cost 3 %, so larger calls launch
+// plainly.
+constexpr uint32_t PDL_MAX_ITEMS = 1u << 23;
+
 constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_ITEMS = 16;  // consecutive items per thread, moved as four 16-byte words
 constexpr uint32_t SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -51,6 +58,7 @@ constexpr uint32_t SCAN_WAIT_LIMIT = 1u << 20;
 __global__ void __launch_bounds__(SCAN_THREADS, 3)
 scan_chained(const uint32_t* in, uint32_t* out, const uint32_t* n_dev, uint32_t n_max,
              uint32_t* total, uint32_t* tmp, uint32_t* fault) {
+    pdl_entry();
     __shared__ uint32_t sm[40];
     __shared__ uint32_t s_tile, s_prefix;
     unsigned long long* status = reinterpret_cast<unsigned long long*>(tmp + 4);
@@ -178,14 +186,14 @@ inline uint32_t tile_grid(uint32_t tiles, int per_sm) {
 // before its first scan; fault (may be null) is set if a wait gave up.
 inline void exclusive_scan(const uint32_t* in, uint32_t* out, const uint32_t* n_dev,
                            uint32_t n_max, uint32_t* total, uint32_t* tmp, cudaStream_t s,
-                           uint32_t* fault = nullptr) {
+                           uint32_t* fault = nullptr, bool allow_pdl = false) {
     if (n_max == 0) {
         if (total) cudaMemsetAsync(total, 0, 4, s);
         return;
     }
     const uint32_t nb = (n_max + SCAN_TILE - 1) / SCAN_TILE;
-    scan_chained<<<tile_grid(nb, 3), SCAN_THREADS, 0, s>>>(in, out, n_dev, n_max, total, tmp,
-                                                           fault);
+    pdl_if(allow_pdl, scan_chained, tile_grid(nb, 3), SCAN_THREADS, 0, s, in, out,
+           n_dev, n_max, total, tmp, fault);
 }
 
 // ------------------------------------------------------------ radix sort
@@ -203,6 +211,7 @@ __device__ __forceinline__ uint32_t sort_tiles(uint32_t n) { return (n + SORT_TI
 __global__ void __launch_bounds__(SORT_THREADS)
 sort_upsweep(const uint32_t* keys, const uint32_t* n_dev, uint32_t n_max, int shift, int bits,
              uint32_t* hist, uint32_t* hlen) {
+    pdl_entry();
     __shared__ uint32_t h[256];
     const uint32_t n = dev_len(n_dev, n_max);
     const uint32_t ntd = sort_tiles(n);
@@ -231,6 +240,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 4)
 sort_downsweep(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
                uint32_t* vals_out, const uint32_t* n_dev, uint32_t n_max, int shift, int bits,
                const uint32_t* hist_scanned) {
+    pdl_entry();
     constexpr int W = SORT_THREADS / 32;
     constexpr int PER_WARP = SORT_TILE / W;  // 512 items, SORT_ROUNDS rounds of 32
     __shared__ uint32_t base_d[256];   // global start of each digit for this tile
@@ -326,6 +336,7 @@ struct SortTmp {
     uint32_t* scan_tmp;  // scan_tmp_words(256 * ntiles_max), zero before first use
     uint32_t* hlen;      // one device word: histogram length of the current pass
     uint32_t* fault = nullptr;  // set if a scan's wait gave up (may be null)
+    bool pdl = false;           // launch the passes with programmatic dependent launch
 };
 
 inline size_t sort_hist_words(uint32_t n_max) {
@@ -427,6 +438,7 @@ __device__ __forceinline__ void sort_small_body(uint32_t* keys, uint32_t* vals,
 __global__ void __launch_bounds__(SMALL_SORT_THREADS) sort_small(uint32_t* keys, uint32_t* vals,
                                                                  const uint32_t* n_dev,
                                                                  uint32_t n_max, int key_bits) {
+    pdl_entry();
     sort_small_body(keys, vals, n_dev, n_max, key_bits);
 }
 
@@ -466,7 +478,8 @@ inline void radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, ui
                        int key_bits, const SortTmp& t, cudaStream_t s) {
     if (n_max == 0 || key_bits <= 0) return;
     if (n_max <= SMALL_SORT_MAX && sort_small_ready()) {
-        sort_small<<<1, SMALL_SORT_THREADS, SMALL_SORT_SMEM, s>>>(keys, vals, n_dev, n_max, key_bits);
+        pdl_if(t.pdl, sort_small, 1, SMALL_SORT_THREADS, SMALL_SORT_SMEM, s, keys, vals, n_dev,
+               n_max, key_bits);
         return;
     }
     const uint32_t ntiles = (n_max + SORT_TILE - 1) / SORT_TILE;
@@ -479,11 +492,11 @@ inline void radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, ui
     for (int p = 0; p < npass; ++p) {
         const int bits = std::max(1, std::min(per, key_bits - shift));
         const uint32_t hn = (1u << bits) * ntiles;
-        sort_upsweep<<<tile_grid(ntiles, 8), SORT_THREADS, 0, s>>>(k_in, n_dev, n_max, shift, bits,
-                                                                   t.hist, t.hlen);
-        exclusive_scan(t.hist, t.hist, t.hlen, hn, nullptr, t.scan_tmp, s, t.fault);
-        sort_downsweep<<<tile_grid(ntiles, downsweep_per_sm()), SORT_THREADS, 0, s>>>(k_in, v_in, k_out, v_out, n_dev,
-                                                                     n_max, shift, bits, t.hist);
+        pdl_if(t.pdl, sort_upsweep, tile_grid(ntiles, 8), SORT_THREADS, 0, s, k_in,
+               n_dev, n_max, shift, bits, t.hist, t.hlen);
+        exclusive_scan(t.hist, t.hist, t.hlen, hn, nullptr, t.scan_tmp, s, t.fault, t.pdl);
+        pdl_if(t.pdl, sort_downsweep, tile_grid(ntiles, downsweep_per_sm()),
+               SORT_THREADS, 0, s, k_in, v_in, k_out, v_out, n_dev, n_max, shift, bits, t.hist);
         shift += bits;
         std::swap(k_in, k_out);
         std::swap(v_in, v_out);
@@ -572,11 +585,13 @@ __device__ __forceinline__ void table_clear_body(Table t, const uint32_t* count_
 }
 
 __global__ void table_clear(Table t, const uint32_t* count_dev, uint32_t count_max) {
+    pdl_entry();
     table_clear_body(t, count_dev, count_max);
 }
 
 // The same for a split table: keys, then values (NONE32), 16 bytes a write.
 __global__ void table_clear(SplitTable t, const uint32_t* count_dev, uint32_t count_max) {
+    pdl_entry();
     const uint32_t cap = table_cap(dev_len(count_dev, count_max), t.cap_max);
     if (blockIdx.x == 0 && threadIdx.x == 0) *t.cap_dev = cap;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -591,6 +606,7 @@ __global__ void table_clear(SplitTable t, const uint32_t* count_dev, uint32_t co
 
 // The same for a key-only table (one 16-byte write per slot).
 __global__ void table_clear(KeyTable t, const uint32_t* count_dev, uint32_t count_max) {
+    pdl_entry();
     const uint32_t cap = table_cap(dev_len(count_dev, count_max), t.cap_max);
     if (blockIdx.x == 0 && threadIdx.x == 0) *t.cap_dev = cap;
     const uint32_t stride = gridDim.x * blockDim.x;
