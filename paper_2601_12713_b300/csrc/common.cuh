@@ -122,9 +122,8 @@ __device__ __forceinline__ void pdl_entry() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Launches with programmatic serialization when `allow` is set (by default):
-// worth it for short kernels, where the launch gap is a large share of the
-// run time; long kernels are launched plainly.
+// Launches with programmatic serialization when `allow` is set, plainly
+// otherwise (pdl_entry() is then a no-op).
 template <typename... KArgs, typename... Args>
 inline void pdl_if(bool allow, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                    cudaStream_t s, Args... args) {
@@ -144,17 +143,7 @@ inline void pdl_if(bool allow, void (*kernel)(KArgs...), dim3 grid, dim3 block, 
 template <typename... KArgs, typename... Args>
 inline void pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                 Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, args...);
+    pdl_if(true, kernel, grid, block, smem, s, args...);
 }
 
 }  // namespace odp
