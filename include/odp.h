@@ -382,10 +382,24 @@ typedef struct odp_server_stats {
     uint64_t queue_p50_ns, queue_p99_ns;  /* the part of the latency before the
                                        reporting batch was launched (merge
                                        watermark and batch formation) */
+    uint64_t device_bytes;          /* device memory the server allocated
+                                       (at most odp_server_bytes) */
 } odp_server_stats;
 
-/* Creates a server and allocates all of its device memory up front
- * (ODP_ERR_OOM if that exceeds device_budget_bytes or the device). */
+/*
+ * Device bytes a server with this configuration reserves (*bytes): every
+ * block odp_server_create allocates, plus 66 MB per slot for allocation
+ * granularity and the fingerprint call's scratch.  Host arithmetic only (no
+ * device call).  ODP_ERR_INVALID_ARG for a null argument or a zero field
+ * (n_slots < 1), ODP_ERR_UNSUPPORTED for max_events or max_batch_events above
+ * 2^30.
+ */
+int odp_server_bytes(const odp_server_cfg* cfg, uint64_t* bytes);
+
+/* Creates a server and allocates all of its device memory up front.  The
+ * budget is checked first, before any device call: ODP_ERR_OOM if
+ * odp_server_bytes exceeds a non-zero device_budget_bytes, or if the device
+ * refuses an allocation.  Other errors as odp_server_bytes. */
 int odp_server_create(const odp_server_cfg* cfg, odp_server** out);
 
 /*

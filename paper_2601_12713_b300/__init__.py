@@ -12,7 +12,7 @@ _EXPORTS = (
     "fingerprint_noalloc", "fingerprint_tensors", "fingerprint_with", "autotune_fingerprint", "autotune_clear",
     "fingerprint_status", "analyze", "Findings", "EVENT_DTYPE", "FINDING_DTYPE", "SITE_DTYPE",
     "SUMMARY_FIELDS", "set_torch_allocator", "release_scratch", "Server", "log_tensor",
-    "verify_fingerprints", "set_allocator",
+    "verify_fingerprints", "set_allocator", "server_bytes",
 )
 
 

@@ -267,9 +267,12 @@ class ServerStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in (
         "events_submitted", "events_processed", "batches", "findings_streamed", "late_events",
         "latency_p50_ns", "latency_p99_ns", "latency_max_ns", "first_submit_ns", "last_done_ns",
-        "rt_groups_unstreamed", "stream_overflow", "queue_p50_ns", "queue_p99_ns")]
+        "rt_groups_unstreamed", "stream_overflow", "queue_p50_ns", "queue_p99_ns",
+        "device_bytes")]
 
 
+_lib.odp_server_bytes.argtypes = [ctypes.POINTER(ServerCfg), ctypes.POINTER(ctypes.c_uint64)]
+_lib.odp_server_bytes.restype = ctypes.c_int
 _lib.odp_server_create.argtypes = [ctypes.POINTER(ServerCfg), ctypes.POINTER(_vp)]
 _lib.odp_server_create.restype = ctypes.c_int
 _lib.odp_server_submit.argtypes = [_vp, _vp, _vp, ctypes.c_uint64]
@@ -294,6 +297,14 @@ _lib.odp_server_destroy.argtypes = [_vp]
 _lib.odp_server_destroy.restype = ctypes.c_int
 
 
+def server_bytes(n_slots=4, max_events=1 << 23, max_batch_events=4096, max_producers=128) -> int:
+    """Device bytes a Server of this shape reserves (odp_server_bytes)."""
+    cfg = ServerCfg(0, n_slots, 0, max_events, max_batch_events, max_producers, 0, 0)
+    b = ctypes.c_uint64(0)
+    _check(_lib.odp_server_bytes(ctypes.byref(cfg), ctypes.byref(b)), "odp_server_bytes")
+    return int(b.value)
+
+
 class Server:
     """Continuous-batching serving loop (odp_server_*)."""
 
@@ -302,6 +313,7 @@ class Server:
                  batch_interval_us=50):
         cfg = ServerCfg(device, n_slots, device_budget_bytes, max_events, max_batch_events,
                         max_producers, watermark_timeout_us, batch_interval_us)
+        self.h = None
         h = _vp()
         _check(_lib.odp_server_create(ctypes.byref(cfg), ctypes.byref(h)), "odp_server_create")
         self.h = h

@@ -80,6 +80,7 @@ uint64_t now_ns() {
 
 constexpr uint32_t EP_MORE = 1u << 16;  // endpoint set: more than two endpoints
 constexpr int SRV_NDEV = 129;            // host + devices 0..127
+constexpr uint64_t SRV_MAX_CAPACITY = 1ull << 30;  // max_events, max_batch_events
 
 struct SrvDev {
     odp_event* log;
@@ -863,6 +864,7 @@ struct odp_server {
     // device
     odp::SrvDev d;
     std::vector<void*> dev_blocks;
+    uint64_t dev_bytes = 0;  // sum of the dev_blocks' sizes
     cudaStream_t an_stream = nullptr;
     std::vector<odp::Slot> slots;
     uint32_t find_cap = 0;
@@ -904,6 +906,7 @@ int alloc_dev(odp_server* s, void** p, size_t bytes) {
         return ODP_ERR_OOM;
     }
     s->dev_blocks.push_back(*p);
+    s->dev_bytes += bytes;
     return ODP_OK;
 }
 
@@ -1207,25 +1210,47 @@ void batcher_main(odp_server* S) {
 
 extern "C" {
 
+int odp_server_bytes(const odp_server_cfg* cfg, uint64_t* bytes) {
+    using namespace odp;
+    if (!cfg || !bytes) return ODP_ERR_INVALID_ARG;
+    if (cfg->n_slots < 1 || cfg->max_events == 0 || cfg->max_batch_events == 0 ||
+        cfg->max_producers == 0)
+        return ODP_ERR_INVALID_ARG;
+    // tables of 2 * capacity slots, rounded up to a power of two, index in 32 bits
+    if (cfg->max_events > SRV_MAX_CAPACITY || cfg->max_batch_events > SRV_MAX_CAPACITY)
+        return ODP_ERR_UNSUPPORTED;
+    const uint64_t E = cfg->max_events, B = cfg->max_batch_events;
+    const uint64_t cap_p = pow2_at_least(2 * E), cap_b = pow2_at_least(2 * B);
+    const uint64_t pend_cap = std::min<uint64_t>(E, 16 * B);
+    const uint64_t find_cap = 3 * B + pend_cap + 64;
+    const uint64_t table = sizeof(prim::Slot);
+    // the blocks odp_server_create allocates, plus per slot an allowance of
+    // 66 MB for allocation granularity and the fingerprint call's scratch
+    const uint64_t shared = 64 + E * (64 + 4 + 4 + 4) + 7 * table * (cap_p + 1) +
+                            table * (cap_b + 1) + 12 * SRV_NDEV + 40 * pend_cap + 80 +
+                            find_cap * (sizeof(odp_finding) + 8);
+    const uint64_t hist = 4 * prim::sort_hist_words((uint32_t)B);
+    const uint64_t scan = 4 * (prim::scan_tmp_words(256u * ((uint32_t)B / prim::SORT_TILE + 2)) + 16);
+    const uint64_t per_slot = B * (sizeof(odp_event) + 8 + 8 + 16 + 4 + 4 + 12 * 4 + 8) +
+                              sizeof(BatchPar) + hist + scan + find_cap * (sizeof(odp_finding) + 8) +
+                              16 + 2 * 4 * 256 + 16 + (66ull << 20);
+    *bytes = shared + (uint64_t)cfg->n_slots * per_slot;
+    return ODP_OK;
+}
+
 int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     using namespace odp;
     if (!cfg || !out) return ODP_ERR_INVALID_ARG;
-    if (cfg->n_slots < 1 || cfg->max_events == 0 || cfg->max_batch_events == 0 ||
-        cfg->max_producers == 0 || cfg->max_events >= 0xFFFFFFF0ull)
-        return ODP_ERR_INVALID_ARG;
+    uint64_t need = 0;
+    int brc = odp_server_bytes(cfg, &need);
+    if (brc != ODP_OK) return brc;
+    // refused before any device call when the reservation exceeds the budget
+    if (cfg->device_budget_bytes && need > cfg->device_budget_bytes) return ODP_ERR_OOM;
     if (cudaSetDevice(cfg->device) != cudaSuccess) return ODP_ERR_CUDA;
     const uint64_t E = cfg->max_events, B = cfg->max_batch_events;
     const uint32_t cap_p = pow2_at_least(2 * E), cap_b = pow2_at_least(2 * B);
     const uint32_t pend_cap = (uint32_t)std::min<uint64_t>(E, 16 * B);
     const uint64_t find_cap = 3 * B + pend_cap + 64;
-    // device bytes: log + per-event arrays + four persistent tables + slots
-    const uint64_t per_table = 32 * ((uint64_t)cap_p + 1);
-    const uint64_t slot_bytes = B * (64 + 8 + 8 + 16 + 4 + 12 + 16 + 16 + 12) +
-                                256ull * (B / 4096 + 2) * 4 + 2048 + find_cap * (48 + 8) +
-                                (20ull << 20) + (46ull << 20);
-    const uint64_t need = E * (64 + 12) + 7 * per_table + 32 * ((uint64_t)cap_b + 1) +
-                          40ull * pend_cap + ((uint64_t)cfg->n_slots + 1) * slot_bytes;
-    if (cfg->device_budget_bytes && need > cfg->device_budget_bytes) return ODP_ERR_OOM;
 
     static std::atomic<uint64_t> next_server{1};
     odp_server* S = new odp_server();
@@ -1550,6 +1575,7 @@ int odp_server_stats_get(odp_server* S, odp_server_stats* st) {
     // groups with more than two endpoints (counted on the device table), and
     // findings or waiting decisions that did not fit
     st->rt_groups_unstreamed = 0;
+    st->device_bytes = S->dev_bytes;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         cudaSetDevice(S->cfg.device);

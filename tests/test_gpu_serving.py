@@ -420,3 +420,20 @@ def test_streamed_pairs_equal_offline(cuda_ok, orc, max_batch):
         assert np.array_equal(st.view(np.uint8), off.view(np.uint8))
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("n_slots, max_events, max_batch", [(1, 1 << 12, 1), (2, 1 << 16, 2048),
+                                                            (4, 1 << 20, 4096)])
+def test_allocation_within_the_reservation(cuda_ok, n_slots, max_events, max_batch):
+    import paper_2601_12713_b300 as odp
+
+    shape = dict(n_slots=n_slots, max_events=max_events, max_batch_events=max_batch,
+                 max_producers=16)
+    need = odp.server_bytes(**shape)
+    srv = odp.Server(device_budget_bytes=need, watermark_timeout_us=1000, **shape)
+    try:
+        got = srv.stats()["device_bytes"]
+        # every allocated block is counted; the rest is the per-slot allowance
+        assert need - n_slots * (66 << 20) <= got <= need
+    finally:
+        srv.close()
