@@ -1322,10 +1322,9 @@ __global__ void k_empty_outputs(odp_findings out) {
 
 // prim::table_clear for table type T (the overload picked by type).
 template <class T>
-void clear_table(bool P, const T& t, const uint32_t* count, uint32_t count_max, int grid,
-                 cudaStream_t s) {
+void clear_table(const T& t, const uint32_t* count, uint32_t count_max, int grid, cudaStream_t s) {
     void (*kernel)(T, const uint32_t*, uint32_t) = prim::table_clear;
-    pdl_if(P, kernel, grid, TPB, 0, s, t, count, count_max);
+    pdl(kernel, grid, TPB, 0, s, t, count, count_max);
 }
 
 static int grid_for(uint64_t n, int sms) {
@@ -1448,9 +1447,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     srt.scan_tmp = (uint32_t*)(b + o_scan);
     srt.hlen = misc + 3;
     srt.fault = &a.h->scan_fault;
-    // programmatic dependent launch for the whole chain of a small call
-    const bool P = n <= prim::PDL_MAX_ITEMS;
-    srt.pdl = P;
+    srt.pdl = true;  // the whole chain uses programmatic dependent launch
     uint32_t* scan_tmp = srt.scan_tmp;
 
     const int bits_n = prim::bit_length(n);              // keys < n + 1
@@ -1471,88 +1468,88 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     // ---- validate, lists
     uint32_t* ccnt = (uint32_t*)(b + o_wcnt);
     uint32_t* cscan = (uint32_t*)(b + o_wscan);
-    pdl_if(P, k_validate, sms * 16, TPB, 0, s, a, ccnt, nch);
-    prim::exclusive_scan(ccnt, cscan, nullptr, 4 * nch, misc + 2, scan_tmp, s, srt.fault, P);
-    pdl_if(P, k_list_lengths, 1, 32, 0, s, a, cscan, misc + 2, nch);
-    pdl_if(P, k_compact, sms * 16, TPB, 0, s, a, cscan, nch);
+    pdl(k_validate, sms * 16, TPB, 0, s, a, ccnt, nch);
+    prim::exclusive_scan(ccnt, cscan, nullptr, 4 * nch, misc + 2, scan_tmp, s, srt.fault, true);
+    pdl(k_list_lengths, 1, 32, 0, s, a, cscan, misc + 2, nch);
+    pdl(k_compact, sms * 16, TPB, 0, s, a, cscan, nch);
     uint32_t* nX = &a.h->nX;
     uint32_t* nP = &a.h->nP;
     uint32_t* nK = &a.h->nK;
     uint32_t* nU = &a.h->nU;
 
     // ---- Alg. 1: content ids, first receivers
-    clear_table(P, a.tab, nX, n, clear_grid, s);
-    pdl_if(P, k_x_insert_fp, gX, TPB, 0, s, a);
-    pdl_if(P, k_x_cid, gX, TPB, 0, s, a);
+    clear_table(a.tab, nX, n, clear_grid, s);
+    pdl(k_x_insert_fp, gX, TPB, 0, s, a);
+    pdl(k_x_cid, gX, TPB, 0, s, a);
 
     // ---- Alg. 2
     prim::radix_sort(a.sk, a.sv, nX, n, bits_n, srt, s);
-    pdl_if(P, k_rt_flags, gX, TPB, 0, s, a);
-    prim::exclusive_scan(a.f1, a.id1, nX, n, &a.h->nseg, scan_tmp, s, srt.fault, P);
-    prim::exclusive_scan(a.f2, a.id2, nX, n, &a.h->nrun, scan_tmp, s, srt.fault, P);
-    pdl_if(P, k_rt_starts, gX, TPB, 0, s, a);
-    pdl_if(P, k_rt_check, gX, TPB, 0, s, a);
-    pdl_if(P, k_rt_partner, gX, TPB, 0, s, a);
+    pdl(k_rt_flags, gX, TPB, 0, s, a);
+    prim::exclusive_scan(a.f1, a.id1, nX, n, &a.h->nseg, scan_tmp, s, srt.fault, true);
+    prim::exclusive_scan(a.f2, a.id2, nX, n, &a.h->nrun, scan_tmp, s, srt.fault, true);
+    pdl(k_rt_starts, gX, TPB, 0, s, a);
+    pdl(k_rt_check, gX, TPB, 0, s, a);
+    pdl(k_rt_partner, gX, TPB, 0, s, a);
     // groups with more than two endpoints
     uint32_t* nB = &a.h->nB;
-    pdl_if(P, k_mx_flag, gX, TPB, 0, s, a);
-    prim::exclusive_scan(a.f2, a.id2, &a.h->mx_n, n, nB, scan_tmp, s, srt.fault, P);
-    pdl_if(P, k_mx_scatter, gX, TPB, 0, s, a);
+    pdl(k_mx_flag, gX, TPB, 0, s, a);
+    prim::exclusive_scan(a.f2, a.id2, &a.h->mx_n, n, nB, scan_tmp, s, srt.fault, true);
+    pdl(k_mx_scatter, gX, TPB, 0, s, a);
     prim::radix_sort(a.k2, a.v2, nB, n, 8, srt, s);
-    pdl_if(P, k_mx_gkey, gX, TPB, 0, s, a);
+    pdl(k_mx_gkey, gX, TPB, 0, s, a);
     prim::radix_sort(a.k2, a.v2, nB, n, bits_n, srt, s);
-    pdl_if(P, k_mx_heads, gX, TPB, 0, s, a);
-    prim::exclusive_scan(a.f2, a.id2, nB, n, &a.h->nsegB, scan_tmp, s, srt.fault, P);
-    pdl_if(P, k_mx_starts, gX, TPB, 0, s, a);
-    pdl_if(P, k_mx_late, gX, TPB, 0, s, a);
-    pdl_if(P, k_mx_ok, gX, TPB, 0, s, a);
-    pdl_if(P, k_mx_succ, gX, TPB, 0, s, a);
-    prim::exclusive_scan(a.k2, a.sk, nB, n, nullptr, scan_tmp, s, srt.fault, P);
-    pdl_if(P, k_mx_partner, gX, TPB, 0, s, a);
+    pdl(k_mx_heads, gX, TPB, 0, s, a);
+    prim::exclusive_scan(a.f2, a.id2, nB, n, &a.h->nsegB, scan_tmp, s, srt.fault, true);
+    pdl(k_mx_starts, gX, TPB, 0, s, a);
+    pdl(k_mx_late, gX, TPB, 0, s, a);
+    pdl(k_mx_ok, gX, TPB, 0, s, a);
+    pdl(k_mx_succ, gX, TPB, 0, s, a);
+    prim::exclusive_scan(a.k2, a.sk, nB, n, nullptr, scan_tmp, s, srt.fault, true);
+    pdl(k_mx_partner, gX, TPB, 0, s, a);
 
     // ---- pairs
-    clear_table(P, a.ktab, nP, n, clear_grid, s);
-    pdl_if(P, k_p_insert, gX, TPB, 0, s, a);
+    clear_table(a.ktab, nP, n, clear_grid, s);
+    pdl(k_p_insert, gX, TPB, 0, s, a);
     prim::radix_sort(a.sk, a.sv, nP, n, bits_slot, srt, s);
-    pdl_if(P, k_seg_heads, gX, TPB, 0, s, a, nP);
-    prim::exclusive_scan(a.f1, a.id1, nP, n, &a.h->nseg2, scan_tmp, s, srt.fault, P);
-    pdl_if(P, k_seg_starts, gX, TPB, 0, s, a, nP, &a.h->nseg2);
-    pdl_if(P, k_p_check, gX, TPB, 0, s, a);
-    pdl_if(P, k_p_match, gX, TPB, 0, s, a);
-    pdl_if(P, k_p_literal, gX, TPB, 0, s, a);
+    pdl(k_seg_heads, gX, TPB, 0, s, a, nP);
+    prim::exclusive_scan(a.f1, a.id1, nP, n, &a.h->nseg2, scan_tmp, s, srt.fault, true);
+    pdl(k_seg_starts, gX, TPB, 0, s, a, nP, &a.h->nseg2);
+    pdl(k_p_check, gX, TPB, 0, s, a);
+    pdl(k_p_match, gX, TPB, 0, s, a);
+    pdl(k_p_literal, gX, TPB, 0, s, a);
 
     // ---- Alg. 3
-    clear_table(P, a.tab, &a.h->nA, n, clear_grid, s);
-    pdl_if(P, k_ra_insert, gX, TPB, 0, s, a);
-    pdl_if(P, k_ra_flag, gX, TPB, 0, s, a);
+    clear_table(a.tab, &a.h->nA, n, clear_grid, s);
+    pdl(k_ra_insert, gX, TPB, 0, s, a);
+    pdl(k_ra_flag, gX, TPB, 0, s, a);
 
     // ---- kernels per device
-    pdl_if(P, k_dev_keys, gX, TPB, 0, s, a, a.K, nK, &a.h->k_mixed);
-    pdl_if(P, k_sort_count, 1, 32, 0, s, nK, &a.h->k_mixed, &a.h->k_sortn);
+    pdl(k_dev_keys, gX, TPB, 0, s, a, a.K, nK, &a.h->k_mixed);
+    pdl(k_sort_count, 1, 32, 0, s, nK, &a.h->k_mixed, &a.h->k_sortn);
     prim::radix_sort(a.sk, a.sv, &a.h->k_sortn, n, 8, srt, s);
-    pdl_if(P, k_k_bounds, gX, TPB, 0, s, a);
-    pdl_if(P, k_k_pmax, NDEV, PMAX_THREADS, 0, s, a);
+    pdl(k_k_bounds, gX, TPB, 0, s, a);
+    pdl(k_k_pmax, NDEV, PMAX_THREADS, 0, s, a);
 
     // ---- Alg. 4
-    pdl_if(P, k_ua, gX, TPB, 0, s, a);
+    pdl(k_ua, gX, TPB, 0, s, a);
 
     // ---- Alg. 5
-    pdl_if(P, k_dev_keys, gX, TPB, 0, s, a, a.U, nU, &a.h->u_mixed);
-    pdl_if(P, k_sort_count, 1, 32, 0, s, nU, &a.h->u_mixed, &a.h->u_sortn);
+    pdl(k_dev_keys, gX, TPB, 0, s, a, a.U, nU, &a.h->u_mixed);
+    pdl(k_sort_count, 1, 32, 0, s, nU, &a.h->u_mixed, &a.h->u_sortn);
     prim::radix_sort(a.sk, a.sv, &a.h->u_sortn, n, 8, srt, s);
-    pdl_if(P, k_ut_class, gX, TPB, 0, s, a);
-    pdl_if(P, k_ut_heads, gX, TPB, 0, s, a);
-    prim::exclusive_scan(a.f1, a.id1, nU, n, &a.h->nsegU, scan_tmp, s, srt.fault, P);
-    clear_table(P, a.ktab, nU, n, clear_grid, s);
-    pdl_if(P, k_ut_insert, gX, TPB, 0, s, a);
+    pdl(k_ut_class, gX, TPB, 0, s, a);
+    pdl(k_ut_heads, gX, TPB, 0, s, a);
+    prim::exclusive_scan(a.f1, a.id1, nU, n, &a.h->nsegU, scan_tmp, s, srt.fault, true);
+    clear_table(a.ktab, nU, n, clear_grid, s);
+    pdl(k_ut_insert, gX, TPB, 0, s, a);
     prim::radix_sort(a.k2, a.v2, nU, n, bits_slot, srt, s);
-    pdl_if(P, k_ut_next, gX, TPB, 0, s, a);
+    pdl(k_ut_next, gX, TPB, 0, s, a);
 
     // ---- emission
     uint32_t* wcnt = (uint32_t*)(b + o_wcnt);
     uint32_t* wscan = (uint32_t*)(b + o_wscan);
-    pdl_if(P, k_em_count, sms * 8, 256, 0, s, a, wcnt, nch);
-    prim::exclusive_scan(wcnt, wscan, nullptr, 5 * nch, misc + 0, scan_tmp, s, srt.fault, P);
+    pdl(k_em_count, sms * 8, 256, 0, s, a, wcnt, nch);
+    prim::exclusive_scan(wcnt, wscan, nullptr, 5 * nch, misc + 0, scan_tmp, s, srt.fault, true);
     static std::atomic<bool> em_attr[256] = {};
     const int dev = current_device();
     if (dev < 256 && !em_attr[dev].load(std::memory_order_acquire)) {
@@ -1560,12 +1557,12 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
                                             (int)sizeof(SiteSmem)));
         em_attr[dev].store(true, std::memory_order_release);
     }
-    pdl_if(P, k_em_write, sms * 2, EMW_THREADS, sizeof(SiteSmem), s, a, wscan, nch);
-    pdl_if(P, k_site_flags, grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s, a, sflag);
+    pdl(k_em_write, sms * 2, EMW_THREADS, sizeof(SiteSmem), s, a, wscan, nch);
+    pdl(k_site_flags, grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s, a, sflag);
     prim::exclusive_scan(sflag, spos, nullptr, 5u * ODP_MAX_SITES, misc + 1, scan_tmp, s, srt.fault,
-                         P);
-    pdl_if(P, k_site_write, grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s, a, sflag, spos);
-    pdl_if(P, k_finalize, 1, 32, 0, s, a, misc + 0, misc + 1);
+                         true);
+    pdl(k_site_write, grid_for(5u * ODP_MAX_SITES, sms), TPB, 0, s, a, sflag, spos);
+    pdl(k_finalize, 1, 32, 0, s, a, misc + 0, misc + 1);
     return cuda_status(cudaGetLastError());
 }
 

@@ -26,13 +26,6 @@ __device__ __forceinline__ uint32_t dev_len(const uint32_t* n_dev, uint32_t n_ma
 
 // ------------------------------------------------------------------ scan
 
-// Launch chains over at most this many items use programmatic dependent
-// launch (each kernel may be placed while its predecessor drains).  Measured
-// on an analysis of 5e6 events it saved 12 %; on 5e7 events, whose kernels run
-// many waves, the early-resident successors cost 3 %, so larger calls launch
-// plainly.
-constexpr uint32_t PDL_MAX_ITEMS = 1u << 23;
-
 constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_ITEMS = 16;  // consecutive items per thread, moved as four 16-byte words
 constexpr uint32_t SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -336,7 +329,7 @@ struct SortTmp {
     uint32_t* scan_tmp;  // scan_tmp_words(256 * ntiles_max), zero before first use
     uint32_t* hlen;      // one device word: histogram length of the current pass
     uint32_t* fault = nullptr;  // set if a scan's wait gave up (may be null)
-    bool pdl = false;           // launch the passes with programmatic dependent launch
+    bool pdl = false;           // launch the passes with programmatic dependent launch (pdl())
 };
 
 inline size_t sort_hist_words(uint32_t n_max) {
