@@ -14,7 +14,10 @@
  * odp_analyze over the log and prints the counts to stderr; with
  * ODP_OMPT_OUT=<prefix> it writes <prefix>.events (the log, 64-byte
  * records) and <prefix>.sites ("id address" per line).  ODP_OMPT_DISABLE=1
- * makes ompt_start_tool decline; ODP_OMPT_MAX_EVENTS sets the log capacity.
+ * makes ompt_start_tool decline; ODP_OMPT_MAX_EVENTS sets the log capacity
+ * (default 2^22), and with it the device memory the server reserves
+ * (odp_server_bytes).  If the server cannot be created the tool prints why
+ * and stays inactive (its initializer returns 0).
  *
  * The paper's tool hashes on the host CPU during the transfer; this one
  * hashes on the GPU, synchronously, so a kernel cannot change the bytes

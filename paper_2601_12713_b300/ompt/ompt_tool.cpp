@@ -281,14 +281,25 @@ int tool_initialize(ompt_function_lookup_t lookup, int initial_device_num, ompt_
     odp_server_cfg cfg{};
     cfg.device = 0;
     cfg.n_slots = 2;
-    cfg.device_budget_bytes = 4ull << 30;
     cfg.max_events = 1u << 22;
     cfg.max_batch_events = 4096;
     cfg.max_producers = 256;
     cfg.watermark_timeout_us = 20000;
     cfg.batch_interval_us = 100;
     if (const char* s = std::getenv("ODP_OMPT_MAX_EVENTS")) cfg.max_events = std::strtoull(s, 0, 10);
-    if (odp_server_create(&cfg, &g_tool.server) != ODP_OK) return 0;
+    // the log capacity decides the device reservation; the budget is exactly it
+    uint64_t need = 0;
+    int rc = odp_server_bytes(&cfg, &need);
+    if (rc == ODP_OK) {
+        cfg.device_budget_bytes = need;
+        rc = odp_server_create(&cfg, &g_tool.server);
+    }
+    if (rc != ODP_OK) {
+        std::fprintf(stderr, "[odp] tool inactive: no server for a log of %llu events (%s)\n",
+                     (unsigned long long)cfg.max_events, odp_status_string(rc));
+        g_tool.server = nullptr;
+        return 0;
+    }
     const bool ok = set_cb(OMPT_CB_TARGET_EMI, (ompt_callback_t)cb_target_emi) >= OMPT_SET_SOMETIMES &&
                     set_cb(OMPT_CB_TARGET_DATA_OP_EMI, (ompt_callback_t)cb_target_data_op_emi) >=
                         OMPT_SET_SOMETIMES &&
