@@ -85,3 +85,62 @@ def test_header_record_sizes_compile():
         subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"),
                         "-I", "/usr/local/cuda/include", "-c", c, "-o",
                         os.path.join(d, "t.o")], check=True)
+
+
+def header_layout(structs):
+    """{(struct, field): (offset, size)} as the C compiler lays out include/odp.h."""
+    import tempfile
+
+    lines = ['#include "odp.h"', "#include <stddef.h>", "#include <stdio.h>", "int main(void) {"]
+    for st, fields in structs.items():
+        lines.append(f'printf("{st} . %zu\\n", sizeof({st}));')
+        for f in fields:
+            lines.append(f'printf("{st} {f} %zu %zu\\n", offsetof({st}, {f}), '
+                         f'sizeof((({st}*)0)->{f}));')
+    lines += ["return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "t.c"), os.path.join(d, "t")
+        open(c, "w").write("\n".join(lines))
+        subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"),
+                        "-I", "/usr/local/cuda/include", c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    res = {}
+    for line in out.splitlines():
+        st, f, a, *b = line.split()
+        res[(st, f)] = (int(a), int(b[0])) if b else int(a)
+    return res
+
+
+def test_binding_layouts_match_the_header():
+    import paper_2601_12713_b300 as odp
+    from paper_2601_12713_b300 import _lib
+
+    ctypes_structs = {"odp_fp_schedule": _lib.FpSchedule, "odp_findings": _lib._OdpFindings,
+                      "odp_server_cfg": _lib.ServerCfg, "odp_server_stats": _lib.ServerStats}
+    dtypes = {"odp_event": odp.EVENT_DTYPE, "odp_finding": odp.FINDING_DTYPE,
+              "odp_site_row": odp.SITE_DTYPE}
+    summary_arrays = ("count", "wasted_bytes", "wasted_ns")
+    summary_scalars = [f for f in odp.SUMMARY_FIELDS if f.rstrip("012345") not in summary_arrays]
+    structs = {st: [f for f, *_ in cls._fields_] for st, cls in ctypes_structs.items()}
+    structs.update({st: list(dt.names) for st, dt in dtypes.items()})
+    structs["odp_summary"] = summary_scalars + list(summary_arrays)
+    got = header_layout(structs)
+    for st, cls in ctypes_structs.items():
+        assert got[(st, ".")] == ctypes.sizeof(cls), st
+        for f, *_ in cls._fields_:
+            field = getattr(cls, f)
+            assert got[(st, f)] == (field.offset, field.size), (st, f)
+    for st, dt in dtypes.items():
+        assert got[(st, ".")] == dt.itemsize, st
+        for f in dt.names:
+            sub, off = dt.fields[f][:2]
+            assert got[(st, f)] == (off, sub.itemsize), (st, f)
+    # the summary is read as a flat array of 64-bit words in SUMMARY_FIELDS order
+    assert got[("odp_summary", ".")] == 8 * len(odp.SUMMARY_FIELDS)
+    for i, f in enumerate(odp.SUMMARY_FIELDS):
+        base = f.rstrip("012345")
+        if base in summary_arrays:
+            off, size = got[("odp_summary", base)]
+            assert off + 8 * int(f[len(base):]) == 8 * i and size == 48, f
+        else:
+            assert got[("odp_summary", f)] == (8 * i, 8), f
