@@ -388,9 +388,9 @@ typedef struct odp_server_stats {
 
 /*
  * Device bytes a server with this configuration reserves (*bytes): every
- * block odp_server_create allocates, plus 66 MB per slot for allocation
- * granularity and the fingerprint call's scratch.  Host arithmetic only (no
- * device call).  ODP_ERR_INVALID_ARG for a null argument or a zero field
+ * block odp_server_create allocates, plus per slot the scratch of the slot's
+ * fingerprint calls (their plan for max_batch_events buffers) and 20 MB for
+ * allocation granularity.  Host arithmetic only (no device call).  ODP_ERR_INVALID_ARG for a null argument or a zero field
  * (n_slots < 1), ODP_ERR_UNSUPPORTED for max_events or max_batch_events above
  * 2^30.
  */

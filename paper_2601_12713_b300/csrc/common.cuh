@@ -34,6 +34,14 @@ void* scratch_get(int slot, size_t bytes, cudaStream_t stream, int* status,
 // Frees the (current device, stream, slot) block (stream-ordered).
 void release_slot(int slot, cudaStream_t stream);
 
+// Size of the block scratch_get allocates for a request of `bytes` (it keeps
+// a quarter of headroom, so slightly larger later requests reuse the block).
+size_t scratch_block_bytes(size_t bytes);
+
+// Device scratch of one odp_fingerprint call over n buffers: the block its
+// plan (tile and node offsets, tree counters, subtree roots) takes.
+size_t fp_plan_scratch_bytes(uint64_t n);
+
 int device_sm_count();       // SMs of the current device
 int current_device();
 int32_t* device_status_word(int* status);  // per-device fingerprint status

@@ -846,6 +846,41 @@ static void fp_launch(const FpArgs& a, int W, int S, int grid, cudaStream_t stre
 static std::mutex g_zero_mu;
 static std::map<void*, size_t> g_zeroed;
 
+// Byte offsets of the plan's arrays in its scratch block, for nn buffers.
+struct PlanLayout {
+    size_t hdr, cnt, zero_needed, toff, noff, bsum, tbuf, nodes, bytes;
+};
+
+static PlanLayout plan_layout(uint32_t nn) {
+    const uint32_t cap_tiles = nn + (1u << 20);
+    const uint32_t nblocks = (nn + 1023) / 1024;
+    PlanLayout p{};
+    size_t bytes = 0;
+    auto carve = [&](size_t sz) {
+        size_t o = bytes;
+        bytes = align_up(bytes + sz, 256);
+        return o;
+    };
+    // The header and the tree counters sit at fixed places in front, so a
+    // call with another n finds its counters inside the region earlier calls
+    // left at zero (the last arriver of every group resets its counter).
+    p.hdr = carve(sizeof(PlanHeader));
+    p.cnt = carve(sizeof(uint32_t) * 2 * (size_t)cap_tiles);
+    p.zero_needed = bytes;
+    p.toff = carve(sizeof(uint32_t) * (nn + 1));
+    p.noff = carve(sizeof(uint32_t) * (nn + 1));
+    p.bsum = carve(sizeof(uint32_t) * 2 * (nblocks + 1));
+    p.tbuf = carve(sizeof(uint32_t) * (size_t)cap_tiles);
+    p.nodes = carve(sizeof(U128) * 2 * (size_t)cap_tiles);
+    p.bytes = bytes;
+    return p;
+}
+
+size_t fp_plan_scratch_bytes(uint64_t n) {
+    if (n > (1ull << 28)) n = 1ull << 28;  // larger calls are refused
+    return scratch_block_bytes(plan_layout((uint32_t)n).bytes);
+}
+
 int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128* out,
            cudaStream_t stream, const FpLaunch& L, const void* one_ptr, uint64_t one_size) {
     const bool host_one = ptrs == nullptr && sizes == nullptr && n == 1;
@@ -866,23 +901,10 @@ int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128
     const uint32_t nn = (uint32_t)n;
     const uint32_t cap_tiles = nn + (1u << 20);
     const uint32_t nblocks = (nn + 1023) / 1024;
-    size_t bytes = 0;
-    auto carve = [&](size_t sz) {
-        size_t o = bytes;
-        bytes = align_up(bytes + sz, 256);
-        return o;
-    };
-    // The header and the tree counters sit at fixed places in front, so a
-    // call with another n finds its counters inside the region earlier calls
-    // left at zero (the last arriver of every group resets its counter).
-    size_t o_hdr = carve(sizeof(PlanHeader));
-    size_t o_cnt = carve(sizeof(uint32_t) * 2 * (size_t)cap_tiles);
-    const size_t zero_needed = bytes;
-    size_t o_toff = carve(sizeof(uint32_t) * (nn + 1));
-    size_t o_noff = carve(sizeof(uint32_t) * (nn + 1));
-    size_t o_bsum = carve(sizeof(uint32_t) * 2 * (nblocks + 1));
-    size_t o_tbuf = carve(sizeof(uint32_t) * (size_t)cap_tiles);
-    size_t o_nodes = carve(sizeof(U128) * 2 * (size_t)cap_tiles);
+    const PlanLayout lay = plan_layout(nn);
+    const size_t bytes = lay.bytes, zero_needed = lay.zero_needed;
+    const size_t o_hdr = lay.hdr, o_cnt = lay.cnt, o_toff = lay.toff, o_noff = lay.noff;
+    const size_t o_bsum = lay.bsum, o_tbuf = lay.tbuf, o_nodes = lay.nodes;
     bool fresh = false;
     uint8_t* s = (uint8_t*)scratch_get(SLOT_FP_PLAN, bytes, stream, &st, &fresh);
     if (!s) return st;

@@ -77,6 +77,10 @@ int device_sm_count() {
     return n;
 }
 
+size_t scratch_block_bytes(size_t bytes) {
+    return align_up(bytes < 4096 ? 4096 : bytes + bytes / 4, 1 << 16);
+}
+
 void* scratch_get(int slot, size_t bytes, cudaStream_t stream, int* status, bool* fresh) {
     int d = current_device();
     std::lock_guard<std::mutex> lk(g_mu);
@@ -87,7 +91,7 @@ void* scratch_get(int slot, size_t bytes, cudaStream_t stream, int* status, bool
     if (b.ptr) raw_free(b.ptr, stream);  // stream-ordered after earlier uses
     b.ptr = nullptr;
     b.bytes = 0;
-    size_t want = align_up(bytes < 4096 ? 4096 : bytes + bytes / 4, 1 << 16);
+    size_t want = scratch_block_bytes(bytes);
     void* p = raw_alloc(want, stream);
     if (!p) {
         *status = ODP_ERR_OOM;

@@ -1224,8 +1224,8 @@ int odp_server_bytes(const odp_server_cfg* cfg, uint64_t* bytes) {
     const uint64_t pend_cap = std::min<uint64_t>(E, 16 * B);
     const uint64_t find_cap = 3 * B + pend_cap + 64;
     const uint64_t table = sizeof(prim::Slot);
-    // the blocks odp_server_create allocates, plus per slot an allowance of
-    // 66 MB for allocation granularity and the fingerprint call's scratch
+    // the blocks odp_server_create allocates, plus per slot the scratch of the
+    // slot's fingerprint calls and 20 MB for allocation granularity
     const uint64_t shared = 64 + E * (64 + 4 + 4 + 4) + 7 * table * (cap_p + 1) +
                             table * (cap_b + 1) + 12 * SRV_NDEV + 40 * pend_cap + 80 +
                             find_cap * (sizeof(odp_finding) + 8);
@@ -1233,7 +1233,7 @@ int odp_server_bytes(const odp_server_cfg* cfg, uint64_t* bytes) {
     const uint64_t scan = 4 * (prim::scan_tmp_words(256u * ((uint32_t)B / prim::SORT_TILE + 2)) + 16);
     const uint64_t per_slot = B * (sizeof(odp_event) + 8 + 8 + 16 + 4 + 4 + 12 * 4 + 8) +
                               sizeof(BatchPar) + hist + scan + find_cap * (sizeof(odp_finding) + 8) +
-                              16 + 2 * 4 * 256 + 16 + (66ull << 20);
+                              16 + 2 * 4 * 256 + 16 + fp_plan_scratch_bytes(B) + (20ull << 20);
     *bytes = shared + (uint64_t)cfg->n_slots * per_slot;
     return ODP_OK;
 }

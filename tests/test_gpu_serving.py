@@ -433,7 +433,8 @@ def test_allocation_within_the_reservation(cuda_ok, n_slots, max_events, max_bat
     srv = odp.Server(device_budget_bytes=need, watermark_timeout_us=1000, **shape)
     try:
         got = srv.stats()["device_bytes"]
-        # every allocated block is counted; the rest is the per-slot allowance
-        assert need - n_slots * (66 << 20) <= got <= need
+        # every allocated block is counted; the rest is per slot the fingerprint
+        # plan's scratch (about 58 MB for a batch of at most 4,096) and 20 MB
+        assert need - n_slots * (100 << 20) <= got <= need
     finally:
         srv.close()

@@ -8,7 +8,7 @@ import pytest
 import paper_2601_12713_b300 as odp
 
 OOM, CUDA, INVALID, UNSUPPORTED = -3, -2, -1, -7
-SLOT_ALLOWANCE = 66 << 20
+SLOT_ALLOWANCE = 20 << 20  # granularity, beside the fingerprint scratch
 
 
 def shape(**kw):
@@ -28,8 +28,9 @@ def test_reservation_is_linear_in_slots():
     b = [odp.server_bytes(**shape(n_slots=k)) for k in (1, 2, 3, 8)]
     per_slot = b[1] - b[0]
     assert b[2] - b[1] == per_slot and b[3] - b[0] == 7 * per_slot
-    # each slot holds at least its batch's event records and the allowance
-    assert per_slot >= 4096 * 64 + SLOT_ALLOWANCE
+    # each slot holds at least its batch's event records, the allowance and
+    # the fingerprint plan's tile arrays (44 bytes for each of 2^20 + n tiles)
+    assert per_slot >= 4096 * 64 + SLOT_ALLOWANCE + 44 * ((1 << 20) + 4096)
 
 
 def test_reservation_covers_the_resident_log():
