@@ -26,7 +26,11 @@
 // Parity status: FP128 is project-defined, so it is pinned by the published
 // SplitMix64 test vectors (its constants), by algebraic invariants (every
 // single 16-byte word change alters the hash, the mixers are bijections with
-// explicit inverses), by tree-shape equivalence and by collision tests; the
+// explicit inverses), by running each lane backwards to its start constants
+// (chain step and Feistel finish inverted by the tests), by the closed form
+// of the lane tree (lane l reaches the root through G^popcount(l)), by the
+// leaf constants recovered through the inverse of Q, by worked examples
+// checked step by step, by tree-shape equivalence and by collision tests; the
 // analysis is pinned by the paper's worked listings, Table 2 count semantics
 // and brute-force definitions on exhaustive small traces.  The predicted-
 // speedup *accuracy* against real applications is parity unpinned (it needs
@@ -136,31 +140,39 @@ u64 load_le64(const uint8_t* p) {
 
 const u64 CHUNK = 4096;
 
+// State of lane l (0..31) of a chunk zero-padded to 4096 bytes: the lane
+// absorbs words l, l+32, ..., l+224 into two chains, then a two-round
+// Feistel couples the two chains.
+U128 lane_state(const uint8_t* padded, int l) {
+    u64 a = K().c[32 + 2 * l];
+    u64 b = K().c[33 + 2 * l];
+    for (int j = 0; j < 8; ++j) {
+        int w = l + 32 * j;
+        u64 lo = load_le64(padded + 16 * w);
+        u64 hi = load_le64(padded + 16 * w + 8);
+        a = chain_step(a ^ lo, K().odd(0), K().odd(1));
+        b = chain_step(b ^ hi, K().odd(2), K().odd(3));
+    }
+    a = a ^ (b * K().odd(4));
+    b = b ^ (a * K().odd(5));
+    U128 s = {a, b};
+    return s;
+}
+
+// The chunk at `p` with `r` valid bytes, zero-padded to 4096 bytes.
+void pad_chunk(const uint8_t* p, u64 r, uint8_t* padded) {
+    std::memset(padded, 0, (size_t)CHUNK);
+    std::memcpy(padded, p, (size_t)r);
+}
+
 // Leaf of one chunk: `r` valid bytes (1..4096) starting at `p`.
 U128 chunk_leaf(const uint8_t* p, u64 r) {
     // The chunk zero-padded to 4096 bytes, as 256 sixteen-byte words.
     uint8_t padded[CHUNK];
-    std::memset(padded, 0, sizeof padded);
-    std::memcpy(padded, p, (size_t)r);
+    pad_chunk(p, r, padded);
 
-    // Lane l (0..31) absorbs words l, l+32, ..., l+224 into two chains.
     U128 lane[32];
-    for (int l = 0; l < 32; ++l) {
-        u64 a = K().c[32 + 2 * l];
-        u64 b = K().c[33 + 2 * l];
-        for (int j = 0; j < 8; ++j) {
-            int w = l + 32 * j;
-            u64 lo = load_le64(padded + 16 * w);
-            u64 hi = load_le64(padded + 16 * w + 8);
-            a = chain_step(a ^ lo, K().odd(0), K().odd(1));
-            b = chain_step(b ^ hi, K().odd(2), K().odd(3));
-        }
-        // Lane finish: a two-round Feistel couples the two chains.
-        a = a ^ (b * K().odd(4));
-        b = b ^ (a * K().odd(5));
-        lane[l].x = a;
-        lane[l].y = b;
-    }
+    for (int l = 0; l < 32; ++l) lane[l] = lane_state(padded, l);
 
     // Lane combine: a complete binary tree over the 32 lanes, left operand is
     // the lower lane range; node = left ^ G(right).
@@ -718,6 +730,15 @@ void orc_chunk_leaf(const uint8_t* p, uint64_t r, uint64_t* out) {
     U128 h = chunk_leaf(p, r);
     out[0] = h.x;
     out[1] = h.y;
+}
+// State of lane l after its Feistel finish, for the chunk at p with r valid
+// bytes (1..4096); out[0] = a chain, out[1] = b chain.
+void orc_lane_state(const uint8_t* p, uint64_t r, int l, uint64_t* out) {
+    uint8_t padded[CHUNK];
+    pad_chunk(p, r, padded);
+    U128 s = lane_state(padded, l);
+    out[0] = s.x;
+    out[1] = s.y;
 }
 void orc_tree_node(const uint64_t* left, const uint64_t* right, uint64_t count, uint64_t* out) {
     U128 l = {left[0], left[1]}, r = {right[0], right[1]};

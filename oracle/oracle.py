@@ -84,6 +84,8 @@ def lib():
         so.orc_constant.argtypes = [ctypes.c_int, u64p]
         so.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, u64p]
         so.orc_chunk_leaf.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+        so.orc_lane_state.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                      ctypes.c_void_p]
         so.orc_tree_node.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                      ctypes.c_void_p]
         so.orc_mix128.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]

@@ -208,3 +208,29 @@ def test_reference_vectors(cuda_ok, odp):
     assert gpu_fp(odp, bufs) == want
     for b, w in zip(bufs, want):
         assert gpu_fp(odp, [b]) == [w]
+
+
+def test_worked_examples(cuda_ok, odp):
+    """The GPU reproduces the FP128 v1 worked examples of tests/golden (each
+    step of which the CPU tests check against the definition by inversion),
+    alone, in one batch, and at an odd start address."""
+    import sys
+
+    sys.path.insert(0, __import__("os").path.dirname(__file__))
+    from test_oracle_fp128_lanes import WORKED_NAMES, load_worked, worked_input
+
+    _, ex = load_worked()
+    t = torch.zeros(3 * 8192, dtype=torch.uint8, device="cuda")
+    views, want = [], []
+    for k, name in enumerate(WORKED_NAMES):
+        data = worked_input(name)
+        for off in (8192 * (k % 3), 8192 * (k % 3) + 4097):
+            if off + len(data) > t.numel():
+                continue
+            if data:
+                t[off:off + len(data)] = torch.frombuffer(bytearray(data), dtype=torch.uint8).cuda()
+            v = t[off:off + len(data)]
+            assert gpu_fp(odp, [v]) == [ex[name]["out"]], (name, off)
+            views.append(v.clone())
+            want.append(ex[name]["out"])
+    assert gpu_fp(odp, views) == want
