@@ -118,9 +118,13 @@ int odp_fingerprint(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
  *
  * The first call on each device looks up the array's device address (with
  * that device current) and may return ODP_ERR_CUDA if that fails; make the
- * first call on a device before capturing a stream.  Every call reuses the
- * same array: calls whose work overlaps on the GPU (different streams, or
- * another thread) race and give wrong results, so serialise them.  A null
+ * first call on a device before capturing a stream.  The address is kept
+ * until the process exits: do not call this after cudaDeviceReset on a
+ * device it has already been called on.  Every call reuses the same array:
+ * calls whose work overlaps on the GPU (different streams, or another
+ * thread) race and give wrong results, so serialise them.  Each call clears
+ * the array's header and tree counters first, so a racing or failed call
+ * spoils only its own results and those of the calls it overlapped.  A null
  * ptrs[i] with sizes[i] > 0 yields {0, 0} in out128[i]; this variant does
  * not update the status word of odp_fingerprint_status.
  */
@@ -467,6 +471,31 @@ int odp_server_origin(odp_server* s, uint32_t* producer, uint64_t* seq, uint64_t
 int odp_server_stats_get(odp_server* s, odp_server_stats* st);
 
 int odp_server_destroy(odp_server* s);
+
+/* ----------------------------------------------- fingerprints of a log */
+
+/*
+ * odp_fingerprint_log -- writes the FP128 v1 fingerprint of every transfer's
+ * bytes into that transfer's record (fp_lo, fp_hi), all transfers of the log
+ * in one batched odp_fingerprint call.  The paper (Sec. 5) stores a hash of
+ * the transferred data in each data-op record; this is that step for a log
+ * whose payloads are still in device memory, in the batched form instead of
+ * one launch per transfer.
+ *
+ *   events    device, n 64-byte records, 8-byte aligned.  Records of kind
+ *             ODP_TO_DEV, ODP_FROM_DEV or ODP_DEV_TO_DEV get their fp_lo and
+ *             fp_hi overwritten with the fingerprint of `bytes` bytes at
+ *             payloads[i]; every other record is left unchanged.
+ *   payloads  device array of n device pointers (any alignment); entries of
+ *             non-transfers are not read.  A null pointer with bytes > 0
+ *             gives {0, 0} and records ODP_ERR_INVALID_ARG in the status
+ *             word of odp_fingerprint_status.
+ * Asynchronous on `stream`; scratch from the library's allocator (32 bytes
+ * per record plus the fingerprint plan).  ODP_ERR_INVALID_ARG for null
+ * arrays with n > 0 or a misaligned `events`.
+ */
+int odp_fingerprint_log(odp_event* events, const void* const* payloads, uint64_t n,
+                        cudaStream_t stream);
 
 /* ------------------------------------------------------- collision check */
 

@@ -9,7 +9,7 @@ is no CPU fallback.  ``paper_2601_12713_b300.build`` compiles it.
 
 _EXPORTS = (
     "LIB_PATH", "lib", "status_string", "OdpError", "fingerprint", "fingerprint_one",
-    "fingerprint_noalloc", "fingerprint_tensors", "fingerprint_with", "autotune_fingerprint", "autotune_clear",
+    "fingerprint_noalloc", "fingerprint_log", "fingerprint_tensors", "fingerprint_with", "autotune_fingerprint", "autotune_clear",
     "fingerprint_status", "analyze", "Findings", "EVENT_DTYPE", "FINDING_DTYPE", "SITE_DTYPE",
     "SUMMARY_FIELDS", "set_torch_allocator", "release_scratch", "Server", "log_tensor",
     "verify_fingerprints", "set_allocator", "server_bytes",

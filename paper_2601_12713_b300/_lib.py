@@ -28,6 +28,8 @@ _lib.odp_fingerprint_one.argtypes = [_vp, ctypes.c_uint64, _vp, _vp]
 _lib.odp_fingerprint_one.restype = ctypes.c_int
 _lib.odp_fingerprint_noalloc.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, _vp]
 _lib.odp_fingerprint_noalloc.restype = ctypes.c_int
+_lib.odp_fingerprint_log.argtypes = [_vp, _vp, ctypes.c_uint64, _vp]
+_lib.odp_fingerprint_log.restype = ctypes.c_int
 class FpSchedule(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("tmin_scale", ctypes.c_int32), ("load_stages", ctypes.c_int32)]
@@ -239,6 +241,18 @@ def analyze(events: torch.Tensor, n: int, out: Findings, stream=None) -> None:
     assert events.is_cuda and events.numel() >= 64 * n
     _check(_lib.odp_analyze(events.data_ptr() if n else None, n, ctypes.byref(out.struct),
                             _stream(stream)), "odp_analyze")
+
+
+def fingerprint_log(events: torch.Tensor, n: int, payload_ptrs: torch.Tensor,
+                    stream=None) -> None:
+    """Writes the fingerprint of every transfer's payload (``payload_ptrs``:
+    int64 CUDA tensor of n device pointers) into its record of ``events``
+    (a CUDA byte tensor of n 64-byte records)."""
+    assert events.is_cuda and events.numel() >= 64 * n
+    assert payload_ptrs.is_cuda and payload_ptrs.numel() >= n
+    _check(_lib.odp_fingerprint_log(events.data_ptr() if n else None,
+                                    payload_ptrs.data_ptr() if n else None, n, _stream(stream)),
+           "odp_fingerprint_log")
 
 
 def verify_fingerprints(events: torch.Tensor, n: int, payload_ptrs: torch.Tensor,

@@ -22,6 +22,7 @@ enum ScratchSlot {
     SLOT_AN_SORT = 3,
     SLOT_AN_SITES = 4,
     SLOT_SERVE = 5,
+    SLOT_FP_LOG = 6,
     SLOT_COUNT = 8
 };
 

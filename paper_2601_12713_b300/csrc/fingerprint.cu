@@ -468,52 +468,111 @@ struct Ring {
     uint8_t* buf;        // STAGES * 4096 bytes of this warp
     uint64_t* bars;      // STAGES mbarriers
     uint32_t parity;     // expected phase parity per slot (bit s)
-    int32_t* timeout;    // set when a wait gave up
+    uint32_t pending;    // slots with a copy issued and not yet waited for (bit s)
+    bool failed;         // a wait ran out: no further copies, no further hashing
+    int32_t* timeout;    // status word set when a wait gives up
 };
 
-constexpr uint32_t RING_WAIT_LIMIT = 1u << 26;  // polls before a wait gives up
+// A wait for one chunk copy gives up after this long (a 4 KiB copy normally
+// lands within microseconds); the warp then stops using its ring.
+constexpr uint64_t RING_WAIT_NS = 50ull * 1000 * 1000;
+
+// Bytes each slot's mbarrier expects per chunk copy.  Always CHUNK in the
+// library; the bounded-wait test builds the sources with a larger value, so
+// that a phase can never complete and every wait runs out with no copy left
+// in flight.
+#ifndef ODP_RING_TX_BYTES
+#define ODP_RING_TX_BYTES CHUNK
+#endif
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Every kernel variant starts its ring state here (STAGES = 0 has no slots
+// and never fails); the mbarriers are initialised only where slots exist.
 __device__ __forceinline__ void ring_init(Ring& r, int stages, int lane) {
+    r.parity = 0;
+    r.pending = 0;
+    r.failed = false;
+    if (stages == 0) return;
     if (lane == 0) {
         for (int s = 0; s < stages; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(r.bars + s)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    r.parity = 0;
     __syncwarp();
 }
 
-// Lane 0 starts the copy of one 4 KiB chunk into slot s.
-__device__ __forceinline__ void ring_issue(Ring& r, int s, const uint8_t* src) {
-    const uint32_t bar = smem_addr(r.bars + s), dst = smem_addr(r.buf + (size_t)s * CHUNK);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(CHUNK)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(dst), "l"(src), "r"(CHUNK), "r"(bar)
-        : "memory");
+// Called by the whole warp: lane 0 starts the copy of one 4 KiB chunk into
+// slot s; every lane records the slot as pending.
+__device__ __forceinline__ void ring_issue(Ring& r, int s, const uint8_t* src, int lane) {
+    if (lane == 0) {
+        const uint32_t bar = smem_addr(r.bars + s), dst = smem_addr(r.buf + (size_t)s * CHUNK);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)ODP_RING_TX_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+            ::"r"(dst), "l"(src), "r"(CHUNK), "r"(bar)
+            : "memory");
+    }
+    r.pending |= 1u << s;
 }
 
-// All lanes wait for slot s (bounded), then flip its expected parity.
-__device__ __forceinline__ void ring_wait(Ring& r, int s) {
+// Polls slot s's phase until every lane has seen it complete, or until
+// RING_WAIT_NS have passed on lane 0's clock (a warp-uniform decision).
+__device__ __forceinline__ bool ring_poll(const Ring& r, int s) {
     const uint32_t bar = smem_addr(r.bars + s), par = (r.parity >> s) & 1u;
-    uint32_t done = 0;
-    for (uint32_t it = 0; it < RING_WAIT_LIMIT && !done; ++it) {
+    uint64_t deadline = 0;
+    for (uint32_t it = 1;; ++it) {
+        uint32_t done;
         asm volatile(
             "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
             "selp.u32 %0, 1, 0, p; }"
             : "=r"(done)
             : "r"(bar), "r"(par)
             : "memory");
+        if (__all_sync(ODP_FULL_MASK, done)) return true;
+        if ((it & 63) == 0) {
+            const uint64_t now = shfl64(global_ns(), 0);
+            if (deadline == 0)
+                deadline = now + RING_WAIT_NS;
+            else if (now > deadline)
+                return false;
+        }
     }
-    if (!done && r.timeout) atomicCAS((int*)r.timeout, 0, ODP_ERR_TIMEOUT);
-    r.parity ^= 1u << s;
+}
+
+// All lanes wait for slot s.  A wait that runs out records ODP_ERR_TIMEOUT
+// and marks the ring failed; the caller then abandons the tile.
+__device__ __forceinline__ bool ring_wait(Ring& r, int s, int lane) {
+    if (ring_poll(r, s)) {
+        r.parity ^= 1u << s;
+        r.pending &= ~(1u << s);
+        return true;
+    }
+    if (lane == 0 && r.timeout) atomicCAS((int*)r.timeout, 0, ODP_ERR_TIMEOUT);
+    r.failed = true;
+    return false;
+}
+
+// Before the warp exits: wait (bounded again) for copies still in flight
+// into its ring.  Nothing is pending unless a wait ran out.
+__device__ __forceinline__ void ring_drain(Ring& r) {
+    for (int s = 0; r.pending != 0 && s < 32; ++s) {
+        if (!((r.pending >> s) & 1u)) continue;
+        if (ring_poll(r, s)) r.parity ^= 1u << s;
+        r.pending &= ~(1u << s);
+    }
 }
 
 // Hash chunks [c0, c0 + cnt) of a buffer (`cnt` <= 2^m); returns the subtree
@@ -529,9 +588,8 @@ __device__ __forceinline__ U128 hash_tile(const uint8_t* base, uint64_t size, ui
     uint64_t nbulk = 0;
     if constexpr (STAGES > 0) {
         if (ALIGNED) nbulk = (size - (c0 + cnt - 1) * CHUNK) >= CHUNK ? cnt : cnt - 1;
-        if (lane == 0)
-            for (uint64_t k = 0; k < nbulk && k < (uint64_t)STAGES; ++k)
-                ring_issue(ring, (int)k, base + (c0 + k) * CHUNK);
+        for (uint64_t k = 0; k < nbulk && k < (uint64_t)STAGES; ++k)
+            ring_issue(ring, (int)k, base + (c0 + k) * CHUNK, lane);
     }
     for (uint64_t g0 = 0; g0 < cnt; g0 += 32) {
         const uint32_t gc = (uint32_t)umin64(32, cnt - g0);
@@ -546,14 +604,14 @@ __device__ __forceinline__ U128 hash_tile(const uint8_t* base, uint64_t size, ui
                 const uint64_t kk = g0 + k;  // chunk index within the tile
                 if (kk < nbulk) {
                     const int slot = (int)(kk % STAGES);
-                    ring_wait(ring, slot);
+                    if (!ring_wait(ring, slot, lane)) return U128{0, 0};  // timed out
                     const uint8_t* sb = ring.buf + (size_t)slot * CHUNK;
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
                         w[j] = *reinterpret_cast<const uint4*>(sb + 16 * (lane + 32 * j));
                     __syncwarp();
-                    if (lane == 0 && kk + STAGES < nbulk)
-                        ring_issue(ring, slot, base + (c0 + kk + STAGES) * CHUNK);
+                    if (kk + STAGES < nbulk)
+                        ring_issue(ring, slot, base + (c0 + kk + STAGES) * CHUNK, lane);
                     from_ring = true;
                 }
             }
@@ -706,7 +764,7 @@ __global__ void __launch_bounds__(WARPS * 32, fp_min_ctas<WARPS, STAGES>()) fp_t
     ring.buf = ring_smem + (size_t)warp * STAGES * CHUNK;
     ring.bars = reinterpret_cast<uint64_t*>(ring_smem + (size_t)WARPS * STAGES * CHUNK) + warp * 8;
     ring.timeout = a.status;
-    if constexpr (STAGES > 0) ring_init(ring, STAGES, lane);
+    ring_init(ring, STAGES, lane);
     uint64_t a0, b0;
     fp::lane_init(lane, a0, b0);
     uint32_t T, m_floor;
@@ -755,14 +813,20 @@ __global__ void __launch_bounds__(WARPS * 32, fp_min_ctas<WARPS, STAGES>()) fp_t
         if (!first && lane == 0) t_next = 2 * total + atomicAdd(&a.hdr->tile_counter, 1u);
         first = false;
         const TileInfo cur = tile_info(a, t, m_floor);
-        U128 root;
-        if (((uintptr_t)cur.base & 15) == 0)
+        U128 root{0, 0};
+        // After a bulk-copy wait ran out (ODP_ERR_TIMEOUT is recorded) the
+        // warp hashes nothing more, but still climbs, so every tree counter
+        // and the tile counter end the call reset for the next one.
+        if (ring.failed) {
+        } else if (((uintptr_t)cur.base & 15) == 0) {
             root = hash_tile<true, STAGES>(cur.base, cur.size, cur.c0, cur.cnt, lane, a0, b0, st, ring);
-        else
+        } else {
             root = hash_tile<false, STAGES>(cur.base, cur.size, cur.c0, cur.cnt, lane, a0, b0, st, ring);
+        }
         climb(a, cur, root, lane);
         t = __shfl_sync(ODP_FULL_MASK, t_next, 0);
     }
+    if constexpr (STAGES > 0) ring_drain(ring);
     // The last warp out (of the min(T, warps) that took tiles) resets the
     // tile counter for the next call and publishes the plan's error code (the
     // first error index is not kept).
@@ -998,6 +1062,73 @@ extern "C" int odp_fingerprint_one(const void* ptr, uint64_t size, odp_fp128* ou
 }
 
 // ---------------------------------------------------------------------------
+// odp_fingerprint_log: the fingerprint of every transfer of an event log,
+// written into the transfer's record, in one batched odp_fingerprint call.
+// ---------------------------------------------------------------------------
+namespace odp {
+namespace {
+
+__device__ __forceinline__ bool log_is_transfer(const uint8_t* ev, uint64_t i) {
+    const uint32_t k = ev[64 * i + 60];
+    return k == ODP_TO_DEV || k == ODP_FROM_DEV || k == ODP_DEV_TO_DEV;
+}
+
+// Buffer list of the batched call: a transfer's payload and byte count, an
+// empty buffer for every other record.
+__global__ void __launch_bounds__(256) fp_log_prep(const uint8_t* ev, const void* const* payloads,
+                                                   uint64_t n, const void** ptrs,
+                                                   uint64_t* sizes) {
+    for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull) {
+        const bool x = log_is_transfer(ev, i);
+        ptrs[i] = x ? payloads[i] : nullptr;
+        sizes[i] = x ? reinterpret_cast<const uint64_t*>(ev + 64 * i)[4] : 0;
+    }
+}
+
+// Fingerprints into the records' fp_lo / fp_hi words (transfers only).
+__global__ void __launch_bounds__(256) fp_log_store(uint8_t* ev, const odp_fp128* fps,
+                                                    uint64_t n) {
+    for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull) {
+        if (!log_is_transfer(ev, i)) continue;
+        uint64_t* r = reinterpret_cast<uint64_t*>(ev + 64 * i);
+        const odp_fp128 f = fps[i];
+        r[5] = f.lo;
+        r[6] = f.hi;
+    }
+}
+
+}  // namespace
+
+static int fp_run_log(odp_event* events, const void* const* payloads, uint64_t n,
+                      cudaStream_t stream) {
+    if (n == 0) return ODP_OK;
+    if (!events || !payloads) return ODP_ERR_INVALID_ARG;
+    if (((uintptr_t)events & 7) != 0) return ODP_ERR_INVALID_ARG;
+    if (n > (1ull << 28)) return ODP_ERR_UNSUPPORTED;
+    int st = ODP_OK;
+    const size_t o_sizes = align_up(8 * n, 256), o_fps = o_sizes + align_up(8 * n, 256);
+    uint8_t* s = (uint8_t*)scratch_get(SLOT_FP_LOG, o_fps + 16 * n, stream, &st);
+    if (!s) return st;
+    const void** ptrs = (const void**)s;
+    uint64_t* sizes = (uint64_t*)(s + o_sizes);
+    odp_fp128* fps = (odp_fp128*)(s + o_fps);
+    const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)device_sm_count() * 8);
+    fp_log_prep<<<grid, 256, 0, stream>>>((const uint8_t*)events, payloads, n, ptrs, sizes);
+    ODP_CHECK_CUDA(cudaGetLastError());
+    st = fp_run(ptrs, sizes, n, fps, stream, fp_schedule_for(n));
+    if (st != ODP_OK) return st;
+    fp_log_store<<<grid, 256, 0, stream>>>((uint8_t*)events, fps, n);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace odp
+
+extern "C" int odp_fingerprint_log(odp_event* events, const void* const* payloads, uint64_t n,
+                                   cudaStream_t stream) {
+    return odp::fp_run_log(events, payloads, n, stream);
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free variant of odp_fingerprint (no counterpart in the paper).
 //
 // For callers that cannot allocate device memory -- for example code running
@@ -1031,7 +1162,9 @@ std::mutex g_na_mu;
 std::map<int, uint8_t*> g_na_base;  // device -> address of g_na_scratch
 
 // Device address of the array on the current device (looked up once per
-// device with that device current).
+// device with that device current).  The address is kept for the life of
+// the process, so it is stale after cudaDeviceReset (which destroys the
+// context holding the array).
 uint8_t* na_base(int* status) {
     int dev = current_device();
     std::lock_guard<std::mutex> lk(g_na_mu);
@@ -1085,10 +1218,14 @@ static int fp_run_noalloc(const void* const* ptrs, const uint64_t* sizes, uint64
     const uint32_t total_warps = (uint32_t)(sms * ctas * TILE_WARPS);
     a.tmin = std::max<uint32_t>(1, (uint32_t)(2ull * total_warps / a.n));
 
-    // the header (chunk total, error word, tile counter) must start cleared;
-    // the plan kernels rewrite every offset and zero the tree counters
+    // The header (chunk total, error word, tile counter) and the tree
+    // counters (160 KiB) start cleared on every call: a call that overlapped
+    // another one, or a launch that failed, may have left a counter set, and
+    // that must not spoil the calls after it.  The plan kernels rewrite every
+    // offset and the tile list.
     ODP_CHECK_CUDA(cudaMemsetAsync(a.hdr, 0, sizeof(PlanHeader), stream));
     ODP_CHECK_CUDA(cudaMemsetAsync(&a.hdr->err, 0xFF, sizeof(unsigned long long), stream));
+    ODP_CHECK_CUDA(cudaMemsetAsync(a.counters, 0, 4ull * 2 * NA_CAP_TILES, stream));
     fp_plan_small<<<1, 1024, 0, stream>>>(a);
     fp_plan_tiles<<<sms * 4, 256, 0, stream>>>(a);
     fp_tiles<TILE_WARPS, 0><<<sms * ctas, TILE_WARPS * 32, 0, stream>>>(a);

@@ -387,15 +387,32 @@ def plain_small(seed: int = 0x0DB1, n_buffers: int = 128, n_cycles: int = 1000,
 # Trace at scale: an iterative offload solver
 # ---------------------------------------------------------------------------
 
+def skip_kernels(events: np.ndarray, fraction: float, seed: int, device: int = 0) -> np.ndarray:
+    """Moves a seeded ``fraction`` of the KERNEL events of ``device`` to device
+    ``device + 1`` (in place) and returns their indices.  In the iterative
+    solver trace such an iteration launches nothing on the device its arrays
+    are mapped to: its allocations are unused (Alg. 4), and its to-device
+    transfers wait for the next iteration's kernel, where a resend of the same
+    array overwrites them unused (Alg. 5)."""
+    k = np.flatnonzero((events["kind"] == KERNEL) & (events["dst_dev"] == device))
+    r = prng.Rng(prng.derive(seed, 23))
+    moved = k[r.uniform(k.size) < fraction]
+    events["dst_dev"][moved] = device + 1
+    return moved
+
+
 def iterative_solver(seed: int = 0x0DB4, n_iter: int = 2000, n_arrays: int = 25_000,
                      per_iter: int = 6_250, p_change: float = 0.2, n_sites: int = 500,
-                     device: int = 0) -> TraceBundle:
+                     device: int = 0, p_skip_kernel: float = 0.0) -> TraceBundle:
     """Each iteration maps a seeded sample of ``per_iter`` float64 arrays
     (sizes log-uniform 1 KiB .. 64 MiB): ALLOC and TO_DEV at region entry, one
     KERNEL, FROM_DEV and DELETE at exit -- 4 * per_iter data-op events plus one
     kernel per iteration.  Before every transfer the array's content version
     changes with probability ``p_change``.  Content ids are (array, version);
-    fingerprints are filled with :func:`fill_fp_from_content`.
+    fingerprints are filled with :func:`fill_fp_from_content`.  With
+    ``p_skip_kernel`` > 0 that fraction of the iterations runs its kernel on
+    another device (:func:`skip_kernels`), which gives unused allocations
+    and unused transfers.
     """
     r = prng.Rng(prng.derive(seed, 21))
     lo, hi = np.log(1024.0), np.log(64.0 * (1 << 20))
@@ -479,4 +496,6 @@ def iterative_solver(seed: int = 0x0DB4, n_iter: int = 2000, n_arrays: int = 25_
     start = 1_000 + np.concatenate([[0], np.cumsum(dur + gap)[:-1]])
     ev["t_start_ns"] = start
     ev["t_end_ns"] = start + dur
+    if p_skip_kernel > 0:
+        skip_kernels(ev, p_skip_kernel, seed, device)
     return TraceBundle(events=ev, content=content)

@@ -112,3 +112,73 @@ def test_scan_lookback_wait_is_bounded(cuda_ok, tmp_path):
     assert lib.scan_timeout_case(ctypes.byref(fault), ctypes.byref(correct)) == 0
     assert fault.value == 1
     assert correct.value == 1
+
+
+def test_bulk_copy_wait_is_bounded(cuda_ok, tmp_path):
+    """The fingerprint kernel's waits for its bulk chunk copies are bounded in
+    time.  The test builds the library's fingerprint sources with each ring
+    slot's mbarrier expecting 8,192 bytes per 4,096-byte chunk copy, so no
+    phase can complete and every wait runs out with nothing left in flight.
+    The calls (batched and single-buffer) must end within seconds and report
+    ODP_ERR_TIMEOUT; the same library's register-load path must then give
+    correct fingerprints with a clean status, so no tree or tile counter was
+    left set by the abandoned tiles."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+    import time
+
+    import paper_2601_12713_b300 as odp
+    from paper_2601_12713_b300._lib import FpSchedule
+    from synth import gpu
+
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(root, "paper_2601_12713_b300", "csrc")
+    so = str(tmp_path / "libodp_ring_hook.so")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                    "-shared", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+                    "-Xlinker", "-Bsymbolic", "-DODP_RING_TX_BYTES=8192u",
+                    "-I", os.path.join(root, "include"), "-I", csrc,
+                    *(os.path.join(csrc, f) for f in ("fingerprint.cu", "runtime.cu",
+                                                      "autotune.cu")),
+                    "-o", so], check=True)
+    hook = ctypes.CDLL(so)
+    vp = ctypes.c_void_p
+    hook.odp_fingerprint_with.argtypes = [ctypes.POINTER(FpSchedule), vp, vp, ctypes.c_uint64,
+                                          vp, vp]
+    hook.odp_fingerprint_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+
+    t = torch.empty((3 << 20) + 8192, dtype=torch.uint8, device="cuda")
+    gpu.fill(t, content.RANDOM, 21)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def case(views):
+        ptrs = torch.tensor([v.data_ptr() for v in views], dtype=torch.int64, device="cuda")
+        sizes = torch.tensor([v.numel() for v in views], dtype=torch.int64, device="cuda")
+        want = torch.empty((len(views), 2), dtype=torch.int64, device="cuda")
+        odp.fingerprint(ptrs, sizes, want)
+        return ptrs, sizes, want
+
+    def run(schedule, ptrs, sizes):
+        out = torch.full((ptrs.numel(), 2), -1, dtype=torch.int64, device="cuda")
+        rc = hook.odp_fingerprint_with(ctypes.byref(schedule), ptrs.data_ptr(), sizes.data_ptr(),
+                                       ptrs.numel(), out.data_ptr(), stream)
+        assert rc == 0
+        torch.cuda.synchronize()
+        st = ctypes.c_int32(0)
+        assert hook.odp_fingerprint_status(stream, ctypes.byref(st)) == 0
+        return out, st.value
+
+    ring, regs = FpSchedule(8, 0, 2, 2), FpSchedule(8, 0, 2, 0)
+    for views in ([t[:2 << 20], t[4096:4096 + (1 << 20) + 100]], [t[8192:8192 + (3 << 20)]]):
+        ptrs, sizes, want = case(views)
+        t0 = time.monotonic()
+        _, status = run(ring, ptrs, sizes)
+        assert time.monotonic() - t0 < 20
+        assert status == -4  # ODP_ERR_TIMEOUT
+        for _ in range(2):
+            out, status = run(regs, ptrs, sizes)
+            assert status == 0
+            assert torch.equal(out, want)

@@ -121,6 +121,30 @@ def test_null_pointer_reports_status(cuda_ok, odp):
     assert odp.fingerprint_status() == 0
 
 
+@pytest.mark.parametrize("variant", [content.ZERO, content.PAGE, content.RANDOM])
+def test_sweep_sizes_16mib_and_up(cuda_ok, orc, odp, variant):
+    """The bandwidth sweep's sizes from 16 MiB up, one buffer per call as
+    benchmarked: zero and page contents at every size to 4 GiB, random bytes
+    to 1 GiB (4 GiB of random bytes has a test of its own)."""
+    import concurrent.futures
+
+    top = 4 << 30 if variant != content.RANDOM else 1 << 30
+    size = 16 << 20
+    cases = []
+    while size <= top:
+        t = dev_buffer(size, variant, seed=0x0DB2 + size.bit_length(), pad=0)
+        got = gpu_fp(odp, [t])[0]
+        host = t.cpu().numpy()
+        del t
+        torch.cuda.empty_cache()
+        cases.append((size, got, host))
+        size *= 4
+    with concurrent.futures.ThreadPoolExecutor(len(cases)) as ex:
+        wants = list(ex.map(lambda c: orc.fp128(c[2]), cases))
+    for (size, got, _), want in zip(cases, wants):
+        assert got == want, size
+
+
 def test_full_size_4gib_buffer(cuda_ok, orc, odp):
     """The bandwidth sweep's largest buffer (4 GiB, random bytes) in the launch
     configuration the benchmark times, checked against the oracle."""
@@ -133,10 +157,30 @@ def test_full_size_4gib_buffer(cuda_ok, orc, odp):
     assert got == [orc.fp128(host)]
 
 
+def oracle_all_cores(orc, host, offs, sizes):
+    """The oracle's FP128 of every buffer, split over the host's cores (the
+    oracle call releases the interpreter lock)."""
+    import concurrent.futures
+    import os
+
+    n = sizes.size
+    parts = np.array_split(np.arange(n), max(1, 4 * (os.cpu_count() or 1)))
+    want = np.zeros((n, 2), dtype=np.uint64)
+
+    def run(idx):
+        if idx.size:
+            want[idx] = orc.fp128_many(host, offs[idx], sizes[idx])
+
+    with concurrent.futures.ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        list(ex.map(run, parts))
+    return want
+
+
 def test_full_scale_batched_ragged(cuda_ok, orc, odp):
     """The 10^6-buffer, 16 GiB ragged batch in one call (as benchmarked):
-    sampled buffers equal the oracle, duplicates share fingerprints, and
-    distinct contents get distinct fingerprints."""
+    every buffer equals the oracle (the arena's bytes copied to the host and
+    hashed on all host cores), duplicates share fingerprints, and distinct
+    contents get distinct fingerprints."""
     from synth import gpu
 
     sizes, offs, seeds, dup_of = content.batched_ragged(seed=0x0DB3)
@@ -148,13 +192,17 @@ def test_full_scale_batched_ragged(cuda_ok, orc, odp):
     out = torch.empty((n, 2), dtype=torch.int64, device="cuda")
     odp.fingerprint(ptrs, sz, out)
     fps = out.cpu().numpy().view(np.uint64)
+    host = arena.cpu().numpy()
     del arena
     torch.cuda.empty_cache()
     rng = np.random.default_rng(99)
-    sample = np.concatenate([rng.choice(n, 300, replace=False), np.argsort(sizes)[-4:]])
-    for i in sample:
+    for i in np.concatenate([rng.choice(n, 50, replace=False), np.argsort(sizes)[-2:]]):
         data = content.bytes_of(content.RANDOM, int(seeds[i]), int(sizes[i]))
-        assert orc.fp128(data) == (int(fps[i, 0]), int(fps[i, 1])), i
+        assert np.array_equal(host[offs[i]:offs[i] + sizes[i]], data), i
+    want = oracle_all_cores(orc, host, offs, sizes)
+    del host
+    bad = np.flatnonzero((fps != want).any(axis=1))
+    assert bad.size == 0, f"{bad.size} buffers differ, first {bad[:5]}"
     d = np.flatnonzero(dup_of >= 0)
     assert np.array_equal(fps[d], fps[dup_of[d]])
     orig = fps[dup_of < 0]
@@ -234,3 +282,48 @@ def test_worked_examples(cuda_ok, odp):
             views.append(v.clone())
             want.append(ex[name]["out"])
     assert gpu_fp(odp, views) == want
+
+
+def test_fingerprint_log_fills_transfer_records(cuda_ok, orc, odp):
+    """odp_fingerprint_log over the plain-small trace: every transfer record
+    gets the oracle's fingerprint of its payload (payloads packed at mixed
+    alignments), every other record is left byte for byte unchanged, and a
+    second call over the filled log changes nothing."""
+    from synth import gpu, traces
+
+    b = traces.plain_small()
+    ev = b.events.copy()
+    ev["fp_lo"] = 0x1111
+    ev["fp_hi"] = 0x2222
+    n = ev.size
+    xfer = np.flatnonzero(np.isin(ev["kind"], [2, 3, 4]))
+    sizes = ev["bytes"][xfer].astype(np.int64)
+    rng = np.random.default_rng(3)
+    offs = np.zeros(xfer.size, dtype=np.int64)
+    cur = 0
+    for k in range(xfer.size):
+        cur += int(rng.integers(0, 16)) * 16 + (k % 3)  # some starts off 16-byte boundaries
+        offs[k] = cur
+        cur += int(sizes[k])
+    arena = torch.empty(cur + 64, dtype=torch.uint8, device="cuda")
+    gpu.fill_many(arena, offs, sizes, b.payload_seed[xfer].astype(np.uint64))
+    ptrs = np.zeros(n, dtype=np.int64)
+    ptrs[xfer] = arena.data_ptr() + offs
+    d_ptrs = torch.from_numpy(ptrs).cuda()
+    d_ev = torch.from_numpy(ev.view(np.uint8).reshape(-1).copy()).cuda()
+    odp.fingerprint_log(d_ev, n, d_ptrs)
+    got = d_ev.cpu().numpy().view(traces.EVENT_DTYPE)
+    assert odp.fingerprint_status() == 0
+    host = arena.cpu().numpy()
+    want = orc.fp128_many(host, offs, sizes)
+    assert np.array_equal(got["fp_lo"][xfer], want[:, 0])
+    assert np.array_equal(got["fp_hi"][xfer], want[:, 1])
+    other = np.setdiff1d(np.arange(n), xfer)
+    assert np.array_equal(got[other].view(np.uint8), ev[other].view(np.uint8))
+    keep = ev.copy()
+    keep["fp_lo"][xfer], keep["fp_hi"][xfer] = want[:, 0], want[:, 1]
+    assert np.array_equal(got.view(np.uint8), keep.view(np.uint8))
+    odp.fingerprint_log(d_ev, n, d_ptrs)
+    assert np.array_equal(d_ev.cpu().numpy(), keep.view(np.uint8).reshape(-1))
+    with pytest.raises(odp.OdpError):
+        odp.fingerprint_log(d_ev[4:], n - 1, d_ptrs)  # records not 8-byte aligned

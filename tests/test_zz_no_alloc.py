@@ -73,3 +73,49 @@ def test_noalloc_rejects_too_many_buffers(cuda_ok):
     with pytest.raises(odp.OdpError) as e:
         odp.fingerprint_noalloc(p, s, out)
     assert e.value.status == -7
+
+
+@pytest.mark.parametrize("big,n_small", [((3 << 30) + 12345, 300), ((6 << 30) + 777, 1)])
+def test_noalloc_large_tiles_match(cuda_ok, big, n_small):
+    """Batches large enough that the fixed array's tile capacity forces tiles
+    of 64 or 128 chunks (the stack merge inside a tile and the climb over
+    spans above 32 chunks), with chunk counts that are not powers of two.
+    odp_fingerprint cuts the same buffers into tiles of at most 32 chunks, so
+    equality checks the larger tiles' tree shape independently."""
+    import paper_2601_12713_b300 as odp
+
+    arena, p, s = batch(303 + n_small, n_small, 50_000, big=big + 16)
+    assert int(s.sum()) > (5 << 29)
+    got, want = both(odp, p, s)
+    del arena
+    torch.cuda.empty_cache()
+    assert np.array_equal(got, want)
+
+
+def test_noalloc_allocates_nothing(cuda_ok):
+    """After one call on the device (which looks up the array's address),
+    calls succeed with an allocator that refuses every request installed, and
+    the device's free memory is the same before and after a call."""
+    import paper_2601_12713_b300 as odp
+
+    arena, p, s = batch(404, 2000, 40_000, big=8 << 20)
+    n = p.numel()
+    want = torch.empty((n, 2), dtype=torch.int64, device="cuda")
+    odp.fingerprint(p, s, want)
+    got = torch.full((n, 2), -1, dtype=torch.int64, device="cuda")
+    odp.fingerprint_noalloc(p, s, got)  # warm-up: address lookup, modules loaded
+    torch.cuda.synchronize()
+    calls = []
+    try:
+        odp.set_allocator(lambda nbytes, stream: calls.append(nbytes) or 0, lambda q, st: None)
+        got.fill_(-1)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        odp.fingerprint_noalloc(p, s, got)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+    finally:
+        odp.set_allocator(None, None)
+    assert calls == []
+    assert free0 == free1
+    assert torch.equal(got, want)
