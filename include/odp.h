@@ -109,7 +109,7 @@ int odp_fingerprint(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
  * is for callers that cannot call cudaMalloc or an allocator at the moment
  * they need a fingerprint (code running inside an allocator or an
  * out-of-memory path, or a host program that forbids allocation after
- * start-up).  Its scratch is one file-scope device array of about 0.9 MiB
+ * start-up).  Its scratch is one file-scope device array of about 1.5 MiB
  * that every GPU loading the library keeps until the process exits.
  *
  *   ptrs, sizes, out128: as for odp_fingerprint (device arrays, n entries).

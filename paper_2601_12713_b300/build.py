@@ -58,8 +58,7 @@ def _nvcc(out, srcs, extra=(), log=None):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     if force or _stale(LIB, _deps()):
-        _nvcc(LIB, _sources(), extra=["-lcuda"] if False else [],
-              log=os.path.join(PKG, "build.log"))
+        _nvcc(LIB, _sources(), log=os.path.join(PKG, "build.log"))
         if verbose:
             print(open(os.path.join(PKG, "build.log")).read())
     if force or _stale(OMPT_LIB, [OMPT_SRC, LIB, os.path.join(INCLUDE, "odp.h"),

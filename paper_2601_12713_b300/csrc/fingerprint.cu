@@ -44,6 +44,16 @@ struct PlanHeader {
     uint32_t pad;
 };
 
+// Where one tile lies, written by the plan so that a warp finds a tile with
+// one 32-byte load: the buffer's address and size, its index and the tile's
+// index within the buffer.
+struct __align__(16) TileRec {
+    const uint8_t* base;
+    uint64_t size;
+    uint32_t b, tb, pad[2];
+};
+static_assert(sizeof(TileRec) == 32, "tile record is one 32-byte sector");
+
 struct FpArgs {
     const void* const* ptrs;
     const uint64_t* sizes;
@@ -55,7 +65,7 @@ struct FpArgs {
     uint32_t* tile_off;   // n + 1
     uint32_t* node_off;   // n + 1
     uint32_t* block_sums; // 2 * plan blocks
-    uint32_t* tile_buf;   // cap_tiles
+    TileRec* tile_rec;    // cap_tiles
     uint32_t* counters;   // 2 * cap_tiles
     U128* nodes;          // 2 * cap_tiles
     int32_t* status;      // per-device status word (null: not published)
@@ -272,8 +282,9 @@ __global__ void __launch_bounds__(256) fp_plan_add(FpArgs a) {
     }
 }
 
-// Tile -> buffer list (binary search over tile offsets).  The tree counters
-// need no reset: each group's last arriver sets its counter back to zero.
+// Tile records (binary search over tile offsets for the tile's buffer).
+// The tree counters need no reset: each group's last arriver sets its
+// counter back to zero.
 __global__ void __launch_bounds__(256) fp_plan_tiles(FpArgs a) {
     const uint32_t T = a.hdr->total_tiles;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -284,7 +295,12 @@ __global__ void __launch_bounds__(256) fp_plan_tiles(FpArgs a) {
             uint32_t mid = (lo + hi) >> 1;
             if (a.tile_off[mid] <= t) lo = mid; else hi = mid;
         }
-        a.tile_buf[t] = lo;
+        const uint64_t base = (uint64_t)a.ptrs[lo];
+        const uint64_t size = a.sizes[lo];
+        uint4* r = reinterpret_cast<uint4*>(a.tile_rec + t);
+        r[0] = make_uint4((uint32_t)base, (uint32_t)(base >> 32), (uint32_t)size,
+                          (uint32_t)(size >> 32));
+        r[1] = make_uint4(lo, t - a.tile_off[lo], 0u, 0u);
     }
 }
 
@@ -365,11 +381,15 @@ __device__ __forceinline__ void absorb_and_combine(const uint4 (&w)[8], uint64_t
     ry = b;
 }
 
-// Left-balanced combine of `cnt` (1..32) nodes held by lanes 0..cnt-1, each
-// with its leaf count c.  Every lane returns the root and its count.
+// Left-balanced combine of `cnt` (1..32, the same in every lane) nodes held
+// by lanes 0..cnt-1, each with its leaf count c.  Every lane returns the root
+// and its count.  Levels with d >= cnt combine nothing and are skipped: a
+// one-chunk tile (most tiles of a batch of small buffers) then costs no
+// node mix at all.
 __device__ __forceinline__ U128 warp_tree(U128 v, uint64_t& c, uint32_t cnt, int lane) {
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
+        if ((uint32_t)d >= cnt) break;
         uint64_t rx = shfl_down64(v.x, d), ry = shfl_down64(v.y, d);
         uint64_t rc = shfl_down64(c, d);
         U128 nd = fp::node(v, U128{rx, ry}, c + rc);
@@ -678,17 +698,42 @@ struct TileInfo {
     int m;
 };
 
-__device__ __forceinline__ TileInfo tile_info(const FpArgs& a, uint32_t t, uint32_t m_floor) {
-    TileInfo ti;
-    ti.b = a.n == 1 ? 0u : a.tile_buf[t];
-    ti.tb = a.single ? t : t - a.tile_off[ti.b];
-    ti.size = a.host_one ? a.one_size : a.sizes[ti.b];
-    ti.base = (const uint8_t*)(a.host_one ? a.one_ptr : a.ptrs[ti.b]);
+// The raw record of tile t (a planned batch).
+struct RawRec {
+    uint4 w0, w1;
+};
+
+__device__ __forceinline__ RawRec load_rec(const FpArgs& a, uint32_t t) {
+    const uint4* r = reinterpret_cast<const uint4*>(a.tile_rec + t);
+    return RawRec{__ldg(r), __ldg(r + 1)};
+}
+
+__device__ __forceinline__ TileInfo finish_info(TileInfo ti, const FpArgs& a, uint32_t m_floor) {
     ti.nchunk = n_chunks(ti.size);
     ti.m = tile_log2(ti.nchunk, a.tmin, m_floor);
     ti.c0 = (uint64_t)ti.tb << ti.m;
     ti.cnt = umin64(1ull << ti.m, ti.nchunk - ti.c0);
     return ti;
+}
+
+// Tile t of a planned batch, from its record.
+__device__ __forceinline__ TileInfo decode_rec(const RawRec& r, const FpArgs& a, uint32_t m_floor) {
+    TileInfo ti;
+    ti.base = (const uint8_t*)(((uint64_t)r.w0.y << 32) | r.w0.x);
+    ti.size = ((uint64_t)r.w0.w << 32) | r.w0.z;
+    ti.b = r.w1.x;
+    ti.tb = r.w1.y;
+    return finish_info(ti, a, m_floor);
+}
+
+// Tile t of the one buffer of a single-buffer call (no plan, no records).
+__device__ __forceinline__ TileInfo single_info(const FpArgs& a, uint32_t t, uint32_t m_floor) {
+    TileInfo ti;
+    ti.b = 0;
+    ti.tb = t;
+    ti.size = a.host_one ? a.one_size : a.sizes[0];
+    ti.base = (const uint8_t*)(a.host_one ? a.one_ptr : a.ptrs[0]);
+    return finish_info(ti, a, m_floor);
 }
 
 // Finishes a buffer of one tile, or climbs the 32-ary groups of tile roots:
@@ -812,7 +857,8 @@ __global__ void __launch_bounds__(WARPS * 32, fp_min_ctas<WARPS, STAGES>()) fp_t
     while (t < T) {
         if (!first && lane == 0) t_next = 2 * total + atomicAdd(&a.hdr->tile_counter, 1u);
         first = false;
-        const TileInfo cur = tile_info(a, t, m_floor);
+        const TileInfo cur =
+            a.single ? single_info(a, t, m_floor) : decode_rec(load_rec(a, t), a, m_floor);
         U128 root{0, 0};
         // After a bulk-copy wait ran out (ODP_ERR_TIMEOUT is recorded) the
         // warp hashes nothing more, but still climbs, so every tree counter
@@ -934,7 +980,7 @@ static PlanLayout plan_layout(uint32_t nn) {
     p.toff = carve(sizeof(uint32_t) * (nn + 1));
     p.noff = carve(sizeof(uint32_t) * (nn + 1));
     p.bsum = carve(sizeof(uint32_t) * 2 * (nblocks + 1));
-    p.tbuf = carve(sizeof(uint32_t) * (size_t)cap_tiles);
+    p.tbuf = carve(sizeof(TileRec) * (size_t)cap_tiles);
     p.nodes = carve(sizeof(U128) * 2 * (size_t)cap_tiles);
     p.bytes = bytes;
     return p;
@@ -994,7 +1040,7 @@ int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128
     a.tile_off = (uint32_t*)(s + o_toff);
     a.node_off = (uint32_t*)(s + o_noff);
     a.block_sums = (uint32_t*)(s + o_bsum);
-    a.tile_buf = (uint32_t*)(s + o_tbuf);
+    a.tile_rec = (TileRec*)(s + o_tbuf);
     a.counters = (uint32_t*)(s + o_cnt);
     a.nodes = (U128*)(s + o_nodes);
     a.status = status;
@@ -1152,7 +1198,7 @@ constexpr size_t NA_O_TOFF = na_up(NA_O_HDR + sizeof(PlanHeader));
 constexpr size_t NA_O_NOFF = na_up(NA_O_TOFF + 4ull * (NA_MAX_BUFFERS + 1));
 constexpr size_t NA_O_BSUM = na_up(NA_O_NOFF + 4ull * (NA_MAX_BUFFERS + 1));
 constexpr size_t NA_O_TBUF = na_up(NA_O_BSUM + 4ull * 2 * 8);
-constexpr size_t NA_O_CNT = na_up(NA_O_TBUF + 4ull * NA_CAP_TILES);
+constexpr size_t NA_O_CNT = na_up(NA_O_TBUF + sizeof(TileRec) * NA_CAP_TILES);
 constexpr size_t NA_O_NODES = na_up(NA_O_CNT + 4ull * 2 * NA_CAP_TILES);
 constexpr size_t NA_BYTES = na_up(NA_O_NODES + sizeof(U128) * 2 * NA_CAP_TILES);
 
@@ -1202,7 +1248,7 @@ static int fp_run_noalloc(const void* const* ptrs, const uint64_t* sizes, uint64
     a.tile_off = (uint32_t*)(s + NA_O_TOFF);
     a.node_off = (uint32_t*)(s + NA_O_NOFF);
     a.block_sums = (uint32_t*)(s + NA_O_BSUM);
-    a.tile_buf = (uint32_t*)(s + NA_O_TBUF);
+    a.tile_rec = (TileRec*)(s + NA_O_TBUF);
     a.counters = (uint32_t*)(s + NA_O_CNT);
     a.nodes = (U128*)(s + NA_O_NODES);
     a.status = nullptr;
