@@ -354,7 +354,12 @@ def bench_batched(args, odp, dist, rank, stream, peak, peak_kind):
     ptrs = torch.from_numpy(arena.data_ptr() + offs).cuda()
     sz = torch.from_numpy(sizes).cuda()
     out = torch.empty((n, 2), dtype=torch.int64, device="cuda")
-    sched, tuned_ms = odp.autotune_fingerprint(ptrs, sz, out, reps=2, stream=stream)
+    if args.no_autotune:
+        # the schedule cached by an earlier tuning run (ODP_AUTOTUNE_CACHE), or
+        # the defaults: lets a profiler see the kernel the timed calls use
+        sched, tuned_ms = ("cached",), 0.0
+    else:
+        sched, tuned_ms = odp.autotune_fingerprint(ptrs, sz, out, reps=2, stream=stream)
     steps = max(3, min(args.steps, 10))
     d_total, d_per = time_calls(lambda: odp.fingerprint(ptrs, sz, out, stream), steps,
                                 args.warmup, stream)
@@ -1028,6 +1033,8 @@ def main():
                     help="producers open each event with odp_server_begin (the merge waits only "
                          "for open events) or stamp it themselves (the merge waits for every "
                          "producer's next event)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched part: no tuning; use the schedule cached in ODP_AUTOTUNE_CACHE")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if captured")
     args = ap.parse_args()

@@ -109,7 +109,7 @@ int odp_fingerprint(const void* const* ptrs, const uint64_t* sizes, uint64_t n,
  * is for callers that cannot call cudaMalloc or an allocator at the moment
  * they need a fingerprint (code running inside an allocator or an
  * out-of-memory path, or a host program that forbids allocation after
- * start-up).  Its scratch is one file-scope device array of about 1.5 MiB
+ * start-up).  Its scratch is one file-scope device array of about 0.9 MiB
  * that every GPU loading the library keeps until the process exits.
  *
  *   ptrs, sizes, out128: as for odp_fingerprint (device arrays, n entries).
@@ -340,16 +340,20 @@ int odp_analyze(const odp_event* events, uint64_t n, const odp_findings* out,
  * forms batches continuously, fingerprints every transfer's payload on the
  * GPU, appends the events to a log resident in device memory and updates
  * state kept on the device for Algorithm 1 (duplicate transfers), Algorithm
- * 2 (round trips, content groups with at most two endpoints), the
- * alloc/delete pairing, Algorithm 3 (repeated allocations), Algorithm 4
- * (unused allocations: a pair is decided once a kernel on its device
+ * 2 (round trips; in a content group that shows a third endpoint a round
+ * trip can depend on receptions still to come, so the group's round trips
+ * from then on are reported by odp_server_flush, which replays Alg. 2's
+ * queues over the group), the alloc/delete pairing, Algorithm 3 (repeated
+ * allocations), Algorithm 4 (unused allocations: a pair is decided once a kernel on its device
  * overlaps it or the merged stream has passed its delete's end) and
  * Algorithm 5 (unused transfers: decided when the next kernel of the
  * transfer's device arrives), so those findings are reported while the
- * program runs.  The streamed findings equal odp_analyze's over the same log
- * when round-trip groups have at most two endpoints and allocations of one
- * <host address, device, bytes> key do not nest; odp_analyze over the
- * resident log (odp_server_log) after odp_server_flush is exact always.
+ * program runs.  After odp_server_flush the streamed findings equal
+ * odp_analyze's over the same log unless allocations of one <host address,
+ * device, bytes> key nest (a pair that completes while an earlier
+ * allocation of its key is still open) or a capacity overflowed
+ * (stream_overflow); odp_analyze over the resident log (odp_server_log)
+ * after odp_server_flush is exact always.
  */
 typedef struct odp_server odp_server;
 
@@ -374,7 +378,9 @@ typedef struct odp_server_stats {
                                        (they break the log's order) */
     uint64_t latency_p50_ns, latency_p99_ns, latency_max_ns;
     uint64_t first_submit_ns, last_done_ns;  /* steady-clock stamps */
-    uint64_t rt_groups_unstreamed;  /* content groups with > 2 endpoints */
+    uint64_t rt_groups_at_flush;    /* content groups with > 2 endpoints: their
+                                       round trips after the third endpoint
+                                       appeared are reported at the flush */
     uint64_t stream_overflow;       /* findings, and decisions waiting for a
                                        later event, that did not fit the
                                        server's capacities (3 * max_batch_events
@@ -455,9 +461,11 @@ int odp_server_poll(odp_server* s, odp_finding* host_out, uint64_t cap, uint64_t
  * until all batches are done, and ends the trace for Algorithms 4 and 5:
  * pairs still waiting for a kernel are unused, allocations never deleted are
  * unused unless a kernel seen on their device ends at or after their start,
- * and to-device transfers still waiting for a kernel come after the last one
- * (these findings carry no latency).  Events submitted after a flush extend
- * the log; findings already reported are not revisited. */
+ * and to-device transfers still waiting for a kernel come after the last one;
+ * content groups with more than two endpoints get their round trips by a
+ * replay of Alg. 2's queues over the group's transfers, reporting those not
+ * streamed before (these findings carry no latency).  Events submitted after
+ * a flush extend the log; findings already reported are not revisited. */
 int odp_server_flush(odp_server* s);
 
 /* The resident merged log (device pointer) and its length; valid until the

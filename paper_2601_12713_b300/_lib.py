@@ -281,7 +281,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in (
         "events_submitted", "events_processed", "batches", "findings_streamed", "late_events",
         "latency_p50_ns", "latency_p99_ns", "latency_max_ns", "first_submit_ns", "last_done_ns",
-        "rt_groups_unstreamed", "stream_overflow", "queue_p50_ns", "queue_p99_ns",
+        "rt_groups_at_flush", "stream_overflow", "queue_p50_ns", "queue_p99_ns",
         "device_bytes")]
 
 

@@ -41,18 +41,8 @@ struct PlanHeader {
     uint32_t total_nodes;
     uint32_t tile_counter;
     uint32_t warps_done;   // warps that left the tile loop (reset by the last one)
-    uint32_t pad;
+    uint32_t n_big;        // buffers listed for fp_plan_big
 };
-
-// Where one tile lies, written by the plan so that a warp finds a tile with
-// one 32-byte load: the buffer's address and size, its index and the tile's
-// index within the buffer.
-struct __align__(16) TileRec {
-    const uint8_t* base;
-    uint64_t size;
-    uint32_t b, tb, pad[2];
-};
-static_assert(sizeof(TileRec) == 32, "tile record is one 32-byte sector");
 
 struct FpArgs {
     const void* const* ptrs;
@@ -65,7 +55,8 @@ struct FpArgs {
     uint32_t* tile_off;   // n + 1
     uint32_t* node_off;   // n + 1
     uint32_t* block_sums; // 2 * plan blocks
-    TileRec* tile_rec;    // cap_tiles
+    uint32_t* tile_buf;   // cap_tiles: the buffer of each tile
+    uint32_t* big;        // n: buffers whose later tile entries fp_plan_big writes
     uint32_t* counters;   // 2 * cap_tiles
     U128* nodes;          // 2 * cap_tiles
     int32_t* status;      // per-device status word (null: not published)
@@ -118,15 +109,15 @@ __device__ __forceinline__ uint64_t n_nodes(uint64_t nt) {
 
 // Per-buffer work shared by the plan kernels: chunk count; empty buffers and
 // null pointers are finished here.
-__device__ __forceinline__ uint64_t plan_chunks(const FpArgs& a, uint32_t i) {
-    uint64_t size = a.sizes[i];
+__device__ __forceinline__ uint64_t plan_chunks(const FpArgs& a, uint32_t i, uint64_t size,
+                                                const void* ptr) {
     if (size == 0) {
         U128 e = fp::empty_input();
         a.out[i].lo = e.x;
         a.out[i].hi = e.y;
         return 0;
     }
-    if (a.ptrs[i] == nullptr) {
+    if (ptr == nullptr) {
         a.out[i].lo = 0;
         a.out[i].hi = 0;
         record_error(&a.hdr->err, i, ODP_ERR_INVALID_ARG);
@@ -149,7 +140,8 @@ __global__ void __launch_bounds__(1024) fp_plan_small(FpArgs a) {
     if (threadIdx.x == 0) s_total = 0;
     __syncthreads();
     unsigned long long local = 0;
-    for (uint32_t i = threadIdx.x; i < a.n; i += blockDim.x) local += plan_chunks(a, i);
+    for (uint32_t i = threadIdx.x; i < a.n; i += blockDim.x)
+        local += plan_chunks(a, i, a.sizes[i], a.ptrs[i]);
     atomicAdd(&s_total, local);
     __syncthreads();
     const uint32_t budget = a.cap_tiles - a.n;
@@ -193,10 +185,19 @@ __global__ void __launch_bounds__(256) fp_plan_count(FpArgs a) {
     if (threadIdx.x == 0) s_total = 0;
     __syncthreads();
     unsigned long long local = 0;
-    uint32_t base = blockIdx.x * 1024;
+    const uint32_t base = blockIdx.x * 1024;
+    uint64_t sz[4];
+    const void* pt[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {  // every load in flight before the first use
+        const uint32_t i = base + k * 256 + threadIdx.x;
+        sz[k] = i < a.n ? a.sizes[i] : 0;
+        pt[k] = i < a.n ? a.ptrs[i] : nullptr;
+    }
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
-        uint32_t i = base + k * 256 + threadIdx.x;
-        if (i < a.n) local += plan_chunks(a, i);
+        const uint32_t i = base + k * 256 + threadIdx.x;
+        if (i < a.n) local += plan_chunks(a, i, sz[k], pt[k]);
     }
     atomicAdd(&s_total, local);
     __syncthreads();
@@ -269,22 +270,49 @@ __global__ void __launch_bounds__(1024) fp_plan_blocks(FpArgs a, uint32_t nblock
     }
 }
 
-// Pass 4: add the block offsets.
+// A buffer's first REC_DIRECT tile-list entries are written by its thread in
+// fp_plan_add; buffers with more tiles are listed, and fp_plan_big writes the
+// rest with a warp per buffer.  Most buffers of a ragged batch have one tile.
+constexpr uint32_t REC_DIRECT = 4;
+
+// Pass 4: add the block offsets; write the tile list.
 __global__ void __launch_bounds__(256) fp_plan_add(FpArgs a) {
-    uint32_t bt = a.block_sums[2 * blockIdx.x], bn = a.block_sums[2 * blockIdx.x + 1];
-    uint32_t base = blockIdx.x * 1024 + threadIdx.x * 4;
+    const uint32_t bt = a.block_sums[2 * blockIdx.x], bn = a.block_sums[2 * blockIdx.x + 1];
+    const uint32_t m_floor = a.hdr->m_floor;
+    const uint32_t base = blockIdx.x * 1024 + threadIdx.x * 4;
     for (int k = 0; k < 4; ++k) {
-        uint32_t i = base + k;
-        if (i < a.n) {
-            a.tile_off[i] += bt;
-            a.node_off[i] += bn;
-        }
+        const uint32_t i = base + k;
+        if (i >= a.n) break;
+        const uint32_t t0 = a.tile_off[i] + bt;
+        a.tile_off[i] = t0;
+        a.node_off[i] += bn;
+        const uint64_t size = a.sizes[i];
+        if (size == 0 || a.ptrs[i] == nullptr) continue;
+        const uint64_t nc = n_chunks(size);
+        const uint32_t nt = (uint32_t)n_tiles(nc, tile_log2(nc, a.tmin, m_floor));
+        for (uint32_t j = 0; j < nt && j < REC_DIRECT; ++j) a.tile_buf[t0 + j] = i;
+        if (nt > REC_DIRECT) a.big[atomicAdd(&a.hdr->n_big, 1u)] = i;
     }
 }
 
-// Tile records (binary search over tile offsets for the tile's buffer).
-// The tree counters need no reset: each group's last arriver sets its
-// counter back to zero.
+// Pass 5 (multi-block plan): the remaining tile-list entries of listed buffers.
+__global__ void __launch_bounds__(256) fp_plan_big(FpArgs a) {
+    const uint32_t nb = a.hdr->n_big, m_floor = a.hdr->m_floor;
+    const int lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t q = gw; q < nb; q += nw) {
+        const uint32_t i = a.big[q];
+        const uint64_t nc = n_chunks(a.sizes[i]);
+        const uint32_t nt = (uint32_t)n_tiles(nc, tile_log2(nc, a.tmin, m_floor));
+        const uint32_t t0 = a.tile_off[i];
+        for (uint32_t j = REC_DIRECT + lane; j < nt; j += 32) a.tile_buf[t0 + j] = i;
+    }
+}
+
+// Tile list of the one-block plan (binary search over tile offsets).  The
+// tree counters need no reset: each group's last arriver sets its counter
+// back to zero.
 __global__ void __launch_bounds__(256) fp_plan_tiles(FpArgs a) {
     const uint32_t T = a.hdr->total_tiles;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -295,12 +323,7 @@ __global__ void __launch_bounds__(256) fp_plan_tiles(FpArgs a) {
             uint32_t mid = (lo + hi) >> 1;
             if (a.tile_off[mid] <= t) lo = mid; else hi = mid;
         }
-        const uint64_t base = (uint64_t)a.ptrs[lo];
-        const uint64_t size = a.sizes[lo];
-        uint4* r = reinterpret_cast<uint4*>(a.tile_rec + t);
-        r[0] = make_uint4((uint32_t)base, (uint32_t)(base >> 32), (uint32_t)size,
-                          (uint32_t)(size >> 32));
-        r[1] = make_uint4(lo, t - a.tile_off[lo], 0u, 0u);
+        a.tile_buf[t] = lo;
     }
 }
 
@@ -698,16 +721,6 @@ struct TileInfo {
     int m;
 };
 
-// The raw record of tile t (a planned batch).
-struct RawRec {
-    uint4 w0, w1;
-};
-
-__device__ __forceinline__ RawRec load_rec(const FpArgs& a, uint32_t t) {
-    const uint4* r = reinterpret_cast<const uint4*>(a.tile_rec + t);
-    return RawRec{__ldg(r), __ldg(r + 1)};
-}
-
 __device__ __forceinline__ TileInfo finish_info(TileInfo ti, const FpArgs& a, uint32_t m_floor) {
     ti.nchunk = n_chunks(ti.size);
     ti.m = tile_log2(ti.nchunk, a.tmin, m_floor);
@@ -716,17 +729,17 @@ __device__ __forceinline__ TileInfo finish_info(TileInfo ti, const FpArgs& a, ui
     return ti;
 }
 
-// Tile t of a planned batch, from its record.
-__device__ __forceinline__ TileInfo decode_rec(const RawRec& r, const FpArgs& a, uint32_t m_floor) {
+// Tile t of a planned batch: its buffer from the tile list.
+__device__ __forceinline__ TileInfo batch_info(const FpArgs& a, uint32_t t, uint32_t m_floor) {
     TileInfo ti;
-    ti.base = (const uint8_t*)(((uint64_t)r.w0.y << 32) | r.w0.x);
-    ti.size = ((uint64_t)r.w0.w << 32) | r.w0.z;
-    ti.b = r.w1.x;
-    ti.tb = r.w1.y;
+    ti.b = a.tile_buf[t];
+    ti.tb = t - a.tile_off[ti.b];
+    ti.size = a.sizes[ti.b];
+    ti.base = (const uint8_t*)a.ptrs[ti.b];
     return finish_info(ti, a, m_floor);
 }
 
-// Tile t of the one buffer of a single-buffer call (no plan, no records).
+// Tile t of the one buffer of a single-buffer call (no plan, no tile list).
 __device__ __forceinline__ TileInfo single_info(const FpArgs& a, uint32_t t, uint32_t m_floor) {
     TileInfo ti;
     ti.b = 0;
@@ -857,8 +870,7 @@ __global__ void __launch_bounds__(WARPS * 32, fp_min_ctas<WARPS, STAGES>()) fp_t
     while (t < T) {
         if (!first && lane == 0) t_next = 2 * total + atomicAdd(&a.hdr->tile_counter, 1u);
         first = false;
-        const TileInfo cur =
-            a.single ? single_info(a, t, m_floor) : decode_rec(load_rec(a, t), a, m_floor);
+        const TileInfo cur = a.single ? single_info(a, t, m_floor) : batch_info(a, t, m_floor);
         U128 root{0, 0};
         // After a bulk-copy wait ran out (ODP_ERR_TIMEOUT is recorded) the
         // warp hashes nothing more, but still climbs, so every tree counter
@@ -958,7 +970,7 @@ static std::map<void*, size_t> g_zeroed;
 
 // Byte offsets of the plan's arrays in its scratch block, for nn buffers.
 struct PlanLayout {
-    size_t hdr, cnt, zero_needed, toff, noff, bsum, tbuf, nodes, bytes;
+    size_t hdr, cnt, zero_needed, toff, noff, bsum, big, tbuf, nodes, bytes;
 };
 
 static PlanLayout plan_layout(uint32_t nn) {
@@ -980,7 +992,8 @@ static PlanLayout plan_layout(uint32_t nn) {
     p.toff = carve(sizeof(uint32_t) * (nn + 1));
     p.noff = carve(sizeof(uint32_t) * (nn + 1));
     p.bsum = carve(sizeof(uint32_t) * 2 * (nblocks + 1));
-    p.tbuf = carve(sizeof(TileRec) * (size_t)cap_tiles);
+    p.big = carve(sizeof(uint32_t) * (nn + 1));
+    p.tbuf = carve(sizeof(uint32_t) * (size_t)cap_tiles);
     p.nodes = carve(sizeof(U128) * 2 * (size_t)cap_tiles);
     p.bytes = bytes;
     return p;
@@ -1040,7 +1053,8 @@ int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128
     a.tile_off = (uint32_t*)(s + o_toff);
     a.node_off = (uint32_t*)(s + o_noff);
     a.block_sums = (uint32_t*)(s + o_bsum);
-    a.tile_rec = (TileRec*)(s + o_tbuf);
+    a.tile_buf = (uint32_t*)(s + o_tbuf);
+    a.big = (uint32_t*)(s + lay.big);
     a.counters = (uint32_t*)(s + o_cnt);
     a.nodes = (U128*)(s + o_nodes);
     a.status = status;
@@ -1068,8 +1082,9 @@ int fp_run(const void* const* ptrs, const uint64_t* sizes, uint64_t n, odp_fp128
             fp_plan_scan<<<nblocks, 256, 0, stream>>>(a);
             fp_plan_blocks<<<1, 1024, 0, stream>>>(a, nblocks);
             fp_plan_add<<<nblocks, 256, 0, stream>>>(a);
+            fp_plan_big<<<sms * 4, 256, 0, stream>>>(a);
         }
-        fp_plan_tiles<<<sms * 4, 256, 0, stream>>>(a);
+        if (nn <= (uint32_t)MAX_SMALL_PLAN) fp_plan_tiles<<<sms * 4, 256, 0, stream>>>(a);
     }
     int grid = sms * ctas;
     if (host_one) {
@@ -1198,7 +1213,7 @@ constexpr size_t NA_O_TOFF = na_up(NA_O_HDR + sizeof(PlanHeader));
 constexpr size_t NA_O_NOFF = na_up(NA_O_TOFF + 4ull * (NA_MAX_BUFFERS + 1));
 constexpr size_t NA_O_BSUM = na_up(NA_O_NOFF + 4ull * (NA_MAX_BUFFERS + 1));
 constexpr size_t NA_O_TBUF = na_up(NA_O_BSUM + 4ull * 2 * 8);
-constexpr size_t NA_O_CNT = na_up(NA_O_TBUF + sizeof(TileRec) * NA_CAP_TILES);
+constexpr size_t NA_O_CNT = na_up(NA_O_TBUF + 4ull * NA_CAP_TILES);
 constexpr size_t NA_O_NODES = na_up(NA_O_CNT + 4ull * 2 * NA_CAP_TILES);
 constexpr size_t NA_BYTES = na_up(NA_O_NODES + sizeof(U128) * 2 * NA_CAP_TILES);
 
@@ -1248,7 +1263,8 @@ static int fp_run_noalloc(const void* const* ptrs, const uint64_t* sizes, uint64
     a.tile_off = (uint32_t*)(s + NA_O_TOFF);
     a.node_off = (uint32_t*)(s + NA_O_NOFF);
     a.block_sums = (uint32_t*)(s + NA_O_BSUM);
-    a.tile_rec = (TileRec*)(s + NA_O_TBUF);
+    a.tile_buf = (uint32_t*)(s + NA_O_TBUF);
+    a.big = nullptr;  // the one-block plan writes the whole tile list in fp_plan_tiles
     a.counters = (uint32_t*)(s + NA_O_CNT);
     a.nodes = (U128*)(s + NA_O_NODES);
     a.status = nullptr;

@@ -22,8 +22,15 @@
 // a batch that is the next run of destinations in the batch's content-sorted
 // transfers; transfers left unpaired wait in a per-<content id, endpoint>
 // list, which the first reception at that endpoint in a later batch closes.
-// Groups that ever show a third endpoint stop streaming round trips; their
-// exact result comes from odp_analyze over the log.
+// Groups that ever show a third endpoint stop streaming round trips: what a
+// transfer pairs with may then depend on receptions still to come.  Every
+// group's transfers are kept linked in log order, and odp_server_flush walks
+// the groups with more than two endpoints with the literal queues of Alg. 2
+// (per endpoint: receptions counted, a cursor at the front of its queue) and
+// reports the round trips that were not streamed.  Those streamed while the
+// group had two endpoints stay exact: a transfer from A to B follows every
+// earlier reception at A, so they all succeed, and its partner is the first
+// later reception at A, which comes before any event of a third endpoint.
 // Streaming pairs and Alg. 3: a table <device address, device> holds the top
 // of each address's stack of open allocations (links per log index); a
 // DELETE closes the nearest open ALLOC, in batch order per address.  A
@@ -85,6 +92,9 @@ constexpr uint64_t SRV_MAX_CAPACITY = 1ull << 30;  // max_events, max_batch_even
 struct SrvDev {
     odp_event* log;
     uint32_t* cid;     // per log index (transfers)
+    uint32_t* gtail;   // per content id: the group's last transfer so far (NONE32: none)
+    uint32_t* glink;   // per log index: the next transfer of its content group (log order)
+    uint8_t* rt_done;  // per log index: a round trip of this transfer has been reported
     uint32_t* next;    // per log index: pending-list links (transfers), open-alloc stack links
     Table t_fp, t_dd, t_pend, t_ep, t_b;
     Table t_pair;      // <device address, device> -> top of the open-alloc stack
@@ -184,6 +194,13 @@ __device__ __forceinline__ void emit(const SlotDev& s, uint32_t cap, const odp_e
 }
 
 __device__ __forceinline__ uint64_t dur_of(const odp_event& e) { return e.t_end_ns - e.t_start_ns; }
+
+// A round trip <tx e, rx p> (the wasted trip is p), marked as reported.
+__device__ __forceinline__ void emit_rt(const SrvDev& d, const SlotDev& s, uint32_t cap, uint64_t e,
+                                        uint64_t p, uint64_t completing) {
+    d.rt_done[e] = 1;
+    emit(s, cap, d.log, ODP_RT, e, p, p, completing);
+}
 
 // A finding with explicit wasted bytes and time; partner NONE32 = none.
 __device__ __forceinline__ void emit_w(const SlotDev& s, uint32_t cap, const odp_event* log,
@@ -288,7 +305,7 @@ __device__ __forceinline__ void srv_dd_resolve_body(SrvDev d, SlotDev s, uint32_
         if (ps == NONE32) continue;
         uint32_t e = atomicExch(&d.t_pend.slots[ps].v, NONE32);
         for (uint64_t guard = 0; e != NONE32 && guard < max_events; ++guard) {
-            emit(s, cap, d.log, ODP_RT, e, g, g, g);
+            emit_rt(d, s, cap, e, g, g);
             e = d.next[e];
         }
     }
@@ -327,7 +344,7 @@ __device__ __forceinline__ void srv_rt_batch_body(SrvDev d, SlotDev s, uint32_t 
         while (t < nx && s.skeys[t] == cid && ep_of(d.log[g0 + s.svals[t]].dst_dev) == dst) ++t;
         if (t < nx && s.skeys[t] == cid) {
             const uint64_t p = g0 + s.svals[t];
-            emit(s, cap, d.log, ODP_RT, g, p, p, p);
+            emit_rt(d, s, cap, g, p, p);
         } else {
             const Key128 k{(uint64_t)cid | ((uint64_t)ep_of(d.log[g].src_dev) << 32), 2};
             const uint32_t ps = prim::table_insert_min(d.t_pend, cap_pend, k, NONE32);
@@ -339,6 +356,28 @@ __device__ __forceinline__ void srv_rt_batch_body(SrvDev d, SlotDev s, uint32_t 
 }
 
 __global__ void srv_rt_batch(SrvDev d, SlotDev s, uint32_t cap) { srv_rt_batch_body(d, s, cap); }
+
+// Appends the batch's transfers to their content groups' lists, in log order:
+// in the content-sorted transfers (stable, so log order inside a group) each
+// run links its members, and the run's head links the group's previous tail.
+__device__ __forceinline__ void srv_group_link_body(SrvDev d, SlotDev s) {
+    const uint64_t g0 = s.par->g0;
+    const uint32_t nx = *s.nx;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nx; r += gridDim.x * blockDim.x) {
+        const uint32_t cid = s.skeys[r];
+        const uint32_t g = (uint32_t)(g0 + s.svals[r]);
+        const bool more = r + 1 < nx && s.skeys[r + 1] == cid;
+        d.glink[g] = more ? (uint32_t)(g0 + s.svals[r + 1]) : NONE32;
+        if (r > 0 && s.skeys[r - 1] == cid) continue;
+        uint32_t t = r;
+        while (t + 1 < nx && s.skeys[t + 1] == cid) ++t;
+        const uint32_t old = d.gtail[cid];
+        if (old != NONE32) d.glink[old] = g;
+        d.gtail[cid] = (uint32_t)(g0 + s.svals[t]);
+    }
+}
+
+__global__ void srv_group_link(SrvDev d, SlotDev s) { srv_group_link_body(d, s); }
 
 // Alloc/delete events of the batch keyed by their <device address, device>
 // slot (other events sort last); value = batch position.
@@ -605,6 +644,52 @@ __global__ void srv_flush(SrvDev d, SlotDev s, uint32_t cap, uint64_t max_events
     }
 }
 
+// Flush, Alg. 2 for the content groups with more than two endpoints: one
+// thread per group replays the literal queues over the group's list: a
+// transfer from A peeks at the front of A's queue (the receptions at A, all
+// of the group's, in order) and, if there is one, reports the round trip and
+// pops the front of its destination's queue.  Round trips already reported
+// (streamed before the third endpoint, or by an earlier round or flush) are
+// skipped; a round trip is marked reported only when it fit the findings
+// buffer, so the host repeats the replay until a round drops nothing.
+__global__ void srv_mx_flush(SrvDev d, SlotDev s, uint32_t cap, uint64_t n_log,
+                             uint64_t max_events) {
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < n_log;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        if (!is_xfer(d.log[g].kind) || d.cid[g] != (uint32_t)g) continue;  // not a group's first
+        if (!complex_group(d, (uint32_t)g)) continue;
+        uint32_t nrx[SRV_NDEV], popped[SRV_NDEV], front[SRV_NDEV];
+        for (int k = 0; k < SRV_NDEV; ++k) nrx[k] = popped[k] = 0, front[k] = NONE32;
+        uint64_t guard = 0;
+        for (uint32_t x = (uint32_t)g; x != NONE32 && guard < max_events; x = d.glink[x], ++guard) {
+            const uint32_t b = ep_of(d.log[x].dst_dev);
+            if (nrx[b]++ == 0) front[b] = x;
+        }
+        guard = 0;
+        for (uint32_t x = (uint32_t)g; x != NONE32 && guard < max_events; x = d.glink[x], ++guard) {
+            const uint32_t a = ep_of(d.log[x].src_dev), b = ep_of(d.log[x].dst_dev);
+            if (popped[a] >= nrx[a]) continue;  // A's queue is empty: no round trip
+            if (!d.rt_done[x]) {
+                const uint32_t j = atomicAdd(s.nfind, 1u);
+                if (j < cap) {
+                    const uint32_t p = front[a];
+                    store_finding(s.find, j, ODP_RT, d.log[x].site_id, d.log[p].site_id, x, p,
+                                  d.log[p].bytes, dur_of(d.log[p]));
+                    s.complete[j] = ~0ull;
+                    d.rt_done[x] = 1;
+                }
+            }
+            if (++popped[b] < nrx[b]) {  // pop B's front: move to its next reception
+                uint32_t y = d.glink[front[b]];
+                for (uint64_t k = 0; y != NONE32 && ep_of(d.log[y].dst_dev) != b && k < max_events;
+                     ++k)
+                    y = d.glink[y];
+                front[b] = y;
+            }
+        }
+    }
+}
+
 __global__ void srv_zero(uint32_t* p) { *p = 0; }
 
 // First step of a batch: append its events to the log; reset the batch's
@@ -768,6 +853,8 @@ srv_batch_small(SrvDev d, SlotDev s, uint32_t B, uint32_t cap, uint64_t max_even
     prim::sort_small_body<SRV_SMALL_BATCH>(s.skeys, s.svals, s.nx, SRV_SMALL_BATCH, bits_cid);
     __syncthreads();
     srv_rt_batch_body(d, s, cap);
+    __syncthreads();
+    srv_group_link_body(d, s);
     __syncthreads();
     srv_pair_keys_body(d, s);
     __syncthreads();
@@ -937,6 +1024,7 @@ void enqueue_analysis(odp_server* S, Slot& sl, cudaStream_t as) {
     prim::radix_sort(sl.d.skeys, sl.d.svals, sl.d.nx, B, prim::bit_length(S->cfg.max_events),
                      sl.d.sort, as);
     srv_rt_batch<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap);
+    srv_group_link<<<grid, 256, 0, as>>>(S->d, sl.d);
     srv_pair_keys<<<grid, 256, 0, as>>>(S->d, sl.d);
     prim::radix_sort(sl.d.skeys, sl.d.svals, m_dev, B, prim::bit_length(S->d.t_pair.cap_max + 1),
                      sl.d.sort, as);
@@ -1226,7 +1314,7 @@ int odp_server_bytes(const odp_server_cfg* cfg, uint64_t* bytes) {
     const uint64_t table = sizeof(prim::Slot);
     // the blocks odp_server_create allocates, plus per slot the scratch of the
     // slot's fingerprint calls and 20 MB for allocation granularity
-    const uint64_t shared = 64 + E * (64 + 4 + 4 + 4) + 7 * table * (cap_p + 1) +
+    const uint64_t shared = 64 + E * (64 + 4 + 4 + 4 + 4 + 4 + 1) + 7 * table * (cap_p + 1) +
                             table * (cap_b + 1) + 12 * SRV_NDEV + 40 * pend_cap + 80 +
                             find_cap * (sizeof(odp_finding) + 8);
     const uint64_t hist = 4 * prim::sort_hist_words((uint32_t)B);
@@ -1270,6 +1358,9 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     if (!rc) rc = alloc_dev(S, (void**)&S->d.log, sizeof(odp_event) * E);
     if (!rc) rc = alloc_dev(S, (void**)&S->d.cid, 4 * E);
     if (!rc) rc = alloc_dev(S, (void**)&S->d.next, 4 * E);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.gtail, 4 * E);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.glink, 4 * E);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.rt_done, E);
     if (!rc) rc = make_table(S, S->d.t_fp, cap_p, caps + 0, S->an_stream);
     if (!rc) rc = make_table(S, S->d.t_dd, cap_p, caps + 1, S->an_stream);
     if (!rc) rc = make_table(S, S->d.t_pend, cap_p, caps + 2, S->an_stream);
@@ -1296,6 +1387,8 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     if (!rc) rc = alloc_dev(S, (void**)&S->fl.nfind, 16);
     if (rc) return fail(rc);
     cudaMemsetAsync(S->d.kmax, 0, 8 * SRV_NDEV, S->an_stream);
+    cudaMemsetAsync(S->d.gtail, 0xFF, 4 * E, S->an_stream);
+    cudaMemsetAsync(S->d.rt_done, 0, E, S->an_stream);
     cudaMemsetAsync(S->d.npend, 0, 16, S->an_stream);
     cudaMemsetAsync(S->d.kcnt, 0, 4 * SRV_NDEV, S->an_stream);
     cudaMemsetAsync(S->d.nut, 0, 32, S->an_stream);
@@ -1508,19 +1601,44 @@ int odp_server_flush(odp_server* S) {
         std::lock_guard<std::mutex> an_lk(S->an_mu);
         cudaSetDevice(S->cfg.device);
         cudaStream_t as = S->an_stream;
-        odp::srv_zero<<<1, 1, 0, as>>>(S->fl.nfind);
-        odp::srv_flush<<<256, 256, 0, as>>>(S->d, S->fl, S->find_cap, S->cfg.max_events);
+        // pending decisions of Alg. 4 and 5 (one round), then the round trips of
+        // groups with more than two endpoints, in rounds until none is dropped
+        const uint32_t grid_mx =
+            (unsigned)std::min<uint64_t>(1024, (std::max<uint64_t>(S->n_done, 1) + 255) / 256);
+        const uint64_t max_rounds = S->cfg.max_events / std::max<uint32_t>(S->find_cap, 1) + 2;
+        for (uint64_t round = 0; round <= max_rounds; ++round) {
+            odp::srv_zero<<<1, 1, 0, as>>>(S->fl.nfind);
+            if (round == 0)
+                odp::srv_flush<<<256, 256, 0, as>>>(S->d, S->fl, S->find_cap, S->cfg.max_events);
+            else
+                odp::srv_mx_flush<<<grid_mx, 256, 0, as>>>(S->d, S->fl, S->find_cap, S->n_done,
+                                                           S->cfg.max_events);
+            cudaMemcpyAsync(S->h_fl_n, S->fl.nfind, 4, cudaMemcpyDeviceToHost, as);
+            if (cudaStreamSynchronize(as) != cudaSuccess) {
+                S->error = ODP_ERR_CUDA;
+                break;
+            }
+            const uint32_t tried = *S->h_fl_n, n = std::min(tried, S->find_cap);
+            cudaMemcpyAsync(S->h_fl_find, S->fl.find, sizeof(odp_finding) * n,
+                            cudaMemcpyDeviceToHost, as);
+            if (cudaStreamSynchronize(as) != cudaSuccess) {
+                S->error = ODP_ERR_CUDA;
+                break;
+            }
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                for (uint32_t j = 0; j < n; ++j) S->outq.push_back(S->h_fl_find[j]);
+                S->streamed += n;
+                if (round == 0) S->find_overflow += tried - n;
+            }
+            if (round > 0 && tried <= S->find_cap) break;  // nothing dropped: done
+            if (round == max_rounds) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->find_overflow += tried - n;
+            }
+        }
         odp::srv_flush_reset<<<1, 1, 0, as>>>(S->d);
-        cudaMemcpyAsync(S->h_fl_n, S->fl.nfind, 4, cudaMemcpyDeviceToHost, as);
         if (cudaStreamSynchronize(as) != cudaSuccess) S->error = ODP_ERR_CUDA;
-        const uint32_t n = std::min(*S->h_fl_n, S->find_cap);
-        cudaMemcpyAsync(S->h_fl_find, S->fl.find, sizeof(odp_finding) * n, cudaMemcpyDeviceToHost,
-                        as);
-        if (cudaStreamSynchronize(as) != cudaSuccess) S->error = ODP_ERR_CUDA;
-        std::lock_guard<std::mutex> lk(S->mu);
-        for (uint32_t j = 0; j < n; ++j) S->outq.push_back(S->h_fl_find[j]);
-        S->streamed += n;
-        S->find_overflow += *S->h_fl_n - n;
     }
     S->flushing = false;
     return S->error;
@@ -1574,7 +1692,7 @@ int odp_server_stats_get(odp_server* S, odp_server_stats* st) {
     st->queue_p99_ns = pct(qlat, 0.99);
     // groups with more than two endpoints (counted on the device table), and
     // findings or waiting decisions that did not fit
-    st->rt_groups_unstreamed = 0;
+    st->rt_groups_at_flush = 0;
     st->device_bytes = S->dev_bytes;
     {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -1590,7 +1708,7 @@ int odp_server_stats_get(odp_server* S, odp_server_stats* st) {
             if (cudaMemcpy(v.data(), S->d.t_ep.slots, sizeof(odp::prim::Slot) * (cap + 1),
                            cudaMemcpyDeviceToHost) == cudaSuccess)
                 for (const auto& x : v)
-                    if (x.v != odp::prim::NONE32 && (x.v & odp::EP_MORE)) ++st->rt_groups_unstreamed;
+                    if (x.v != odp::prim::NONE32 && (x.v & odp::EP_MORE)) ++st->rt_groups_at_flush;
         }
     }
     return ODP_OK;

@@ -88,7 +88,7 @@ def test_streamed_findings_equal_offline(cuda_ok, orc, n_slots, max_batch, annou
         s = srv.stats()
         assert s["events_processed"] == n and s["late_events"] == 0
         assert s["latency_p50_ns"] > 0 and s["latency_p99_ns"] >= s["latency_p50_ns"]
-        assert s["rt_groups_unstreamed"] == 0
+        assert s["rt_groups_at_flush"] == 0
     finally:
         srv.close()
         lg.close()
@@ -380,7 +380,7 @@ def test_streamed_kernel_heavy_batches_equal_offline(cuda_ok, orc, max_batch):
         srv.flush()
         st = srv.stats()
         assert st["events_processed"] == ev.size
-        assert st["stream_overflow"] == 0 and st["rt_groups_unstreamed"] == 0
+        assert st["stream_overflow"] == 0 and st["rt_groups_at_flush"] == 0
         log = odp.log_tensor(srv, ev.size).cpu().numpy().view(odp.EVENT_DTYPE).copy()
         o = orc.analyze(log)
         counts = [int((o.findings["kind"] == k).sum()) for k in range(1, 6)]
@@ -436,5 +436,81 @@ def test_allocation_within_the_reservation(cuda_ok, n_slots, max_events, max_bat
         # every allocated block is counted; the rest is per slot the fingerprint
         # plan's scratch (about 58 MB for a batch of at most 4,096) and 20 MB
         assert need - n_slots * (100 << 20) <= got <= need
+    finally:
+        srv.close()
+
+
+def multi_endpoint_events(seed, n_transfers, n_devices, stretch=1):
+    """Transfers among the host and n_devices devices (device-to-device
+    included) whose content groups gain a third endpoint along the trace,
+    fingerprints given; times stretched by `stretch`."""
+    from synth import traces as T
+
+    b = T.multi_endpoint(seed, n_transfers=n_transfers, n_contents=40, n_devices=n_devices)
+    T.fill_fp_from_content(b)
+    ev = b.events.copy()
+    ev["t_start_ns"] *= stretch
+    ev["t_end_ns"] = ev["t_start_ns"] + 10
+    ev["flags"] = 1
+    return ev
+
+
+@pytest.mark.parametrize("seed,n_devices,max_batch", [(1, 2, 128), (2, 2, 256), (3, 3, 512),
+                                                      (4, 7, 4096), (5, 127, 16384)])
+def test_streamed_round_trips_with_three_or_more_endpoints(cuda_ok, orc, seed, n_devices,
+                                                           max_batch):
+    """Content groups that reach a third endpoint (devices 2 to 127, device-to-
+    device transfers): their round trips after that are reported at the
+    flush by replaying Alg. 2's queues (in rounds when they outnumber the
+    findings buffer), so after the flush the streamed duplicate transfers,
+    round trips and unused transfers equal the oracle's over the log, in
+    batches of 128 to 16384 events (every to-device transfer waits for a
+    kernel that never comes, so the waiting list, 16 batches long, must hold
+    them)."""
+    import paper_2601_12713_b300 as odp
+
+    ev = multi_endpoint_events(seed, 4000 if max_batch < 16384 else 40_000, n_devices)
+    srv = odp.Server(n_slots=2, max_events=1 << 16, max_batch_events=max_batch,
+                     device_budget_bytes=4 << 30)
+    try:
+        srv.attach(0)
+        srv.submit(ev, np.zeros(ev.size, dtype=np.uint64))
+        srv.flush()
+        st = srv.stats()
+        assert st["events_processed"] == ev.size and st["stream_overflow"] == 0
+        assert st["rt_groups_at_flush"] > 0
+        log = odp.log_tensor(srv, ev.size).cpu().numpy().view(odp.EVENT_DTYPE).copy()
+        o = orc.analyze(log)
+        assert int((o.findings["kind"] == 2).sum()) > 100
+        got = sorted_findings(srv.poll(1 << 20))
+        assert np.array_equal(got.view(np.uint8), o.findings.view(np.uint8))
+    finally:
+        srv.close()
+
+
+def test_streamed_mixed_trace_with_multi_endpoint_groups(cuda_ok, orc):
+    """The kernel-heavy allocation cycles on three devices interleaved with
+    multi-endpoint transfers: all five kinds streamed, the multi-endpoint
+    round trips completed at the flush, equal to the oracle's over the log."""
+    import paper_2601_12713_b300 as odp
+
+    a = kernel_heavy_trace(12, n_cycles=800)
+    b = multi_endpoint_events(6, 3000, 3, stretch=25)
+    ev = np.concatenate([a, b])
+    ev = ev[np.argsort(ev["t_start_ns"], kind="stable")]
+    srv = odp.Server(n_slots=2, max_events=1 << 15, max_batch_events=256,
+                     device_budget_bytes=2 << 30)
+    try:
+        srv.attach(0)
+        srv.submit(ev, np.zeros(ev.size, dtype=np.uint64))
+        srv.flush()
+        st = srv.stats()
+        assert st["stream_overflow"] == 0 and st["rt_groups_at_flush"] > 0
+        log = odp.log_tensor(srv, ev.size).cpu().numpy().view(odp.EVENT_DTYPE).copy()
+        o = orc.analyze(log)
+        counts = [int((o.findings["kind"] == k).sum()) for k in range(1, 6)]
+        assert all(c > 0 for c in counts)
+        got = sorted_findings(srv.poll(1 << 20))
+        assert np.array_equal(got.view(np.uint8), o.findings.view(np.uint8))
     finally:
         srv.close()
