@@ -32,10 +32,14 @@ BUF_BYTES = 4 << 30
 SEED = 0x0DB2
 # dram read+write bytes of one fp_tiles launch over 512 MiB from an ncu full
 # capture of the default (8 warps, 2 bulk slots) kernel: 536.97 MB read +
-# 3.75 MB written.
+# 4.02 MB written.
 # Traffic grows with the bytes hashed: a launch over B bytes moves about
 # B / 512 MiB times this.
-FP_TILES_TRAFFIC_512MIB = 540.73e6
+FP_TILES_TRAFFIC_512MIB = 540.99e6
+# DRAM read+write bytes of one odp_analyze call on the 50,002,000-event
+# iterative-solver trace, summed over its 123 launches (ncu, dram__bytes_read.sum
+# + dram__bytes_write.sum, one pass per launch): 37.25 GB read + 8.99 GB written.
+ANALYZE_TRAFFIC_PER_EVENT = 46.23e9 / 50_002_000
 
 
 def peaks():
@@ -819,6 +823,9 @@ def bench_analysis(args, odp, dist, rank, stream, peak, peak_kind):
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "peak_kind": f"{peak_kind} (copy read+write)",
                      "algorithmic_bytes_per_launch": alg_bytes,
+                     "traffic": round(ANALYZE_TRAFFIC_PER_EVENT * n),
+                     "traffic_source": "ncu capture of one call on this 50,002,000-event trace "
+                                       "(all 123 launches), per event times the events",
                      "note": "whole odp_analyze call against the bytes the method must read "
                              "and write: 64 B per event, 48 B per finding, 32 B per site row"},
         "e2e": {"value": round(e_val, 2), "unit": "M events/s", "h2d_bytes_per_step": 64 * n,
