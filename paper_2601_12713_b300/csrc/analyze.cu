@@ -75,6 +75,21 @@ struct Ev {
     __device__ __forceinline__ uint64_t bytes(uint32_t i) const { return u64(i, 32); }
 };
 
+// Dense copies of the record fields the later passes read, one entry per
+// event, written by k_validate (which reads every record anyway).  A pass over
+// a list gathers 8-16 bytes per entry from them instead of a whole 128-byte
+// line of records per entry.
+struct EvCols {
+    uint4* tt;        // {t_start, t_end}
+    uint4* hd;        // {host_addr, dev_addr}
+    uint64_t* bytes;  // bytes
+    uint4* fp;        // {fp_lo, fp_hi}
+    uint32_t* site;   // site_id
+};
+
+__device__ __forceinline__ uint64_t lo64(uint4 v) { return ((uint64_t)v.y << 32) | v.x; }
+__device__ __forceinline__ uint64_t hi64(uint4 v) { return ((uint64_t)v.w << 32) | v.z; }
+
 // cls word: kind | (src + 1) << 8 | (dst + 1) << 16
 __device__ __forceinline__ uint32_t c_kind(uint32_t c) { return c & 0xFF; }
 __device__ __forceinline__ uint32_t c_src(uint32_t c) { return (c >> 8) & 0xFF; }
@@ -82,6 +97,7 @@ __device__ __forceinline__ uint32_t c_dst(uint32_t c) { return (c >> 16) & 0xFF;
 
 struct A {
     Ev ev;
+    EvCols col;
     uint32_t n;
     uint32_t pack_alloc;  // slot keys leave bit 31 free: it carries "is ALLOC" through the pairs sort
     Hdr* h;
@@ -141,13 +157,19 @@ __global__ void __launch_bounds__(TPB) k_validate(A a, uint32_t* ccnt, uint32_t 
         const uint32_t i = c * 32 + lane;
         const bool valid = i < a.n;
         uint64_t t0 = 0;
-        uint4 q0 = make_uint4(0, 0, 0, 0), q2 = q0, q3 = q0;
+        uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0, q2 = q0, q3 = q0;
         if (valid) {
             const uint4* r = reinterpret_cast<const uint4*>(a.ev.p + 64ull * i);
             q0 = __ldg(r);
+            q1 = __ldg(r + 1);
             q2 = __ldg(r + 2);
             q3 = __ldg(r + 3);
             t0 = ((uint64_t)q0.y << 32) | q0.x;
+            a.col.tt[i] = q0;
+            a.col.hd[i] = q1;
+            a.col.bytes[i] = lo64(q2);
+            a.col.fp[i] = make_uint4(q2.z, q2.w, q3.x, q3.y);
+            a.col.site[i] = q3.z;
         }
         // start time of the previous event: the neighbour lane's, or a load
         uint64_t prev = __shfl_up_sync(ODP_FULL_MASK, t0, 1);
@@ -296,11 +318,8 @@ __global__ void k_x_insert_fp(A a) {
         }
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
-            const uint4 f = use[b] ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * e[b] + 2)
-                                   : make_uint4(0, 0, 0, 0);
-            const uint4 g = use[b] ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * e[b] + 3)
-                                   : make_uint4(0, 0, 0, 0);
-            key[b] = Key128{((uint64_t)f.w << 32) | f.z, ((uint64_t)g.y << 32) | g.x};
+            const uint4 f = use[b] ? a.col.fp[e[b]] : make_uint4(0, 0, 0, 0);
+            key[b] = Key128{lo64(f), hi64(f)};
         }
         prim::table_insert_batch<INS_B, true, false, true>(a.tab, cap, key, e, use, out);
 #pragma unroll
@@ -649,7 +668,7 @@ __global__ void k_p_insert(A a) {
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             const uint32_t c = use[b] ? a.cls[e[b]] : 0;
-            key[b] = use[b] ? Key128{a.ev.daddr(e[b]), (uint64_t)c_dst(c)} : Key128{0, 0};
+            key[b] = use[b] ? Key128{hi64(a.col.hd[e[b]]), (uint64_t)c_dst(c)} : Key128{0, 0};
             flag[b] = a.pack_alloc && c_kind(c) == ODP_ALLOC ? 0x80000000u : 0u;
         }
         prim::table_insert_batch<INS_B, false, true, false>(a.ktab, cap, key, e, use, out);
@@ -759,7 +778,8 @@ __global__ void k_ra_insert(A a) {
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             use[b] = in[b] && is_alloc(a, e[b]) && a.del_of[e[b]] != NONE32;
-            key[b] = use[b] ? Key128{a.ev.host(e[b]), a.ev.bytes(e[b]) | ((uint64_t)c_dst(a.cls[e[b]]) << 56)}
+            key[b] = use[b] ? Key128{lo64(a.col.hd[e[b]]),
+                                     a.col.bytes[e[b]] | ((uint64_t)c_dst(a.cls[e[b]]) << 56)}
                             : Key128{0, 0};
         }
         prim::table_insert_batch<INS_B, true, true, true>(a.tab, cap, key, e, use, out);
@@ -825,8 +845,9 @@ __global__ void k_k_bounds(A a) {
         const uint32_t d = a.sk[q];
         if (q == 0 || a.sk[q - 1] != d) a.dstart[d] = q;
         if (q + 1 == n || a.sk[q + 1] != d) a.dend[d] = q + 1;
-        a.ks[q] = a.ev.t0(a.sv[q]);
-        a.ke[q] = a.ev.t1(a.sv[q]);
+        const uint4 t = a.col.tt[a.sv[q]];
+        a.ks[q] = lo64(t);
+        a.ke[q] = hi64(t);
     }
 }
 
@@ -897,8 +918,8 @@ __global__ void k_ua(A a) {
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             const bool al = c_kind(c[b]) == ODP_ALLOC;
-            t0[b] = al ? a.ev.t0(e[b]) : 0;
-            end[b] = !al ? 0 : del[b] != NONE32 ? a.ev.t1(del[b]) : trace_end;
+            t0[b] = al ? lo64(a.col.tt[e[b]]) : 0;
+            end[b] = !al ? 0 : del[b] != NONE32 ? hi64(a.col.tt[del[b]]) : trace_end;
         }
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
@@ -918,7 +939,7 @@ __global__ void k_ut_class(A a) {
     GRID_STRIDE(q, a.h->nU) {
         const uint32_t e = a.sv[q];
         const uint32_t d = a.sk[q];  // device number + 1
-        const uint64_t t = a.ev.t0(e);
+        const uint64_t t = lo64(a.col.tt[e]);
         const uint32_t p = first_kernel(a, d, t);
         uint8_t c;
         if (p == a.dend[d]) {
@@ -959,7 +980,7 @@ __global__ void k_ut_insert(A a) {
             const uint32_t q = q0 + b * str;
             use[b] = q < n && a.uc[q] == 0;
             e[b] = use[b] ? a.sv[q] : 0;
-            key[b] = use[b] ? Key128{a.ev.host(e[b]), 1} : Key128{0, 0};
+            key[b] = use[b] ? Key128{lo64(a.col.hd[e[b]]), 1} : Key128{0, 0};
         }
         prim::table_insert_batch<INS_B, false, true, false>(a.ktab, cap, key, e, use, out);
 #pragma unroll
@@ -1137,8 +1158,10 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
         uint32_t part[5];
         uint32_t bal[5];
         uint32_t any = 0;
-        const uint4* rec = reinterpret_cast<const uint4*>(a.ev.p) + 4ull * (valid ? i : 0u);
-        const uint4 o0 = __ldg(rec), o2 = __ldg(rec + 2), o3 = __ldg(rec + 3);
+        const uint32_t iv = valid ? i : 0u;
+        const uint4 o0 = __ldg(a.col.tt + iv);  // t_start, t_end
+        const uint64_t own_bytes = __ldg(reinterpret_cast<const unsigned long long*>(a.col.bytes) + iv);
+        const uint32_t site = __ldg(a.col.site + iv);
         const uint32_t del = valid ? __ldg(a.del_of + i) : NONE32;
         for (int kind = 0; kind < 5; ++kind) {
             part[kind] = valid ? partner_of(a, kind + 1, i) : NONE32;
@@ -1175,8 +1198,7 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
                                   : z4;
             const uint4 d0 = d != NONE32 ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * d) : z4;
             // Stores.
-            const uint64_t t0 = lohi(o0.x, o0.y), t1 = lohi(o0.z, o0.w), own_bytes = lohi(o2.x, o2.y);
-            const uint32_t site = o3.z;
+            const uint64_t t0 = lohi(o0.x, o0.y), t1 = lohi(o0.z, o0.w);
 #pragma unroll
             for (int kind = 0; kind < 5; ++kind) {
                 const uint32_t p = part[kind];
@@ -1378,6 +1400,8 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
                  o_id2 = carve(N4), o_H = carve(N4), o_R = carve(N4), o_stk = carve(N4),
                  o_pq = carve(N4);
     const size_t o_uc = carve(n + 16);
+    const size_t o_ctt = carve(16ull * n), o_chd = carve(16ull * n), o_cby = carve(8ull * n),
+                 o_cfp = carve(16ull * n), o_cst = carve(4ull * n);
     const size_t o_kse = carve(16ull * (n + 2));  // ks | ke (also 16 B per endpoint segment)
     const size_t o_dev = carve(2 * 4 * NDEV);
     const size_t o_sites = carve(8ull * 3 * 5 * ODP_MAX_SITES);
@@ -1424,6 +1448,11 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     a.stk = (uint32_t*)(b + o_stk);
     a.pq = (uint32_t*)(b + o_pq);
     a.uc = b + o_uc;
+    a.col.tt = (uint4*)(b + o_ctt);
+    a.col.hd = (uint4*)(b + o_chd);
+    a.col.bytes = (uint64_t*)(b + o_cby);
+    a.col.fp = (uint4*)(b + o_cfp);
+    a.col.site = (uint32_t*)(b + o_cst);
     a.ks = (uint64_t*)(b + o_kse);
     a.ke = a.ks + (n + 2);
     a.dstart = (uint32_t*)(b + o_dev);
