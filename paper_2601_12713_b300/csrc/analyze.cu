@@ -1184,19 +1184,20 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
 #pragma unroll
             for (int kind = 0; kind < 5; ++kind) {
                 const uint32_t p = part[kind];
-                psite[kind] = (p != NONE32 && p != NOPART)
-                                  ? __ldg(reinterpret_cast<const uint32_t*>(a.ev.p + 64ull * p + 56))
-                                  : 0xFFFFFFFFu;
+                psite[kind] = (p != NONE32 && p != NOPART) ? __ldg(a.col.site + p) : 0xFFFFFFFFu;
             }
             const uint32_t p_rt = part[ODP_RT - 1], p_ua = part[ODP_UA - 1];
-            const uint4* rrt = reinterpret_cast<const uint4*>(a.ev.p) + 4ull * p_rt;
+            // (from the columns: their lines are shared with nearby events'
+            // own reads, where whole records would each take a line of their own)
             const uint4 z4 = make_uint4(0, 0, 0, 0);
-            const uint4 rt0 = p_rt != NONE32 ? __ldg(rrt) : z4;
-            const uint4 rt2 = p_rt != NONE32 ? __ldg(rrt + 2) : z4;
-            const uint4 ua0 = (p_ua != NONE32 && p_ua != NOPART)
-                                  ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * p_ua)
-                                  : z4;
-            const uint4 d0 = d != NONE32 ? __ldg(reinterpret_cast<const uint4*>(a.ev.p) + 4ull * d) : z4;
+            const uint4 rt0 = p_rt != NONE32 ? __ldg(a.col.tt + p_rt) : z4;
+            uint4 rt2 = z4;
+            if (p_rt != NONE32) {
+                const uint64_t by = __ldg(reinterpret_cast<const unsigned long long*>(a.col.bytes) + p_rt);
+                rt2 = make_uint4((uint32_t)by, (uint32_t)(by >> 32), 0, 0);
+            }
+            const uint4 ua0 = (p_ua != NONE32 && p_ua != NOPART) ? __ldg(a.col.tt + p_ua) : z4;
+            const uint4 d0 = d != NONE32 ? __ldg(a.col.tt + d) : z4;
             // Stores.
             const uint64_t t0 = lohi(o0.x, o0.y), t1 = lohi(o0.z, o0.w);
 #pragma unroll

@@ -235,8 +235,12 @@ def test_plain_small_with_payload_fingerprints(cuda_ok, orc, odp):
 
 
 @pytest.mark.parametrize("n_iter,n_arrays,per_iter,p_skip",
-                         [(20, 400, 100, 0.0), (60, 2000, 500, 0.0), (60, 2000, 500, 0.1)])
+                         [(20, 400, 100, 0.0), (60, 2000, 500, 0.0), (60, 2000, 500, 0.1),
+                          (200, 5000, 2500, 0.05)])
 def test_iterative_solver_reduced(cuda_ok, orc, odp, n_iter, n_arrays, per_iter, p_skip):
+    """Reduced iterative-solver traces; the last one (10^6 transfers) makes a
+    content table of 2^21 slots, which is inserted into partition by
+    partition."""
     b = traces.iterative_solver(n_iter=n_iter, n_arrays=n_arrays, per_iter=per_iter, n_sites=50,
                                 p_skip_kernel=p_skip)
     g = check(odp, orc, with_fp(b))
