@@ -38,8 +38,8 @@ SEED = 0x0DB2
 FP_TILES_TRAFFIC_512MIB = 540.99e6
 # DRAM read+write bytes of one odp_analyze call on the 50,002,000-event
 # iterative-solver trace, summed over its 123 launches (ncu, dram__bytes_read.sum
-# + dram__bytes_write.sum, one pass per launch): 37.25 GB read + 8.99 GB written.
-ANALYZE_TRAFFIC_PER_EVENT = 46.23e9 / 50_002_000
+# + dram__bytes_write.sum, one pass per launch): 24.47 GB read + 11.84 GB written.
+ANALYZE_TRAFFIC_PER_EVENT = 36.31e9 / 50_002_000
 
 
 def peaks():
