@@ -348,12 +348,12 @@ int odp_analyze(const odp_event* events, uint64_t n, const odp_findings* out,
  * overlaps it or the merged stream has passed its delete's end) and
  * Algorithm 5 (unused transfers: decided when the next kernel of the
  * transfer's device arrives), so those findings are reported while the
- * program runs.  After odp_server_flush the streamed findings equal
- * odp_analyze's over the same log unless allocations of one <host address,
- * device, bytes> key nest (a pair that completes while an earlier
- * allocation of its key is still open) or a capacity overflowed
- * (stream_overflow); odp_analyze over the resident log (odp_server_log)
- * after odp_server_flush is exact always.
+ * program runs.  A completed pair whose <host address, device, bytes> key
+ * still has an allocation open waits until none is (that allocation, once
+ * completed, could be the key's first pair).  After odp_server_flush the
+ * streamed findings equal odp_analyze's over the same log unless a capacity
+ * overflowed (stream_overflow); odp_analyze over the resident log
+ * (odp_server_log) is exact always.
  */
 typedef struct odp_server odp_server;
 

@@ -33,11 +33,15 @@
 // later reception at A, which comes before any event of a third endpoint.
 // Streaming pairs and Alg. 3: a table <device address, device> holds the top
 // of each address's stack of open allocations (links per log index); a
-// DELETE closes the nearest open ALLOC, in batch order per address.  A
-// completed pair inserts <host address, device, bytes> with its alloc into a
-// second table; a pair whose alloc is not that key's first is a repeated
-// allocation.  (Equal to the offline result when pairs of one key complete
-// in alloc order, i.e. unless allocations of one key nest.)
+// DELETE closes the nearest open ALLOC, in batch order per address.  Per
+// <host address, device, bytes> key, a second table counts the key's open
+// allocations and keeps its first completed pair's alloc; each batch walks its
+// allocations and completed pairs key by key in log order.  A completed pair
+// waits in its key's list while another allocation of the key is open (that
+// one, completed later, could be the key's first pair); when none is open,
+// every waiting pair of the key is decided against the first, which no later
+// allocation can precede.  The flush decides what still waits (allocations
+// never deleted are not pairs).
 // Streaming Alg. 4: an allocation is used iff some kernel on its device
 // overlaps [alloc start, delete end].  Kernels of earlier batches are summed
 // up by their largest end per device; the pair's batch's kernels are indexed
@@ -99,6 +103,10 @@ struct SrvDev {
     Table t_fp, t_dd, t_pend, t_ep, t_b;
     Table t_pair;      // <device address, device> -> top of the open-alloc stack
     Table t_rid;       // <host address, device, bytes> -> first completed pair's alloc
+    uint32_t* rid_open;  // per t_rid slot: open allocations of the key
+    uint32_t* rid_wait;  // per t_rid slot: last waiting pair's alloc (NONE32: none)
+    uint32_t* wait_next; // per log index (alloc of a waiting pair): the key's previous one
+    uint32_t* wait_del;  // per log index (alloc of a waiting pair): its delete
     unsigned long long* kmax;  // per device: 1 + largest kernel end seen (0: none)
     uint2* pend[2];    // pairs waiting for the Alg. 4 decision (alloc, delete), ping-pong
     uint32_t* npend;   // [2] counts, [2] overflow count
@@ -143,6 +151,7 @@ struct SlotDev {
     uint32_t* nfind;
     uint32_t* pa;          // pairs completed in the batch: alloc, delete
     uint32_t* pd;
+    uint32_t* dalloc;      // per batch position of a DELETE: the alloc it closed (NONE32: none)
     uint32_t* rslot;       // their slot in t_rid
     uint32_t* bk;          // kernels of the batch (log indices), by device, in log order
     uint32_t* bktmp;       // the same in log order
@@ -419,7 +428,10 @@ __device__ __forceinline__ void srv_pair_walk_body(SrvDev d, SlotDev s) {
                 const uint32_t i = atomicAdd(&s.cnt[0], 1u);
                 s.pa[i] = top;
                 s.pd[i] = g;
+                s.dalloc[s.svals[t]] = top;
                 top = d.next[top];
+            } else {
+                s.dalloc[s.svals[t]] = NONE32;  // no open allocation: unmatched
             }
         }
         d.t_pair.slots[k].v = top;
@@ -432,27 +444,76 @@ __device__ __forceinline__ Key128 rid_key(const odp_event& e) {
     return Key128{e.host_addr, e.bytes | ((uint64_t)ep_of(e.dst_dev) << 56)};
 }
 
-__device__ __forceinline__ void srv_ra_insert_body(SrvDev d, SlotDev s) {
-    const uint32_t cap = *d.t_rid.cap_dev, n = s.cnt[0];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        s.rslot[i] = prim::table_insert_min(d.t_rid, cap, rid_key(d.log[s.pa[i]]), s.pa[i]);
-}
-
-__global__ void srv_ra_insert(SrvDev d, SlotDev s) { srv_ra_insert_body(d, s); }
-
-__device__ __forceinline__ void srv_ra_emit_body(SrvDev d, SlotDev s, uint32_t cap) {
-    const uint32_t n = s.cnt[0];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (s.rslot[i] == NONE32) continue;
-        const uint32_t a = s.pa[i], first = d.t_rid.slots[s.rslot[i]].v;
-        if (first == a) continue;
-        const odp_event& ea = d.log[a];
-        emit_w(s, cap, d.log, ODP_RA, a, first, ea.bytes, dur_of(ea) + dur_of(d.log[s.pd[i]]),
-               s.pd[i]);
+// Alg. 3 sort keys: the batch's allocations by their own <host address,
+// device, bytes> slot, and its completed pairs (at their delete) by their
+// alloc's slot; other events sort last.  Value = batch position.
+__device__ __forceinline__ void srv_ra_keys_body(SrvDev d, SlotDev s) {
+    const uint64_t g0 = s.par->g0;
+    const uint32_t m = s.par->m;
+    const uint32_t cap = *d.t_rid.cap_dev, none_key = d.t_rid.cap_max + 1;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+        const odp_event& e = d.log[g0 + q];
+        uint32_t k = none_key;
+        if (e.kind == ODP_ALLOC) {
+            k = prim::table_insert(d.t_rid, cap, rid_key(e));
+        } else if (e.kind == ODP_DELETE && s.dalloc[q] != NONE32) {
+            k = prim::table_insert(d.t_rid, cap, rid_key(d.log[s.dalloc[q]]));
+        }
+        s.skeys[q] = k == NONE32 ? none_key : k;
+        s.svals[q] = q;
     }
 }
 
-__global__ void srv_ra_emit(SrvDev d, SlotDev s, uint32_t cap) { srv_ra_emit_body(d, s, cap); }
+__global__ void srv_ra_keys(SrvDev d, SlotDev s) { srv_ra_keys_body(d, s); }
+
+__device__ __forceinline__ void ra_decide(const SrvDev& d, const SlotDev& s, uint32_t cap,
+                                          uint32_t a, uint32_t first, uint64_t completing) {
+    if (a == first) return;
+    const odp_event& ea = d.log[a];
+    const uint32_t del = d.wait_del[a];
+    emit_w(s, cap, d.log, ODP_RA, a, first, ea.bytes, dur_of(ea) + dur_of(d.log[del]), completing);
+}
+
+// One thread per key of the batch walks its allocations and completions in
+// log order (see the header comment).
+__device__ __forceinline__ void srv_ra_walk_body(SrvDev d, SlotDev s, uint32_t cap,
+                                                 uint64_t max_events) {
+    const uint64_t g0 = s.par->g0;
+    const uint32_t m = s.par->m;
+    const uint32_t none_key = d.t_rid.cap_max + 1;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+        const uint32_t k = s.skeys[r];
+        if (k == none_key || (r > 0 && s.skeys[r - 1] == k)) continue;
+        uint32_t open = d.rid_open[k], first = d.t_rid.slots[k].v, wait = d.rid_wait[k];
+        for (uint32_t t = r; t < m && s.skeys[t] == k; ++t) {
+            const uint32_t q = s.svals[t];
+            const uint32_t g = (uint32_t)(g0 + q);
+            if (d.log[g].kind == ODP_ALLOC) {
+                ++open;
+                continue;
+            }
+            const uint32_t a = s.dalloc[q];  // a completed pair (a, g)
+            if (open > 0) --open;
+            first = min(first, a);
+            d.wait_del[a] = g;
+            d.wait_next[a] = wait;
+            wait = a;
+            if (open == 0) {  // no allocation of the key is open: decide the waiting pairs
+                uint64_t guard = 0;
+                for (uint32_t x = wait; x != NONE32 && guard < max_events; x = d.wait_next[x], ++guard)
+                    ra_decide(d, s, cap, x, first, g);
+                wait = NONE32;
+            }
+        }
+        d.rid_open[k] = open;
+        d.t_rid.slots[k].v = first;
+        d.rid_wait[k] = wait;
+    }
+}
+
+__global__ void srv_ra_walk(SrvDev d, SlotDev s, uint32_t cap, uint64_t max_events) {
+    srv_ra_walk_body(d, s, cap, max_events);
+}
 
 // Some kernel of the batch on `dev` overlaps [lo, hi]: of the device's
 // kernels that start by hi (a prefix: the log is in start order), the
@@ -631,6 +692,17 @@ __global__ void srv_flush(SrvDev d, SlotDev s, uint32_t cap, uint64_t max_events
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_open; i += stride) {
         const uint32_t g = d.utopen[cur][i];
         emit_w(s, cap, d.log, ODP_UT, g, NONE32, d.log[g].bytes, dur_of(d.log[g]), ~0ull);
+    }
+    // Alg. 3: pairs still waiting for an allocation of their key that was
+    // never deleted (not a pair) are decided against the key's first pair
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= d.t_rid.cap_max; k += stride) {
+        const uint32_t w = d.rid_wait[k];
+        if (w == NONE32) continue;
+        const uint32_t first = d.t_rid.slots[k].v;
+        uint64_t guard = 0;
+        for (uint32_t x = w; x != NONE32 && guard < max_events; x = d.wait_next[x], ++guard)
+            ra_decide(d, s, cap, x, first, ~0ull);
+        d.rid_wait[k] = NONE32;
     }
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= d.t_pair.cap_max; k += stride) {
         uint32_t a = d.t_pair.slots[k].v;
@@ -833,7 +905,7 @@ constexpr int SRV_SMALL_THREADS = 1024;  // = BKI_THREADS = SMALL_SORT_THREADS
 
 __global__ void __launch_bounds__(SRV_SMALL_THREADS)
 srv_batch_small(SrvDev d, SlotDev s, uint32_t B, uint32_t cap, uint64_t max_events, int bits_cid,
-                int bits_pair, int bits_ut) {
+                int bits_pair, int bits_ut, int bits_rid) {
     const uint32_t* m_dev = &s.par->m;
     srv_append_body(d, s);
     __syncthreads();
@@ -862,9 +934,11 @@ srv_batch_small(SrvDev d, SlotDev s, uint32_t B, uint32_t cap, uint64_t max_even
     __syncthreads();
     srv_pair_walk_body(d, s);
     __syncthreads();
-    srv_ra_insert_body(d, s);
+    srv_ra_keys_body(d, s);
     __syncthreads();
-    srv_ra_emit_body(d, s, cap);
+    prim::sort_small_body<SRV_SMALL_BATCH>(s.skeys, s.svals, m_dev, SRV_SMALL_BATCH, bits_rid);
+    __syncthreads();
+    srv_ra_walk_body(d, s, cap, max_events);
     __syncthreads();
     srv_ua_body(d, s, cap);
     __syncthreads();
@@ -1029,8 +1103,10 @@ void enqueue_analysis(odp_server* S, Slot& sl, cudaStream_t as) {
     prim::radix_sort(sl.d.skeys, sl.d.svals, m_dev, B, prim::bit_length(S->d.t_pair.cap_max + 1),
                      sl.d.sort, as);
     srv_pair_walk<<<grid, 256, 0, as>>>(S->d, sl.d);
-    srv_ra_insert<<<grid, 256, 0, as>>>(S->d, sl.d);
-    srv_ra_emit<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap);
+    srv_ra_keys<<<grid, 256, 0, as>>>(S->d, sl.d);
+    prim::radix_sort(sl.d.skeys, sl.d.svals, m_dev, B, prim::bit_length(S->d.t_rid.cap_max + 1),
+                     sl.d.sort, as);
+    srv_ra_walk<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap, S->cfg.max_events);
     srv_ua<<<grid, 256, 0, as>>>(S->d, sl.d, S->find_cap);
     srv_ut_keys<<<grid, 256, 0, as>>>(S->d, sl.d);
     prim::radix_sort(sl.d.skeys, sl.d.svals, m_dev, B, prim::bit_length(S->d.t_ut.cap_max + 1),
@@ -1086,7 +1162,8 @@ int warm_up(odp_server* S) {
         if (S->small_ok)
             srv_batch_small<<<1, SRV_SMALL_THREADS, prim::small_sort_smem(SRV_SMALL_BATCH), as>>>(
                 S->d, sl.d, B, S->find_cap, S->cfg.max_events, prim::bit_length(S->cfg.max_events),
-                prim::bit_length(S->d.t_pair.cap_max + 1), prim::bit_length(S->d.t_ut.cap_max + 1));
+                prim::bit_length(S->d.t_pair.cap_max + 1), prim::bit_length(S->d.t_ut.cap_max + 1),
+                prim::bit_length(S->d.t_rid.cap_max + 1));
         if (cudaGraphLaunch(sl.an_graph, as) != cudaSuccess) return ODP_ERR_CUDA;
         if (cudaStreamSynchronize(fs) != cudaSuccess) return ODP_ERR_CUDA;
     }
@@ -1134,7 +1211,8 @@ void launch_batch(odp_server* S, Slot& sl) {
         const uint32_t B = S->cfg.max_batch_events;
         srv_batch_small<<<1, SRV_SMALL_THREADS, prim::small_sort_smem(SRV_SMALL_BATCH), as>>>(
             S->d, sl.d, B, S->find_cap, S->cfg.max_events, prim::bit_length(S->cfg.max_events),
-            prim::bit_length(S->d.t_pair.cap_max + 1), prim::bit_length(S->d.t_ut.cap_max + 1));
+            prim::bit_length(S->d.t_pair.cap_max + 1), prim::bit_length(S->d.t_ut.cap_max + 1),
+            prim::bit_length(S->d.t_rid.cap_max + 1));
     } else if (cudaGraphLaunch(sl.an_graph, as) != cudaSuccess) {
         S->error = ODP_ERR_CUDA;
     }
@@ -1314,12 +1392,13 @@ int odp_server_bytes(const odp_server_cfg* cfg, uint64_t* bytes) {
     const uint64_t table = sizeof(prim::Slot);
     // the blocks odp_server_create allocates, plus per slot the scratch of the
     // slot's fingerprint calls and 20 MB for allocation granularity
-    const uint64_t shared = 64 + E * (64 + 4 + 4 + 4 + 4 + 4 + 1) + 7 * table * (cap_p + 1) +
+    const uint64_t shared = 64 + E * (64 + 4 + 4 + 4 + 4 + 4 + 1 + 4 + 4) + 7 * table * (cap_p + 1) +
+                            8 * (cap_p + 1) +
                             table * (cap_b + 1) + 12 * SRV_NDEV + 40 * pend_cap + 80 +
                             find_cap * (sizeof(odp_finding) + 8);
     const uint64_t hist = 4 * prim::sort_hist_words((uint32_t)B);
     const uint64_t scan = 4 * (prim::scan_tmp_words(256u * ((uint32_t)B / prim::SORT_TILE + 2)) + 16);
-    const uint64_t per_slot = B * (sizeof(odp_event) + 8 + 8 + 16 + 4 + 4 + 12 * 4 + 8) +
+    const uint64_t per_slot = B * (sizeof(odp_event) + 8 + 8 + 16 + 4 + 4 + 13 * 4 + 8) +
                               sizeof(BatchPar) + hist + scan + find_cap * (sizeof(odp_finding) + 8) +
                               16 + 2 * 4 * 256 + 16 + fp_plan_scratch_bytes(B) + (20ull << 20);
     *bytes = shared + (uint64_t)cfg->n_slots * per_slot;
@@ -1368,6 +1447,10 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     if (!rc) rc = make_table(S, S->d.t_b, cap_b, caps + 4, S->an_stream);
     if (!rc) rc = make_table(S, S->d.t_pair, cap_p, caps + 5, S->an_stream);
     if (!rc) rc = make_table(S, S->d.t_rid, cap_p, caps + 6, S->an_stream);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.rid_open, 4ull * (cap_p + 1));
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.rid_wait, 4ull * (cap_p + 1));
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.wait_next, 4 * E);
+    if (!rc) rc = alloc_dev(S, (void**)&S->d.wait_del, 4 * E);
     if (!rc) rc = alloc_dev(S, (void**)&S->d.kmax, 8 * SRV_NDEV);
     if (!rc) rc = alloc_dev(S, (void**)&S->d.pend[0], 8ull * pend_cap);
     if (!rc) rc = alloc_dev(S, (void**)&S->d.pend[1], 8ull * pend_cap);
@@ -1388,6 +1471,8 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
     if (rc) return fail(rc);
     cudaMemsetAsync(S->d.kmax, 0, 8 * SRV_NDEV, S->an_stream);
     cudaMemsetAsync(S->d.gtail, 0xFF, 4 * E, S->an_stream);
+    cudaMemsetAsync(S->d.rid_open, 0, 4ull * (cap_p + 1), S->an_stream);
+    cudaMemsetAsync(S->d.rid_wait, 0xFF, 4ull * (cap_p + 1), S->an_stream);
     cudaMemsetAsync(S->d.rt_done, 0, E, S->an_stream);
     cudaMemsetAsync(S->d.npend, 0, 16, S->an_stream);
     cudaMemsetAsync(S->d.kcnt, 0, 4 * SRV_NDEV, S->an_stream);
@@ -1428,6 +1513,7 @@ int odp_server_create(const odp_server_cfg* cfg, odp_server** out) {
         if (!rc) rc = alloc_dev(S, (void**)&d.nfind, 16);
         if (!rc) rc = alloc_dev(S, (void**)&d.pa, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.pd, 4 * B);
+        if (!rc) rc = alloc_dev(S, (void**)&d.dalloc, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.rslot, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.bk, 4 * B);
         if (!rc) rc = alloc_dev(S, (void**)&d.bktmp, 4 * B);

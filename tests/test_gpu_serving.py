@@ -514,3 +514,58 @@ def test_streamed_mixed_trace_with_multi_endpoint_groups(cuda_ok, orc):
         assert np.array_equal(got.view(np.uint8), o.findings.view(np.uint8))
     finally:
         srv.close()
+
+
+def nested_completions(ev):
+    """Pairs (the nearest open ALLOC of the same device and device address,
+    closed by a DELETE) that complete while an earlier allocation of their
+    <host address, device, bytes> key is still open."""
+    from synth import traces as T
+
+    stacks, open_by_key, nested = {}, {}, 0
+    for i, e in enumerate(ev):
+        pk = (int(e["dst_dev"]), int(e["dev_addr"]))
+        if e["kind"] == T.ALLOC:
+            stacks.setdefault(pk, []).append(i)
+            k = (int(e["host_addr"]), int(e["dst_dev"]), int(e["bytes"]))
+            open_by_key.setdefault(k, set()).add(i)
+        elif e["kind"] == T.DELETE and stacks.get(pk):
+            a = stacks[pk].pop()
+            k = (int(ev[a]["host_addr"]), int(ev[a]["dst_dev"]), int(ev[a]["bytes"]))
+            open_by_key[k].discard(a)
+            nested += any(x < a for x in open_by_key[k])
+    return nested
+
+
+@pytest.mark.parametrize("seed,max_batch", [(1, 64), (2, 256), (3, 1024), (4, 4096)])
+def test_streamed_random_traces_with_nested_allocations(cuda_ok, orc, seed, max_batch):
+    """Random traces over three devices with device-to-device transfers,
+    overlapping allocations and deletes that close any open allocation: pairs
+    of one <host address, device, bytes> key complete out of allocation order
+    (a pair waits while an earlier allocation of its key is open), and content
+    groups reach three endpoints.  After the flush the streamed findings of all
+    five kinds equal the oracle's over the log."""
+    import paper_2601_12713_b300 as odp
+    from synth import traces as T
+
+    b = T.random_small(seed, n_ops=4000, n_contents=8, n_hosts=3, n_devices=3, d2d=True)
+    T.fill_fp_from_content(b)
+    ev = b.events.copy()
+    ev["flags"] = np.where(np.isin(ev["kind"], [2, 3, 4]), 1, 0)
+    assert nested_completions(ev) > 20
+    srv = odp.Server(n_slots=2, max_events=1 << 14, max_batch_events=max_batch,
+                     device_budget_bytes=2 << 30)
+    try:
+        srv.attach(0)
+        srv.submit(ev, np.zeros(ev.size, dtype=np.uint64))
+        srv.flush()
+        st = srv.stats()
+        assert st["events_processed"] == ev.size and st["stream_overflow"] == 0
+        log = odp.log_tensor(srv, ev.size).cpu().numpy().view(odp.EVENT_DTYPE).copy()
+        o = orc.analyze(log)
+        counts = [int((o.findings["kind"] == k).sum()) for k in range(1, 6)]
+        assert counts[2] > 50, counts
+        got = sorted_findings(srv.poll(1 << 20))
+        assert np.array_equal(got.view(np.uint8), o.findings.view(np.uint8))
+    finally:
+        srv.close()
