@@ -327,3 +327,49 @@ def test_fingerprint_log_fills_transfer_records(cuda_ok, orc, odp):
     assert np.array_equal(d_ev.cpu().numpy(), keep.view(np.uint8).reshape(-1))
     with pytest.raises(odp.OdpError):
         odp.fingerprint_log(d_ev[4:], n - 1, d_ptrs)  # records not 8-byte aligned
+
+
+def test_batch_with_large_buffers_in_multiblock_plan(cuda_ok, orc, odp):
+    """More than 8,192 buffers (the multi-block plan), some of them large
+    enough for many tiles each: their tile lists are written by the plan's
+    per-buffer pass and its warp-per-buffer pass; every fingerprint equals the
+    oracle's."""
+    rng = np.random.default_rng(21)
+    n = 12_000
+    sizes = rng.integers(0, 20_000, n)
+    big = rng.choice(n, 40, replace=False)
+    sizes[big] = rng.integers(1 << 20, 24 << 20, big.size)  # 256..6,144 chunks
+    offs = np.concatenate([[0], np.cumsum((sizes + 15) // 16 * 16)[:-1]])
+    arena = dev_buffer(int(offs[-1] + sizes[-1]) + 64, seed=23)
+    host = arena.cpu().numpy()
+    ptrs = torch.tensor(arena.data_ptr() + offs, dtype=torch.int64, device="cuda")
+    sz = torch.tensor(sizes, dtype=torch.int64, device="cuda")
+    out = torch.empty((n, 2), dtype=torch.int64, device="cuda")
+    for schedule in [(8, 0, 1, 0), (8, 0, 16, 2), (4, 0, 2, 0)]:
+        out.fill_(-1)
+        odp.fingerprint_with(schedule, ptrs, sz, out)
+        got = out.cpu().numpy().view(np.uint64)
+        want = orc.fp128_many(host, offs, sizes)
+        assert np.array_equal(got, want), schedule
+
+
+def test_fingerprint_log_null_payload(cuda_ok, odp):
+    """A transfer record whose payload pointer is null gets {0, 0} and
+    ODP_ERR_INVALID_ARG in the status word; the other transfers are hashed."""
+    from synth import traces
+
+    b = traces.listing2(3)
+    ev = b.events.copy()
+    n = ev.size
+    xfer = np.flatnonzero(np.isin(ev["kind"], [2, 3, 4]))
+    t = dev_buffer(8192, seed=5)
+    ptrs = np.zeros(n, dtype=np.int64)
+    ptrs[xfer] = t.data_ptr()
+    ptrs[xfer[1]] = 0
+    d_ev = torch.from_numpy(ev.view(np.uint8).reshape(-1).copy()).cuda()
+    odp.fingerprint_log(d_ev, n, torch.from_numpy(ptrs).cuda())
+    got = d_ev.cpu().numpy().view(traces.EVENT_DTYPE)
+    assert odp.fingerprint_status() == -1
+    assert got["fp_lo"][xfer[1]] == 0 and got["fp_hi"][xfer[1]] == 0
+    same = gpu_fp(odp, [t[:int(ev["bytes"][xfer[0]])]])[0]
+    assert (int(got["fp_lo"][xfer[0]]), int(got["fp_hi"][xfer[0]])) == same

@@ -569,3 +569,38 @@ def test_streamed_random_traces_with_nested_allocations(cuda_ok, orc, seed, max_
         assert np.array_equal(got.view(np.uint8), o.findings.view(np.uint8))
     finally:
         srv.close()
+
+
+def test_flush_round_trips_in_rounds(cuda_ok, orc):
+    """More round trips are left to the flush (content groups with three
+    endpoints) than one batch's findings buffer holds (3 * 128 + 2,048 + 64):
+    the flush replays the groups in rounds until none is dropped.  Kernels on
+    both devices every 40 events keep the unused-transfer lists short."""
+    import paper_2601_12713_b300 as odp
+    from synth import traces as T
+
+    x = multi_endpoint_events(7, 24_000, 2, stretch=10)
+    kern = np.zeros(x.size // 40, dtype=x.dtype)
+    kern["kind"] = T.KERNEL
+    kern["src_dev"] = -1
+    kern["dst_dev"] = np.arange(kern.size) % 2
+    kern["t_start_ns"] = x["t_start_ns"][::40][: kern.size] + 3
+    kern["t_end_ns"] = kern["t_start_ns"] + 4
+    ev = np.concatenate([x, kern])
+    ev = ev[np.argsort(ev["t_start_ns"], kind="stable")]
+    srv = odp.Server(n_slots=2, max_events=1 << 16, max_batch_events=128,
+                     device_budget_bytes=2 << 30)
+    try:
+        srv.attach(0)
+        srv.submit(ev, np.zeros(ev.size, dtype=np.uint64))
+        srv.flush()
+        st = srv.stats()
+        assert st["stream_overflow"] == 0 and st["rt_groups_at_flush"] > 0
+        log = odp.log_tensor(srv, ev.size).cpu().numpy().view(odp.EVENT_DTYPE).copy()
+        o = orc.analyze(log)
+        rt = o.findings[o.findings["kind"] == 2]
+        assert rt.size > 3 * (3 * 128 + 2048 + 64)
+        got = sorted_findings(srv.poll(1 << 20))
+        assert np.array_equal(got.view(np.uint8), o.findings.view(np.uint8))
+    finally:
+        srv.close()
