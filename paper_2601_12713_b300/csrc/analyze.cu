@@ -60,6 +60,7 @@ struct Hdr {
     uint32_t scan_fault; // a scan's bounded wait gave up (reported as ODP_ERR_TIMEOUT)
     uint32_t total_findings, n_site_rows;
     uint32_t tcap;
+    uint32_t n_gid_p, n_gid_u;  // distinct (device, device address) / candidate host-address keys
 };
 
 // Event field access (64-byte records).
@@ -115,6 +116,8 @@ struct A {
     unsigned long long* sites;  // [5][65536][3]
     prim::SplitTable tab;  // keys, then values: content ids (Alg. 1/2), then Alg. 3
     prim::KeyTable ktab;   // the same memory as tab, keys only
+    uint32_t* gid;         // per ktab slot: the dense group id of its key (tab's value array,
+                           // which holds nothing between Alg. 1 and Alg. 3 or after Alg. 3)
     odp_findings out;
 };
 
@@ -280,10 +283,13 @@ __global__ void __launch_bounds__(TPB) k_compact(A a, const uint32_t* scanned, u
 
 // ----------------------------------------------------- Alg. 1 (and ids)
 
-// Group keys are table slot indices: one slot per distinct key, so sorting
-// by slot groups equal keys (in an order of groups that nothing depends on)
-// without a second pass that reads each slot's value.  A full table cannot
-// occur (capacity >= 1.25 x count); it would be reported, not mis-grouped.
+// Group keys start as table slot indices: one slot per distinct key.  The
+// pairs and Alg. 5 tables then replace each slot by a dense id numbered by
+// the insert that put its key there (k_gid_keys), so the sorts that group
+// equal keys (in an order of groups that nothing depends on) need only the
+// bits of the number of distinct keys -- usually far fewer than the slots'.
+// A full table cannot occur (capacity >= 1.25 x count); it would be
+// reported, not mis-grouped.
 __device__ __forceinline__ uint32_t slot_key(const A& a, uint32_t s, uint32_t e) {
     if (s == NONE32) record_error(&a.h->err, e, ODP_ERR_UNSUPPORTED);
     return s;
@@ -671,10 +677,13 @@ __global__ void k_p_insert(A a) {
             key[b] = use[b] ? Key128{hi64(a.col.hd[e[b]]), (uint64_t)c_dst(c)} : Key128{0, 0};
             flag[b] = a.pack_alloc && c_kind(c) == ODP_ALLOC ? 0x80000000u : 0u;
         }
-        prim::table_insert_batch<INS_B, false, true, false>(a.ktab, cap, key, e, use, out);
+        bool fresh[INS_B];
+        prim::table_insert_batch<INS_B, false, true, false>(a.ktab, cap, key, e, use, out, fresh);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             if (!use[b]) continue;
+            // (a key's high half is a device number: never the all-ones key)
+            if (fresh[b]) a.gid[out[b]] = atomicAdd(&a.h->n_gid_p, 1u) + 1u;
             a.sk[j0 + b * str] = slot_key(a, out[b], e[b]) | flag[b];
             a.sv[j0 + b * str] = e[b];
         }
@@ -964,8 +973,8 @@ __global__ void k_ut_heads(A a) {
 }
 
 // Candidates grouped by host address (few distinct addresses: the table
-// stays in L2); the group key is the address's slot, non-candidates get
-// cap_max + 1 (above every slot).
+// stays in L2); the group key is the address's slot (then its dense id),
+// non-candidates get NONE32 (then 0).
 __global__ void k_ut_insert(A a) {
     pdl_entry();
     if (failed(a)) return;
@@ -982,14 +991,28 @@ __global__ void k_ut_insert(A a) {
             e[b] = use[b] ? a.sv[q] : 0;
             key[b] = use[b] ? Key128{lo64(a.col.hd[e[b]]), 1} : Key128{0, 0};
         }
-        prim::table_insert_batch<INS_B, false, true, false>(a.ktab, cap, key, e, use, out);
+        bool fresh[INS_B];
+        prim::table_insert_batch<INS_B, false, true, false>(a.ktab, cap, key, e, use, out, fresh);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             const uint32_t q = q0 + b * str;
             if (q >= n) continue;
-            a.k2[q] = use[b] ? slot_key(a, out[b], e[b]) : a.ktab.cap_max + 1;
+            // (a key's high half is 1: never the all-ones key)
+            if (fresh[b]) a.gid[out[b]] = atomicAdd(&a.h->n_gid_u, 1u) + 1u;
+            a.k2[q] = use[b] ? slot_key(a, out[b], e[b]) : NONE32;
             a.v2[q] = q;
         }
+    }
+}
+
+// Slot keys to dense group ids, after the inserts: keys[q] = gid[slot], bit
+// `flag` carried over; NONE32 (no slot) becomes 0.
+__global__ void k_gid_keys(A a, uint32_t* keys, const uint32_t* count, uint32_t flag) {
+    pdl_entry();
+    if (failed(a)) return;
+    GRID_STRIDE(q, *count) {
+        const uint32_t k = keys[q];
+        keys[q] = k == NONE32 ? 0u : a.gid[k & ~flag] | (k & flag);
     }
 }
 
@@ -1000,7 +1023,7 @@ __global__ void k_ut_next(A a) {
     if (failed(a)) return;
     const uint32_t nU = a.h->nU;
     GRID_STRIDE(r, nU) {
-        if (a.k2[r] > a.ktab.cap_max || r + 1 >= nU || a.k2[r + 1] != a.k2[r]) continue;
+        if (a.k2[r] == 0 || r + 1 >= nU || a.k2[r + 1] != a.k2[r]) continue;
         const uint32_t q = a.v2[r], q2 = a.v2[r + 1];
         const uint32_t s1 = a.id1[q] + a.f1[q] - 1, s2 = a.id1[q2] + a.f1[q2] - 1;
         if (s1 == s2) a.ut[a.sv[q]] = a.sv[q2];
@@ -1124,6 +1147,35 @@ __device__ __forceinline__ void site_add(SiteSmem& t, const A& a, uint32_t kind0
 // totals, and its wasted events are marked.  No block barrier inside the loop.
 constexpr int EMW_THREADS = 512;
 
+// Chunks ahead of the current one whose coalesced reads a warp prefetches
+// into L2, so its first wait of a chunk is on L2 rather than DRAM.
+constexpr uint32_t EMW_PREFETCH_AHEAD = 2;
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// The 18 lines chunk cn reads before its first wait (its events' times,
+// bytes, sites, deletes and partners) and its five scanned offsets, one line
+// per lane; lines that start past the last event are skipped.
+__device__ __forceinline__ void em_prefetch_chunk(const A& a, const uint32_t* wscan, uint32_t nch,
+                                                  uint32_t cn, int lane) {
+    if (cn >= nch || lane >= 18) return;
+    const uint32_t base = cn * 32;
+    uint32_t e = base;
+    const void* p;
+    if (lane < 4) e = base + 8 * lane, p = a.col.tt + e;
+    else if (lane < 6) e = base + 16 * (lane - 4), p = a.col.bytes + e;
+    else if (lane < 8) e = base + 16 * (lane - 6), p = a.drt + e;
+    else if (lane == 8) p = a.col.site + base;
+    else if (lane == 9) p = a.del_of + base;
+    else if (lane == 10) p = a.ra + base;
+    else if (lane == 11) p = a.ua + base;
+    else if (lane == 12) p = a.ut + base;
+    else p = wscan + (size_t)(lane - 13) * nch + cn;
+    if (e < a.n) prefetch_l2(p);
+}
+
 // Sets event e's wasted bit; returns its duration if this call set it.
 __device__ __forceinline__ uint64_t mark_wasted(const A& a, uint32_t e, uint64_t duration) {
     const uint32_t bit = 1u << (e & 31);
@@ -1135,7 +1187,9 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
     if (failed(a)) return;
     extern __shared__ __align__(16) unsigned char em_dyn[];
     SiteSmem& st = *reinterpret_cast<SiteSmem*>(em_dyn);
+    __shared__ uint32_t chunk_off[EMW_THREADS / 32][5];  // the chunk's scanned offset per kind
     const int lane = threadIdx.x & 31;
+    uint32_t* my_off = chunk_off[threadIdx.x >> 5];
     const uint32_t lt = (1u << lane) - 1;
     odp_finding* items = a.out.items;
     const uint64_t cap = a.out.capacity;
@@ -1149,9 +1203,11 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     unsigned long long saved = 0;
+    for (uint32_t k = 1; k < EMW_PREFETCH_AHEAD; ++k) em_prefetch_chunk(a, wscan, nch, gw + k * nw, lane);
     for (uint32_t c = gw; c < nch; c += nw) {
         const uint32_t i = c * 32 + lane;
         const bool valid = i < a.n;
+        em_prefetch_chunk(a, wscan, nch, c + EMW_PREFETCH_AHEAD * nw, lane);
         // First loads: the partner arrays, and with them (before knowing whether
         // the event has a finding) its own record and the delete that closes
         // it, so a chunk waits for memory twice, not three times.
@@ -1163,11 +1219,15 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
         const uint64_t own_bytes = __ldg(reinterpret_cast<const unsigned long long*>(a.col.bytes) + iv);
         const uint32_t site = __ldg(a.col.site + iv);
         const uint32_t del = valid ? __ldg(a.del_of + i) : NONE32;
+        const uint32_t off = lane < 5 ? __ldg(wscan + (size_t)lane * nch + c) : 0u;
         for (int kind = 0; kind < 5; ++kind) {
             part[kind] = valid ? partner_of(a, kind + 1, i) : NONE32;
             bal[kind] = __ballot_sync(ODP_FULL_MASK, part[kind] != NONE32);
             any |= bal[kind];
         }
+        __syncwarp();  // the previous chunk's stores have read my_off
+        if (lane < 5) my_off[lane] = off;
+        __syncwarp();
         // Wasted events: the event itself for DD, RA, UA and UT findings (one
         // atomic per chunk), the partner for RT, the delete for RA and UA.
         // Whoever sets an event's bit adds its duration to the saved time, so
@@ -1230,7 +1290,7 @@ __global__ void __launch_bounds__(EMW_THREADS) k_em_write(A a, const uint32_t* w
                         break;
                 }
                 site_add(st, a, kind, site, wb, wn);
-                const uint64_t pos = (uint64_t)wscan[kind * nch + c] + __popc(bal[kind] & lt);
+                const uint64_t pos = (uint64_t)my_off[kind] + __popc(bal[kind] & lt);
                 if (pos < cap)
                     store_finding(items, pos, kind + 1, site, psite[kind], i,
                                   np ? ODP_NO_EVENT : (uint64_t)p, wb, wn);
@@ -1469,6 +1529,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     a.ktab.keys = (Key128*)(b + o_tslots);
     a.ktab.cap_max = cap_max;
     a.ktab.cap_dev = &a.h->tcap;
+    a.gid = a.tab.vals;
     a.out = out;
     prim::SortTmp srt;
     srt.keys_alt = (uint32_t*)(b + o_keys_alt);
@@ -1540,7 +1601,8 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     // ---- pairs
     clear_table(a.ktab, nP, n, clear_grid, s);
     pdl(k_p_insert, gX, TPB, 0, s, a);
-    prim::radix_sort(a.sk, a.sv, nP, n, bits_slot, srt, s);
+    pdl(k_gid_keys, gX, TPB, 0, s, a, a.sk, nP, a.pack_alloc ? 0x80000000u : 0u);
+    prim::radix_sort(a.sk, a.sv, nP, n, bits_slot, srt, s, &a.h->n_gid_p);
     pdl(k_seg_heads, gX, TPB, 0, s, a, nP);
     prim::exclusive_scan(a.f1, a.id1, nP, n, &a.h->nseg2, scan_tmp, s, srt.fault, true);
     pdl(k_seg_starts, gX, TPB, 0, s, a, nP, &a.h->nseg2);
@@ -1572,7 +1634,8 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     prim::exclusive_scan(a.f1, a.id1, nU, n, &a.h->nsegU, scan_tmp, s, srt.fault, true);
     clear_table(a.ktab, nU, n, clear_grid, s);
     pdl(k_ut_insert, gX, TPB, 0, s, a);
-    prim::radix_sort(a.k2, a.v2, nU, n, bits_slot, srt, s);
+    pdl(k_gid_keys, gX, TPB, 0, s, a, a.k2, nU, 0u);
+    prim::radix_sort(a.k2, a.v2, nU, n, bits_slot, srt, s, &a.h->n_gid_u);
     pdl(k_ut_next, gX, TPB, 0, s, a);
 
     // ---- emission

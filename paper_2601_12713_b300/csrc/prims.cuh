@@ -195,6 +195,44 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_ROUNDS = 16;
 constexpr uint32_t SORT_TILE = SORT_THREADS * SORT_ROUNDS;  // 4096 items per tile
 
+// The digit layout of a sort by the low `key_bits` bits: an even number of
+// passes (the data ends where it started), at most 8 bits each, the bits
+// split evenly.  With a device-side bound on the keys (key_max, may be null)
+// the device takes only the bits the bound needs, so some of the passes the
+// host launched for key_bits do nothing.  The host and the device compute it
+// the same way.
+struct SortPass {
+    int shift, bits;
+    bool active;
+};
+
+__host__ __device__ __forceinline__ int sort_passes(int key_bits) {
+    const int passes = (key_bits + 7) / 8;
+    return passes + (passes & 1);
+}
+
+__host__ __device__ __forceinline__ SortPass sort_pass(int p, int key_bits) {
+    const int npass = sort_passes(key_bits);
+    SortPass r{0, 0, p < npass};
+    if (!r.active) return r;
+    const int per = (key_bits + npass - 1) / npass;
+    for (int q = 0;; ++q) {
+        int b = key_bits - r.shift;
+        b = b < per ? b : per;
+        r.bits = b > 1 ? b : 1;
+        if (q == p) return r;
+        r.shift += r.bits;
+    }
+}
+
+__device__ __forceinline__ SortPass sort_pass_dev(int p, int key_bits, const uint32_t* key_max) {
+    if (key_max) {
+        const int need = 32 - __clz(*key_max);
+        if (need < key_bits) key_bits = need;
+    }
+    return sort_pass(p, key_bits);
+}
+
 // Tiles of the device length n: ntd = ceil(n / SORT_TILE).  Histograms are
 // stored digit-major over the device tile count, hist[d * ntd + tile], so
 // the scan between the sweeps covers radix * ntd words (written to *hlen).
@@ -202,13 +240,15 @@ __device__ __forceinline__ uint32_t sort_tiles(uint32_t n) { return (n + SORT_TI
 
 // Per-tile digit histograms; blocks loop over tiles.
 __global__ void __launch_bounds__(SORT_THREADS)
-sort_upsweep(const uint32_t* keys, const uint32_t* n_dev, uint32_t n_max, int shift, int bits,
-             uint32_t* hist, uint32_t* hlen) {
+sort_upsweep(const uint32_t* keys, const uint32_t* n_dev, uint32_t n_max, int pass, int key_bits,
+             const uint32_t* key_max, uint32_t* hist, uint32_t* hlen) {
     pdl_entry();
     __shared__ uint32_t h[256];
-    const uint32_t n = dev_len(n_dev, n_max);
+    const SortPass sp = sort_pass_dev(pass, key_bits, key_max);
+    const int shift = sp.shift;
+    const uint32_t n = sp.active ? dev_len(n_dev, n_max) : 0;
     const uint32_t ntd = sort_tiles(n);
-    const uint32_t radix = 1u << bits;
+    const uint32_t radix = 1u << sp.bits;
     if (blockIdx.x == 0 && threadIdx.x == 0) *hlen = radix * ntd;
     for (uint32_t t = blockIdx.x; t < ntd; t += gridDim.x) {
         for (uint32_t d = threadIdx.x; d < radix; d += SORT_THREADS) h[d] = 0;
@@ -231,9 +271,11 @@ sort_upsweep(const uint32_t* keys, const uint32_t* n_dev, uint32_t n_max, int sh
 // the tile lands contiguously at its global start.  Blocks loop over tiles.
 __global__ void __launch_bounds__(SORT_THREADS, 4)
 sort_downsweep(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
-               uint32_t* vals_out, const uint32_t* n_dev, uint32_t n_max, int shift, int bits,
-               const uint32_t* hist_scanned) {
+               uint32_t* vals_out, const uint32_t* n_dev, uint32_t n_max, int pass, int key_bits,
+               const uint32_t* key_max, const uint32_t* hist_scanned) {
     pdl_entry();
+    const SortPass sp = sort_pass_dev(pass, key_bits, key_max);
+    const int shift = sp.shift, bits = sp.bits;
     constexpr int W = SORT_THREADS / 32;
     constexpr int PER_WARP = SORT_TILE / W;  // 512 items, SORT_ROUNDS rounds of 32
     __shared__ uint32_t base_d[256];   // global start of each digit for this tile
@@ -242,7 +284,7 @@ sort_downsweep(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
     __shared__ uint32_t ks[SORT_TILE];
     __shared__ uint32_t vs[SORT_TILE];
     __shared__ uint32_t scan_tmp[40];
-    const uint32_t n = dev_len(n_dev, n_max);
+    const uint32_t n = sp.active ? dev_len(n_dev, n_max) : 0;
     const uint32_t ntd = sort_tiles(n);
     const uint32_t radix = 1u << bits;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -466,9 +508,12 @@ inline int downsweep_per_sm() {
 }
 
 // Stable sort of (keys, vals) by the low `key_bits` bits of the keys; the
-// result ends in (keys, vals) (ping-pong through the alternates).
+// result ends in (keys, vals) (ping-pong through the alternates).  key_max
+// (device word, may be null): an upper bound on the keys known only on the
+// device; the passes it makes unnecessary return at once.
 inline void radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, uint32_t n_max,
-                       int key_bits, const SortTmp& t, cudaStream_t s) {
+                       int key_bits, const SortTmp& t, cudaStream_t s,
+                       const uint32_t* key_max = nullptr) {
     if (n_max == 0 || key_bits <= 0) return;
     if (n_max <= SMALL_SORT_MAX && sort_small_ready()) {
         pdl_if(t.pdl, sort_small, 1, SMALL_SORT_THREADS, SMALL_SORT_SMEM, s, keys, vals, n_dev,
@@ -476,21 +521,17 @@ inline void radix_sort(uint32_t* keys, uint32_t* vals, const uint32_t* n_dev, ui
         return;
     }
     const uint32_t ntiles = (n_max + SORT_TILE - 1) / SORT_TILE;
-    const int passes = (key_bits + 7) / 8;
-    // an even number of passes leaves the data in place
-    const int npass = passes + (passes & 1);
-    const int per = (key_bits + npass - 1) / npass;
+    const int npass = sort_passes(key_bits);
     uint32_t *k_in = keys, *v_in = vals, *k_out = t.keys_alt, *v_out = t.vals_alt;
-    int shift = 0;
     for (int p = 0; p < npass; ++p) {
-        const int bits = std::max(1, std::min(per, key_bits - shift));
-        const uint32_t hn = (1u << bits) * ntiles;
+        // (a device-side bound can split its fewer bits into wider digits)
+        const uint32_t hn = (key_max ? 256u : 1u << sort_pass(p, key_bits).bits) * ntiles;
         pdl_if(t.pdl, sort_upsweep, tile_grid(ntiles, 8), SORT_THREADS, 0, s, k_in,
-               n_dev, n_max, shift, bits, t.hist, t.hlen);
+               n_dev, n_max, p, key_bits, key_max, t.hist, t.hlen);
         exclusive_scan(t.hist, t.hist, t.hlen, hn, nullptr, t.scan_tmp, s, t.fault, t.pdl);
         pdl_if(t.pdl, sort_downsweep, tile_grid(ntiles, downsweep_per_sm()),
-               SORT_THREADS, 0, s, k_in, v_in, k_out, v_out, n_dev, n_max, shift, bits, t.hist);
-        shift += bits;
+               SORT_THREADS, 0, s, k_in, v_in, k_out, v_out, n_dev, n_max, p, key_bits, key_max,
+               t.hist);
         std::swap(k_in, k_out);
         std::swap(v_in, v_out);
     }
@@ -688,10 +729,13 @@ __device__ __forceinline__ uint32_t table_insert(const Table& t, uint32_t cap, K
 // round trip where most keys are new or rarely repeated in a table far
 // larger than L2.  LOWER: read the value before lowering it (lower_to),
 // which spares the atomic when an earlier insert already set a smaller one.
+// fresh (may be null): set for the inserts whose compare-and-swap put the
+// key into its slot (one per distinct key, except the all-ones key, which is
+// never marked).
 template <int B, bool MIN, bool PEEK, bool LOWER, class TableT>
 __device__ __forceinline__ void table_insert_batch(const TableT& t, uint32_t cap, const Key128* k,
                                                    const uint32_t* v, const bool* use,
-                                                   uint32_t* out) {
+                                                   uint32_t* out, bool* fresh = nullptr) {
     const uint32_t mask = cap - 1;
     const Key128 empty{EMPTY_KEY, EMPTY_KEY};
     uint32_t slot[B];
@@ -699,6 +743,7 @@ __device__ __forceinline__ void table_insert_batch(const TableT& t, uint32_t cap
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         out[b] = NONE32;
+        if (fresh) fresh[b] = false;
         done[b] = !use[b];
         slot[b] = 0;
         if (!use[b]) continue;
@@ -729,6 +774,7 @@ __device__ __forceinline__ void table_insert_batch(const TableT& t, uint32_t cap
                 if (MIN && LOWER) lower_to(t.val_at(slot[b]), v[b]);
                 else if (MIN) atomicMin(t.val_at(slot[b]), v[b]);
                 out[b] = slot[b];
+                if (fresh) fresh[b] = key_eq(cur[b], empty);
                 done[b] = true;
             } else {
                 slot[b] = (slot[b] + 1) & mask;
