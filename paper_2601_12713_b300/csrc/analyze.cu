@@ -114,10 +114,10 @@ struct A {
     uint64_t *ks, *ke;    // kernels sorted by device: start, running max of end
     uint32_t *dstart, *dend;  // kernel ranges per device, indexed by device number + 1
     unsigned long long* sites;  // [5][65536][3]
-    prim::SplitTable tab;  // keys, then values: content ids (Alg. 1/2), then Alg. 3
-    prim::KeyTable ktab;   // the same memory as tab, keys only
+    prim::SplitTable tab;  // keys, then values: Alg. 3's first allocations
+    prim::KeyTable ktab;   // the same memory as tab, keys only: contents, pairs, Alg. 5
     uint32_t* gid;         // per ktab slot: the dense group id of its key (tab's value array,
-                           // which holds nothing between Alg. 1 and Alg. 3 or after Alg. 3)
+                           // which holds nothing before Alg. 3 or after it)
     odp_findings out;
 };
 
@@ -295,9 +295,13 @@ __device__ __forceinline__ uint32_t slot_key(const A& a, uint32_t s, uint32_t e)
     return s;
 }
 
-// Content groups are keyed by their first transfer (the slot's minimum event
-// index), not by slot: groups then sort in time order, and the passes that
-// follow the sorted order touch the event-indexed arrays nearly sequentially.
+// Content groups are keyed by the event whose insert put the fingerprint
+// into the table (the all-ones fingerprint, which has a slot of its own, by
+// its first event): one store per content instead of a minimum kept per
+// insert.  The inserting threads sweep the transfer list in time order, so
+// the groups sort in nearly the order of their first transfers, and the
+// passes that follow the sorted order touch the event-indexed arrays within
+// a window that stays in L2.
 // Four list entries per thread per step (spaced a grid apart, so the list
 // loads and slot stores stay coalesced), their table probes in flight
 // together.
@@ -327,10 +331,15 @@ __global__ void k_x_insert_fp(A a) {
             const uint4 f = use[b] ? a.col.fp[e[b]] : make_uint4(0, 0, 0, 0);
             key[b] = Key128{lo64(f), hi64(f)};
         }
-        prim::table_insert_batch<INS_B, true, false, true>(a.tab, cap, key, e, use, out);
+        bool fresh[INS_B];
+        prim::table_insert_batch<INS_B, false, false, false>(a.ktab, cap, key, e, use, out, fresh);
 #pragma unroll
-        for (int b = 0; b < INS_B; ++b)
-            if (use[b]) a.slot[j0 + b * str] = slot_key(a, out[b], e[b]);
+        for (int b = 0; b < INS_B; ++b) {
+            if (!use[b]) continue;
+            if (fresh[b]) a.gid[out[b]] = e[b];
+            else if (out[b] == a.ktab.cap_max) atomicMin(a.gid + out[b], e[b]);
+            a.slot[j0 + b * str] = slot_key(a, out[b], e[b]);
+        }
     }
 }
 
@@ -343,7 +352,7 @@ __global__ void k_x_cid(A a) {
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) sl[b] = j0 + b * str < n ? a.slot[j0 + b * str] : NONE32;
 #pragma unroll
-        for (int b = 0; b < INS_B; ++b) v[b] = sl[b] != NONE32 ? a.tab.vals[sl[b]] : 0;
+        for (int b = 0; b < INS_B; ++b) v[b] = sl[b] != NONE32 ? a.gid[sl[b]] : 0;
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             const uint32_t j = j0 + b * str;
@@ -1555,6 +1564,8 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     ODP_CHECK_CUDA(cudaMemsetAsync(a.dstart, 0, 2 * 4 * NDEV, s));
     ODP_CHECK_CUDA(cudaMemsetAsync(a.sites, 0, 8ull * 3 * 5 * ODP_MAX_SITES, s));
     ODP_CHECK_CUDA(cudaMemsetAsync(scan_tmp, 0, 4 * (scan_words + 16), s));
+    // the all-ones fingerprint's group key (its first event, an atomic minimum)
+    ODP_CHECK_CUDA(cudaMemsetAsync(a.gid + cap_max, 0xFF, 4, s));
 
     // ---- validate, lists
     uint32_t* ccnt = (uint32_t*)(b + o_wcnt);
@@ -1569,7 +1580,7 @@ static int an_run(const odp_event* events, uint64_t n64, const odp_findings* out
     uint32_t* nU = &a.h->nU;
 
     // ---- Alg. 1: content ids, first receivers
-    clear_table(a.tab, nX, n, clear_grid, s);
+    clear_table(a.ktab, nX, n, clear_grid, s);
     pdl(k_x_insert_fp, gX, TPB, 0, s, a);
     pdl(k_x_cid, gX, TPB, 0, s, a);
 

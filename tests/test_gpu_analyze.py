@@ -327,3 +327,21 @@ def test_full_scale_iterative_solver(cuda_ok, orc, odp, p_skip):
     assert np.array_equal(g["findings"].view(np.uint8), o.findings.view(np.uint8))
     if p_skip:
         assert g["summary"]["count4"] > 100_000 and g["summary"]["count5"] > 10_000
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_all_ones_and_zero_fingerprints(cuda_ok, orc, odp, seed):
+    """Contents whose fingerprint is all ones (the hash table's empty key,
+    kept in a slot of its own) or all zeros group like any other content."""
+    b = traces.random_small(2000 + seed, n_ops=3000 + 2000 * seed, n_contents=12, n_hosts=9,
+                            n_devices=1 + seed % 3, d2d=seed % 2 == 0)
+    ev = with_fp(b)
+    xfer = np.isin(ev["kind"], [traces.TO_DEV, traces.FROM_DEV, traces.DEV_TO_DEV])
+    cont = b.content
+    ones = xfer & (cont == cont[xfer].min())
+    zeros = xfer & (cont == cont[xfer].max())
+    assert ones.any() and zeros.any()
+    ev["fp_lo"][ones] = ev["fp_hi"][ones] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    ev["fp_lo"][zeros] = ev["fp_hi"][zeros] = 0
+    g = check(odp, orc, ev)
+    assert g["count"] > 0
