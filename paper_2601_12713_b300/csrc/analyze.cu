@@ -84,7 +84,7 @@ struct EvCols {
     uint4* tt;        // {t_start, t_end}
     uint4* hd;        // {host_addr, dev_addr}
     uint64_t* bytes;  // bytes
-    uint4* fp;        // {fp_lo, fp_hi}
+    uint4* fp;        // {fp_lo, fp_hi} (dense: one DRAM fetch serves several transfers)
     uint32_t* site;   // site_id
 };
 
@@ -123,8 +123,11 @@ struct A {
 
 __device__ __forceinline__ bool failed(const A& a) { return a.h->err != NO_ERR; }
 
-#define GRID_STRIDE(i, n) \
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+// (n is read once: a device-side count re-read after every store would put
+// its load on each iteration's path)
+#define GRID_STRIDE(i, n)                                                          \
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x, i##_end = (n); i < i##_end; \
+         i += gridDim.x * blockDim.x)
 
 
 // ------------------------------------------------------------ validate
@@ -383,11 +386,26 @@ __global__ void k_rt_flags(A a) {
 __global__ void k_rt_starts(A a) {
     pdl_entry();
     if (failed(a)) return;
-    const uint32_t n = a.h->nX;
-    GRID_STRIDE(q, n) {
-        if (a.f1[q]) a.H[a.id1[q]] = q;
-        if (a.f2[q]) a.R[a.id2[q]] = q;
-        a.bad[q] = 0;
+    const uint32_t n = a.h->nX, str = gridDim.x * blockDim.x;
+    BATCH_STRIDE(q0, n) {
+        uint32_t f1[INS_B], f2[INS_B], i1[INS_B], i2[INS_B];
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const uint32_t q = q0 + b * str;
+            const bool in = q < n;
+            f1[b] = in ? a.f1[q] : 0u;
+            f2[b] = in ? a.f2[q] : 0u;
+            i1[b] = in ? a.id1[q] : 0u;
+            i2[b] = in ? a.id2[q] : 0u;
+        }
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const uint32_t q = q0 + b * str;
+            if (q >= n) continue;
+            if (f1[b]) a.H[i1[b]] = q;
+            if (f2[b]) a.R[i2[b]] = q;
+            a.bad[q] = 0;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.H[a.h->nseg] = n;
@@ -745,11 +763,24 @@ __global__ void k_p_check(A a) {
 __global__ void k_p_match(A a) {
     pdl_entry();
     if (failed(a)) return;
-    GRID_STRIDE(q, a.h->nP) {
-        const uint32_t s = a.id1[q] + a.f1[q] - 1;
-        if (a.bad[s]) continue;
-        const uint32_t hi = a.H[s + 1];
-        if (a.k2[q] && q + 1 < hi) a.del_of[a.sv[q]] = a.sv[q + 1];
+    const uint32_t n = a.h->nP, str = gridDim.x * blockDim.x;
+    BATCH_STRIDE(q0, n) {
+        uint32_t sg[INS_B], e[INS_B], d[INS_B];
+        bool al[INS_B];
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const uint32_t q = q0 + b * str;
+            al[b] = q < n && a.k2[q];
+            sg[b] = al[b] ? a.id1[q] + a.f1[q] - 1 : 0u;
+            e[b] = al[b] ? a.sv[q] : 0u;
+            d[b] = al[b] && q + 1 < n ? a.sv[q + 1] : NONE32;
+        }
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) {
+            const uint32_t q = q0 + b * str;
+            // the next entry closes this ALLOC if it lies in the same group
+            if (al[b] && !a.bad[sg[b]] && q + 1 < a.H[sg[b] + 1]) a.del_of[e[b]] = d[b];
+        }
     }
 }
 
@@ -1019,9 +1050,16 @@ __global__ void k_ut_insert(A a) {
 __global__ void k_gid_keys(A a, uint32_t* keys, const uint32_t* count, uint32_t flag) {
     pdl_entry();
     if (failed(a)) return;
-    GRID_STRIDE(q, *count) {
-        const uint32_t k = keys[q];
-        keys[q] = k == NONE32 ? 0u : a.gid[k & ~flag] | (k & flag);
+    const uint32_t n = *count, str = gridDim.x * blockDim.x;
+    BATCH_STRIDE(q0, n) {
+        uint32_t k[INS_B];
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) k[b] = q0 + b * str < n ? keys[q0 + b * str] : NONE32;
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b) k[b] = k[b] == NONE32 ? 0u : a.gid[k[b] & ~flag] | (k[b] & flag);
+#pragma unroll
+        for (int b = 0; b < INS_B; ++b)
+            if (q0 + b * str < n) keys[q0 + b * str] = k[b];
     }
 }
 
