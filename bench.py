@@ -37,9 +37,9 @@ SEED = 0x0DB2
 # B / 512 MiB times this.
 FP_TILES_TRAFFIC_512MIB = 540.99e6
 # DRAM read+write bytes of one odp_analyze call on the 50,002,000-event
-# iterative-solver trace, summed over its 123 launches (ncu, dram__bytes_read.sum
-# + dram__bytes_write.sum, one pass per launch): 24.47 GB read + 11.84 GB written.
-ANALYZE_TRAFFIC_PER_EVENT = 36.31e9 / 50_002_000
+# iterative-solver trace, summed over its 124 launches (ncu, dram__bytes_read.sum
+# + dram__bytes_write.sum, one pass per launch): 22.74 GB read + 11.04 GB written.
+ANALYZE_TRAFFIC_PER_EVENT = 33.78e9 / 50_002_000
 
 
 def peaks():
@@ -825,7 +825,7 @@ def bench_analysis(args, odp, dist, rank, stream, peak, peak_kind):
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "traffic": round(ANALYZE_TRAFFIC_PER_EVENT * n),
                      "traffic_source": "ncu capture of one call on this 50,002,000-event trace "
-                                       "(all 123 launches), per event times the events",
+                                       "(all 124 launches), per event times the events",
                      "note": "whole odp_analyze call against the bytes the method must read "
                              "and write: 64 B per event, 48 B per finding, 32 B per site row"},
         "e2e": {"value": round(e_val, 2), "unit": "M events/s", "h2d_bytes_per_step": 64 * n,

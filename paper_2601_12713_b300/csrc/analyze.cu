@@ -335,7 +335,7 @@ __global__ void k_x_insert_fp(A a) {
             key[b] = Key128{lo64(f), hi64(f)};
         }
         bool fresh[INS_B];
-        prim::table_insert_batch<INS_B, false, false, false>(a.ktab, cap, key, e, use, out, fresh);
+        prim::table_insert_batch<INS_B, false, true, false>(a.ktab, cap, key, e, use, out, fresh);
 #pragma unroll
         for (int b = 0; b < INS_B; ++b) {
             if (!use[b]) continue;
