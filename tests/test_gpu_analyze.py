@@ -345,3 +345,56 @@ def test_all_ones_and_zero_fingerprints(cuda_ok, orc, odp, seed):
     ev["fp_lo"][zeros] = ev["fp_hi"][zeros] = 0
     g = check(odp, orc, ev)
     assert g["count"] > 0
+
+
+def many_keys_trace(seed, n_arrays, n_rounds, n_devices):
+    """n_arrays arrays (one host address, device address and device each),
+    each mapped n_rounds times at random times (ALLOC, TO_DEV, FROM_DEV,
+    DELETE), with kernels at random times on random devices; content versions
+    change at random.  More than 2^16 distinct (device, device address) keys
+    and candidate host addresses."""
+    rng = np.random.default_rng(seed)
+    m = n_arrays * n_rounds
+    arr = np.repeat(np.arange(n_arrays), n_rounds)
+    start = 1000 + 4 * rng.integers(0, 40 * m, m)
+    dev = arr % n_devices
+    ver = rng.integers(0, 3, (m, 2))
+    n_k = m // 50
+    ev = np.zeros(4 * m + n_k, dtype=traces.EVENT_DTYPE)
+    content = np.full(ev.size, -1, dtype=np.int64)
+    parts = [(0, traces.ALLOC), (1, traces.TO_DEV), (20, traces.FROM_DEV), (21, traces.DELETE)]
+    for j, (off, kind) in enumerate(parts):
+        sl = slice(j * m, (j + 1) * m)
+        ev["t_start_ns"][sl] = start + off
+        ev["kind"][sl] = kind
+        ev["host_addr"][sl] = 0x1000 * (1 + arr)
+        ev["dev_addr"][sl] = 0x100 * (1 + arr)
+        ev["bytes"][sl] = 64 * (1 + arr % 3)
+        ev["site_id"][sl] = arr % 500
+        ev["src_dev"][sl] = dev if kind == traces.FROM_DEV else traces.HOST
+        ev["dst_dev"][sl] = traces.HOST if kind == traces.FROM_DEV else dev
+        if kind == traces.TO_DEV:
+            content[sl] = 10 * arr + ver[:, 0]
+        elif kind == traces.FROM_DEV:
+            content[sl] = 10 * arr + ver[:, 1]
+    sl = slice(4 * m, None)
+    ev["t_start_ns"][sl] = 1000 + rng.integers(0, 160 * m, n_k)
+    ev["kind"][sl] = traces.KERNEL
+    ev["src_dev"][sl] = traces.HOST
+    ev["dst_dev"][sl] = rng.integers(0, n_devices, n_k)
+    ev["t_end_ns"] = ev["t_start_ns"] + 2
+    ev["t_end_ns"][sl] = ev["t_start_ns"][sl] + 5
+    order = np.argsort(ev["t_start_ns"], kind="stable")
+    b = traces.TraceBundle(events=ev[order], content=content[order])
+    return with_fp(b)
+
+
+@pytest.mark.parametrize("n_devices", [1, 3])
+def test_grouping_sorts_past_16_bits(cuda_ok, orc, odp, n_devices):
+    """More than 2^16 distinct allocation keys and candidate host addresses:
+    the grouping sorts on dense ids need more than two passes."""
+    ev = many_keys_trace(17 + n_devices, 100_000, 2, n_devices)
+    al = ev[ev["kind"] == traces.ALLOC]
+    assert np.unique(al["dev_addr"]).size > 1 << 16
+    g = check(odp, orc, ev)
+    assert g["count"] > 0
