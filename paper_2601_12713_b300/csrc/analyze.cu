@@ -70,10 +70,6 @@ struct Ev {
         return *(const uint64_t*)(p + 64ull * i + off);
     }
     __device__ __forceinline__ uint64_t t0(uint32_t i) const { return u64(i, 0); }
-    __device__ __forceinline__ uint64_t t1(uint32_t i) const { return u64(i, 8); }
-    __device__ __forceinline__ uint64_t host(uint32_t i) const { return u64(i, 16); }
-    __device__ __forceinline__ uint64_t daddr(uint32_t i) const { return u64(i, 24); }
-    __device__ __forceinline__ uint64_t bytes(uint32_t i) const { return u64(i, 32); }
 };
 
 // Dense copies of the record fields the later passes read, one entry per
