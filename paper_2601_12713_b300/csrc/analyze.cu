@@ -3,8 +3,8 @@
 //
 //   validate   record checks, order check, class of every event, lists of
 //              transfers (X), alloc/deletes (P), kernels (K), to-device (U)
-//   Alg. 1/2   table <fingerprint> -> content id (the content's first
-//              transfer); stable sort of X by content id.  The group
+//   Alg. 1/2   table <fingerprint> -> content group key (the transfer whose
+//              insert placed the fingerprint); stable sort of X by it.  The group
 //              head and the start of the group's second run give each
 //              destination's first receiver; every later transfer to it is a
 //              duplicate.  With two endpoints in a content group the literal
@@ -13,7 +13,7 @@
 //              destinations; groups with more endpoints: sort by (group,
 //              destination), per-endpoint "all receptions succeeded" in order
 //              of last reception, partners by binary search
-//   pairs      table <device, device address> -> slot; stable sort of P;
+//   pairs      table <device, device address> -> dense id; stable sort of P;
 //              alternating groups pair each ALLOC with the next DELETE, other
 //              groups replay the nearest-open-ALLOC rule with a stack
 //   Alg. 3     table <host address, device, bytes> -> first pair's alloc
@@ -22,7 +22,7 @@
 //              reaches the allocation's start (the literal monotone pointer)
 //   Alg. 5     same search per to-device transfer; transfers after the last
 //              kernel, barriers (overlapping the kernel) and candidates;
-//              candidates sorted stably by host-address slot, each member
+//              candidates sorted stably by host-address id, each member
 //              overwritten by the next one of its segment
 //   emit       per-kind ballot compaction in event order, wasted bytes/ns,
 //              per-site rows, union of wasted events, summary
