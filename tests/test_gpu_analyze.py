@@ -398,3 +398,15 @@ def test_grouping_sorts_past_16_bits(cuda_ok, orc, odp, n_devices):
     assert np.unique(al["dev_addr"]).size > 1 << 16
     g = check(odp, orc, ev)
     assert g["count"] > 0
+
+
+def test_many_contents(cuda_ok, orc, odp):
+    """600,000 transfers of 361,000 distinct contents on two devices (a
+    content table of 2^20 slots, three in five of its inserts new)."""
+    ev = many_keys_trace(31, 150_000, 2, 2)
+    xfer = ev[np.isin(ev["kind"], [traces.TO_DEV, traces.FROM_DEV])]
+    assert 1.25 * xfer.size > (1 << 19)
+    fps = np.unique(np.stack([xfer["fp_lo"], xfer["fp_hi"]], axis=1), axis=0)
+    assert fps.shape[0] > (1 << 18)
+    g = check(odp, orc, ev)
+    assert g["count"] > 0
