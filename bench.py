@@ -36,6 +36,12 @@ SEED = 0x0DB2
 # Traffic grows with the bytes hashed: a launch over B bytes moves about
 # B / 512 MiB times this.
 FP_TILES_TRAFFIC_512MIB = 540.99e6
+# DRAM read+write bytes of fp_tiles per algorithmic byte on a batch of 10^5
+# ragged buffers (1.6 GiB, the batched workload's size distribution): 1,686.9 MB
+# read + 4.4 MB written for 1,680.9 MB of buffers and per-buffer records.
+# Traffic grows with the bytes hashed, so the 10^6-buffer call moves this
+# ratio times its algorithmic bytes.
+FP_BATCHED_TRAFFIC_RATIO = 1691.3e6 / 1680.9e6
 # DRAM read+write bytes of one odp_analyze call on the 50,002,000-event
 # iterative-solver trace, summed over its 124 launches (ncu, dram__bytes_read.sum
 # + dram__bytes_write.sum, one pass per launch): 22.74 GB read + 11.04 GB written.
@@ -441,7 +447,11 @@ def bench_batched(args, odp, dist, rank, stream, peak, peak_kind):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
                      "peak_kind": f"{peak_kind} (copy read+write)",
-                     "algorithmic_bytes_per_launch": total + 32 * n},
+                     "algorithmic_bytes_per_launch": total + 32 * n,
+                     "traffic": round(FP_BATCHED_TRAFFIC_RATIO * (total + 32 * n)),
+                     "traffic_source": "ncu capture of fp_tiles on a 10^5-buffer, 1.6 GiB batch "
+                                       "of the same size distribution, scaled by the "
+                                       "algorithmic bytes"},
         "parity": parity,
     }
     if rank == 0 and not args.skip_cpu:
