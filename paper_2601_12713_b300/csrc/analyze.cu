@@ -47,7 +47,7 @@ struct Hdr {
     unsigned long long t_end_max;
     unsigned long long saved_ns;
     unsigned long long unmatched;
-    unsigned long long n_allocs, n_deletes, n_pairs, n_unpaired;
+    unsigned long long n_allocs, n_deletes, n_pairs;  // pairs counted where they are matched
     unsigned long long count[6], bytes[6], ns[6];
     uint32_t nX, nP, nK, nU;
     uint32_t nseg, nrun, nseg2, nsegU;
@@ -760,6 +760,7 @@ __global__ void k_p_match(A a) {
     pdl_entry();
     if (failed(a)) return;
     const uint32_t n = a.h->nP, str = gridDim.x * blockDim.x;
+    uint32_t pairs = 0;
     BATCH_STRIDE(q0, n) {
         uint32_t sg[INS_B], e[INS_B], d[INS_B];
         bool al[INS_B];
@@ -775,9 +776,14 @@ __global__ void k_p_match(A a) {
         for (int b = 0; b < INS_B; ++b) {
             const uint32_t q = q0 + b * str;
             // the next entry closes this ALLOC if it lies in the same group
-            if (al[b] && !a.bad[sg[b]] && q + 1 < a.H[sg[b] + 1]) a.del_of[e[b]] = d[b];
+            if (al[b] && !a.bad[sg[b]] && q + 1 < a.H[sg[b] + 1]) {
+                a.del_of[e[b]] = d[b];
+                ++pairs;
+            }
         }
     }
+    for (int k = 16; k > 0; k >>= 1) pairs += __shfl_xor_sync(ODP_FULL_MASK, pairs, k);
+    if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(&a.h->n_pairs, (unsigned long long)pairs);
 }
 
 // Non-alternating groups: a DELETE closes the nearest earlier open ALLOC.
@@ -788,18 +794,20 @@ __global__ void k_p_literal(A a) {
         if (!a.bad[s]) continue;
         const uint32_t lo = a.H[s], hi = a.H[s + 1];
         uint32_t depth = 0;
-        unsigned long long unmatched = 0;
+        unsigned long long unmatched = 0, pairs = 0;
         for (uint32_t q = lo; q < hi; ++q) {
             const uint32_t e = a.sv[q];
             if (is_alloc(a, e)) {
                 a.stk[lo + depth++] = e;
             } else if (depth > 0) {
                 a.del_of[a.stk[lo + --depth]] = e;
+                ++pairs;
             } else {
                 ++unmatched;
             }
         }
         if (unmatched) atomicAdd(&a.h->unmatched, unmatched);
+        if (pairs) atomicAdd(&a.h->n_pairs, pairs);
     }
 }
 
@@ -1096,9 +1104,9 @@ __device__ __forceinline__ const uint32_t* partner_array(const A& a, int kind) {
 }
 
 
-// Findings per (kind, 32-event chunk) from the partner arrays alone, and
-// pair counts.  A warp takes 128 events (four chunks), four per lane with
-// 16-byte loads; lanes 8k..8k+7 sum chunk k.
+// Findings per (kind, 32-event chunk) from the partner arrays alone (the
+// pairs are counted where they are matched).  A warp takes 128 events (four
+// chunks), four per lane with 16-byte loads; lanes 8k..8k+7 sum chunk k.
 __global__ void k_em_count(A a, uint32_t* wcnt, uint32_t nch) {
     pdl_entry();
     if (failed(a)) return;
@@ -1106,7 +1114,6 @@ __global__ void k_em_count(A a, uint32_t* wcnt, uint32_t nch) {
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t nq = (nch + 3) / 4;
-    unsigned long long pairs = 0, unpaired = 0;
     for (uint32_t g = gw; g < nq; g += nw) {
         const uint32_t i0 = g * 128 + lane * 4;
         const uint32_t c = g * 4 + (lane >> 3);
@@ -1131,23 +1138,6 @@ __global__ void k_em_count(A a, uint32_t* wcnt, uint32_t nch) {
             k += __shfl_xor_sync(ODP_FULL_MASK, k, 4);
             if ((lane & 7) == 0 && c < nch) wcnt[(kind - 1) * nch + c] = k;
         }
-        const uint4 cl = load4(a.cls, i0, a.n, 0);
-        const uint4 dl = load4(a.del_of, i0, a.n, NONE32);
-        const uint32_t cv[4] = {cl.x, cl.y, cl.z, cl.w}, dv[4] = {dl.x, dl.y, dl.z, dl.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (c_kind(cv[j]) == ODP_ALLOC) {
-                if (dv[j] != NONE32) ++pairs; else ++unpaired;
-            }
-        }
-    }
-    for (int d = 16; d > 0; d >>= 1) {
-        pairs += __shfl_xor_sync(ODP_FULL_MASK, pairs, d);
-        unpaired += __shfl_xor_sync(ODP_FULL_MASK, unpaired, d);
-    }
-    if (lane == 0) {
-        if (pairs) atomicAdd(&a.h->n_pairs, pairs);
-        if (unpaired) atomicAdd(&a.h->n_unpaired, unpaired);
     }
 }
 
@@ -1413,7 +1403,7 @@ __global__ void k_finalize(A a, const uint32_t* n_findings, const uint32_t* n_ro
     S->n_deletes = h->n_deletes;
     S->n_kernels = h->nK;
     S->n_pairs = h->n_pairs;
-    S->n_unpaired_allocs = h->n_unpaired;
+    S->n_unpaired_allocs = h->n_allocs - h->n_pairs;
     S->n_unmatched_deletes = h->unmatched;
     for (int k = 0; k < 6; ++k) {
         S->count[k] = h->count[k];
