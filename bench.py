@@ -44,8 +44,8 @@ FP_TILES_TRAFFIC_512MIB = 540.99e6
 FP_BATCHED_TRAFFIC_RATIO = 1691.3e6 / 1680.9e6
 # DRAM read+write bytes of one odp_analyze call on the 50,002,000-event
 # iterative-solver trace, summed over its 124 launches (ncu, dram__bytes_read.sum
-# + dram__bytes_write.sum, one pass per launch): 22.74 GB read + 11.04 GB written.
-ANALYZE_TRAFFIC_PER_EVENT = 33.78e9 / 50_002_000
+# + dram__bytes_write.sum, one pass per launch): 22.33 GB read + 11.03 GB written.
+ANALYZE_TRAFFIC_PER_EVENT = 33.37e9 / 50_002_000
 
 
 def peaks():
